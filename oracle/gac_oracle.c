@@ -1,0 +1,424 @@
+/*
+ * gac_oracle.c -- plain FP64 CPU oracle for the voxel-wise Metropolis-Hastings
+ * sampler of GACELLE's mcmc.m (Chan et al., arXiv 2511.22094, Sec. 2.2.2).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the package smoke check and the
+ * CPU-baseline leg of the benchmark load this library.  The CUDA library never
+ * links, includes or calls it, and it shares no source with the CUDA path:
+ * its Philox generator, forward models, likelihood, sampler and moment code
+ * are written here a second time, slowly and plainly, in double precision.
+ *
+ * What it computes, in the paper's order:
+ *   - Gaussian log-likelihood of the measured signal given the forward model
+ *     (Sec. 2.2.2: "the likelihood is Gaussian"; weighting by voxel SNR as in
+ *     Eq. 1);
+ *   - a normal random-walk proposal with a per-parameter step (the xStepSize
+ *     option, Sec. 2.2.2), clamped to the uniform-prior bounds;
+ *   - Metropolis acceptance, burn-in, thinning and the posterior mean/SD of the
+ *     thinned samples (Sec. 2.2.2 options; Sec. 2.3.1 out.mean / out.std).
+ *   Forward models: mono-exponential decay (Eq. 3), the 3-pool complex
+ *   myelin-water GRE model and the spherical-mean Standard Model (Sec. 2.1,
+ *   model list; closed forms stated below), and a linear test model whose
+ *   posterior is known exactly.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), from its published
+ * definition: counter (t, voxel, chain<<8 | call, 0), key (seed lo, seed hi).
+ *
+ * Parity status: every function here is pinned by tests/test_oracle_*.py
+ * against closed forms, library routines (erf/erfi, Gauss-Legendre
+ * quadrature, cuRAND's host Philox), exact linear-Gaussian posteriors and
+ * brute-force grid posteriors.  No function is "parity unpinned".
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_MONOEXP 1
+#define ORC_MWI3 2
+#define ORC_SMT 3
+#define ORC_LINEAR 100
+
+#define ORC_INIT_ITER 0xFFFFFFFFu
+
+static const double ORC_PI = 3.14159265358979323846264338327950288;
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as  */
+/* easy as 1, 2, 3" (SC'11): ten rounds of a multiply-hi/lo + xor bijection */
+/* on four 32-bit words, with a Weyl-sequence key schedule.                  */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    const uint32_t mult0 = 0xD2511F53u, mult1 = 0xCD9E8D57u;
+    const uint32_t weyl0 = 0x9E3779B9u, weyl1 = 0xBB67AE85u;
+    uint32_t x[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t prod0 = (uint64_t)mult0 * (uint64_t)x[0];
+        uint64_t prod1 = (uint64_t)mult1 * (uint64_t)x[2];
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t n0 = hi1 ^ x[1] ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ x[3] ^ k1;
+        uint32_t n3 = lo0;
+        x[0] = n0; x[1] = n1; x[2] = n2; x[3] = n3;
+        k0 += weyl0;
+        k1 += weyl1;
+    }
+    out[0] = x[0]; out[1] = x[1]; out[2] = x[2]; out[3] = x[3];
+}
+
+/* The n words of one (iteration t, voxel v, chain c) draw: call k of the
+ * generator supplies words 4k..4k+3. */
+void orc_words(uint64_t seed, uint32_t t, uint32_t v, uint32_t c, int n, uint32_t *w) {
+    uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+    for (int k = 0; 4 * k < n; ++k) {
+        uint32_t ctr[4] = {t, v, (c << 8) | (uint32_t)k, 0u};
+        uint32_t out[4];
+        orc_philox4x32_10(ctr, key, out);
+        for (int j = 0; j < 4 && 4 * k + j < n; ++j) w[4 * k + j] = out[j];
+    }
+}
+
+/* A 32-bit word to a uniform on the open interval (0, 1): (w + 1/2) 2^-32. */
+double orc_u01(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
+
+/* Words used per MH iteration for P parameters: two per Box-Muller pair for
+ * the P normals, then one for the acceptance uniform (the last word). */
+int orc_n_words(int n_par) { return 2 * ((n_par + 1) / 2) + 1; }
+
+/* Box-Muller: pair j takes u1 = u01(w[2j]), u2 = u01(w[2j+1]);
+ * z[2j] = sqrt(-2 ln u1) cos(2 pi u2), z[2j+1] = sqrt(-2 ln u1) sin(2 pi u2). */
+void orc_normals_from_words(const uint32_t *w, int n_par, double *z) {
+    for (int j = 0; 2 * j < n_par; ++j) {
+        double u1 = orc_u01(w[2 * j]);
+        double u2 = orc_u01(w[2 * j + 1]);
+        double radius = sqrt(-2.0 * log(u1));
+        double angle = 2.0 * ORC_PI * u2;
+        z[2 * j] = radius * cos(angle);
+        if (2 * j + 1 < n_par) z[2 * j + 1] = radius * sin(angle);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forward signal models                                                     */
+/* ------------------------------------------------------------------------ */
+
+int orc_n_par(int kind) {
+    switch (kind) {
+    case ORC_MONOEXP: return 2;
+    case ORC_MWI3: return 9;
+    case ORC_SMT: return 4;
+    case ORC_LINEAR: return 2;
+    default: return -1;
+    }
+}
+
+/* Real-valued measurements per voxel: complex models count re and im. */
+int orc_n_meas(int kind, int n_acq) {
+    if (kind == ORC_MWI3) return 2 * n_acq;
+    if (orc_n_par(kind) < 0) return -1;
+    return n_acq;
+}
+
+/* g(x) = integral_0^1 exp(-x u^2) du, the orientation average of a stick
+ * (spherical-mean technique).  For x > 1 it is sqrt(pi) erf(sqrt x)/(2 sqrt x);
+ * for x <= 1 (including x < 0, the erfi branch) the power series
+ * sum_n (-x)^n / (n! (2n+1)), whose terms are all positive when x < 0. */
+double orc_g(double x) {
+    if (x > 1.0) {
+        double s = sqrt(x);
+        return sqrt(ORC_PI) * erf(s) / (2.0 * s);
+    }
+    double term = 1.0; /* (-x)^n / n! */
+    double sum = 1.0;
+    for (int n = 1; n < 400; ++n) {
+        term *= -x / (double)n;
+        double add = term / (double)(2 * n + 1);
+        sum += add;
+        if (fabs(add) <= 1e-18 * fabs(sum)) break;
+    }
+    return sum;
+}
+
+/* Evaluates the forward model at theta; writes n_meas(kind, n_acq) reals.
+ *  MONOEXP (Eq. 3):  s_k = S0 exp(-R2* TE_k), theta = (S0, R2* [1/s]),
+ *                    acq = TE [ms].
+ *  MWI3:  S(t) = exp(i phi0) sum_{j in MW,IW,EW} A_j exp(-t/T2*_j) exp(-i 2 pi df_j t),
+ *         theta = (A_MW, A_IW, A_EW, T2*_MW, T2*_IW, T2*_EW [ms], df_MW, df_IW [Hz],
+ *         phi0 [rad]), df_EW = 0, acq = TE [ms]; output (re, im) per echo.
+ *  SMT:   s(b) = f g(b Da) + (1 - f) exp(-b De_perp) g(b (De_par - De_perp)), S0 = 1,
+ *         theta = (f, Da, De_par, De_perp) [um^2/ms], acq = b [ms/um^2].
+ *  LINEAR: s_k = a + c t_k, theta = (a, c), acq = t. */
+int orc_forward(int kind, const double *acq, int n_acq, const double *theta, double *s) {
+    switch (kind) {
+    case ORC_MONOEXP:
+        for (int k = 0; k < n_acq; ++k) s[k] = theta[0] * exp(-theta[1] * acq[k] * 1e-3);
+        return 0;
+    case ORC_MWI3:
+        for (int k = 0; k < n_acq; ++k) {
+            double t = acq[k], re = 0.0, im = 0.0;
+            for (int j = 0; j < 3; ++j) {
+                double amp = theta[j] * exp(-t / theta[3 + j]);
+                double df = (j < 2) ? theta[6 + j] : 0.0;
+                double ang = theta[8] - 2.0 * ORC_PI * df * t * 1e-3;
+                re += amp * cos(ang);
+                im += amp * sin(ang);
+            }
+            s[2 * k] = re;
+            s[2 * k + 1] = im;
+        }
+        return 0;
+    case ORC_SMT:
+        for (int k = 0; k < n_acq; ++k) {
+            double b = acq[k];
+            double f = theta[0], da = theta[1], dpar = theta[2], dperp = theta[3];
+            double intra = orc_g(b * da);
+            double extra = exp(-b * dperp) * orc_g(b * (dpar - dperp));
+            s[k] = f * intra + (1.0 - f) * extra;
+        }
+        return 0;
+    case ORC_LINEAR:
+        for (int k = 0; k < n_acq; ++k) s[k] = theta[0] + theta[1] * acq[k];
+        return 0;
+    default:
+        return -1;
+    }
+}
+
+/* Gaussian log-likelihood, constant dropped: L = -1/2 sum_m ((y_m - s_m)/sigma)^2. */
+double orc_loglik(int kind, const double *acq, int n_acq, const double *theta,
+                  const float *y, double sigma) {
+    int m = orc_n_meas(kind, n_acq);
+    double s[512];
+    if (m < 0 || m > 512) return NAN;
+    orc_forward(kind, acq, n_acq, theta, s);
+    double sum = 0.0;
+    for (int i = 0; i < m; ++i) {
+        double r = ((double)y[i] - s[i]) / sigma;
+        sum += r * r;
+    }
+    return -0.5 * sum;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Metropolis-Hastings sampler                                               */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int kind;
+    int n_acq;
+    const double *acq;
+    int n_par;
+    const double *lb, *ub, *step;
+} orc_model;
+
+typedef struct {
+    int iterations; /* I */
+    int burnin;     /* B, a count of iterations */
+    int thin;       /* T */
+    int n_chains;   /* C */
+    uint64_t seed;
+    uint64_t voxel_base;  /* global index of voxel 0, used in the counter */
+    int moments_mode;     /* 0: thinned samples, 1: every post-burn-in state */
+    int n_threads;        /* 0: all available */
+} orc_opts;
+
+/* Number of thinned samples per chain: t in {B+T, B+2T, ...} <= I. */
+int orc_n_samples(int iterations, int burnin, int thin) {
+    if (thin <= 0 || iterations <= burnin) return 0;
+    return (iterations - burnin) / thin;
+}
+
+static double clampd(double x, double lo, double hi) { return fmin(fmax(x, lo), hi); }
+
+/* One chain of one voxel.  path (optional) receives the state after each
+ * iteration t = 0..I as [I+1][P]; pooled (optional) receives the states that
+ * enter the moments, `per_chain` values per parameter, as [P][per_chain]. */
+static void run_chain(const orc_model *m, const float *y, double sigma, const float *x0,
+                      const orc_opts *o, uint32_t vg, uint32_t c, int64_t v, int64_t n_vox,
+                      double *samples, double *pooled, int per_chain, double *accept_rate,
+                      int32_t *nonfinite, double *path) {
+    int P = m->n_par, I = o->iterations, B = o->burnin, T = o->thin;
+    int S = orc_n_samples(I, B, T);
+    int nw = orc_n_words(P);
+    double theta[64], prop[64], z[64];
+    uint32_t w[160];
+
+    if (x0) {
+        for (int p = 0; p < P; ++p) theta[p] = clampd((double)x0[p], m->lb[p], m->ub[p]);
+    } else {
+        orc_words(o->seed, ORC_INIT_ITER, vg, c, P, w);
+        for (int p = 0; p < P; ++p) theta[p] = m->lb[p] + (m->ub[p] - m->lb[p]) * orc_u01(w[p]);
+    }
+    double L = orc_loglik(m->kind, m->acq, m->n_acq, theta, y, sigma);
+    if (path) memcpy(path, theta, sizeof(double) * P);
+
+    long n_acc = 0, n_bad = 0;
+    int n_pooled = 0;
+    for (int t = 1; t <= I; ++t) {
+        orc_words(o->seed, (uint32_t)t, vg, c, nw, w);
+        orc_normals_from_words(w, P, z);
+        for (int p = 0; p < P; ++p) prop[p] = clampd(theta[p] + m->step[p] * z[p], m->lb[p], m->ub[p]);
+        double Lp = orc_loglik(m->kind, m->acq, m->n_acq, prop, y, sigma);
+        if (!isfinite(Lp)) ++n_bad;
+        double log_u = log(orc_u01(w[nw - 1]));
+        if (log_u < Lp - L) { /* strict; NaN compares false and rejects */
+            memcpy(theta, prop, sizeof(double) * P);
+            L = Lp;
+            ++n_acc;
+        }
+        if (path) memcpy(path + (size_t)t * P, theta, sizeof(double) * P);
+        int on_grid = (t > B) && T > 0 && ((t - B) % T == 0);
+        if (on_grid) {
+            int s = (t - B) / T - 1;
+            if (samples && s < S)
+                for (int p = 0; p < P; ++p)
+                    samples[(((size_t)s * o->n_chains + c) * P + p) * n_vox + v] = theta[p];
+        }
+        if (pooled) {
+            int take = (o->moments_mode == 1) ? (t > B) : on_grid;
+            if (take && n_pooled < per_chain) {
+                for (int p = 0; p < P; ++p) pooled[(size_t)p * per_chain + n_pooled] = theta[p];
+                ++n_pooled;
+            }
+        }
+    }
+    if (accept_rate) accept_rate[(size_t)c * n_vox + v] = I > 0 ? (double)n_acc / (double)I : 0.0;
+    if (nonfinite) nonfinite[(size_t)c * n_vox + v] = (int32_t)n_bad;
+}
+
+/* Runs C chains for each of n_vox voxels.  data: [n_vox][n_meas] float (complex
+ * data interleaved re, im); sigma: [n_vox] or NULL (then sigma_scalar);
+ * x0: [n_vox][C][P] or NULL.  Outputs (each may be NULL):
+ *   mean, std   [P][n_vox]      pooled over chains (two-pass, n-1 divisor);
+ *   samples     [S][C][P][n_vox];
+ *   accept_rate [C][n_vox]      accepted / I;
+ *   nonfinite   [C][n_vox]      iterations with a non-finite proposal likelihood.
+ * Moments of n = 0 values are NaN; the SD of one value is 0.
+ * Returns 0, or -1 on invalid arguments; *threads_used = OpenMP threads. */
+int orc_mcmc_run(const orc_model *m, const float *data, int64_t n_vox, const float *sigma,
+                 float sigma_scalar, const float *x0, const orc_opts *o, double *mean,
+                 double *std, double *samples, double *accept_rate, int32_t *nonfinite,
+                 int *threads_used) {
+    int P = m->n_par;
+    if (P != orc_n_par(m->kind) || P > 64 || o->n_chains < 1 || o->iterations < 0 ||
+        o->burnin < 0 || o->thin < 1 || n_vox < 0)
+        return -1;
+    int M = orc_n_meas(m->kind, m->n_acq);
+    int C = o->n_chains, I = o->iterations, B = o->burnin;
+    int S = orc_n_samples(I, B, o->thin);
+    int per_chain = (o->moments_mode == 1) ? (I > B ? I - B : 0) : S;
+    int nt = 1;
+#ifdef _OPENMP
+    nt = o->n_threads > 0 ? o->n_threads : omp_get_max_threads();
+#endif
+    if (threads_used) *threads_used = nt;
+
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int64_t v = 0; v < n_vox; ++v) {
+        const float *y = data + (size_t)v * M;
+        double sig = sigma ? (double)sigma[v] : (double)sigma_scalar;
+        uint32_t vg = (uint32_t)(o->voxel_base + (uint64_t)v);
+        size_t n_all = (size_t)C * per_chain;
+        double *pooled = (double *)malloc(sizeof(double) * (n_all * P + 1));
+        for (int c = 0; c < C; ++c) {
+            const float *x0v = x0 ? x0 + ((size_t)v * C + c) * P : NULL;
+            run_chain(m, y, sig, x0v, o, vg, (uint32_t)c, v, n_vox, samples,
+                      pooled + (size_t)c * per_chain * P, per_chain, accept_rate, nonfinite,
+                      NULL);
+        }
+        /* pooled holds, chain after chain, [P][per_chain] blocks */
+        for (int p = 0; p < P; ++p) {
+            double sum = 0.0;
+            for (int c = 0; c < C; ++c)
+                for (int i = 0; i < per_chain; ++i)
+                    sum += pooled[(size_t)c * per_chain * P + (size_t)p * per_chain + i];
+            double mu = n_all > 0 ? sum / (double)n_all : NAN;
+            double ss = 0.0;
+            for (int c = 0; c < C; ++c)
+                for (int i = 0; i < per_chain; ++i) {
+                    double d = pooled[(size_t)c * per_chain * P + (size_t)p * per_chain + i] - mu;
+                    ss += d * d;
+                }
+            double sd = n_all > 1 ? sqrt(ss / (double)(n_all - 1)) : (n_all == 1 ? 0.0 : NAN);
+            if (mean) mean[(size_t)p * n_vox + v] = mu;
+            if (std) std[(size_t)p * n_vox + v] = sd;
+        }
+        free(pooled);
+    }
+    return 0;
+}
+
+/* The whole path of one chain (state after each iteration, [I+1][P]), for
+ * tests of the thinning grid and of the sampler's stationary distribution. */
+int orc_chain_path(const orc_model *m, const float *y, double sigma, const float *x0,
+                   const orc_opts *o, uint64_t voxel, int chain, double *path,
+                   double *accept_rate) {
+    if (m->n_par != orc_n_par(m->kind) || m->n_par > 64 || o->iterations < 0) return -1;
+    orc_opts one = *o;
+    one.n_chains = chain + 1;
+    double acc = 0.0;
+    int32_t bad = 0;
+    /* accept_rate/nonfinite are indexed [c][v] with n_vox = 1, v = 0 */
+    double acc_buf[256];
+    int32_t bad_buf[256];
+    if (chain >= 256) return -1;
+    run_chain(m, y, sigma, x0, &one, (uint32_t)(o->voxel_base + voxel), (uint32_t)chain, 0, 1,
+              NULL, NULL, 0, acc_buf, bad_buf, path);
+    acc = acc_buf[chain];
+    bad = bad_buf[chain];
+    (void)bad;
+    if (accept_rate) *accept_rate = acc;
+    return 0;
+}
+
+/* Lock-step acceptance check: for each recorded step n, recompute in FP64 the
+ * likelihoods of the current state theta[n] and the proposal prop[n] (each
+ * [n][P]) and the decision log u01(w_acc[n]) < L' - L. */
+int orc_lockstep(const orc_model *m, const float *y, double sigma, int64_t n,
+                 const double *theta, const double *prop, const uint32_t *w_acc, double *L,
+                 double *Lp, int32_t *accept) {
+    int P = m->n_par;
+    for (int64_t i = 0; i < n; ++i) {
+        double l0 = orc_loglik(m->kind, m->acq, m->n_acq, theta + (size_t)i * P, y, sigma);
+        double l1 = orc_loglik(m->kind, m->acq, m->n_acq, prop + (size_t)i * P, y, sigma);
+        if (L) L[i] = l0;
+        if (Lp) Lp[i] = l1;
+        if (accept) accept[i] = log(orc_u01(w_acc[i])) < l1 - l0;
+    }
+    return 0;
+}
+
+/* Forward model over many parameter vectors: theta [n][P] -> s [n][M]. */
+int orc_forward_many(int kind, const double *acq, int n_acq, int64_t n, const double *theta,
+                     double *s) {
+    int P = orc_n_par(kind), M = orc_n_meas(kind, n_acq);
+    if (P < 0) return -1;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) orc_forward(kind, acq, n_acq, theta + (size_t)i * P, s + (size_t)i * M);
+    return 0;
+}
+
+/* Log-likelihood over many (theta, voxel) pairs: theta [n][P], y [n][M], sigma [n]. */
+int orc_loglik_many(int kind, const double *acq, int n_acq, int64_t n, const double *theta,
+                    const float *y, const float *sigma, double *L) {
+    int P = orc_n_par(kind), M = orc_n_meas(kind, n_acq);
+    if (P < 0) return -1;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+        L[i] = orc_loglik(kind, acq, n_acq, theta + (size_t)i * P, y + (size_t)i * M, (double)sigma[i]);
+    return 0;
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,78 @@
+"""Plausible mistakes planted in copies of the oracle must fail a pin.
+
+Each case rewrites one line of ``oracle/gac_oracle.c`` in a temporary copy
+(never the oracle itself), builds it, and runs the pin that is meant to catch
+that kind of mistake.  A pin that still passed would not be pinning anything.
+"""
+import numpy as np
+import pytest
+
+import test_oracle_models as M
+import test_oracle_rng as R
+import test_oracle_sampler as S
+
+
+def _kat(orc):
+    for ctr, key, exp in R.KAT:
+        R.test_philox_known_answers(orc, ctr, key, exp)
+
+
+def _g_pins(orc):
+    for x in (-10.0, -1.0, 0.5, 7.5):
+        M.test_smt_g_against_gauss_legendre(orc, x)
+
+
+CASES = [
+    # (name, old text, new text, pin)
+    ("philox output word", "uint32_t n1 = lo1;", "uint32_t n1 = hi1;", _kat),
+    ("philox key schedule", "k1 += weyl1;", "k1 += weyl0;", _kat),
+    ("philox counter word 3", "uint32_t n2 = hi0 ^ x[3] ^ k1;", "uint32_t n2 = hi0 ^ x[1] ^ k1;", _kat),
+    ("uniform offset", "((double)w + 0.5) * 0x1p-32", "((double)w) * 0x1p-32",
+     R.test_u01_open_interval_and_exact),
+    ("box-muller sin/cos swapped", "z[2 * j] = radius * cos(angle);",
+     "z[2 * j] = radius * sin(angle);", R.test_box_muller_radius_and_angle),
+    ("acceptance word", "log(orc_u01(w[nw - 1]))", "log(orc_u01(w[0]))",
+     S.test_chain_init_and_every_transition),
+    ("counter layout", "uint32_t ctr[4] = {t, v, (c << 8) | (uint32_t)k, 0u};",
+     "uint32_t ctr[4] = {v, t, (c << 8) | (uint32_t)k, 0u};", R.test_word_layout),
+    ("mono-exponential TE units", "exp(-theta[1] * acq[k] * 1e-3)", "exp(-theta[1] * acq[k])",
+     M.test_monoexp_closed_form_limits),
+    ("3-pool frequency sign", "theta[8] - 2.0 * ORC_PI * df", "theta[8] + 2.0 * ORC_PI * df",
+     M.test_mwi3_single_pool_phase_and_modulus),
+    ("3-pool EW frequency", "(j < 2) ? theta[6 + j] : 0.0", "theta[6 + (j % 2)]",
+     M.test_mwi3_single_pool_phase_and_modulus),
+    ("3-pool decay as rate", "exp(-t / theta[3 + j])", "exp(-t * theta[3 + j] * 1e-3)",
+     M.test_mwi3_real_when_no_frequency_and_phase),
+    ("SMT dropped perpendicular decay", "double extra = exp(-b * dperp) * orc_g(b * (dpar - dperp));",
+     "double extra = orc_g(b * (dpar - dperp));", M.test_smt_limits),
+    ("SMT series sign", "term *= -x / (double)n;", "term *= x / (double)n;", _g_pins),
+    ("SMT erf branch factor", "return sqrt(ORC_PI) * erf(s) / (2.0 * s);",
+     "return sqrt(ORC_PI) * erf(s) / s;", _g_pins),
+    ("likelihood factor", "return -0.5 * sum;", "return -sum;",
+     M.test_loglik_is_gaussian_log_density_up_to_constant),
+    ("likelihood sigma", "double r = ((double)y[i] - s[i]) / sigma;",
+     "double r = ((double)y[i] - s[i]) / (sigma * sigma);",
+     M.test_loglik_zero_at_exact_fit_and_scales_with_sigma),
+    ("thinning origin", "int s = (t - B) / T - 1;", "int s = (t - B) / T;",
+     S.test_thinning_grid_and_moments),
+    ("acceptance sign", "if (log_u < Lp - L)", "if (log_u < L - Lp)",
+     S.test_chain_init_and_every_transition),
+    ("no clamp", "prop[p] = clampd(theta[p] + m->step[p] * z[p], m->lb[p], m->ub[p]);",
+     "prop[p] = theta[p] + m->step[p] * z[p];", S.test_degenerate_runs),
+    ("SD divisor n", "sqrt(ss / (double)(n_all - 1))", "sqrt(ss / (double)n_all)",
+     S.test_thinning_grid_and_moments),
+    ("MH without acceptance test", "if (log_u < Lp - L) {", "if (1) {",
+     S.test_linear_gaussian_posterior),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pin", CASES, ids=[c[0] for c in CASES])
+def test_planted_mistake_is_caught(orc, name, old, new, pin):
+    src = orc.source()
+    assert src.count(old) == 1, f"mutation anchor not found once: {old!r}"
+    so = orc.build_variant(src.replace(old, new), name.replace(" ", "_").replace("/", "_"))
+    with orc.variant(so):
+        with pytest.raises((AssertionError, ValueError)):
+            pin(orc)
+    # and the unmodified oracle passes the same pin
+    pin(orc)
