@@ -1,0 +1,327 @@
+"""Benchmark of the voxel-wise MH sampler (GACELLE mcmc.m hot path) on GB300.
+
+One step = one gac_mcmc_run over the whole workload (every step of the path:
+load, initialise, propose, forward model, likelihood, accept, thin/store,
+moments).  Default workload: the 3-pool complex myelin-water model at
+1,000,000 voxels x 4 chains x 5,000 iterations (burn-in 500, thinning 100,
+samples stored), synthetic seeded data, inputs resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload mwi3_1m|smt_1p5m|monoexp_4k]
+
+Prints one JSON line (rank 0).  Under torchrun each rank samples its own
+volume of the same size (voxel_base = rank * N: weak scaling, no collective on
+the data path; the barrier and max-over-ranks timing use the process group).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2511_22094_gb300 import workloads as W  # noqa: E402
+
+METRIC = "voxel-MCMC chain-iterations/s"
+UNIT = "chain-iter/s"
+
+# Algorithmic operation counts per chain-iteration of the direct form of each
+# model (every echo evaluated with its own exp / sin / cos), counted from the
+# oracle's expression tree: MUFU = exp, log, sin, cos, sqrt, reciprocal;
+# FP32 = add/mul/fma/min/max; INT = Philox (10 rounds x (2 wide multiplies,
+# 2 three-input xors, 2 key adds) per call).  See DESIGN.md, "Roofline".
+OPS = {
+    "mwi3_1m": dict(mufu=240, fp32=734, int=180),
+    "smt_1p5m": dict(mufu=78, fp32=380, int=120),
+    "monoexp_4k": dict(mufu=19, fp32=70, int=60),
+}
+MUFU_PER_CLK_SM = 16
+FP32_PER_CLK_SM = 128
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _host_inputs_for_oracle(w, n):
+    import oracle
+    th = W.truths(w, 0, n)
+    sig = W.sigma(w, th)
+    y = W.noisy_data(oracle.forward(w.kind, w.acq, th), W.noise(w, 0, n), sig)
+    return y, sig
+
+
+def cpu_oracle_rate(w, target_s=15.0):
+    """Oracle (as it stands) on a bounded voxel sample of the workload, all
+    host cores; returns (chain-iterations/s, threads, sample description)."""
+    import oracle
+    oracle.build()
+    kw = dict(iterations=w.iterations, burnin=w.burnin, thin=w.thin, n_chains=w.n_chains,
+              seed=w.mcmc_seed)
+    pilot = 8
+    y, sig = _host_inputs_for_oracle(w, pilot)
+    t0 = time.perf_counter()
+    oracle.mcmc_run(w.kind, w.acq, w.lb, w.ub, w.step, y, sig, **kw)
+    per_vox = (time.perf_counter() - t0) / pilot
+    threads = oracle.max_threads()
+    n = int(max(threads, min(w.n_vox, target_s / max(per_vox, 1e-9))))
+    n = max(threads, (n // threads) * threads)
+    y, sig = _host_inputs_for_oracle(w, n)
+    t0 = time.perf_counter()
+    r = oracle.mcmc_run(w.kind, w.acq, w.lb, w.ub, w.step, y, sig, **kw)
+    dt = time.perf_counter() - t0
+    ci = n * w.n_chains * w.iterations
+    return ci / dt, r["threads"], f"first {n} of {w.n_vox} voxels, all {w.n_chains} chains x {w.iterations} iterations ({dt:.1f} s)"
+
+
+def run_reference(args, w):
+    """Reference arm: the FP64 CPU oracle, timed on the host cores."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    rates = []
+    for i in range(args.warmup + args.steps):
+        rate, threads, sample = cpu_oracle_rate(w, target_s=max(5.0, 60.0 / max(args.steps + args.warmup, 1)))
+        if i >= args.warmup:
+            rates.append(rate)
+    value = float(np.median(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": w.chain_iterations / value * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n_vox": w.n_vox, "n_chains": w.n_chains,
+                       "iterations": w.iterations, "burnin": w.burnin, "thin": w.thin},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, w):
+    import torch
+    from paper_2511_22094_gb300 import build
+    build.build()
+    from paper_2511_22094_gb300 import gac
+
+    world, rank, local = _dist()
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    stream = torch.cuda.current_stream()
+
+    N, C, P, M = w.n_vox, w.n_chains, w.n_par, w.n_meas
+    S = w.n_samples
+    mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
+    base = rank * N
+
+    # synthetic inputs: seeded truths and noise; the signal from the library's
+    # own forward model on the device
+    th = torch.from_numpy(W.truths(w, 0, N)).to(dev)
+    sig = torch.from_numpy(W.sigma(w, th.cpu().numpy())).to(dev)
+    s = torch.empty((N, M), dtype=torch.float64, device=dev)
+    gac.gac_forward(mid, th, N, gac.PREC_FP64, s, stream)
+    z = torch.from_numpy(W.noise(w, 0, N)).to(dev)
+    y = (s + sig.double()[:, None] * z).float().contiguous()
+    del s, z, th
+    out = dict(mean=torch.empty((P, N), dtype=torch.float64, device=dev),
+               std=torch.empty((P, N), dtype=torch.float64, device=dev),
+               samples=torch.empty((S, C, P, N), dtype=torch.float32, device=dev),
+               accept_rate=torch.empty((C, N), dtype=torch.float32, device=dev),
+               nonfinite=torch.empty((C, N), dtype=torch.int32, device=dev))
+    opts = gac.make_opts(w.iterations, w.burnin, w.thin, C, w.mcmc_seed, voxel_base=base)
+
+    def step():
+        gac.gac_mcmc_run(mid, y, N, sig, 0.0, None, opts, out, stream)
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        t_wall = time.perf_counter()
+        for e0, e1 in ev:
+            e0.record(stream)
+            step()
+            e1.record(stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    per_step = [e0.elapsed_time(e1) / 1e3 for e0, e1 in ev]
+    t_total = sum(per_step)
+    if pg is not None:
+        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        t_total = tt.item()
+    ci_per_step = N * C * w.iterations
+    value = world * ci_per_step * args.steps / t_total
+    kernel_s = t_total / args.steps
+
+    # end to end through the same public call with pinned host buffers
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        hy = y.cpu().pin_memory()
+        hs = sig.cpu().pin_memory()
+        hout = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
+        h2d = hy.numel() * 4 + hs.numel() * 4
+        d2h = sum(v.numel() * v.element_size() for v in hout.values())
+        gac.gac_mcmc_run(mid, hy, N, hs, 0.0, None, opts, hout, stream)  # warm the allocator
+        torch.cuda.synchronize()
+        reps = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            gac.gac_mcmc_run(mid, hy, N, hs, 0.0, None, opts, hout, stream)
+            _ = float(hout["accept_rate"][0, 0])  # read the result on the host
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / reps
+        e2e = {"value": ci_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}
+
+    if rank != 0:
+        if pg is not None:
+            pg.destroy_process_group()
+        return
+    clocks = clk.summary()
+    peaks = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    f_max = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
+    ops = OPS[w.name]
+    ci_s = ci_per_step / kernel_s
+    t_mufu = ops["mufu"] / (sms * MUFU_PER_CLK_SM * f_max)
+    t_alu = (ops["fp32"] + ops["int"]) / (sms * FP32_PER_CLK_SM * f_max)
+    if t_mufu >= t_alu:
+        pipe, achieved, peak = "mufu", ops["mufu"] * ci_s / 1e9, sms * MUFU_PER_CLK_SM * f_max / 1e9
+    else:
+        pipe, achieved = "fp32+int", (ops["fp32"] + ops["int"]) * ci_s / 1e9
+        peak = sms * FP32_PER_CLK_SM * f_max / 1e9
+    f_med = (clocks.get("sm_mhz") or 0) * 1e6
+    roof = {"bound": "alu", "pipe": pipe, "count": "direct-form", "achieved": achieved,
+            "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
+            "peak_basis": f"{sms} SMs x {MUFU_PER_CLK_SM if pipe == 'mufu' else FP32_PER_CLK_SM}/clk x {f_max / 1e6:.0f} MHz (max SM clock)",
+            "frac_at_sampled_clock": (achieved / peak * f_max / f_med) if f_med else None,
+            "traffic": None, "kernel_ms": kernel_s * 1e3}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic (seeded truths + Gaussian noise, signal from the library's forward model)",
+            "config": {"workload": w.name, "n_vox": N, "n_chains": C, "iterations": w.iterations,
+                       "burnin": w.burnin, "thin": w.thin, "samples_stored": True,
+                       "precision": "mixed", "parallelism": f"voxel-shard x{world}",
+                       "l2": f"inputs {y.numel() * 4 / 1e6:.0f} MB + samples {S * C * P * N * 4 / 1e9:.1f} GB written per step > 129 MB L2"},
+            "roofline": roof, "clocks": clocks, "gpu_launches": args.steps,
+            "wall_s": t_wall}
+    if e2e:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline:
+        rate, threads, sample = cpu_oracle_rate(w)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default="mwi3_1m", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = W.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * gac.h -- C ABI of libgac.so: GB300-native voxel-wise Metropolis-Hastings
+ * sampling of qMRI forward models (the hot path of GACELLE's mcmc.m, Chan et
+ * al., arXiv 2511.22094, Sec. 2.2.2).
+ *
+ * Conventions for every entry point
+ *   - Every function returns a gac_status; nothing aborts or exits.  On a
+ *     status other than GAC_OK, gac_last_error() returns a message for the
+ *     calling thread, and output buffers may have been partially written only
+ *     where the description says so.
+ *   - Array pointers may be host or device memory; the library asks CUDA
+ *     which (cudaPointerGetAttributes).  Host buffers are staged through
+ *     device memory the library allocates and frees within the call.  Device
+ *     buffers are used in place and must stay valid until the call returns.
+ *   - Inputs are owned by the caller and only read during the call;
+ *     gac_model_register and gac_server_submit copy what they keep.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     are synchronous with respect to the host: when one returns GAC_OK its
+ *     results are in the caller's buffers.
+ *   - All layouts are C order (last index fastest).
+ */
+#ifndef GAC_H
+#define GAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GAC_OK = 0,
+    GAC_ERR_INVALID_ARG = 1,   /* a pointer, size, bound or option is invalid */
+    GAC_ERR_UNKNOWN_MODEL = 2, /* model_id / kind not registered or not known */
+    GAC_ERR_BUDGET = 3,        /* serving: a job larger than the whole HBM budget */
+    GAC_ERR_OOM = 4,           /* device allocation failed */
+    GAC_ERR_CUDA = 5,          /* a CUDA call failed (message names it) */
+    GAC_ERR_TIMEOUT = 6,       /* a bounded wait expired */
+    GAC_ERR_NOT_READY = 7,     /* reserved */
+    GAC_ERR_CANCELLED = 8,     /* serving: the job was cancelled */
+    GAC_ERR_UNKNOWN_JOB = 9    /* serving: no such job id */
+} gac_status;
+
+/* Forward signal models (Sec. 2.1 model list; Eq. 3).  Parameter order and
+ * units:
+ *  MONOEXP (Eq. 3)  s_k = S0 exp(-R2* TE_k).  theta = (S0, R2* [1/s]),
+ *                   acq = TE [ms].  2 parameters, n_acq real measurements.
+ *  MWI3   3-pool complex multi-echo GRE myelin-water model
+ *         S(t) = exp(i phi0) sum_{j=MW,IW,EW} A_j exp(-t/T2*_j) exp(-i 2 pi df_j t),
+ *         df_EW = 0.  theta = (A_MW, A_IW, A_EW, T2*_MW, T2*_IW, T2*_EW [ms],
+ *         df_MW, df_IW [Hz], phi0 [rad]); acq = TE [ms].  9 parameters,
+ *         2*n_acq real measurements (re, im interleaved per echo).
+ *  SMT    spherical-mean Standard Model, S(b=0) = 1:
+ *         s(b) = f g(b Da) + (1-f) exp(-b De_perp) g(b (De_par - De_perp)),
+ *         g(x) = integral_0^1 exp(-x u^2) du.  theta = (f, Da, De_par, De_perp)
+ *         [um^2/ms]; acq = b [ms/um^2].  4 parameters, n_acq measurements.
+ *         Registration requires b >= 0 and b*(ub[De_perp] - lb[De_par]) <= 12.
+ *  LINEAR_TEST  s_k = a + c t_k, theta = (a, c), acq = t (a test model whose
+ *         posterior is known exactly). */
+typedef enum {
+    GAC_MODEL_MONOEXP = 1,
+    GAC_MODEL_MWI3 = 2,
+    GAC_MODEL_SMT = 3,
+    GAC_MODEL_LINEAR_TEST = 100
+} gac_model_kind;
+
+#define GAC_MAX_PAR 12
+#define GAC_MAX_ACQ 64
+#define GAC_MAX_MODELS 64
+
+typedef struct {
+    int kind;           /* gac_model_kind */
+    int n_acq;          /* echoes or b-values, 1..GAC_MAX_ACQ */
+    const double *acq;  /* host [n_acq]: TE [ms], b [ms/um^2] or t */
+    int n_par;          /* must equal the kind's parameter count */
+    const double *lb;   /* host [n_par]: uniform-prior lower bounds */
+    const double *ub;   /* host [n_par]: upper bounds, ub >= lb */
+    const double *step; /* host [n_par]: proposal SD per parameter (xStepSize), >= 0 */
+} gac_model_desc;
+
+/* Registers a forward model with its acquisition parameters, prior bounds and
+ * proposal steps (Sec. 2.3.1: users supply the forward model, bounds and
+ * options; Sec. 2.2.2: xStepSize).  Copies every array.  Single-precision
+ * paths round acq/lb/ub/step to float.  Returns a model id >= 1 in *model_id.
+ * Errors: INVALID_ARG (NULL, sizes, lb > ub, negative step, non-finite
+ * values, SMT range), UNKNOWN_MODEL (kind), and INVALID_ARG when
+ * GAC_MAX_MODELS are registered already.  Thread-safe. */
+gac_status gac_model_register(const gac_model_desc *desc, int *model_id);
+
+/* Parameter count and real measurements per voxel of a registered model. */
+gac_status gac_model_info(int model_id, int *n_par, int *n_meas);
+
+/* Arithmetic of the sampler.  MIXED (default): forward model and residuals in
+ * FP32 with a compensated (Kahan) likelihood sum, the acceptance decision
+ * taken with FP64 semantics, FP64 moment accumulators.  FP32: everything in
+ * FP32, plain sums.  FP64: everything in FP64. */
+enum { GAC_PREC_MIXED = 0, GAC_PREC_FP32 = 1, GAC_PREC_FP64 = 2 };
+/* What the posterior moments average: the thinned samples (default, as the
+ * paper's output) or every post-burn-in state. */
+enum { GAC_MOMENTS_THINNED = 0, GAC_MOMENTS_ALL_POSTBURNIN = 1 };
+
+typedef struct {
+    int iterations;      /* I >= 0 (the `iteration` option, Sec. 2.2.2) */
+    int burnin;          /* B >= 0, a count (the paper's ratio r is floor(r*I)) */
+    int thin;            /* T >= 1 (`thinning`) */
+    int n_chains;        /* C, 1..64 (Table 1: "4 independent proposals") */
+    uint64_t seed;       /* Philox key */
+    uint64_t voxel_base; /* global index of voxel 0 in the RNG counter; lets a
+                            volume split into pieces reproduce the whole run */
+    int precision;       /* GAC_PREC_* */
+    int moments_mode;    /* GAC_MOMENTS_* */
+    int trace_n_vox;     /* >0: record every step of the chains of voxels
+                            [0, trace_n_vox) into gac_result.trace */
+} gac_mcmc_opts;
+
+/* One recorded MH step (lock-step parity checks): state before the step,
+ * the clamped proposal, both log-likelihoods, the acceptance word and the
+ * decision.  Values are the kernel's own, widened to double. */
+typedef struct {
+    double theta[GAC_MAX_PAR];
+    double prop[GAC_MAX_PAR];
+    double L, Lp;
+    uint32_t w_acc;
+    int32_t accepted;
+} gac_trace_rec;
+
+/* Caller-allocated outputs; any pointer may be NULL to skip that output.
+ * S = floor((I - B)/T) when I > B, else 0.  Moments of n = 0 values are NaN,
+ * the SD of one value is 0. */
+typedef struct {
+    double *mean;         /* [P][N] posterior mean (out.mean.<p>, Sec. 2.3.1) */
+    double *std;          /* [P][N] posterior SD, n-1 divisor (out.std.<p>) */
+    float *samples;       /* [S][C][P][N] thinned states, t = B+T, B+2T, ... */
+    float *accept_rate;   /* [C][N] accepted proposals / I */
+    int32_t *nonfinite;   /* [C][N] steps whose proposal likelihood was not finite */
+    gac_trace_rec *trace; /* [trace_n_vox][C][I] */
+} gac_result;
+
+/* Bytes of each gac_result buffer in the order mean, std, samples,
+ * accept_rate, nonfinite, trace (bytes[6]). */
+gac_status gac_result_sizes(int model_id, int64_t n_vox, const gac_mcmc_opts *opts,
+                            size_t bytes[6]);
+
+/* Runs C Metropolis-Hastings chains for each of n_vox voxels (Sec. 2.2.2):
+ * per iteration a Gaussian random-walk proposal clamped to [lb, ub], the
+ * forward model at all acquisitions, the Gaussian log-likelihood
+ * L = -1/2 sum_m ((y_m - s_m)/sigma)^2, acceptance iff log u < L' - L, and on
+ * the thinning grid a stored sample and a Welford moment update.
+ *   data   [n_vox][n_meas] float32 (complex data as re, im pairs)
+ *   sigma  [n_vox] float32 noise SD per real measurement, or NULL to use
+ *          sigma_scalar for every voxel (must then be > 0)
+ *   x0     [n_vox][C][P] float32 initial states (clamped into the bounds), or
+ *          NULL for a uniform-prior draw from the RNG
+ * Random numbers: Philox4x32-10 with counter (t, voxel_base + v,
+ * c << 8 | call, 0) and key (seed lo, seed hi); t = 0xFFFFFFFF for the initial
+ * draw.  Results depend only on (inputs, opts), not on the GPU's occupancy or
+ * on how a volume is split (use voxel_base).  n_vox = 0 returns GAC_OK.
+ * Errors: INVALID_ARG, UNKNOWN_MODEL, OOM, CUDA. */
+gac_status gac_mcmc_run(int model_id, const void *data, int64_t n_vox, const float *sigma,
+                        float sigma_scalar, const float *x0, const gac_mcmc_opts *opts,
+                        gac_result *out, void *stream);
+
+/* Forward model at n parameter vectors theta [n][P] (double) into s [n][M]
+ * (double), using the same device arithmetic as the sampler for `precision`
+ * (theta is rounded to float first on the FP32/MIXED paths).  Used to build
+ * synthetic data and to test the forward model (Eq. 3 and the forms above). */
+gac_status gac_forward(int model_id, const double *theta, int64_t n, int precision, double *s,
+                       void *stream);
+
+/* Log-likelihood L = -1/2 sum_m ((y_m - s_m(theta_i))/sigma_i)^2 of n
+ * (theta_i, voxel i) pairs: theta [n][P] double, data [n][M] float32,
+ * sigma [n] float32; L [n] double.  Same arithmetic as the sampler. */
+gac_status gac_loglik(int model_id, const double *theta, int64_t n, const float *data,
+                      const float *sigma, int precision, double *L, void *stream);
+
+/* Test entry points of the random-number layer.
+ * gac_philox_words: for i in [0, n): the n_words words of (t_i, v_i, c_i) for
+ *   key `seed` -> out [n][n_words] (uint32); t, v, c are [n] uint32.
+ * gac_normals: the P proposal normals of (t_i, v_i, c_i) as the sampler draws
+ *   them (Box-Muller on words 2j, 2j+1) -> z [n][P] double, and the
+ *   acceptance word -> w_acc [n]. */
+gac_status gac_philox_words(uint64_t seed, const uint32_t *t, const uint32_t *v,
+                            const uint32_t *c, int64_t n, int n_words, uint32_t *out,
+                            void *stream);
+gac_status gac_normals(uint64_t seed, const uint32_t *t, const uint32_t *v, const uint32_t *c,
+                       int64_t n, int n_par, int precision, double *z, uint32_t *w_acc,
+                       void *stream);
+
+/* Message for the last non-OK status on the calling thread ("" if none). */
+const char *gac_last_error(void);
+
+/* Library version string. */
+const char *gac_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GAC_H */

@@ -126,7 +126,7 @@ def _declare(L):
     L.orc_max_threads.argtypes = []
     L.orc_max_threads.restype = ct.c_int
     for name in ("orc_forward_many", "orc_loglik_many", "orc_mcmc_run", "orc_chain_path",
-                 "orc_lockstep"):
+                 "orc_lockstep", "orc_words_many", "orc_normals_many"):
         getattr(L, name).restype = ct.c_int
     return L
 
@@ -151,6 +151,22 @@ def words(seed: int, t: int, v: int, c: int, n: int) -> np.ndarray:
     w = np.zeros(n, np.uint32)
     lib().orc_words(seed, t & 0xFFFFFFFF, v, c, n, w)
     return w
+
+
+def words_many(seed: int, t, v, c, nw: int) -> np.ndarray:
+    """Words of draws (t[i], v[i], c[i]) -> [n][nw] uint32."""
+    t, v, c = (np.ascontiguousarray(a, np.uint32) for a in (t, v, c))
+    out = np.zeros((t.size, nw), np.uint32)
+    lib().orc_words_many(ct.c_uint64(seed), _vp(t), _vp(v), _vp(c), ct.c_int64(t.size), nw, _vp(out))
+    return out
+
+
+def normals_many(words, n_par: int) -> np.ndarray:
+    """Proposal normals of draws whose words are words [n][nw] -> [n][P]."""
+    w = np.ascontiguousarray(words, np.uint32)
+    z = np.zeros((w.shape[0], n_par))
+    lib().orc_normals_many(_vp(w), ct.c_int64(w.shape[0]), w.shape[1], n_par, _vp(z))
+    return z
 
 
 def u01(w: int) -> float:

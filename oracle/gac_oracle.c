@@ -422,3 +422,18 @@ int orc_max_threads(void) {
     return 1;
 #endif
 }
+
+/* Words of many draws: out [n][nw] for (t[i], v[i], c[i]). */
+int orc_words_many(uint64_t seed, const uint32_t *t, const uint32_t *v, const uint32_t *c,
+                   int64_t n, int nw, uint32_t *out) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) orc_words(seed, t[i], v[i], c[i], nw, out + (size_t)i * nw);
+    return 0;
+}
+
+/* Proposal normals of many draws: words [n][nw] -> z [n][P]. */
+int orc_normals_many(const uint32_t *words, int64_t n, int nw, int n_par, double *z) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) orc_normals_from_words(words + (size_t)i * nw, n_par, z + (size_t)i * n_par);
+    return 0;
+}

@@ -1,0 +1,399 @@
+// C ABI of libgac.so (include/gac.h): model registry, argument validation,
+// host/device pointer handling and the launch of the persistent MH kernel.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gac.h"
+#include "gac_internal.h"
+#include "launch.h"
+
+namespace gac {
+
+// ------------------------------------------------------------ errors -------
+static thread_local std::string g_last_error;
+
+gac_status fail(gac_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+gac_status cuda_fail(cudaError_t e, const char *what) {
+    cudaGetLastError();  // clear a sticky launch error state where possible
+    if (e == cudaErrorMemoryAllocation)
+        return fail(GAC_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(GAC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void clear_error() { g_last_error.clear(); }
+
+// ----------------------------------------------------------- registry ------
+static std::mutex g_reg_mu;
+static std::vector<ModelConst> g_models;  // id = index + 1
+
+gac_status model_get(int id, ModelConst *out) {
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    if (id < 1 || id > static_cast<int>(g_models.size()))
+        return fail(GAC_ERR_UNKNOWN_MODEL, "unknown model id %d", id);
+    *out = g_models[id - 1];
+    return GAC_OK;
+}
+
+static bool all_finite(const double *a, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+// ------------------------------------------------------ pointer kinds ------
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+DevBuf::~DevBuf() {
+    if (owned && ptr) cudaFreeAsync(ptr, stream);
+}
+
+// Makes a device view of a caller buffer: device pointers are used in place,
+// host pointers get a stream-ordered device allocation (copied in if `in`).
+gac_status DevBuf::make(void *user, size_t nbytes, bool in, cudaStream_t s, const char *name) {
+    stream = s;
+    bytes = nbytes;
+    host = user;
+    if (!user || nbytes == 0) {
+        ptr = nullptr;
+        owned = false;
+        return GAC_OK;
+    }
+    if (is_device_ptr(user)) {
+        ptr = user;
+        owned = false;
+        return GAC_OK;
+    }
+    cudaError_t e = cudaMallocAsync(&ptr, nbytes, s);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        return cuda_fail(e, name);
+    }
+    owned = true;
+    if (in) {
+        e = cudaMemcpyAsync(ptr, user, nbytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, name);
+    }
+    return GAC_OK;
+}
+
+gac_status DevBuf::copy_out() {
+    if (!owned || !ptr || !host) return GAC_OK;
+    cudaError_t e = cudaMemcpyAsync(host, ptr, bytes, cudaMemcpyDeviceToHost, stream);
+    return e == cudaSuccess ? GAC_OK : cuda_fail(e, "copy result to host");
+}
+
+int n_samples(int I, int B, int T) { return (T > 0 && I > B) ? (I - B) / T : 0; }
+
+// ----------------------------------------------------- launch sizing -------
+static int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+int row_stride_for(int kind, int M) {
+    // odd stride in the unit the kernel reads (float, or float2 for complex)
+    // so that the voxels of a warp fall into distinct shared-memory banks
+    if (model_complex(kind)) return 2 * ((M / 2) | 1);
+    return M | 1;
+}
+
+size_t smem_bytes_for(int kind, int prec, int C, int M) {
+    const int P = model_n_par(kind);
+    const size_t w = (prec == GAC_PREC_FP32) ? sizeof(float) : sizeof(double);
+    const int VB = kBlock / C;
+    return 2 * static_cast<size_t>(P) * kBlock * w +
+           static_cast<size_t>(VB) * row_stride_for(kind, M) * sizeof(float);
+}
+
+const void *mh_kernel_ptr(int kind, int prec, bool trace) {
+    switch (kind) {
+    case GAC_MODEL_MONOEXP: return mh_ptr_monoexp(prec, trace);
+    case GAC_MODEL_MWI3: return mh_ptr_mwi3(prec, trace);
+    case GAC_MODEL_SMT: return mh_ptr_smt(prec, trace);
+    case GAC_MODEL_LINEAR_TEST: return mh_ptr_linear(prec, trace);
+    default: return nullptr;
+    }
+}
+
+cudaError_t launch_mh(int kind, int prec, bool trace, const ModelConst &mc, const RunArgs &ra,
+                      const LaunchCfg &cfg) {
+    switch (kind) {
+    case GAC_MODEL_MONOEXP: return launch_mh_monoexp(prec, trace, mc, ra, cfg);
+    case GAC_MODEL_MWI3: return launch_mh_mwi3(prec, trace, mc, ra, cfg);
+    case GAC_MODEL_SMT: return launch_mh_smt(prec, trace, mc, ra, cfg);
+    case GAC_MODEL_LINEAR_TEST: return launch_mh_linear(prec, trace, mc, ra, cfg);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// Grid: one block per tile of voxels, capped at the number of blocks that
+// are resident at once (the kernel strides over the remaining tiles).
+gac_status plan_launch(const ModelConst &mc, int prec, bool trace, int C, int64_t n_vox,
+                       LaunchCfg *cfg, int64_t *n_tiles, int *vb) {
+    const void *fn = mh_kernel_ptr(mc.kind, prec, trace);
+    if (!fn) return fail(GAC_ERR_INVALID_ARG, "no kernel for kind %d precision %d", mc.kind, prec);
+    const size_t smem = smem_bytes_for(mc.kind, prec, C, mc.n_meas);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (per_sm < 1) return fail(GAC_ERR_INVALID_ARG, "kernel does not fit on an SM (smem %zu)", smem);
+    *vb = kBlock / C;
+    *n_tiles = (n_vox + *vb - 1) / *vb;
+    const int64_t resident = static_cast<int64_t>(per_sm) * sm_count();
+    cfg->grid = static_cast<int>(std::min<int64_t>(*n_tiles, resident));
+    cfg->smem = smem;
+    return GAC_OK;
+}
+
+gac_status validate_opts(const gac_mcmc_opts *o, int64_t n_vox) {
+    if (!o) return fail(GAC_ERR_INVALID_ARG, "opts is NULL");
+    if (o->iterations < 0 || o->iterations == INT32_MAX)
+        return fail(GAC_ERR_INVALID_ARG, "iterations must be in [0, 2^31-2]");
+    if (o->burnin < 0) return fail(GAC_ERR_INVALID_ARG, "burnin must be >= 0");
+    if (o->thin < 1) return fail(GAC_ERR_INVALID_ARG, "thin must be >= 1");
+    if (o->n_chains < 1 || o->n_chains > 64) return fail(GAC_ERR_INVALID_ARG, "n_chains must be in [1, 64]");
+    if (o->precision < GAC_PREC_MIXED || o->precision > GAC_PREC_FP64)
+        return fail(GAC_ERR_INVALID_ARG, "unknown precision %d", o->precision);
+    if (o->moments_mode != GAC_MOMENTS_THINNED && o->moments_mode != GAC_MOMENTS_ALL_POSTBURNIN)
+        return fail(GAC_ERR_INVALID_ARG, "unknown moments_mode %d", o->moments_mode);
+    if (o->trace_n_vox < 0 || o->trace_n_vox > n_vox)
+        return fail(GAC_ERR_INVALID_ARG, "trace_n_vox must be in [0, n_vox]");
+    if (o->voxel_base > (1ull << 32) || static_cast<uint64_t>(n_vox) > (1ull << 32) - o->voxel_base)
+        return fail(GAC_ERR_INVALID_ARG, "voxel_base + n_vox must be <= 2^32 (32-bit counter word)");
+    return GAC_OK;
+}
+
+}  // namespace gac
+
+using namespace gac;
+
+// ===================================================================== ABI ==
+extern "C" {
+
+const char *gac_last_error(void) { return g_last_error.c_str(); }
+
+const char *gac_version(void) { return "gac 0.1 (sm_103a)"; }
+
+gac_status gac_model_register(const gac_model_desc *d, int *model_id) {
+    clear_error();
+    if (!d || !model_id) return fail(GAC_ERR_INVALID_ARG, "desc and model_id must not be NULL");
+    const int P = model_n_par(d->kind);
+    if (P < 0) return fail(GAC_ERR_UNKNOWN_MODEL, "unknown model kind %d", d->kind);
+    if (d->n_par != P) return fail(GAC_ERR_INVALID_ARG, "kind %d has %d parameters, n_par = %d", d->kind, P, d->n_par);
+    if (d->n_acq < 1 || d->n_acq > GAC_MAX_ACQ)
+        return fail(GAC_ERR_INVALID_ARG, "n_acq must be in [1, %d]", GAC_MAX_ACQ);
+    if (!d->acq || !d->lb || !d->ub || !d->step)
+        return fail(GAC_ERR_INVALID_ARG, "acq, lb, ub and step must not be NULL");
+    if (!all_finite(d->acq, d->n_acq) || !all_finite(d->lb, P) || !all_finite(d->ub, P) ||
+        !all_finite(d->step, P))
+        return fail(GAC_ERR_INVALID_ARG, "non-finite acquisition, bound or step");
+    for (int p = 0; p < P; ++p) {
+        if (d->lb[p] > d->ub[p]) return fail(GAC_ERR_INVALID_ARG, "lb[%d] > ub[%d]", p, p);
+        if (d->step[p] < 0) return fail(GAC_ERR_INVALID_ARG, "step[%d] < 0", p);
+    }
+    if (d->kind == GAC_MODEL_MWI3) {
+        for (int j = 3; j < 6; ++j)
+            if (d->lb[j] <= 0) return fail(GAC_ERR_INVALID_ARG, "T2* lower bounds must be > 0");
+    }
+    if (d->kind == GAC_MODEL_SMT) {
+        for (int k = 0; k < d->n_acq; ++k) {
+            const double b = d->acq[k];
+            if (b < 0) return fail(GAC_ERR_INVALID_ARG, "b-values must be >= 0");
+            if (b * (d->ub[3] - d->lb[2]) > kSeriesYMax || b * (-d->lb[1]) > kSeriesYMax)
+                return fail(GAC_ERR_INVALID_ARG,
+                            "SMT bounds outside the validated range: need b*(ub[De_perp]-lb[De_par]) <= 12");
+        }
+    }
+
+    ModelConst mc;
+    std::memset(&mc, 0, sizeof mc);
+    mc.kind = d->kind;
+    mc.n_par = P;
+    mc.n_acq = d->n_acq;
+    mc.n_meas = model_complex(d->kind) ? 2 * d->n_acq : d->n_acq;
+    for (int k = 0; k < d->n_acq; ++k) {
+        mc.acq_d[k] = d->acq[k];
+        mc.acq_f[k] = static_cast<float>(d->acq[k]);
+    }
+    for (int p = 0; p < P; ++p) {
+        mc.lb_d[p] = d->lb[p];
+        mc.ub_d[p] = d->ub[p];
+        mc.step_d[p] = d->step[p];
+        mc.lb_f[p] = static_cast<float>(d->lb[p]);
+        mc.ub_f[p] = static_cast<float>(d->ub[p]);
+        mc.step_f[p] = static_cast<float>(d->step[p]);
+    }
+    // evenly spaced acquisitions (to 1e-9 relative) allow the recurrence
+    mc.even = 0;
+    if (d->n_acq >= 2) {
+        const double t0 = d->acq[0];
+        const double dt = (d->acq[d->n_acq - 1] - t0) / (d->n_acq - 1);
+        bool even = dt > 0;
+        for (int k = 0; k < d->n_acq && even; ++k) {
+            const double want = t0 + k * dt;
+            if (std::fabs(d->acq[k] - want) > 1e-9 * std::max(1.0, std::fabs(want))) even = false;
+        }
+        if (even) {
+            mc.even = 1;
+            mc.t0_f = static_cast<float>(t0);
+            mc.dt_f = static_cast<float>(dt);
+            mc.dtk_f = static_cast<float>(kAnchor * dt);
+        }
+    }
+    // g(-y) = sum_n y^n / (n! (2n+1)) rewritten in u = y / 12: c_n = 12^n / (n! (2n+1))
+    {
+        double pw = 1.0;  // 12^n / n!
+        for (int n = 0; n <= kSeriesDegree; ++n) {
+            if (n > 0) pw *= static_cast<double>(kSeriesYMax) / n;
+            mc.gser_f[n] = static_cast<float>(pw / (2.0 * n + 1.0));
+        }
+    }
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    if (g_models.size() >= GAC_MAX_MODELS)
+        return fail(GAC_ERR_INVALID_ARG, "at most %d models can be registered", GAC_MAX_MODELS);
+    g_models.push_back(mc);
+    *model_id = static_cast<int>(g_models.size());
+    return GAC_OK;
+}
+
+gac_status gac_model_info(int model_id, int *n_par, int *n_meas) {
+    clear_error();
+    ModelConst mc;
+    gac_status st = model_get(model_id, &mc);
+    if (st != GAC_OK) return st;
+    if (n_par) *n_par = mc.n_par;
+    if (n_meas) *n_meas = mc.n_meas;
+    return GAC_OK;
+}
+
+gac_status gac_result_sizes(int model_id, int64_t n_vox, const gac_mcmc_opts *o, size_t bytes[6]) {
+    clear_error();
+    ModelConst mc;
+    gac_status st = model_get(model_id, &mc);
+    if (st != GAC_OK) return st;
+    if (!bytes) return fail(GAC_ERR_INVALID_ARG, "bytes must not be NULL");
+    if (n_vox < 0) return fail(GAC_ERR_INVALID_ARG, "n_vox must be >= 0");
+    if ((st = validate_opts(o, n_vox)) != GAC_OK) return st;
+    const size_t N = static_cast<size_t>(n_vox), P = mc.n_par, C = o->n_chains;
+    const size_t S = n_samples(o->iterations, o->burnin, o->thin);
+    bytes[0] = P * N * sizeof(double);
+    bytes[1] = P * N * sizeof(double);
+    bytes[2] = S * C * P * N * sizeof(float);
+    bytes[3] = C * N * sizeof(float);
+    bytes[4] = C * N * sizeof(int32_t);
+    bytes[5] = static_cast<size_t>(o->trace_n_vox) * C * o->iterations * sizeof(gac_trace_rec);
+    return GAC_OK;
+}
+
+gac_status gac_mcmc_run(int model_id, const void *data, int64_t n_vox, const float *sigma,
+                        float sigma_scalar, const float *x0, const gac_mcmc_opts *o,
+                        gac_result *out, void *stream) {
+    clear_error();
+    ModelConst mc;
+    gac_status st = model_get(model_id, &mc);
+    if (st != GAC_OK) return st;
+    if (n_vox < 0) return fail(GAC_ERR_INVALID_ARG, "n_vox must be >= 0");
+    if ((st = validate_opts(o, n_vox)) != GAC_OK) return st;
+    if (!out) return fail(GAC_ERR_INVALID_ARG, "out must not be NULL");
+    if (n_vox > 0 && !data) return fail(GAC_ERR_INVALID_ARG, "data must not be NULL");
+    if (!sigma && !(sigma_scalar > 0.0f && std::isfinite(sigma_scalar)))
+        return fail(GAC_ERR_INVALID_ARG, "sigma is NULL and sigma_scalar is not a positive number");
+    if (o->trace_n_vox > 0 && !out->trace)
+        return fail(GAC_ERR_INVALID_ARG, "trace_n_vox > 0 needs out->trace");
+    if (n_vox == 0) return GAC_OK;
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int P = mc.n_par, C = o->n_chains, M = mc.n_meas;
+    const int S = n_samples(o->iterations, o->burnin, o->thin);
+    const size_t N = static_cast<size_t>(n_vox);
+
+    DevBuf d_data, d_sigma, d_x0, d_mean, d_std, d_samples, d_acc, d_bad, d_trace;
+    if ((st = d_data.make(const_cast<void *>(data), N * M * sizeof(float), true, s, "data")) != GAC_OK) return st;
+    if ((st = d_sigma.make(const_cast<float *>(sigma), sigma ? N * sizeof(float) : 0, true, s, "sigma")) != GAC_OK) return st;
+    if ((st = d_x0.make(const_cast<float *>(x0), x0 ? N * C * P * sizeof(float) : 0, true, s, "x0")) != GAC_OK) return st;
+    if ((st = d_mean.make(out->mean, P * N * sizeof(double), false, s, "mean")) != GAC_OK) return st;
+    if ((st = d_std.make(out->std, P * N * sizeof(double), false, s, "std")) != GAC_OK) return st;
+    if ((st = d_samples.make(out->samples, static_cast<size_t>(S) * C * P * N * sizeof(float), false, s, "samples")) != GAC_OK) return st;
+    if ((st = d_acc.make(out->accept_rate, C * N * sizeof(float), false, s, "accept_rate")) != GAC_OK) return st;
+    if ((st = d_bad.make(out->nonfinite, C * N * sizeof(int32_t), false, s, "nonfinite")) != GAC_OK) return st;
+    if ((st = d_trace.make(out->trace, static_cast<size_t>(o->trace_n_vox) * C * o->iterations * sizeof(gac_trace_rec), false, s, "trace")) != GAC_OK) return st;
+
+    const bool trace = o->trace_n_vox > 0;
+    LaunchCfg cfg;
+    int64_t n_tiles = 0;
+    int vb = 0;
+    if ((st = plan_launch(mc, o->precision, trace, C, n_vox, &cfg, &n_tiles, &vb)) != GAC_OK) return st;
+    cfg.stream = s;
+
+    RunArgs ra;
+    std::memset(&ra, 0, sizeof ra);
+    ra.data = static_cast<const float *>(d_data.ptr);
+    ra.sigma = static_cast<const float *>(d_sigma.ptr);
+    ra.sigma_scalar = sigma_scalar;
+    ra.x0 = static_cast<const float *>(d_x0.ptr);
+    ra.mean = static_cast<double *>(d_mean.ptr);
+    ra.std = static_cast<double *>(d_std.ptr);
+    ra.samples = static_cast<float *>(d_samples.ptr);
+    ra.accept = static_cast<float *>(d_acc.ptr);
+    ra.nonfinite = static_cast<int32_t *>(d_bad.ptr);
+    ra.trace = static_cast<gac_trace_rec *>(d_trace.ptr);
+    ra.n_vox = n_vox;
+    ra.C = C;
+    ra.I = o->iterations;
+    ra.B = o->burnin;
+    ra.T = o->thin;
+    ra.S = S;
+    ra.k0 = static_cast<uint32_t>(o->seed & 0xFFFFFFFFu);
+    ra.k1 = static_cast<uint32_t>(o->seed >> 32);
+    ra.voxel_base = o->voxel_base;
+    ra.moments_mode = o->moments_mode;
+    ra.trace_n = o->trace_n_vox;
+    ra.vox_per_block = vb;
+    ra.row_stride = row_stride_for(mc.kind, M);
+    ra.data_vec4 = (M % 4 == 0) && ((reinterpret_cast<uintptr_t>(ra.data) & 15) == 0);
+    ra.n_tiles = n_tiles;
+
+    cudaError_t e = launch_mh(mc.kind, o->precision, trace, mc, ra, cfg);
+    if (e != cudaSuccess) return cuda_fail(e, "MH kernel launch");
+    for (DevBuf *b : {&d_mean, &d_std, &d_samples, &d_acc, &d_bad, &d_trace})
+        if ((st = b->copy_out()) != GAC_OK) return st;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "MH kernel");
+    return GAC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,320 @@
+// Persistent Metropolis-Hastings kernel (mcmc.m hot path, Sec. 2.2.2).
+//
+// One thread owns one (voxel, chain): a block holds VB = floor(256 / C)
+// voxels x C chains (chain fastest).  Per tile of voxels the block
+//   a1  stages the voxels' measurements in shared memory (coalesced 16-byte
+//       global loads, odd row stride so that the lanes of a warp hit
+//       distinct banks), then every thread
+//   a2  draws or loads its initial state and evaluates its likelihood,
+//   a3  per iteration draws Philox words for (t, voxel, chain),
+//   a4  proposes theta' = clamp(theta + step * z, lb, ub),
+//   a5  evaluates the forward model at every acquisition and
+//   a6  accumulates the Gaussian log-likelihood in registers,
+//   a7  accepts iff log u < L' - L,
+//   a8  on the thinning grid stores the state (coalesced over voxels) and
+//       updates Welford accumulators in shared memory,
+// and at the end
+//   a9  merges the C chains' accumulators of each voxel in chain order
+//       (Chan et al.'s pairwise update) and writes mean, SD, acceptance
+//       rate and the non-finite count.
+// Nothing but thinned samples touches HBM inside the iteration loop.
+//
+// Precision variants (template PREC):
+//   MIXED  FP32 model and residuals, Kahan-compensated sum, acceptance with
+//          FP64 semantics (an FP32 test with a proven error margin decides
+//          almost every step; steps inside the margin are decided in FP64
+//          from the same L, L' and acceptance word), FP64 Welford.
+//   FP32   FP32 everywhere (plain sum, FP32 decision, FP32 Welford).
+//   FP64   FP64 everywhere.
+#pragma once
+#include <cstdint>
+
+#include "gac.h"
+#include "models.cuh"
+#include "philox.cuh"
+
+namespace gac {
+
+constexpr int kBlock = 256;
+
+struct RunArgs {
+    const float *data;   // [N][M]
+    const float *sigma;  // [N] or nullptr
+    float sigma_scalar;
+    const float *x0;     // [N][C][P] or nullptr
+    double *mean;        // [P][N]
+    double *std;         // [P][N]
+    float *samples;      // [S][C][P][N]
+    float *accept;       // [C][N]
+    int32_t *nonfinite;  // [C][N]
+    gac_trace_rec *trace;  // [trace_n][C][I]
+    int64_t n_vox;
+    int C, I, B, T, S;
+    uint32_t k0, k1;     // Philox key (seed lo, hi)
+    uint64_t voxel_base;
+    int moments_mode;
+    int trace_n;
+    int vox_per_block;   // VB
+    int row_stride;      // shared-memory floats per voxel row (padded)
+    int data_vec4;       // rows are whole float4s and data is 16-byte aligned
+    int64_t n_tiles;
+};
+
+template <int PREC>
+struct PrecTraits;
+template <>
+struct PrecTraits<GAC_PREC_MIXED> {
+    using R = float;   // state, model
+    using W = double;  // Welford accumulators
+    using Acc = KahanSum;
+};
+template <>
+struct PrecTraits<GAC_PREC_FP32> {
+    using R = float;
+    using W = float;
+    using Acc = PlainSumF;
+};
+template <>
+struct PrecTraits<GAC_PREC_FP64> {
+    using R = double;
+    using W = double;
+    using Acc = PlainSumD;
+};
+
+template <int KIND, int PREC>
+__device__ __forceinline__ typename PrecTraits<PREC>::R loglik_any(
+    const typename PrecTraits<PREC>::R *th, const float *y, typename PrecTraits<PREC>::R inv_s2,
+    const ModelConst &mc) {
+    if constexpr (PREC == GAC_PREC_FP64) return loglik_d<KIND>(th, y, inv_s2, mc);
+    else return loglik_f<KIND, typename PrecTraits<PREC>::Acc>(th, y, inv_s2, mc);
+}
+
+// Acceptance: log u < Lp - L.
+template <int PREC>
+__device__ __forceinline__ bool accept_step(typename PrecTraits<PREC>::R Lp,
+                                            typename PrecTraits<PREC>::R L, uint32_t w) {
+    if constexpr (PREC == GAC_PREC_FP64) {
+        return log(u01_d(w)) < Lp - L;
+    } else if constexpr (PREC == GAC_PREC_FP32) {
+        return logf(u01_f(w)) < Lp - L;
+    } else {
+        // FP64 semantics at FP32 cost.  Error of the FP32 quantities:
+        //   d32 = Lp - L:        <= 2^-24 |d32|  (Lp, L are exact floats)
+        //   lu32 = __logf(u32):  <= 2^-21.41 absolute on [0.5, 2], 3 ulp
+        //                        otherwise (|ln u| <= 22.2 -> < 6e-6), plus
+        //                        2^-24 from rounding u to float.
+        // A margin of 1e-5 + 2^-20 (|L| + |Lp|) covers both; inside it the
+        // decision is recomputed in FP64.  NaN lands in the FP64 branch and
+        // rejects.
+        const float d32 = Lp - L;
+        const float lu32 = __logf(u01_f(w));
+        const float margin = 1e-5f + 0x1p-20f * (fabsf(L) + fabsf(Lp));
+        const float gap = d32 - lu32;
+        if (fabsf(gap) > margin) return gap > 0.0f;
+        return log(u01_d(w)) < static_cast<double>(Lp) - static_cast<double>(L);
+    }
+}
+
+template <int KIND, int PREC, bool TRACE>
+__global__ void __launch_bounds__(kBlock) mh_kernel(const ModelConst mc, const RunArgs ra) {
+    using R = typename PrecTraits<PREC>::R;
+    using W = typename PrecTraits<PREC>::W;
+    constexpr int P = model_n_par(KIND);
+    constexpr int NW = n_words(P);
+    constexpr int NWA = 4 * n_calls(P);
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    W *wf_mean = reinterpret_cast<W *>(smem_raw);     // [P][kBlock]
+    W *wf_m2 = wf_mean + P * kBlock;                   // [P][kBlock]
+    float *ytile = reinterpret_cast<float *>(wf_m2 + P * kBlock);  // [VB][row_stride]
+
+    const int tid = threadIdx.x;
+    const int C = ra.C;
+    const int VB = ra.vox_per_block;
+    const int M = mc.n_meas;
+    const int lv = tid / C;
+    const int c = tid - lv * C;
+    const bool lane_used = tid < VB * C;
+
+    for (int64_t tile = blockIdx.x; tile < ra.n_tiles; tile += gridDim.x) {
+        const int64_t v0 = tile * VB;
+        const int64_t left = ra.n_vox - v0;
+        const int nv = left < VB ? static_cast<int>(left) : VB;
+
+        // a1: stage measurements of voxels [v0, v0 + nv) in shared memory
+        __syncthreads();
+        {
+            const float *src = ra.data + v0 * M;
+            const int total = nv * M;
+            if (ra.data_vec4) {
+                const float4 *src4 = reinterpret_cast<const float4 *>(src);
+                for (int i = tid; i < total / 4; i += kBlock) {
+                    const float4 q = __ldg(src4 + i);
+                    const int e = 4 * i, row = e / M, col = e - row * M;
+                    float *dst = ytile + row * ra.row_stride + col;
+                    dst[0] = q.x;
+                    dst[1] = q.y;
+                    dst[2] = q.z;
+                    dst[3] = q.w;
+                }
+            } else {
+                for (int i = tid; i < total; i += kBlock) {
+                    const int row = i / M, col = i - row * M;
+                    ytile[row * ra.row_stride + col] = __ldg(src + i);
+                }
+            }
+        }
+        __syncthreads();
+
+        const bool active = lane_used && lv < nv;
+        const int64_t v = v0 + lv;
+        int n_acc = 0, n_bad = 0;
+        if (active) {
+            const float *y = ytile + lv * ra.row_stride;
+            const float sig = ra.sigma ? __ldg(ra.sigma + v) : ra.sigma_scalar;
+            const R inv_s2 = R(1) / (R(sig) * R(sig));
+            const uint32_t vg = static_cast<uint32_t>(ra.voxel_base + static_cast<uint64_t>(v));
+            const uint32_t cu = static_cast<uint32_t>(c);
+
+            // a2: initial state
+            R th[P];
+            if (ra.x0) {
+                const float *x0 = ra.x0 + (v * C + c) * P;
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    if constexpr (PREC == GAC_PREC_FP64)
+                        th[p] = fmin(fmax(static_cast<double>(x0[p]), mc.lb_d[p]), mc.ub_d[p]);
+                    else
+                        th[p] = fminf(fmaxf(x0[p], mc.lb_f[p]), mc.ub_f[p]);
+                }
+            } else {
+                uint32_t w0[4 * ((P + 3) / 4)];
+                draw_words(w0, kInitIteration, vg, cu, ra.k0, ra.k1);
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    if constexpr (PREC == GAC_PREC_FP64)
+                        th[p] = mc.lb_d[p] + (mc.ub_d[p] - mc.lb_d[p]) * u01_d(w0[p]);
+                    else
+                        th[p] = fmaf(mc.ub_f[p] - mc.lb_f[p], u01_f(w0[p]), mc.lb_f[p]);
+                }
+            }
+            R L = loglik_any<KIND, PREC>(th, y, inv_s2, mc);
+
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                wf_mean[p * kBlock + tid] = W(0);
+                wf_m2[p * kBlock + tid] = W(0);
+            }
+            int n_mom = 0;
+            int to_thin = ra.B + ra.T;  // next iteration on the thinning grid
+
+            for (int t = 1; t <= ra.I; ++t) {
+                // a3: random words for (t, voxel, chain)
+                uint32_t w[NWA];
+                draw_words(w, static_cast<uint32_t>(t), vg, cu, ra.k0, ra.k1);
+                // a4: proposal
+                R prop[P];
+#pragma unroll
+                for (int j = 0; 2 * j < P; ++j) {
+                    R z0, z1;
+                    if constexpr (PREC == GAC_PREC_FP64) box_muller_d(w[2 * j], w[2 * j + 1], z0, z1);
+                    else box_muller_f(w[2 * j], w[2 * j + 1], z0, z1);
+                    if constexpr (PREC == GAC_PREC_FP64) {
+                        prop[2 * j] = fmin(fmax(fma(mc.step_d[2 * j], z0, th[2 * j]), mc.lb_d[2 * j]),
+                                           mc.ub_d[2 * j]);
+                        if (2 * j + 1 < P)
+                            prop[2 * j + 1] = fmin(fmax(fma(mc.step_d[2 * j + 1], z1, th[2 * j + 1]),
+                                                        mc.lb_d[2 * j + 1]), mc.ub_d[2 * j + 1]);
+                    } else {
+                        prop[2 * j] = fminf(fmaxf(fmaf(mc.step_f[2 * j], z0, th[2 * j]), mc.lb_f[2 * j]),
+                                            mc.ub_f[2 * j]);
+                        if (2 * j + 1 < P)
+                            prop[2 * j + 1] = fminf(fmaxf(fmaf(mc.step_f[2 * j + 1], z1, th[2 * j + 1]),
+                                                          mc.lb_f[2 * j + 1]), mc.ub_f[2 * j + 1]);
+                    }
+                }
+                // a5 + a6: forward model and likelihood
+                const R Lp = loglik_any<KIND, PREC>(prop, y, inv_s2, mc);
+                // a7: accept / reject
+                const uint32_t w_acc = w[NW - 1];
+                const bool acc = accept_step<PREC>(Lp, L, w_acc);
+                n_bad += !isfinite(Lp);
+                if constexpr (TRACE) {
+                    if (v < ra.trace_n) {
+                        gac_trace_rec *rec = ra.trace + (v * C + c) * static_cast<int64_t>(ra.I) + (t - 1);
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            rec->theta[p] = static_cast<double>(th[p]);
+                            rec->prop[p] = static_cast<double>(prop[p]);
+                        }
+                        rec->L = static_cast<double>(L);
+                        rec->Lp = static_cast<double>(Lp);
+                        rec->w_acc = w_acc;
+                        rec->accepted = acc ? 1 : 0;
+                    }
+                }
+                if (acc) {
+#pragma unroll
+                    for (int p = 0; p < P; ++p) th[p] = prop[p];
+                    L = Lp;
+                    ++n_acc;
+                }
+                // a8: thinning grid t = B + T, B + 2T, ... and moments
+                const bool on_grid = (t == to_thin);
+                if (on_grid) {
+                    to_thin += ra.T;
+                    if (ra.samples) {
+                        const int s = (t - ra.B) / ra.T - 1;
+                        float *dst = ra.samples + ((static_cast<int64_t>(s) * C + c) * P) * ra.n_vox + v;
+#pragma unroll
+                        for (int p = 0; p < P; ++p) dst[p * ra.n_vox] = static_cast<float>(th[p]);
+                    }
+                }
+                const bool take = (ra.moments_mode == GAC_MOMENTS_ALL_POSTBURNIN) ? (t > ra.B) : on_grid;
+                if (take) {
+                    ++n_mom;
+                    const W inv_n = W(1) / W(n_mom);
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        const W x = static_cast<W>(th[p]);
+                        W m = wf_mean[p * kBlock + tid];
+                        const W d = x - m;
+                        m += d * inv_n;
+                        wf_mean[p * kBlock + tid] = m;
+                        wf_m2[p * kBlock + tid] += d * (x - m);
+                    }
+                }
+            }
+            if (ra.accept) ra.accept[c * ra.n_vox + v] = ra.I > 0 ? float(n_acc) / float(ra.I) : 0.0f;
+            if (ra.nonfinite) ra.nonfinite[c * ra.n_vox + v] = n_bad;
+        }
+
+        // a9: pool the C chains of each voxel in chain order
+        __syncthreads();
+        if (active && c == 0 && (ra.mean || ra.std)) {
+            const int n_each = (ra.moments_mode == GAC_MOMENTS_ALL_POSTBURNIN) ? max(ra.I - ra.B, 0) : ra.S;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                W mu = wf_mean[p * kBlock + tid];
+                W m2 = wf_m2[p * kBlock + tid];
+                double n = n_each;
+                for (int c2 = 1; c2 < C; ++c2) {
+                    const W mb = wf_mean[p * kBlock + tid + c2];
+                    const W m2b = wf_m2[p * kBlock + tid + c2];
+                    const double ntot = n + n_each;
+                    const W delta = mb - mu;
+                    mu += delta * W(n_each / ntot);
+                    m2 += m2b + delta * delta * W(n * n_each / ntot);
+                    n = ntot;
+                }
+                const double nan = __longlong_as_double(0x7ff8000000000000ll);
+                const double mean_out = n > 0 ? static_cast<double>(mu) : nan;
+                const double sd_out = n > 1 ? sqrt(static_cast<double>(m2) / (n - 1.0)) : (n == 1 ? 0.0 : nan);
+                if (ra.mean) ra.mean[p * ra.n_vox + v] = mean_out;
+                if (ra.std) ra.std[p * ra.n_vox + v] = sd_out;
+            }
+        }
+    }
+}
+
+}  // namespace gac

@@ -1,0 +1,338 @@
+// Forward signal models on the device, in FP32 (MIXED and FP32 paths) and
+// FP64, each written as `eval(theta, mc, visit)` that calls visit(k, s_k) or
+// visit(k, re_k, im_k) for every acquisition k.  The sampler's likelihood and
+// the gac_forward test entry point both go through eval, so they share one
+// arithmetic.
+//
+//  MONOEXP (Eq. 3): s_k = S0 exp(-R2* TE_k), TE in ms, R2* in 1/s.
+//  MWI3:  S(t) = exp(i phi0) sum_j A_j exp(-t/T2*_j) exp(-i 2 pi df_j t), df_EW = 0.
+//  SMT:   s(b) = f g(b Da) + (1-f) exp(-b De_perp) g(b (De_par - De_perp)),
+//         g(x) = integral_0^1 exp(-x u^2) du.
+//  LINEAR_TEST: s_k = a + c t_k.
+//
+// FP32 evaluation of evenly spaced echoes (MONOEXP, MWI3) uses an anchored
+// geometric recurrence: with t_k = t_0 + k dt, each pool's term is
+// E_k = E_0 R^k with R = exp(-dt (rate + i w)).  E_0, R and R^K (K = 6) come
+// from accurate expf/sincosf; inside a block of K echoes the term advances by
+// one complex multiply, and each block starts from the previous anchor times
+// R^K.  This replaces 3 transcendental calls per echo and pool by one
+// multiply while keeping the error near that of direct evaluation (every term
+// is at most ~K + n/K roundings away from an accurately computed value).
+// Unevenly spaced echoes, and the FP64 path, evaluate every echo directly.
+#pragma once
+#include <cstdint>
+
+#include "gac.h"
+
+namespace gac {
+
+constexpr int kAnchor = 6;
+constexpr int kSeriesDegree = 40;     // g(x) series for x < 0 in u = -x / kSeriesYMax
+constexpr float kSeriesYMax = 12.0f;  // registration keeps -x <= 12
+
+struct ModelConst {
+    int kind;
+    int n_par;
+    int n_acq;
+    int n_meas;
+    int even;       // acquisitions evenly spaced (recurrence allowed)
+    float t0_f, dt_f, dtk_f;  // first acquisition, spacing, kAnchor * spacing
+    float acq_f[GAC_MAX_ACQ];
+    double acq_d[GAC_MAX_ACQ];
+    float lb_f[GAC_MAX_PAR], ub_f[GAC_MAX_PAR], step_f[GAC_MAX_PAR];
+    double lb_d[GAC_MAX_PAR], ub_d[GAC_MAX_PAR], step_d[GAC_MAX_PAR];
+    // coefficients of g(-y) = sum_n c_n (y / kSeriesYMax)^n, c_n = 12^n / (n! (2n+1))
+    float gser_f[kSeriesDegree + 1];
+};
+
+__host__ __device__ constexpr int model_n_par(int kind) {
+    return kind == GAC_MODEL_MONOEXP ? 2
+         : kind == GAC_MODEL_MWI3 ? 9
+         : kind == GAC_MODEL_SMT ? 4
+         : kind == GAC_MODEL_LINEAR_TEST ? 2 : -1;
+}
+__host__ __device__ constexpr bool model_complex(int kind) { return kind == GAC_MODEL_MWI3; }
+
+constexpr float kTwoPiMilli = 6.28318530717958648e-3f;  // 2 pi * 1e-3: Hz * ms -> rad
+constexpr double kTwoPiMilliD = 6.28318530717958648e-3;
+constexpr float kSqrtPiHalf = 0.886226925452758014f;
+constexpr double kSqrtPiHalfD = 0.886226925452758014;
+
+// ---------------------------------------------------------------- g(x) ----
+__device__ __forceinline__ float smt_g_f(float x, const ModelConst &mc) {
+    if (x > 0.0f) {
+        if (x < 1e-30f) return 1.0f;
+        const float s = sqrtf(x);
+        return kSqrtPiHalf * erff(s) / s;
+    }
+    // x <= 0: all-positive power series, Horner in u = -x / 12 in [0, 1]
+    const float u = -x * (1.0f / kSeriesYMax);
+    float p = mc.gser_f[kSeriesDegree];
+#pragma unroll 8
+    for (int n = kSeriesDegree - 1; n >= 0; --n) p = fmaf(p, u, mc.gser_f[n]);
+    return p;
+}
+
+__device__ __forceinline__ double smt_g_d(double x) {
+    if (x > 0.0) {
+        if (x < 1e-300) return 1.0;
+        const double s = sqrt(x);
+        return kSqrtPiHalfD * erf(s) / s;
+    }
+    const double y = -x;
+    double term = 1.0, sum = 1.0;
+    for (int n = 1; n < 200; ++n) {
+        term *= y / n;
+        const double add = term / (2 * n + 1);
+        sum += add;
+        if (add <= 1e-17 * sum) break;
+    }
+    return sum;
+}
+
+// ----------------------------------------------------------- FP32 models --
+template <class V>
+__device__ __forceinline__ void eval_monoexp_f(const float *th, const ModelConst &mc, V &&visit) {
+    const float s0 = th[0];
+    const float rate = th[1] * 1e-3f;  // 1/s -> 1/ms
+    const int n = mc.n_acq;
+    if (mc.even) {
+        float anchor = s0 * expf(-mc.t0_f * rate);
+        const float r1 = expf(-mc.dt_f * rate);
+        const float rk = expf(-mc.dtk_f * rate);
+        for (int a = 0; a < n; a += kAnchor) {
+            float e = anchor;
+#pragma unroll
+            for (int i = 0; i < kAnchor; ++i) {
+                if (a + i < n) visit(a + i, e);
+                e *= r1;
+            }
+            anchor *= rk;
+        }
+    } else {
+        for (int k = 0; k < n; ++k) visit(k, s0 * expf(-mc.acq_f[k] * rate));
+    }
+}
+
+template <class V>
+__device__ __forceinline__ void eval_mwi3_f(const float *th, const ModelConst &mc, V &&visit) {
+    const float phi0 = th[8];
+    const int n = mc.n_acq;
+    if (mc.even) {
+        float er[3], ei[3], rr[3], ri[3], kr[3], ki[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float rate = 1.0f / th[3 + j];
+            const float w = (j < 2) ? kTwoPiMilli * th[6 + j] : 0.0f;  // rad / ms
+            const float m0 = th[j] * expf(-mc.t0_f * rate);
+            float s, c;
+            sincosf(fmaf(-w, mc.t0_f, phi0), &s, &c);
+            er[j] = m0 * c;
+            ei[j] = m0 * s;
+            const float m1 = expf(-mc.dt_f * rate);
+            const float mk = expf(-mc.dtk_f * rate);
+            if (j < 2) {
+                sincosf(-w * mc.dt_f, &s, &c);
+                rr[j] = m1 * c;
+                ri[j] = m1 * s;
+                sincosf(-w * mc.dtk_f, &s, &c);
+                kr[j] = mk * c;
+                ki[j] = mk * s;
+            } else {  // extra-cellular pool: no frequency offset, real ratio
+                rr[j] = m1;
+                ri[j] = 0.0f;
+                kr[j] = mk;
+                ki[j] = 0.0f;
+            }
+        }
+        for (int a = 0; a < n; a += kAnchor) {
+            float cr[3], ci[3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                cr[j] = er[j];
+                ci[j] = ei[j];
+            }
+#pragma unroll
+            for (int i = 0; i < kAnchor; ++i) {
+                if (a + i < n) visit(a + i, cr[0] + cr[1] + cr[2], ci[0] + ci[1] + ci[2]);
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const float nr = fmaf(cr[j], rr[j], -ci[j] * ri[j]);
+                    const float ni = fmaf(cr[j], ri[j], ci[j] * rr[j]);
+                    cr[j] = nr;
+                    ci[j] = ni;
+                }
+                cr[2] *= rr[2];
+                ci[2] *= rr[2];
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const float nr = fmaf(er[j], kr[j], -ei[j] * ki[j]);
+                const float ni = fmaf(er[j], ki[j], ei[j] * kr[j]);
+                er[j] = nr;
+                ei[j] = ni;
+            }
+            er[2] *= kr[2];
+            ei[2] *= kr[2];
+        }
+    } else {
+        float rate[3], w[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            rate[j] = 1.0f / th[3 + j];
+            w[j] = (j < 2) ? kTwoPiMilli * th[6 + j] : 0.0f;
+        }
+        for (int k = 0; k < n; ++k) {
+            const float t = mc.acq_f[k];
+            float re = 0.0f, im = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const float m = th[j] * expf(-t * rate[j]);
+                float s, c;
+                sincosf(fmaf(-w[j], t, phi0), &s, &c);
+                re = fmaf(m, c, re);
+                im = fmaf(m, s, im);
+            }
+            visit(k, re, im);
+        }
+    }
+}
+
+template <class V>
+__device__ __forceinline__ void eval_smt_f(const float *th, const ModelConst &mc, V &&visit) {
+    const float f = th[0], da = th[1], dpar = th[2], dperp = th[3];
+    const float ddiff = dpar - dperp;
+    for (int k = 0; k < mc.n_acq; ++k) {
+        const float b = mc.acq_f[k];
+        const float intra = smt_g_f(b * da, mc);
+        const float extra = expf(-b * dperp) * smt_g_f(b * ddiff, mc);
+        visit(k, fmaf(f, intra, (1.0f - f) * extra));
+    }
+}
+
+template <class V>
+__device__ __forceinline__ void eval_linear_f(const float *th, const ModelConst &mc, V &&visit) {
+    for (int k = 0; k < mc.n_acq; ++k) visit(k, fmaf(th[1], mc.acq_f[k], th[0]));
+}
+
+// ----------------------------------------------------------- FP64 models --
+template <class V>
+__device__ __forceinline__ void eval_monoexp_d(const double *th, const ModelConst &mc, V &&visit) {
+    for (int k = 0; k < mc.n_acq; ++k) visit(k, th[0] * exp(-th[1] * mc.acq_d[k] * 1e-3));
+}
+
+template <class V>
+__device__ __forceinline__ void eval_mwi3_d(const double *th, const ModelConst &mc, V &&visit) {
+    for (int k = 0; k < mc.n_acq; ++k) {
+        const double t = mc.acq_d[k];
+        double re = 0.0, im = 0.0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double m = th[j] * exp(-t / th[3 + j]);
+            const double df = (j < 2) ? th[6 + j] : 0.0;
+            double s, c;
+            sincos(th[8] - kTwoPiMilliD * df * t, &s, &c);
+            re += m * c;
+            im += m * s;
+        }
+        visit(k, re, im);
+    }
+}
+
+template <class V>
+__device__ __forceinline__ void eval_smt_d(const double *th, const ModelConst &mc, V &&visit) {
+    for (int k = 0; k < mc.n_acq; ++k) {
+        const double b = mc.acq_d[k];
+        const double intra = smt_g_d(b * th[1]);
+        const double extra = exp(-b * th[3]) * smt_g_d(b * (th[2] - th[3]));
+        visit(k, th[0] * intra + (1.0 - th[0]) * extra);
+    }
+}
+
+template <class V>
+__device__ __forceinline__ void eval_linear_d(const double *th, const ModelConst &mc, V &&visit) {
+    for (int k = 0; k < mc.n_acq; ++k) visit(k, th[0] + th[1] * mc.acq_d[k]);
+}
+
+// --------------------------------------------------------- dispatch by kind
+template <int KIND, class V>
+__device__ __forceinline__ void eval_f(const float *th, const ModelConst &mc, V &&visit) {
+    if constexpr (KIND == GAC_MODEL_MONOEXP) eval_monoexp_f(th, mc, visit);
+    else if constexpr (KIND == GAC_MODEL_MWI3) eval_mwi3_f(th, mc, visit);
+    else if constexpr (KIND == GAC_MODEL_SMT) eval_smt_f(th, mc, visit);
+    else eval_linear_f(th, mc, visit);
+}
+
+template <int KIND, class V>
+__device__ __forceinline__ void eval_d(const double *th, const ModelConst &mc, V &&visit) {
+    if constexpr (KIND == GAC_MODEL_MONOEXP) eval_monoexp_d(th, mc, visit);
+    else if constexpr (KIND == GAC_MODEL_MWI3) eval_mwi3_d(th, mc, visit);
+    else if constexpr (KIND == GAC_MODEL_SMT) eval_smt_d(th, mc, visit);
+    else eval_linear_d(th, mc, visit);
+}
+
+// ----------------------------------------------------- likelihood sums -----
+// Kahan-compensated FP32 sum (MIXED path).
+struct KahanSum {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ float value() const { return s; }
+};
+struct PlainSumF {
+    float s = 0.0f;
+    __device__ __forceinline__ void add(float x) { s += x; }
+    __device__ __forceinline__ float value() const { return s; }
+};
+struct PlainSumD {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+// -1/2 * sum_m (y_m - s_m)^2 / sigma^2, with y read from `y` (row of the
+// voxel; complex rows as re, im pairs).  ACC = KahanSum or PlainSumF.
+template <int KIND, class ACC>
+__device__ __forceinline__ float loglik_f(const float *th, const float *y, float inv_s2,
+                                          const ModelConst &mc) {
+    ACC acc;
+    if constexpr (model_complex(KIND)) {
+        eval_f<KIND>(th, mc, [&](int k, float sr, float si) {
+            const float2 yk = reinterpret_cast<const float2 *>(y)[k];
+            const float dr = yk.x - sr;
+            const float di = yk.y - si;
+            acc.add(fmaf(dr, dr, di * di));
+        });
+    } else {
+        eval_f<KIND>(th, mc, [&](int k, float s) {
+            const float d = y[k] - s;
+            acc.add(d * d);
+        });
+    }
+    return -0.5f * acc.value() * inv_s2;
+}
+
+template <int KIND>
+__device__ __forceinline__ double loglik_d(const double *th, const float *y, double inv_s2,
+                                           const ModelConst &mc) {
+    PlainSumD acc;
+    if constexpr (model_complex(KIND)) {
+        eval_d<KIND>(th, mc, [&](int k, double sr, double si) {
+            const double dr = static_cast<double>(y[2 * k]) - sr;
+            const double di = static_cast<double>(y[2 * k + 1]) - si;
+            acc.add(dr * dr + di * di);
+        });
+    } else {
+        eval_d<KIND>(th, mc, [&](int k, double s) {
+            const double d = static_cast<double>(y[k]) - s;
+            acc.add(d * d);
+        });
+    }
+    return -0.5 * acc.value() * inv_s2;
+}
+
+}  // namespace gac

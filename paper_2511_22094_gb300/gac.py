@@ -1,0 +1,236 @@
+"""ctypes binding of libgac.so (include/gac.h) -- argument marshalling only.
+
+Every function here has the name of the C entry point it calls and only
+converts arguments: numpy arrays and host tensors become host pointers, CUDA
+tensors become device pointers, a torch.cuda.Stream becomes a cudaStream_t.
+All arithmetic runs in libgac.so.  There is no fallback: if the library is
+missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgac.so")
+
+GAC_OK = 0
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNKNOWN_MODEL", 3: "BUDGET", 4: "OOM", 5: "CUDA",
+          6: "TIMEOUT", 7: "NOT_READY", 8: "CANCELLED", 9: "UNKNOWN_JOB"}
+MONOEXP, MWI3, SMT, LINEAR_TEST = 1, 2, 3, 100
+PREC_MIXED, PREC_FP32, PREC_FP64 = 0, 1, 2
+MOMENTS_THINNED, MOMENTS_ALL_POSTBURNIN = 0, 1
+MAX_PAR = 12
+
+
+class GacError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ModelDesc(ct.Structure):
+    _fields_ = [("kind", ct.c_int), ("n_acq", ct.c_int), ("acq", ct.POINTER(ct.c_double)),
+                ("n_par", ct.c_int), ("lb", ct.POINTER(ct.c_double)),
+                ("ub", ct.POINTER(ct.c_double)), ("step", ct.POINTER(ct.c_double))]
+
+
+class McmcOpts(ct.Structure):
+    _fields_ = [("iterations", ct.c_int), ("burnin", ct.c_int), ("thin", ct.c_int),
+                ("n_chains", ct.c_int), ("seed", ct.c_uint64), ("voxel_base", ct.c_uint64),
+                ("precision", ct.c_int), ("moments_mode", ct.c_int), ("trace_n_vox", ct.c_int)]
+
+
+class TraceRec(ct.Structure):
+    _fields_ = [("theta", ct.c_double * MAX_PAR), ("prop", ct.c_double * MAX_PAR),
+                ("L", ct.c_double), ("Lp", ct.c_double), ("w_acc", ct.c_uint32),
+                ("accepted", ct.c_int32)]
+
+
+TRACE_DTYPE = np.dtype([("theta", np.float64, MAX_PAR), ("prop", np.float64, MAX_PAR),
+                        ("L", np.float64), ("Lp", np.float64), ("w_acc", np.uint32),
+                        ("accepted", np.int32)])
+assert TRACE_DTYPE.itemsize == ct.sizeof(TraceRec)
+
+
+class Result(ct.Structure):
+    _fields_ = [("mean", ct.c_void_p), ("std", ct.c_void_p), ("samples", ct.c_void_p),
+                ("accept_rate", ct.c_void_p), ("nonfinite", ct.c_void_p), ("trace", ct.c_void_p)]
+
+
+EXPORTS = ["gac_model_register", "gac_model_info", "gac_result_sizes", "gac_mcmc_run",
+           "gac_forward", "gac_loglik", "gac_philox_words", "gac_normals", "gac_last_error",
+           "gac_version"]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libgac.so is not built ({LIB_PATH}); run paper_2511_22094_gb300.build.build()")
+    L = ct.CDLL(LIB_PATH)
+    vp, i64, u64 = ct.c_void_p, ct.c_int64, ct.c_uint64
+    L.gac_last_error.restype = ct.c_char_p
+    L.gac_version.restype = ct.c_char_p
+    sig = {
+        "gac_model_register": [ct.POINTER(ModelDesc), ct.POINTER(ct.c_int)],
+        "gac_model_info": [ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)],
+        "gac_result_sizes": [ct.c_int, i64, ct.POINTER(McmcOpts), ct.POINTER(ct.c_size_t * 6)],
+        "gac_mcmc_run": [ct.c_int, vp, i64, vp, ct.c_float, vp, ct.POINTER(McmcOpts),
+                         ct.POINTER(Result), vp],
+        "gac_forward": [ct.c_int, vp, i64, ct.c_int, vp, vp],
+        "gac_loglik": [ct.c_int, vp, i64, vp, vp, ct.c_int, vp, vp],
+        "gac_philox_words": [u64, vp, vp, vp, i64, ct.c_int, vp, vp],
+        "gac_normals": [u64, vp, vp, vp, i64, ct.c_int, ct.c_int, vp, vp, vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ct.c_int
+    return L
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def last_error() -> str:
+    return _lib.gac_last_error().decode()
+
+
+def version() -> str:
+    return _lib.gac_version().decode()
+
+
+def _check(st: int, where: str):
+    if st != GAC_OK:
+        raise GacError(st, where, last_error())
+
+
+def _ptr(x):
+    """Host (numpy / CPU tensor) or device (CUDA tensor) address, or None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags.c_contiguous, "arrays must be C-contiguous"
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous(), "tensors must be contiguous"
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"cannot pass {type(x)} as a buffer")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    return int(s)
+
+
+# ------------------------------------------------------------- models ------
+def gac_model_register(kind: int, acq, lb, ub, step) -> int:
+    arrs = [np.ascontiguousarray(a, np.float64) for a in (acq, lb, ub, step)]
+    p = [a.ctypes.data_as(ct.POINTER(ct.c_double)) for a in arrs]
+    d = ModelDesc(kind, len(arrs[0]), p[0], len(arrs[1]), p[1], p[2], p[3])
+    mid = ct.c_int(0)
+    _check(_lib.gac_model_register(ct.byref(d), ct.byref(mid)), "gac_model_register")
+    return mid.value
+
+
+def gac_model_info(model_id: int):
+    P, M = ct.c_int(), ct.c_int()
+    _check(_lib.gac_model_info(model_id, ct.byref(P), ct.byref(M)), "gac_model_info")
+    return P.value, M.value
+
+
+def make_opts(iterations, burnin, thin, n_chains, seed, voxel_base=0, precision=PREC_MIXED,
+              moments_mode=MOMENTS_THINNED, trace_n_vox=0) -> McmcOpts:
+    return McmcOpts(iterations, burnin, thin, n_chains, seed, voxel_base, precision, moments_mode,
+                    trace_n_vox)
+
+
+def gac_result_sizes(model_id: int, n_vox: int, opts: McmcOpts):
+    b = (ct.c_size_t * 6)()
+    _check(_lib.gac_result_sizes(model_id, n_vox, ct.byref(opts), ct.byref(b)), "gac_result_sizes")
+    return dict(zip(("mean", "std", "samples", "accept_rate", "nonfinite", "trace"), list(b)))
+
+
+def gac_mcmc_run(model_id: int, data, n_vox: int, sigma, sigma_scalar: float, x0,
+                 opts: McmcOpts, out: dict, stream=None):
+    """out: dict with any of mean, std, samples, accept_rate, nonfinite, trace
+    (caller-allocated numpy arrays or tensors, host or device)."""
+    r = Result(*(_ptr(out.get(k)) for k in ("mean", "std", "samples", "accept_rate", "nonfinite",
+                                             "trace")))
+    _check(_lib.gac_mcmc_run(model_id, _ptr(data), n_vox, _ptr(sigma), sigma_scalar, _ptr(x0),
+                             ct.byref(opts), ct.byref(r), _stream(stream)), "gac_mcmc_run")
+
+
+def gac_forward(model_id: int, theta, n: int, precision: int, s, stream=None):
+    _check(_lib.gac_forward(model_id, _ptr(theta), n, precision, _ptr(s), _stream(stream)),
+           "gac_forward")
+
+
+def gac_loglik(model_id: int, theta, n: int, data, sigma, precision: int, L, stream=None):
+    _check(_lib.gac_loglik(model_id, _ptr(theta), n, _ptr(data), _ptr(sigma), precision, _ptr(L),
+                           _stream(stream)), "gac_loglik")
+
+
+def gac_philox_words(seed: int, t, v, c, n: int, n_words: int, out, stream=None):
+    _check(_lib.gac_philox_words(seed, _ptr(t), _ptr(v), _ptr(c), n, n_words, _ptr(out),
+                                 _stream(stream)), "gac_philox_words")
+
+
+def gac_normals(seed: int, t, v, c, n: int, n_par: int, precision: int, z, w_acc, stream=None):
+    _check(_lib.gac_normals(seed, _ptr(t), _ptr(v), _ptr(c), n, n_par, precision, _ptr(z),
+                            _ptr(w_acc), _stream(stream)), "gac_normals")
+
+
+# --------------------------------------------------- numpy conveniences ----
+def n_samples(iterations: int, burnin: int, thin: int) -> int:
+    return (iterations - burnin) // thin if iterations > burnin and thin > 0 else 0
+
+
+def run_host(model_id: int, data: np.ndarray, sigma, *, iterations, burnin, thin, n_chains, seed,
+             x0=None, sigma_scalar=0.0, voxel_base=0, precision=PREC_MIXED,
+             moments_mode=MOMENTS_THINNED, trace_n_vox=0, want_samples=True):
+    """Runs the sampler on host numpy inputs (the library stages them through
+    device memory) and returns host numpy outputs."""
+    P, M = gac_model_info(model_id)
+    data = np.ascontiguousarray(data, np.float32)
+    N = data.shape[0]
+    S = n_samples(iterations, burnin, thin)
+    C = n_chains
+    out = dict(mean=np.full((P, N), np.nan), std=np.full((P, N), np.nan),
+               samples=np.full((S, C, P, N), np.nan, np.float32) if (want_samples and S) else None,
+               accept_rate=np.zeros((C, N), np.float32), nonfinite=np.zeros((C, N), np.int32),
+               trace=np.zeros((trace_n_vox, C, iterations), TRACE_DTYPE) if trace_n_vox else None)
+    sig = None if sigma is None else np.ascontiguousarray(sigma, np.float32)
+    x0a = None if x0 is None else np.ascontiguousarray(x0, np.float32)
+    opts = make_opts(iterations, burnin, thin, n_chains, seed, voxel_base, precision, moments_mode,
+                     trace_n_vox)
+    gac_mcmc_run(model_id, data, N, sig, sigma_scalar, x0a, opts, out)
+    return out
+
+
+def forward_host(model_id: int, theta, precision=PREC_MIXED) -> np.ndarray:
+    P, M = gac_model_info(model_id)
+    th = np.ascontiguousarray(np.atleast_2d(theta), np.float64)
+    s = np.zeros((th.shape[0], M), np.float64)
+    gac_forward(model_id, th, th.shape[0], precision, s)
+    return s
+
+
+def loglik_host(model_id: int, theta, data, sigma, precision=PREC_MIXED) -> np.ndarray:
+    th = np.ascontiguousarray(np.atleast_2d(theta), np.float64)
+    n = th.shape[0]
+    y = np.ascontiguousarray(np.asarray(data, np.float32).reshape(n, -1))
+    sg = np.ascontiguousarray(np.broadcast_to(np.asarray(sigma, np.float32), (n,)))
+    L = np.zeros(n, np.float64)
+    gac_loglik(model_id, th, n, y, sg, precision, L)
+    return L

@@ -1,0 +1,125 @@
+"""The C-ABI library loads without a GPU, exports every symbol that
+include/gac.h declares, and rejects invalid arguments on the host (no compute
+call needs a GPU here)."""
+import ctypes as ct
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def gac():
+    from paper_2511_22094_gb300 import build
+    build.build()
+    from paper_2511_22094_gb300 import gac as g
+    return g
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(gac_\w+)\s*\(", src))
+    return names
+
+
+def test_exports_every_declared_symbol(gac):
+    declared = _declared()
+    assert {"gac_model_register", "gac_mcmc_run", "gac_forward", "gac_loglik"} <= declared
+    lib = ct.CDLL(gac.LIB_PATH)
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    nm = subprocess.run(["nm", "-D", "--defined-only", gac.LIB_PATH], capture_output=True, text=True)
+    if nm.returncode == 0:
+        exported = set(re.findall(r"\sT\s(gac_\w+)", nm.stdout))
+        assert declared <= exported
+    assert set(gac.EXPORTS) <= declared
+
+
+def test_version(gac):
+    assert "sm_103a" in gac.version()
+
+
+MONO = dict(kind=1, acq=[2.0 + 3 * k for k in range(12)], lb=[0.5, 10.0], ub=[1.5, 80.0],
+            step=[0.01, 1.0])
+
+
+def test_register_and_info(gac):
+    mid = gac.gac_model_register(**MONO)
+    assert gac.gac_model_info(mid) == (2, 12)
+    mid2 = gac.gac_model_register(2, [2.0 + k * 44 / 23 for k in range(24)], [0, 0, 0, 3, 40, 30, -10, -10, -np.pi],
+                                  [1, 1, 1, 20, 80, 60, 20, 20, np.pi], [0.01] * 9)
+    assert gac.gac_model_info(mid2) == (9, 48)
+
+
+@pytest.mark.parametrize("bad,status", [
+    (dict(kind=7), 2),
+    (dict(lb=[0.5, 10.0, 1.0], ub=[1.5, 80.0, 2.0], step=[0.1, 0.1, 0.1]), 1),
+    (dict(lb=[1.6, 10.0]), 1),
+    (dict(step=[-0.1, 1.0]), 1),
+    (dict(acq=[]), 1),
+    (dict(acq=[float("nan")] * 12), 1),
+    (dict(acq=list(range(65))), 1),
+])
+def test_register_rejects(gac, bad, status):
+    d = dict(MONO)
+    d.update(bad)
+    with pytest.raises(gac.GacError) as e:
+        gac.gac_model_register(**d)
+    assert e.value.status == status
+    assert gac.last_error()
+
+
+def test_register_rejects_model_specific_ranges(gac):
+    with pytest.raises(gac.GacError):  # T2* lower bound 0
+        gac.gac_model_register(2, [2.0, 3.0], [0, 0, 0, 0, 40, 30, -10, -10, -3], [1, 1, 1, 20, 80, 60, 20, 20, 3], [0.01] * 9)
+    with pytest.raises(gac.GacError):  # SMT series range exceeded
+        gac.gac_model_register(3, [0, 20.0], [0, 1, 0.5, 0], [1, 3, 3, 1.5], [0.02] * 4)
+    with pytest.raises(gac.GacError):  # negative b
+        gac.gac_model_register(3, [-1.0, 1.0], [0, 1, 0.5, 0], [1, 3, 3, 1.5], [0.02] * 4)
+
+
+def test_run_argument_validation(gac):
+    mid = gac.gac_model_register(**MONO)
+    y = np.zeros((4, 12), np.float32)
+    out = {}
+    cases = [
+        dict(iterations=-1), dict(burnin=-1), dict(thin=0), dict(n_chains=0), dict(n_chains=65),
+        dict(precision=3), dict(moments_mode=2), dict(trace_n_vox=5),
+    ]
+    for c in cases:
+        kw = dict(iterations=10, burnin=0, thin=1, n_chains=1, seed=1)
+        kw.update(c)
+        opts = gac.make_opts(**kw)
+        with pytest.raises(gac.GacError) as e:
+            gac.gac_mcmc_run(mid, y, 4, None, 0.01, None, opts, out)
+        assert e.value.status == 1, c
+    opts = gac.make_opts(10, 0, 1, 1, 1)
+    with pytest.raises(gac.GacError):  # no sigma and no scalar
+        gac.gac_mcmc_run(mid, y, 4, None, 0.0, None, opts, out)
+    with pytest.raises(gac.GacError):  # counter word overflow
+        gac.gac_mcmc_run(mid, y, 4, None, 0.01, None, gac.make_opts(10, 0, 1, 1, 1, voxel_base=(1 << 32) - 2), out)
+    with pytest.raises(gac.GacError) as e:
+        gac.gac_mcmc_run(999, y, 4, None, 0.01, None, opts, out)
+    assert e.value.status == 2
+    with pytest.raises(gac.GacError):  # trace requested without a buffer
+        gac.gac_mcmc_run(mid, y, 4, None, 0.01, None, gac.make_opts(10, 0, 1, 1, 1, trace_n_vox=1), out)
+    # zero voxels: nothing to do, no GPU needed
+    gac.gac_mcmc_run(mid, np.zeros((0, 12), np.float32), 0, None, 0.01, None, opts, out)
+
+
+def test_result_sizes(gac):
+    mid = gac.gac_model_register(**MONO)
+    opts = gac.make_opts(2000, 500, 5, 3, 1, trace_n_vox=2)
+    b = gac.gac_result_sizes(mid, 100, opts)
+    assert b == dict(mean=2 * 100 * 8, std=2 * 100 * 8, samples=300 * 3 * 2 * 100 * 4,
+                     accept_rate=3 * 100 * 4, nonfinite=3 * 100 * 4, trace=2 * 3 * 2000 * 216)
+    b0 = gac.gac_result_sizes(mid, 100, gac.make_opts(400, 500, 5, 1, 1))
+    assert b0["samples"] == 0

@@ -1,0 +1,111 @@
+"""Forward models and log-likelihood on the device against the FP64 oracle.
+
+Tolerances: forward-model relative error <= 1e-5, measured norm-wise per
+voxel (||s_gpu - s_ref|| / ||s_ref||, because elementwise relative error is
+undefined where a complex component crosses zero); log-likelihood absolute
+error <= 1e-3 at posterior-typical parameters (the truth and one-sigma
+neighbourhoods of it, where |L| ~ M/2).  The FP64 variant is held to 1e-12
+and 1e-8.
+"""
+import numpy as np
+import pytest
+
+from conftest import make_voxels
+from paper_2511_22094_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+CASES = [W.MONOEXP_4K, W.MWI3_1M, W.SMT_1P5M]
+
+
+def _edge_thetas(w, rng, n):
+    """Random points in the prior box plus its corners and faces."""
+    lb, ub = np.array(w.lb), np.array(w.ub)
+    th = rng.uniform(lb, ub, size=(n, w.n_par))
+    P = w.n_par
+    corners = np.array([[lb[p] if (i >> p) & 1 else ub[p] for p in range(P)] for i in range(min(2 ** P, 512))])
+    faces = np.repeat(th[:P * 4], 1, axis=0)
+    for i in range(faces.shape[0]):
+        faces[i, i % P] = lb[i % P] if (i // P) % 2 == 0 else ub[i % P]
+    return np.concatenate([th, corners, faces])
+
+
+@pytest.mark.parametrize("w", CASES, ids=[w.name for w in CASES])
+def test_forward_parity(gac, orc, w):
+    rng = np.random.default_rng(w.kind)
+    mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
+    th = np.concatenate([W.truths(w, 0, 60_000), _edge_thetas(w, rng, 40_000)])
+    ref = orc.forward(w.kind, w.acq, th)
+    norm = np.linalg.norm(ref, axis=1)
+    keep = norm > 1e-6 * norm.max()  # an all-zero signal (every amplitude 0) has no relative error
+    for prec, tol in ((gac.PREC_MIXED, 1e-5), (gac.PREC_FP32, 1e-5), (gac.PREC_FP64, 1e-12)):
+        s = gac.forward_host(mid, th, prec)
+        rel = np.linalg.norm(s - ref, axis=1)[keep] / norm[keep]
+        assert rel.max() <= tol, (w.name, prec, rel.max(), np.median(rel))
+        assert np.abs(s[~keep] - ref[~keep]).max(initial=0) <= 1e-6
+
+
+def test_forward_uneven_acquisitions(gac, orc):
+    """Unevenly spaced echoes take the direct (non-recurrent) evaluation."""
+    te = np.array([1.7, 2.9, 5.5, 6.0, 9.1, 14.0, 20.3, 26.1, 33.3, 40.0])
+    w = W.MWI3_1M
+    mid = gac.gac_model_register(w.kind, te, w.lb, w.ub, w.step)
+    th = W.truths(w, 0, 20_000)
+    ref = orc.forward(w.kind, te, th)
+    s = gac.forward_host(mid, th)
+    rel = np.linalg.norm(s - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert rel.max() <= 1e-5
+    mono = gac.gac_model_register(1, te, [0.5, 10], [1.5, 80], [0.01, 1])
+    th2 = W.truths(W.MONOEXP_4K, 0, 20_000)
+    ref2 = orc.forward(1, te, th2)
+    s2 = gac.forward_host(mono, th2)
+    assert (np.linalg.norm(s2 - ref2, axis=1) / np.linalg.norm(ref2, axis=1)).max() <= 1e-5
+
+
+def test_smt_g_both_branches(gac, orc):
+    """x = b (De_par - De_perp) spans the erfi (x < 0), series/erf switch and
+    erf branches; b = 0 gives S = 1 exactly in the FP64 path."""
+    w = W.SMT_1P5M
+    b = np.array([0.0, 1e-6, 0.1, 1.0, 2.5, 5.0, 7.5, 10.0])
+    mid = gac.gac_model_register(w.kind, b, w.lb, w.ub, w.step)
+    rng = np.random.default_rng(3)
+    n = 50_000
+    th = np.stack([rng.uniform(0, 1, n), rng.uniform(1, 3, n), rng.uniform(0.5, 3, n),
+                   rng.uniform(0, 1.5, n)], 1)
+    th[: n // 2, 3] = np.maximum(th[: n // 2, 3], th[: n // 2, 2])  # De_par <= De_perp
+    ref = orc.forward(w.kind, b, th)
+    for prec, tol in ((gac.PREC_MIXED, 1e-5), (gac.PREC_FP64, 1e-12)):
+        s = gac.forward_host(mid, th, prec)
+        rel = np.linalg.norm(s - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert rel.max() <= tol, (prec, rel.max())
+        assert np.abs(s[:, 0] - 1.0).max() <= (1e-6 if prec != gac.PREC_FP64 else 1e-15)
+
+
+@pytest.mark.parametrize("w", CASES + [W.MWI3_1M.with_(name="mwi3_snr300", snr=300.0),
+                                       W.MWI3_1M.with_(name="mwi3_snr50", snr=50.0)],
+                         ids=lambda w: w.name)
+def test_loglik_parity_at_posterior_typical_theta(gac, orc, w):
+    mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
+    n = 40_000
+    th, sig, y = make_voxels(orc, w, 0, n)
+    # the truth, and points about one posterior SD away along each axis
+    rng = np.random.default_rng(7)
+    jitter = np.clip(th + 0.3 * np.array(w.step) * rng.standard_normal(th.shape), w.lb, w.ub)
+    th_all = np.concatenate([th, jitter])
+    # parameters rounded to float first, as the FP32 state holds them
+    th_all = th_all.astype(np.float32).astype(np.float64)
+    y_all = np.concatenate([y, y])
+    s_all = np.concatenate([sig, sig])
+    ref = orc.loglik(w.kind, w.acq, th_all, y_all, s_all)
+    res = {}
+    for prec, tol in ((gac.PREC_MIXED, 1e-3), (gac.PREC_FP32, 2e-3), (gac.PREC_FP64, 1e-8)):
+        L = gac.loglik_host(mid, th_all, y_all, s_all, prec)
+        err = np.abs(L - ref)
+        typical = np.abs(ref) < 4 * w.n_meas  # posterior-typical: |L| of order M/2
+        res[prec] = (err[typical].max(), np.quantile(err[typical], 0.99))
+        assert typical.mean() > 0.5
+        assert err[typical].max() <= tol, (w.name, prec, res[prec])
+        # anywhere: relative error of a few FP32 ulps of |L|
+        if prec != gac.PREC_FP64:
+            assert (err / np.maximum(np.abs(ref), 1.0)).max() <= 5e-5
+    print(w.name, {k: tuple(f"{x:.2e}" for x in v) for k, v in res.items()})

@@ -1,0 +1,232 @@
+"""The MH sampler on the device against the FP64 oracle (mcmc.m, Sec. 2.2.2).
+
+Lock-step checks (every recorded step of traced chains):
+  - the acceptance word is the oracle's word, bit for bit;
+  - the proposal is clamp(theta + step z) with the oracle's normals, to the
+    FP32 error of Box-Muller;
+  - each state follows from the previous record's decision, exactly;
+  - the decision equals the oracle's FP64 decision recomputed from the
+    recorded theta and theta' in >= 99.9% of steps (>= 99.99% for FP64);
+  - the kernel's L' equals the oracle's within 1e-3 after burn-in.
+Free-running checks (same seed): posterior means within 0.05 posterior SD;
+bit-exact determinism, tiling and split invariance, host/device pointers.
+"""
+import numpy as np
+import pytest
+import torch
+
+from conftest import make_voxels
+from paper_2511_22094_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _register(gac, w, acq=None):
+    return gac.gac_model_register(w.kind, w.acq if acq is None else acq, w.lb, w.ub, w.step)
+
+
+def _lockstep_check(gac, orc, w, tr, y, sig, seed, prec, n_tr, C, I, B, min_agree):
+    P = w.n_par
+    lb, ub, step = map(np.array, (w.lb, w.ub, w.step))
+    nw = orc.n_words(P)
+    agree = total = 0
+    dL = []
+    for v in range(n_tr):
+        for c in range(C):
+            rec = tr[v, c]
+            th, pr = rec["theta"][:, :P], rec["prop"][:, :P]
+            # words: bit-exact
+            t = np.arange(1, I + 1, dtype=np.uint32)
+            words = orc.words_many(seed, t, np.full(I, v, np.uint32), np.full(I, c, np.uint32), nw)
+            np.testing.assert_array_equal(rec["w_acc"], words[:, nw - 1])
+            # proposal from the oracle's normals
+            z = orc.normals_many(words, P)
+            want = np.clip(th + step * z, lb, ub)
+            tol = 2.6e-4 * step + 3e-7 * np.abs(want) if prec != gac.PREC_FP64 else 1e-12 * (1 + np.abs(want))
+            assert (np.abs(pr - want) <= tol).all(), (v, c, np.abs(pr - want).max())
+            # chain continuity
+            acc = rec["accepted"] != 0
+            nxt = np.where(acc[:-1, None], pr[:-1], th[:-1])
+            np.testing.assert_array_equal(th[1:], nxt)
+            # decisions
+            L, Lp, dec = orc.lockstep(w.kind, w.acq, w.lb, w.ub, w.step, y[v], float(sig[v]), th, pr,
+                                      rec["w_acc"])
+            agree += int((dec == acc).sum())
+            total += I
+            post = np.arange(I) >= B
+            dL.append(np.abs(rec["Lp"] - Lp)[post])
+    dL = np.concatenate(dL)
+    frac = agree / total
+    print(f"{w.name} prec={prec}: agreement {agree}/{total} = {frac:.6f}; "
+          f"|dL'| post-burn-in max {dL.max():.2e} p99 {np.quantile(dL, 0.99):.2e}")
+    assert frac >= min_agree
+    return frac, dL
+
+
+LOCKSTEP = [
+    (W.MONOEXP_4K, 4096, 64, 0, 0.999),
+    (W.MWI3_1M, 256, 8, 0, 0.999),
+    (W.SMT_1P5M, 256, 8, 0, 0.999),
+    (W.MWI3_1M, 64, 4, 2, 0.9999),
+    (W.MONOEXP_4K, 256, 32, 2, 0.9999),
+    (W.MWI3_1M.with_(name="mwi3_fp32"), 64, 4, 1, 0.99),
+]
+
+
+@pytest.mark.parametrize("w,n,n_tr,prec,min_agree", LOCKSTEP,
+                         ids=[f"{c[0].name}-p{c[3]}" for c in LOCKSTEP])
+def test_lockstep(gac, orc, w, n, n_tr, prec, min_agree):
+    mid = _register(gac, w)
+    th, sig, y = make_voxels(orc, w, 0, n)
+    C, I, B, T = w.n_chains, w.iterations, w.burnin, w.thin
+    out = gac.run_host(mid, y, sig, iterations=I, burnin=B, thin=T, n_chains=C, seed=w.mcmc_seed,
+                       precision=prec, trace_n_vox=n_tr)
+    tr = out["trace"]
+    frac, dL = _lockstep_check(gac, orc, w, tr, y, sig, w.mcmc_seed, prec, n_tr, C, I, B, min_agree)
+    tol_L = 1e-3 if prec == gac.PREC_MIXED else (2e-3 if prec == gac.PREC_FP32 else 1e-8)
+    assert np.quantile(dL, 0.999) <= tol_L
+    # the initial state is the uniform-prior draw of counter iteration 0xFFFFFFFF
+    lb, ub = np.array(w.lb), np.array(w.ub)
+    for v in range(min(n_tr, 4)):
+        wi = orc.words(w.mcmc_seed, 0xFFFFFFFF, v, 0, w.n_par)
+        init = lb + (ub - lb) * np.array([orc.u01(x) for x in wi])
+        assert np.allclose(tr[v, 0, 0]["theta"][:w.n_par], init, rtol=2e-7, atol=1e-6 * (ub - lb).max())
+
+
+def _posterior_gap(gpu, ref):
+    sd = ref["std"]
+    ok = sd > 0
+    return np.abs(gpu["mean"] - ref["mean"])[ok] / sd[ok]
+
+
+FREE = [(W.MONOEXP_4K, 4096), (W.MWI3_1M, 512), (W.SMT_1P5M, 512)]
+
+
+@pytest.mark.parametrize("w,n", FREE, ids=[c[0].name for c in FREE])
+def test_free_running_posterior_parity(gac, orc, w, n):
+    mid = _register(gac, w)
+    th, sig, y = make_voxels(orc, w, 0, n)
+    kw = dict(iterations=w.iterations, burnin=w.burnin, thin=w.thin, n_chains=w.n_chains,
+              seed=w.mcmc_seed)
+    g = gac.run_host(mid, y, sig, **kw)
+    r = orc.mcmc_run(w.kind, w.acq, w.lb, w.ub, w.step, y, sig, **kw)
+    gap = _posterior_gap(g, r)
+    same = np.all(g["samples"] == r["samples"].astype(np.float32), axis=(0, 1))  # [P][N]
+    print(f"{w.name}: |dmean|/SD median {np.median(gap):.2e} p99 {np.quantile(gap, 0.99):.2e} "
+          f"max {gap.max():.2e}; within 0.05 SD: {(gap <= 0.05).mean():.4f}; "
+          f"accept rate gpu {g['accept_rate'].mean():.4f} oracle {r['accept_rate'].mean():.4f}")
+    assert (gap <= 0.05).mean() >= 0.99
+    assert abs(g["accept_rate"].mean() - r["accept_rate"].mean()) < 0.01
+    assert np.all(g["nonfinite"] == 0)
+
+
+def test_moments_match_stored_samples(gac, orc):
+    w = W.MWI3_1M
+    mid = _register(gac, w)
+    th, sig, y = make_voxels(orc, w, 0, 300)
+    for prec, tol in ((gac.PREC_MIXED, 1e-9), (gac.PREC_FP64, 1e-9), (gac.PREC_FP32, 2e-4)):
+        g = gac.run_host(mid, y, sig, iterations=1200, burnin=200, thin=10, n_chains=4, seed=3,
+                         precision=prec)
+        s = g["samples"].astype(np.float64)  # [S][C][P][N]
+        pooled = s.transpose(2, 3, 0, 1).reshape(w.n_par, 300, -1)
+        np.testing.assert_allclose(g["mean"], pooled.mean(-1), rtol=tol, atol=tol * 1e-3)
+        np.testing.assert_allclose(g["std"], pooled.std(-1, ddof=1), rtol=max(tol, 1e-8) * 100,
+                                   atol=1e-9)
+
+
+def test_all_postburnin_moments(gac, orc):
+    w = W.MONOEXP_4K
+    mid = _register(gac, w)
+    th, sig, y = make_voxels(orc, w, 0, 256)
+    kw = dict(iterations=800, burnin=200, thin=50, n_chains=2, seed=4, moments_mode=1)
+    g = gac.run_host(mid, y, sig, precision=gac.PREC_FP64, **kw)
+    r = orc.mcmc_run(w.kind, w.acq, w.lb, w.ub, w.step, y, sig, **kw)
+    gap = _posterior_gap(g, r)
+    assert (gap <= 1e-6).mean() >= 0.99
+
+
+def test_determinism_tiling_split_and_pointer_kinds(gac, orc):
+    w = W.MWI3_1M.with_(n_chains=3)
+    mid = _register(gac, w)
+    n = 777  # ragged against 85 voxels per block
+    th, sig, y = make_voxels(orc, w, 0, n)
+    kw = dict(iterations=300, burnin=100, thin=20, n_chains=3, seed=99)
+    a = gac.run_host(mid, y, sig, **kw)
+    b = gac.run_host(mid, y, sig, **kw)
+    for k in ("mean", "std", "samples", "accept_rate", "nonfinite"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    # split with voxel_base reproduces the whole run
+    k0 = 301
+    p1 = gac.run_host(mid, y[:k0], sig[:k0], **kw)
+    p2 = gac.run_host(mid, y[k0:], sig[k0:], voxel_base=k0, **kw)
+    np.testing.assert_array_equal(np.concatenate([p1["mean"], p2["mean"]], 1), a["mean"])
+    np.testing.assert_array_equal(np.concatenate([p1["samples"], p2["samples"]], 3), a["samples"])
+    # a single voxel
+    one = gac.run_host(mid, y[5:6], sig[5:6], voxel_base=5, **kw)
+    np.testing.assert_array_equal(one["mean"][:, 0], a["mean"][:, 5])
+    # device buffers (and an unaligned data pointer) give the same bits
+    dev = torch.device("cuda:0")
+    P, S, C = w.n_par, gac.n_samples(300, 100, 20), 3
+    yd = torch.zeros(n * w.n_meas + 1, dtype=torch.float32, device=dev)
+    yd[1:] = torch.from_numpy(y.ravel()).to(dev)
+    out = dict(mean=torch.empty((P, n), dtype=torch.float64, device=dev),
+               samples=torch.empty((S, C, P, n), dtype=torch.float32, device=dev))
+    opts = gac.make_opts(300, 100, 20, 3, 99)
+    gac.gac_mcmc_run(mid, yd.data_ptr() + 4, n, torch.from_numpy(sig).to(dev), 0.0, None, opts, out,
+                     torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out["mean"].cpu().numpy(), a["mean"])
+    np.testing.assert_array_equal(out["samples"].cpu().numpy(), a["samples"])
+
+
+def test_degenerate_options(gac, orc):
+    w = W.MONOEXP_4K
+    mid = _register(gac, w)
+    th, sig, y = make_voxels(orc, w, 0, 40)
+    g = gac.run_host(mid, y, sig, iterations=100, burnin=100, thin=5, n_chains=2, seed=1)
+    assert np.isnan(g["mean"]).all() and np.isnan(g["std"]).all()
+    g = gac.run_host(mid, y, sig, iterations=105, burnin=100, thin=5, n_chains=1, seed=1)
+    assert (g["std"] == 0).all()
+    np.testing.assert_array_equal(g["mean"], g["samples"][0, 0].astype(np.float64))
+    g = gac.run_host(mid, y, sig, iterations=0, burnin=0, thin=1, n_chains=1, seed=1)
+    assert (g["accept_rate"] == 0).all() and np.isnan(g["mean"]).all()
+    # a parameter fixed by lb = ub
+    fixed = gac.gac_model_register(w.kind, w.acq, [1.0, 10.0], [1.0, 80.0], [0.3, 1.0])
+    g = gac.run_host(fixed, y, sig, iterations=200, burnin=0, thin=1, n_chains=1, seed=1)
+    assert (g["samples"][:, :, 0, :] == 1.0).all() and (g["std"][0] == 0).all()
+    # scalar sigma equals a constant per-voxel sigma
+    a = gac.run_host(mid, y, None, sigma_scalar=0.01, iterations=200, burnin=50, thin=5, n_chains=1, seed=2)
+    b = gac.run_host(mid, y, np.full(40, 0.01, np.float32), iterations=200, burnin=50, thin=5,
+                     n_chains=1, seed=2)
+    np.testing.assert_array_equal(a["mean"], b["mean"])
+    # x0 given: the chain starts there (clamped into the bounds)
+    x0 = np.tile(np.array([[2.0, 30.0]], np.float32), (40, 1, 1))
+    g = gac.run_host(mid, y, sig, iterations=10, burnin=0, thin=1, n_chains=1, seed=2, x0=x0,
+                     trace_n_vox=3)
+    assert np.allclose(g["trace"][0, 0, 0]["theta"][:2], [1.5, 30.0])
+
+
+def test_linear_gaussian_posterior_on_device(gac, orc):
+    """The GPU sampler's stationary distribution is the exact posterior of
+    the linear-Gaussian test model (checked across many identical voxels)."""
+    t = np.linspace(0.0, 1.0, 12)
+    X = np.stack([np.ones(12), t], 1)
+    sig = 0.1
+    y0 = (X @ np.array([0.5, -1.0]) + sig * np.random.default_rng(11).standard_normal(12)).astype(np.float32)
+    XtX = X.T @ X
+    mu = np.linalg.solve(XtX, X.T @ y0.astype(np.float64))
+    cov = sig ** 2 * np.linalg.inv(XtX)
+    sd = np.sqrt(np.diag(cov))
+    mid = gac.gac_model_register(100, t, mu - 100 * sd, mu + 100 * sd, 1.2 * sd)
+    n = 4096
+    y = np.tile(y0, (n, 1))
+    x0 = np.tile(mu.astype(np.float32), (n, 1, 1))
+    g = gac.run_host(mid, y, np.full(n, sig, np.float32), iterations=3000, burnin=500, thin=25,
+                     n_chains=1, seed=5, x0=x0)
+    s = g["samples"][:, 0].astype(np.float64)  # [S][P][N], voxels independent
+    m = s.mean(axis=(0, 2))
+    # voxel means are independent; their spread gives the MC error
+    se = s.mean(axis=0).std(axis=1) / np.sqrt(n)
+    assert np.all(np.abs(m - mu) < 5 * se), (m, mu, se)
+    var = np.array([np.mean((s[:, p] - mu[p]) ** 2) for p in range(2)])
+    assert np.allclose(var, np.diag(cov), rtol=0.03)
