@@ -39,9 +39,9 @@ UNIT = "chain-iter/s"
 # FP32 = add/mul/fma/min/max; INT = Philox (10 rounds x (2 wide multiplies,
 # 2 three-input xors, 2 key adds) per call).  See DESIGN.md, "Roofline".
 OPS = {
-    "mwi3_1m": dict(mufu=240, fp32=734, int=180),
-    "smt_1p5m": dict(mufu=78, fp32=380, int=120),
-    "monoexp_4k": dict(mufu=19, fp32=70, int=60),
+    "mwi3_1m": dict(mufu=240, fp32=520, int=180),
+    "smt_1p5m": dict(mufu=51, fp32=103, int=120),
+    "monoexp_4k": dict(mufu=17, fp32=65, int=60),
 }
 MUFU_PER_CLK_SM = 16
 FP32_PER_CLK_SM = 128
@@ -306,6 +306,116 @@ def run_ours(args, w):
         pg.destroy_process_group()
 
 
+def run_serving(args):
+    """Serving trace: 200 jobs with Poisson arrivals (mean gap 0.2 s), mixed
+    models, 10k-2M voxels, 1-4 chains, 1k-5k iterations, under a 120 GB HBM
+    budget.  Continuous batching (gac_server_*) against the plain form: the
+    same jobs run one gac_mcmc_run after another in arrival order.  Inputs
+    start in pinned host memory and results end there in both forms."""
+    import torch
+    from paper_2511_22094_gb300 import build
+    build.build()
+    from paper_2511_22094_gb300 import gac
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda:0")
+    trace = W.serving_trace(n_jobs=args.serving_jobs)
+    mids = {}
+    jobs = []
+    t_prep = time.perf_counter()
+    for tj in trace:
+        w = tj.workload
+        key = w.kind
+        if key not in mids:
+            mids[key] = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
+        mid = mids[key]
+        th = torch.from_numpy(W.truths(w, tj.first_voxel, w.n_vox)).to(dev)
+        sig = torch.from_numpy(W.sigma(w, th.cpu().numpy())).to(dev)
+        s = torch.empty((w.n_vox, w.n_meas), dtype=torch.float64, device=dev)
+        gac.gac_forward(mid, th, w.n_vox, gac.PREC_FP64, s)
+        g = torch.Generator(device=dev).manual_seed(1_000_003 * (tj.index + 1))
+        z = torch.randn((w.n_vox, w.n_meas), dtype=torch.float64, device=dev, generator=g)
+        y = (s + sig.double()[:, None] * z).float()
+        hy = torch.empty(y.shape, dtype=torch.float32).pin_memory()
+        hy.copy_(y)
+        hs = torch.empty(sig.shape, dtype=torch.float32).pin_memory()
+        hs.copy_(sig)
+        opts = gac.make_opts(w.iterations, w.burnin, w.thin, w.n_chains, w.mcmc_seed)
+        jobs.append(dict(tj=tj, mid=mid, y=hy, sig=hs, opts=opts, ci=w.chain_iterations,
+                         P=w.n_par, N=w.n_vox, C=w.n_chains))
+        del th, sig, s, z, y
+    torch.cuda.synchronize()
+    t_prep = time.perf_counter() - t_prep
+
+    def outs(j):
+        return dict(mean=np.empty((j["P"], j["N"])), std=np.empty((j["P"], j["N"])),
+                    accept_rate=np.empty((j["C"], j["N"]), np.float32),
+                    nonfinite=np.empty((j["C"], j["N"]), np.int32))
+
+    def summarize(lat, makespan):
+        lat = np.asarray(lat)
+        ci = sum(j["ci"] for j in jobs)
+        return {"throughput": ci / makespan, "unit": UNIT, "makespan_s": makespan,
+                "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "mean_s": float(lat.mean())}
+
+    def serve_pass(compress):
+        srv = gac.gac_server_create(120 << 30, 64)
+        ids, lat = [], [None] * len(jobs)
+        done_t = [0.0] * len(jobs)
+        t0 = time.perf_counter()
+
+        def waiter():
+            for i, jid in enumerate(ids_q):
+                while jid[0] is None:
+                    time.sleep(0.0005)
+                lat[i] = gac.gac_server_wait(srv, jid[0], 3600.0, outs(jobs[i]))
+                done_t[i] = time.perf_counter() - t0
+        ids_q = [[None] for _ in jobs]
+        th = threading.Thread(target=waiter)
+        th.start()
+        for i, j in enumerate(jobs):
+            at = j["tj"].arrival_s * compress
+            dt = t0 + at - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            ids_q[i][0] = gac.gac_server_submit(srv, j["mid"], j["y"], j["N"], j["sig"], 0.0, j["opts"])
+        th.join()
+        st = gac.gac_server_get_stats(srv)
+        gac.gac_server_destroy(srv)
+        r = summarize(lat, max(done_t))
+        r["rounds"] = st["rounds"]
+        return r
+
+    def sequential_pass(compress):
+        lat, t0 = [], time.perf_counter()
+        end = 0.0
+        for j in jobs:
+            at = j["tj"].arrival_s * compress
+            dt = t0 + at - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            gac.gac_mcmc_run(j["mid"], j["y"], j["N"], j["sig"], 0.0, None, j["opts"], outs(j))
+            end = time.perf_counter() - t0
+            lat.append(end - at)
+        return summarize(lat, end)
+
+    # warm up both paths on the first few jobs
+    for j in jobs[:3]:
+        gac.gac_mcmc_run(j["mid"], j["y"], j["N"], j["sig"], 0.0, None, j["opts"], outs(j))
+    res = {"continuous_batching": serve_pass(1.0), "sequential": sequential_pass(1.0)}
+    if args.serving_saturated:
+        res["continuous_batching_all_at_t0"] = serve_pass(0.0)
+        res["sequential_all_at_t0"] = sequential_pass(0.0)
+    line = {"metric": "serving trace: throughput and job latency", "unit": UNIT,
+            "trace": {"jobs": len(jobs), "arrivals": "Poisson, mean gap 0.2 s",
+                      "span_s": trace[-1].arrival_s,
+                      "chain_iterations": sum(j["ci"] for j in jobs),
+                      "budget_bytes": 120 << 30, "max_resident": 64, "prep_s": t_prep},
+            **res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -315,7 +425,13 @@ def main():
     ap.add_argument("--workload", default="mwi3_1m", choices=sorted(W.WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", action="store_true", help="run the serving trace instead")
+    ap.add_argument("--serving-jobs", type=int, default=200)
+    ap.add_argument("--serving-saturated", action="store_true")
     args = ap.parse_args()
+    if args.serving:
+        run_serving(args)
+        return
     w = W.WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, w)

@@ -187,6 +187,69 @@ gac_status gac_normals(uint64_t seed, const uint32_t *t, const uint32_t *v, cons
                        int64_t n, int n_par, int precision, double *z, uint32_t *w_acc,
                        void *stream);
 
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of fit jobs on one GPU.
+ *
+ * A server owns a scheduler thread.  Submitted jobs wait in arrival order
+ * until their device memory fits under the HBM budget (and a resident slot is
+ * free); admitted jobs are uploaded on a copy stream while others compute.
+ * The scheduler then runs rounds: each round is one launch of a persistent
+ * kernel whose blocks claim work items -- (job, tile of voxels, slice of
+ * iterations) -- from every resident job, whatever its model, so small and
+ * large jobs share the GPU.  Chain state (theta, L, counters, Welford
+ * accumulators) stays in HBM between slices.  A job that finishes is copied
+ * back while the next round runs, and its memory is returned to the budget.
+ * Results equal those of gac_mcmc_run with the same inputs: the random
+ * numbers depend only on (seed, t, voxel, chain) and slices resume exactly.
+ * Serving runs the MIXED precision path; trace_n_vox must be 0.
+ * ---------------------------------------------------------------------- */
+typedef struct gac_server gac_server;
+
+/* hbm_budget_bytes: device memory the server may hold for jobs (inputs,
+ * chain state, outputs); max_resident_jobs: jobs on the device at once
+ * (1..1024).  Does not touch the GPU until the first job is admitted. */
+gac_status gac_server_create(size_t hbm_budget_bytes, int max_resident_jobs, gac_server **out);
+
+/* Bytes of device memory a job would hold while resident. */
+gac_status gac_server_job_bytes(int model_id, int64_t n_vox, const gac_mcmc_opts *opts,
+                                int keep_samples, int has_sigma, size_t *bytes);
+
+/* Queues a job: copies data [n_vox][n_meas] and sigma [n_vox] (or uses
+ * sigma_scalar) from host or device memory and returns at once with *job_id.
+ * keep_samples: also return the thinned samples.  Errors: INVALID_ARG
+ * (including precision != MIXED or trace_n_vox != 0), UNKNOWN_MODEL, BUDGET
+ * (the job alone exceeds the whole budget), OOM (host staging). */
+gac_status gac_server_submit(gac_server *srv, int model_id, const void *data, int64_t n_vox,
+                             const float *sigma, float sigma_scalar, const gac_mcmc_opts *opts,
+                             int keep_samples, uint64_t *job_id);
+
+/* Non-blocking.  *done = 0 while the job is queued or running.  When done,
+ * copies the results into `out` (any pointer may be NULL; host or device),
+ * sets *latency_s to the time from submit to completion, forgets the job and
+ * returns GAC_OK -- or the job's error status (CANCELLED, CUDA, OOM).
+ * Errors: UNKNOWN_JOB. */
+gac_status gac_server_poll(gac_server *srv, uint64_t job_id, int *done, gac_result *out,
+                           double *latency_s);
+
+/* Blocks until the job is done or timeout_s passes (GAC_ERR_TIMEOUT); then
+ * behaves as gac_server_poll. */
+gac_status gac_server_wait(gac_server *srv, uint64_t job_id, double timeout_s, gac_result *out,
+                           double *latency_s);
+
+/* Cancels a queued or running job; its memory is released at the next round
+ * boundary.  Polling it afterwards returns GAC_ERR_CANCELLED. */
+gac_status gac_server_cancel(gac_server *srv, uint64_t job_id);
+
+/* Counters: jobs queued, resident, finished; bytes in use; rounds run. */
+typedef struct {
+    int64_t queued, resident, finished, rounds;
+    size_t bytes_in_use, budget;
+} gac_server_stats;
+gac_status gac_server_get_stats(gac_server *srv, gac_server_stats *st);
+
+/* Stops the scheduler (after the current round), frees every job. */
+gac_status gac_server_destroy(gac_server *srv);
+
 /* Message for the last non-OK status on the calling thread ("" if none). */
 const char *gac_last_error(void);
 

@@ -2,6 +2,7 @@
 // host/device pointer handling and the launch of the persistent MH kernel.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -129,11 +130,8 @@ int row_stride_for(int kind, int M) {
 }
 
 size_t smem_bytes_for(int kind, int prec, int C, int M) {
-    const int P = model_n_par(kind);
     const size_t w = (prec == GAC_PREC_FP32) ? sizeof(float) : sizeof(double);
-    const int VB = kBlock / C;
-    return 2 * static_cast<size_t>(P) * kBlock * w +
-           static_cast<size_t>(VB) * row_stride_for(kind, M) * sizeof(float);
+    return tile_smem_bytes(model_n_par(kind), w, kBlock / C, row_stride_for(kind, M), true);
 }
 
 const void *mh_kernel_ptr(int kind, int prec, bool trace) {
@@ -167,6 +165,10 @@ gac_status plan_launch(const ModelConst &mc, int prec, bool trace, int C, int64_
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    // prefer the largest shared-memory carveout: the tile and Welford
+    // accumulators, not L1, decide how many blocks fit
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(carveout)");
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, smem);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
@@ -228,6 +230,13 @@ gac_status gac_model_register(const gac_model_desc *d, int *model_id) {
     if (d->kind == GAC_MODEL_MWI3) {
         for (int j = 3; j < 6; ++j)
             if (d->lb[j] <= 0) return fail(GAC_ERR_INVALID_ARG, "T2* lower bounds must be > 0");
+        // phase arguments phi0 - 2 pi df t must stay in the range of sincos_cw
+        double tmax = 0, dfmax = 0;
+        for (int k = 0; k < d->n_acq; ++k) tmax = std::max(tmax, std::fabs(d->acq[k]));
+        for (int j = 6; j < 8; ++j) dfmax = std::max({dfmax, std::fabs(d->lb[j]), std::fabs(d->ub[j])});
+        const double amax = std::max(std::fabs(d->lb[8]), std::fabs(d->ub[8])) + kTwoPiMilliD * dfmax * tmax * (kAnchor + 1);
+        if (amax > kSinCosMaxArg)
+            return fail(GAC_ERR_INVALID_ARG, "phase range %.0f rad exceeds %.0f", amax, static_cast<double>(kSinCosMaxArg));
     }
     if (d->kind == GAC_MODEL_SMT) {
         for (int k = 0; k < d->n_acq; ++k) {

@@ -1,23 +1,32 @@
-// Persistent Metropolis-Hastings kernel (mcmc.m hot path, Sec. 2.2.2).
+// Persistent Metropolis-Hastings kernels (mcmc.m hot path, Sec. 2.2.2).
 //
 // One thread owns one (voxel, chain): a block holds VB = floor(256 / C)
-// voxels x C chains (chain fastest).  Per tile of voxels the block
+// voxels x C chains (chain fastest).  For a tile of voxels and an iteration
+// range (t_begin, t_end] the block
 //   a1  stages the voxels' measurements in shared memory (coalesced 16-byte
 //       global loads, odd row stride so that the lanes of a warp hit
 //       distinct banks), then every thread
-//   a2  draws or loads its initial state and evaluates its likelihood,
+//   a2  draws or loads its initial state and evaluates its likelihood
+//       (or, when resuming a slice, reloads theta, L and its counters),
 //   a3  per iteration draws Philox words for (t, voxel, chain),
 //   a4  proposes theta' = clamp(theta + step * z, lb, ub),
 //   a5  evaluates the forward model at every acquisition and
 //   a6  accumulates the Gaussian log-likelihood in registers,
 //   a7  accepts iff log u < L' - L,
 //   a8  on the thinning grid stores the state (coalesced over voxels) and
-//       updates Welford accumulators in shared memory,
-// and at the end
+//       updates Welford accumulators,
+// and after the last iteration
 //   a9  merges the C chains' accumulators of each voxel in chain order
 //       (Chan et al.'s pairwise update) and writes mean, SD, acceptance
 //       rate and the non-finite count.
 // Nothing but thinned samples touches HBM inside the iteration loop.
+//
+// Two drivers share this tile routine: mh_kernel runs one job in one launch
+// (t in (0, I], Welford accumulators in shared memory, nothing saved), and
+// the serving kernel runs slices of many jobs (chain state and Welford
+// accumulators in HBM between slices; resuming from them reproduces an
+// uninterrupted run, because the random numbers depend only on (seed, t,
+// voxel, chain)).
 //
 // Precision variants (template PREC):
 //   MIXED  FP32 model and residuals, Kahan-compensated sum, acceptance with
@@ -36,6 +45,10 @@
 namespace gac {
 
 constexpr int kBlock = 256;
+// Blocks per SM the FP32/MIXED kernels are compiled for (register cap).
+#ifndef GAC_MH_MIN_BLOCKS
+#define GAC_MH_MIN_BLOCKS 3
+#endif
 
 struct RunArgs {
     const float *data;   // [N][M]
@@ -58,6 +71,17 @@ struct RunArgs {
     int row_stride;      // shared-memory floats per voxel row (padded)
     int data_vec4;       // rows are whole float4s and data is 16-byte aligned
     int64_t n_tiles;
+};
+
+// Chain state kept in HBM between slices, structure of arrays over the
+// N*C chains (index v*C + c, so a warp's accesses are contiguous).
+struct SliceState {
+    void *theta;     // [P][N*C] of R
+    void *L;         // [N*C] of R
+    int32_t *n_acc;  // [N*C]
+    int32_t *n_bad;  // [N*C]
+    void *wf_mean;   // [P][N*C] of W
+    void *wf_m2;     // [P][N*C] of W
 };
 
 template <int PREC>
@@ -115,18 +139,27 @@ __device__ __forceinline__ bool accept_step(typename PrecTraits<PREC>::R Lp,
     }
 }
 
-template <int KIND, int PREC, bool TRACE>
-__global__ void __launch_bounds__(kBlock) mh_kernel(const ModelConst mc, const RunArgs ra) {
+// Shared-memory bytes of one block: Welford accumulators (one-launch driver
+// only) + the measurement tile.
+__host__ __device__ inline size_t tile_smem_bytes(int P, size_t w_bytes, int VB, int row_stride,
+                                                  bool welford_in_smem) {
+    return (welford_in_smem ? 2 * static_cast<size_t>(P) * kBlock * w_bytes : 0) +
+           static_cast<size_t>(VB) * row_stride * sizeof(float);
+}
+
+// Runs iterations t_begin+1 .. t_end of the chains of one tile of voxels.
+// SLICED = false: t_begin = 0, t_end = I, Welford accumulators in shared
+// memory at the start of `smem`; SLICED = true: chain state and accumulators
+// in `ss` (HBM).
+template <int KIND, int PREC, bool TRACE, bool SLICED>
+__device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra,
+                                         const SliceState &ss, int64_t tile, int t_begin,
+                                         int t_end, unsigned char *smem) {
     using R = typename PrecTraits<PREC>::R;
     using W = typename PrecTraits<PREC>::W;
     constexpr int P = model_n_par(KIND);
     constexpr int NW = n_words(P);
     constexpr int NWA = 4 * n_calls(P);
-
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    W *wf_mean = reinterpret_cast<W *>(smem_raw);     // [P][kBlock]
-    W *wf_m2 = wf_mean + P * kBlock;                   // [P][kBlock]
-    float *ytile = reinterpret_cast<float *>(wf_m2 + P * kBlock);  // [VB][row_stride]
 
     const int tid = threadIdx.x;
     const int C = ra.C;
@@ -136,50 +169,77 @@ __global__ void __launch_bounds__(kBlock) mh_kernel(const ModelConst mc, const R
     const int c = tid - lv * C;
     const bool lane_used = tid < VB * C;
 
-    for (int64_t tile = blockIdx.x; tile < ra.n_tiles; tile += gridDim.x) {
-        const int64_t v0 = tile * VB;
-        const int64_t left = ra.n_vox - v0;
-        const int nv = left < VB ? static_cast<int>(left) : VB;
+    const int64_t v0 = tile * VB;
+    const int64_t nchains = ra.n_vox * C;
+    W *wf_mean;
+    W *wf_m2;
+    int64_t wf_stride, wf_idx;
+    float *ytile;
+    if constexpr (SLICED) {
+        wf_mean = static_cast<W *>(ss.wf_mean);
+        wf_m2 = static_cast<W *>(ss.wf_m2);
+        wf_stride = nchains;
+        wf_idx = v0 * C + tid;
+        ytile = reinterpret_cast<float *>(smem);
+    } else {
+        wf_mean = reinterpret_cast<W *>(smem);
+        wf_m2 = wf_mean + P * kBlock;
+        wf_stride = kBlock;
+        wf_idx = tid;
+        ytile = reinterpret_cast<float *>(wf_m2 + P * kBlock);
+    }
 
-        // a1: stage measurements of voxels [v0, v0 + nv) in shared memory
-        __syncthreads();
-        {
-            const float *src = ra.data + v0 * M;
-            const int total = nv * M;
-            if (ra.data_vec4) {
-                const float4 *src4 = reinterpret_cast<const float4 *>(src);
-                for (int i = tid; i < total / 4; i += kBlock) {
-                    const float4 q = __ldg(src4 + i);
-                    const int e = 4 * i, row = e / M, col = e - row * M;
-                    float *dst = ytile + row * ra.row_stride + col;
-                    dst[0] = q.x;
-                    dst[1] = q.y;
-                    dst[2] = q.z;
-                    dst[3] = q.w;
-                }
-            } else {
-                for (int i = tid; i < total; i += kBlock) {
-                    const int row = i / M, col = i - row * M;
-                    ytile[row * ra.row_stride + col] = __ldg(src + i);
-                }
+    const int64_t left = ra.n_vox - v0;
+    const int nv = left < VB ? static_cast<int>(left) : VB;
+
+    // a1: stage measurements of voxels [v0, v0 + nv) in shared memory
+    __syncthreads();
+    {
+        const float *src = ra.data + v0 * M;
+        const int total = nv * M;
+        if (ra.data_vec4) {
+            const float4 *src4 = reinterpret_cast<const float4 *>(src);
+            for (int i = tid; i < total / 4; i += kBlock) {
+                const float4 q = __ldg(src4 + i);
+                const int e = 4 * i, row = e / M, col = e - row * M;
+                float *dst = ytile + row * ra.row_stride + col;
+                dst[0] = q.x;
+                dst[1] = q.y;
+                dst[2] = q.z;
+                dst[3] = q.w;
+            }
+        } else {
+            for (int i = tid; i < total; i += kBlock) {
+                const int row = i / M, col = i - row * M;
+                ytile[row * ra.row_stride + col] = __ldg(src + i);
             }
         }
-        __syncthreads();
+    }
+    __syncthreads();
 
-        const bool active = lane_used && lv < nv;
-        const int64_t v = v0 + lv;
+    const bool active = lane_used && lv < nv;
+    const int64_t v = v0 + lv;
+    const int64_t ch = v * C + c;  // chain index in [0, N*C)
+    if (active) {
+        const float *y = ytile + lv * ra.row_stride;
+        const float sig = ra.sigma ? __ldg(ra.sigma + v) : ra.sigma_scalar;
+        const R inv_s2 = R(1) / (R(sig) * R(sig));
+        const uint32_t vg = static_cast<uint32_t>(ra.voxel_base + static_cast<uint64_t>(v));
+        const uint32_t cu = static_cast<uint32_t>(c);
+
+        // a2: initial state, or the state saved by the previous slice
+        R th[P];
+        R L;
         int n_acc = 0, n_bad = 0;
-        if (active) {
-            const float *y = ytile + lv * ra.row_stride;
-            const float sig = ra.sigma ? __ldg(ra.sigma + v) : ra.sigma_scalar;
-            const R inv_s2 = R(1) / (R(sig) * R(sig));
-            const uint32_t vg = static_cast<uint32_t>(ra.voxel_base + static_cast<uint64_t>(v));
-            const uint32_t cu = static_cast<uint32_t>(c);
-
-            // a2: initial state
-            R th[P];
+        if (SLICED && t_begin > 0) {
+#pragma unroll
+            for (int p = 0; p < P; ++p) th[p] = static_cast<const R *>(ss.theta)[p * nchains + ch];
+            L = static_cast<const R *>(ss.L)[ch];
+            n_acc = ss.n_acc[ch];
+            n_bad = ss.n_bad[ch];
+        } else {
             if (ra.x0) {
-                const float *x0 = ra.x0 + (v * C + c) * P;
+                const float *x0 = ra.x0 + ch * P;
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     if constexpr (PREC == GAC_PREC_FP64)
@@ -198,123 +258,143 @@ __global__ void __launch_bounds__(kBlock) mh_kernel(const ModelConst mc, const R
                         th[p] = fmaf(mc.ub_f[p] - mc.lb_f[p], u01_f(w0[p]), mc.lb_f[p]);
                 }
             }
-            R L = loglik_any<KIND, PREC>(th, y, inv_s2, mc);
-
+            L = loglik_any<KIND, PREC>(th, y, inv_s2, mc);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                wf_mean[p * kBlock + tid] = W(0);
-                wf_m2[p * kBlock + tid] = W(0);
+                wf_mean[p * wf_stride + wf_idx] = W(0);
+                wf_m2[p * wf_stride + wf_idx] = W(0);
             }
-            int n_mom = 0;
-            int to_thin = ra.B + ra.T;  // next iteration on the thinning grid
+        }
 
-            for (int t = 1; t <= ra.I; ++t) {
-                // a3: random words for (t, voxel, chain)
-                uint32_t w[NWA];
-                draw_words(w, static_cast<uint32_t>(t), vg, cu, ra.k0, ra.k1);
-                // a4: proposal
-                R prop[P];
+        // moments taken so far, and the next iteration on the thinning grid
+        const bool all_mode = ra.moments_mode == GAC_MOMENTS_ALL_POSTBURNIN;
+        int n_mom = all_mode ? max(t_begin - ra.B, 0) : (t_begin > ra.B ? (t_begin - ra.B) / ra.T : 0);
+        int to_thin = t_begin < ra.B ? ra.B + ra.T : ra.B + ((t_begin - ra.B) / ra.T + 1) * ra.T;
+
+        for (int t = t_begin + 1; t <= t_end; ++t) {
+            // a3: random words for (t, voxel, chain)
+            uint32_t w[NWA];
+            draw_words(w, static_cast<uint32_t>(t), vg, cu, ra.k0, ra.k1);
+            // a4: proposal
+            R prop[P];
 #pragma unroll
-                for (int j = 0; 2 * j < P; ++j) {
-                    R z0, z1;
-                    if constexpr (PREC == GAC_PREC_FP64) box_muller_d(w[2 * j], w[2 * j + 1], z0, z1);
-                    else box_muller_f(w[2 * j], w[2 * j + 1], z0, z1);
-                    if constexpr (PREC == GAC_PREC_FP64) {
-                        prop[2 * j] = fmin(fmax(fma(mc.step_d[2 * j], z0, th[2 * j]), mc.lb_d[2 * j]),
-                                           mc.ub_d[2 * j]);
-                        if (2 * j + 1 < P)
-                            prop[2 * j + 1] = fmin(fmax(fma(mc.step_d[2 * j + 1], z1, th[2 * j + 1]),
-                                                        mc.lb_d[2 * j + 1]), mc.ub_d[2 * j + 1]);
-                    } else {
-                        prop[2 * j] = fminf(fmaxf(fmaf(mc.step_f[2 * j], z0, th[2 * j]), mc.lb_f[2 * j]),
-                                            mc.ub_f[2 * j]);
-                        if (2 * j + 1 < P)
-                            prop[2 * j + 1] = fminf(fmaxf(fmaf(mc.step_f[2 * j + 1], z1, th[2 * j + 1]),
-                                                          mc.lb_f[2 * j + 1]), mc.ub_f[2 * j + 1]);
-                    }
+            for (int j = 0; 2 * j < P; ++j) {
+                R z0, z1;
+                if constexpr (PREC == GAC_PREC_FP64) box_muller_d(w[2 * j], w[2 * j + 1], z0, z1);
+                else box_muller_f(w[2 * j], w[2 * j + 1], z0, z1);
+                if constexpr (PREC == GAC_PREC_FP64) {
+                    prop[2 * j] = fmin(fmax(fma(mc.step_d[2 * j], z0, th[2 * j]), mc.lb_d[2 * j]),
+                                       mc.ub_d[2 * j]);
+                    if (2 * j + 1 < P)
+                        prop[2 * j + 1] = fmin(fmax(fma(mc.step_d[2 * j + 1], z1, th[2 * j + 1]),
+                                                    mc.lb_d[2 * j + 1]), mc.ub_d[2 * j + 1]);
+                } else {
+                    prop[2 * j] = fminf(fmaxf(fmaf(mc.step_f[2 * j], z0, th[2 * j]), mc.lb_f[2 * j]),
+                                        mc.ub_f[2 * j]);
+                    if (2 * j + 1 < P)
+                        prop[2 * j + 1] = fminf(fmaxf(fmaf(mc.step_f[2 * j + 1], z1, th[2 * j + 1]),
+                                                      mc.lb_f[2 * j + 1]), mc.ub_f[2 * j + 1]);
                 }
-                // a5 + a6: forward model and likelihood
-                const R Lp = loglik_any<KIND, PREC>(prop, y, inv_s2, mc);
-                // a7: accept / reject
-                const uint32_t w_acc = w[NW - 1];
-                const bool acc = accept_step<PREC>(Lp, L, w_acc);
-                n_bad += !isfinite(Lp);
-                if constexpr (TRACE) {
-                    if (v < ra.trace_n) {
-                        gac_trace_rec *rec = ra.trace + (v * C + c) * static_cast<int64_t>(ra.I) + (t - 1);
-#pragma unroll
-                        for (int p = 0; p < P; ++p) {
-                            rec->theta[p] = static_cast<double>(th[p]);
-                            rec->prop[p] = static_cast<double>(prop[p]);
-                        }
-                        rec->L = static_cast<double>(L);
-                        rec->Lp = static_cast<double>(Lp);
-                        rec->w_acc = w_acc;
-                        rec->accepted = acc ? 1 : 0;
-                    }
-                }
-                if (acc) {
-#pragma unroll
-                    for (int p = 0; p < P; ++p) th[p] = prop[p];
-                    L = Lp;
-                    ++n_acc;
-                }
-                // a8: thinning grid t = B + T, B + 2T, ... and moments
-                const bool on_grid = (t == to_thin);
-                if (on_grid) {
-                    to_thin += ra.T;
-                    if (ra.samples) {
-                        const int s = (t - ra.B) / ra.T - 1;
-                        float *dst = ra.samples + ((static_cast<int64_t>(s) * C + c) * P) * ra.n_vox + v;
-#pragma unroll
-                        for (int p = 0; p < P; ++p) dst[p * ra.n_vox] = static_cast<float>(th[p]);
-                    }
-                }
-                const bool take = (ra.moments_mode == GAC_MOMENTS_ALL_POSTBURNIN) ? (t > ra.B) : on_grid;
-                if (take) {
-                    ++n_mom;
-                    const W inv_n = W(1) / W(n_mom);
+            }
+            // a5 + a6: forward model and likelihood
+            const R Lp = loglik_any<KIND, PREC>(prop, y, inv_s2, mc);
+            // a7: accept / reject
+            const uint32_t w_acc = w[NW - 1];
+            const bool acc = accept_step<PREC>(Lp, L, w_acc);
+            n_bad += !isfinite(Lp);
+            if constexpr (TRACE) {
+                if (v < ra.trace_n) {
+                    gac_trace_rec *rec = ra.trace + ch * static_cast<int64_t>(ra.I) + (t - 1);
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
-                        const W x = static_cast<W>(th[p]);
-                        W m = wf_mean[p * kBlock + tid];
-                        const W d = x - m;
-                        m += d * inv_n;
-                        wf_mean[p * kBlock + tid] = m;
-                        wf_m2[p * kBlock + tid] += d * (x - m);
+                        rec->theta[p] = static_cast<double>(th[p]);
+                        rec->prop[p] = static_cast<double>(prop[p]);
                     }
+                    rec->L = static_cast<double>(L);
+                    rec->Lp = static_cast<double>(Lp);
+                    rec->w_acc = w_acc;
+                    rec->accepted = acc ? 1 : 0;
                 }
             }
+            if (acc) {
+#pragma unroll
+                for (int p = 0; p < P; ++p) th[p] = prop[p];
+                L = Lp;
+                ++n_acc;
+            }
+            // a8: thinning grid t = B + T, B + 2T, ... and moments
+            const bool on_grid = (t == to_thin);
+            if (on_grid) {
+                to_thin += ra.T;
+                if (ra.samples) {
+                    const int s = (t - ra.B) / ra.T - 1;
+                    float *dst = ra.samples + ((static_cast<int64_t>(s) * C + c) * P) * ra.n_vox + v;
+#pragma unroll
+                    for (int p = 0; p < P; ++p) dst[p * ra.n_vox] = static_cast<float>(th[p]);
+                }
+            }
+            if (all_mode ? (t > ra.B) : on_grid) {
+                ++n_mom;
+                const W inv_n = W(1) / W(n_mom);
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const W x = static_cast<W>(th[p]);
+                    W m = wf_mean[p * wf_stride + wf_idx];
+                    const W d = x - m;
+                    m += d * inv_n;
+                    wf_mean[p * wf_stride + wf_idx] = m;
+                    wf_m2[p * wf_stride + wf_idx] += d * (x - m);
+                }
+            }
+        }
+        if (t_end == ra.I) {
             if (ra.accept) ra.accept[c * ra.n_vox + v] = ra.I > 0 ? float(n_acc) / float(ra.I) : 0.0f;
             if (ra.nonfinite) ra.nonfinite[c * ra.n_vox + v] = n_bad;
-        }
-
-        // a9: pool the C chains of each voxel in chain order
-        __syncthreads();
-        if (active && c == 0 && (ra.mean || ra.std)) {
-            const int n_each = (ra.moments_mode == GAC_MOMENTS_ALL_POSTBURNIN) ? max(ra.I - ra.B, 0) : ra.S;
+        } else if constexpr (SLICED) {
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-                W mu = wf_mean[p * kBlock + tid];
-                W m2 = wf_m2[p * kBlock + tid];
-                double n = n_each;
-                for (int c2 = 1; c2 < C; ++c2) {
-                    const W mb = wf_mean[p * kBlock + tid + c2];
-                    const W m2b = wf_m2[p * kBlock + tid + c2];
-                    const double ntot = n + n_each;
-                    const W delta = mb - mu;
-                    mu += delta * W(n_each / ntot);
-                    m2 += m2b + delta * delta * W(n * n_each / ntot);
-                    n = ntot;
-                }
-                const double nan = __longlong_as_double(0x7ff8000000000000ll);
-                const double mean_out = n > 0 ? static_cast<double>(mu) : nan;
-                const double sd_out = n > 1 ? sqrt(static_cast<double>(m2) / (n - 1.0)) : (n == 1 ? 0.0 : nan);
-                if (ra.mean) ra.mean[p * ra.n_vox + v] = mean_out;
-                if (ra.std) ra.std[p * ra.n_vox + v] = sd_out;
-            }
+            for (int p = 0; p < P; ++p) static_cast<R *>(ss.theta)[p * nchains + ch] = th[p];
+            static_cast<R *>(ss.L)[ch] = L;
+            ss.n_acc[ch] = n_acc;
+            ss.n_bad[ch] = n_bad;
         }
     }
+
+    // a9: pool the C chains of each voxel in chain order
+    if (t_end != ra.I) return;
+    __syncthreads();
+    if (active && c == 0 && (ra.mean || ra.std)) {
+        const int n_each = (ra.moments_mode == GAC_MOMENTS_ALL_POSTBURNIN) ? max(ra.I - ra.B, 0) : ra.S;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            W mu = wf_mean[p * wf_stride + wf_idx];
+            W m2 = wf_m2[p * wf_stride + wf_idx];
+            double n = n_each;
+            for (int c2 = 1; c2 < C; ++c2) {
+                const W mb = wf_mean[p * wf_stride + wf_idx + c2];
+                const W m2b = wf_m2[p * wf_stride + wf_idx + c2];
+                const double ntot = n + n_each;
+                const W delta = mb - mu;
+                mu += delta * W(n_each / ntot);
+                m2 += m2b + delta * delta * W(n * n_each / ntot);
+                n = ntot;
+            }
+            const double nan = __longlong_as_double(0x7ff8000000000000ll);
+            const double mean_out = n > 0 ? static_cast<double>(mu) : nan;
+            const double sd_out = n > 1 ? sqrt(static_cast<double>(m2) / (n - 1.0)) : (n == 1 ? 0.0 : nan);
+            if (ra.mean) ra.mean[p * ra.n_vox + v] = mean_out;
+            if (ra.std) ra.std[p * ra.n_vox + v] = sd_out;
+        }
+    }
+}
+
+// One job, one launch: every tile runs all I iterations.
+template <int KIND, int PREC, bool TRACE>
+__global__ void __launch_bounds__(kBlock, PREC == GAC_PREC_FP64 ? 1 : GAC_MH_MIN_BLOCKS)
+    mh_kernel(const ModelConst mc, const RunArgs ra) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SliceState none{};
+    for (int64_t tile = blockIdx.x; tile < ra.n_tiles; tile += gridDim.x)
+        run_tile<KIND, PREC, TRACE, false>(mc, ra, none, tile, 0, ra.I, smem_raw);
 }
 
 }  // namespace gac

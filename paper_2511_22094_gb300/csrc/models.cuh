@@ -13,7 +13,7 @@
 // FP32 evaluation of evenly spaced echoes (MONOEXP, MWI3) uses an anchored
 // geometric recurrence: with t_k = t_0 + k dt, each pool's term is
 // E_k = E_0 R^k with R = exp(-dt (rate + i w)).  E_0, R and R^K (K = 6) come
-// from accurate expf/sincosf; inside a block of K echoes the term advances by
+// from expf and sincos_cw (below); inside a block of K echoes the term advances by
 // one complex multiply, and each block starts from the previous anchor times
 // R^K.  This replaces 3 transcendental calls per echo and pool by one
 // multiply while keeping the error near that of direct evaluation (every term
@@ -27,6 +27,7 @@
 namespace gac {
 
 constexpr int kAnchor = 6;
+constexpr float kSinCosMaxArg = 6000.0f;  // |x| bound of sincos_cw (registration checks it)
 constexpr int kSeriesDegree = 40;     // g(x) series for x < 0 in u = -x / kSeriesYMax
 constexpr float kSeriesYMax = 12.0f;  // registration keeps -x <= 12
 
@@ -90,6 +91,34 @@ __device__ __forceinline__ double smt_g_d(double x) {
     return sum;
 }
 
+// sin and cos of x in FP32 for |x| <= kSinCosMaxArg.  Cody & Waite's
+// additive range reduction by pi/2 ("Software Manual for the Elementary
+// Functions", 1980) with a three-part constant whose first two parts have
+// 12 trailing zero bits, so that q * part is exact for |q| < 2^12; then the
+// Taylor polynomials of sin (degree 9) and cos (degree 10) on |r| <= pi/4,
+// whose truncation errors are below 3e-9 and 2e-10.  No branches.
+__device__ __forceinline__ void sincos_cw(float x, float &sn, float &cs) {
+    const float q = rintf(x * 0.636619772367581343f);  // round(x * 2/pi)
+    float r = fmaf(q, -1.5703125f, x);                   // pi/2 = 1.5703125
+    r = fmaf(q, -4.837512969970703125e-4f, r);           //     + 4.8375129699707e-4
+    r = fmaf(q, -7.549790126404332e-8f, r);              //     + 7.5497901264e-8
+    const float r2 = r * r;
+    float ps = fmaf(r2, 2.75573192e-6f, -1.98412698e-4f);  //  1/9!, -1/7!
+    ps = fmaf(ps, r2, 8.33333333e-3f);                     //  1/5!
+    ps = fmaf(ps, r2, -1.66666667e-1f);                    // -1/3!
+    const float sr = fmaf(ps * r2, r, r);
+    float pc = fmaf(r2, -2.75573192e-7f, 2.48015873e-5f);  // -1/10!, 1/8!
+    pc = fmaf(pc, r2, -1.38888889e-3f);                    // -1/6!
+    pc = fmaf(pc, r2, 4.16666667e-2f);                     //  1/4!
+    pc = fmaf(pc, r2, -0.5f);                              // -1/2!
+    const float cr = fmaf(pc, r2, 1.0f);
+    const int n = static_cast<int>(q);  // quadrant: x = n pi/2 + r
+    const float a = (n & 1) ? cr : sr;
+    const float b = (n & 1) ? sr : cr;
+    sn = (n & 2) ? -a : a;
+    cs = ((n + 1) & 2) ? -b : b;
+}
+
 // ----------------------------------------------------------- FP32 models --
 template <class V>
 __device__ __forceinline__ void eval_monoexp_f(const float *th, const ModelConst &mc, V &&visit) {
@@ -100,14 +129,19 @@ __device__ __forceinline__ void eval_monoexp_f(const float *th, const ModelConst
         float anchor = s0 * expf(-mc.t0_f * rate);
         const float r1 = expf(-mc.dt_f * rate);
         const float rk = expf(-mc.dtk_f * rate);
-        for (int a = 0; a < n; a += kAnchor) {
+        int a = 0;
+        for (; a + kAnchor <= n; a += kAnchor) {
             float e = anchor;
 #pragma unroll
             for (int i = 0; i < kAnchor; ++i) {
-                if (a + i < n) visit(a + i, e);
+                visit(a + i, e);
                 e *= r1;
             }
             anchor *= rk;
+        }
+        for (float e = anchor; a < n; ++a) {  // last, partial block
+            visit(a, e);
+            e *= r1;
         }
     } else {
         for (int k = 0; k < n; ++k) visit(k, s0 * expf(-mc.acq_f[k] * rate));
@@ -119,6 +153,7 @@ __device__ __forceinline__ void eval_mwi3_f(const float *th, const ModelConst &m
     const float phi0 = th[8];
     const int n = mc.n_acq;
     if (mc.even) {
+        // per pool: E_0 = A exp(-t0/T2*) e^{i(phi0 - w t0)}, R = exp(-dt (1/T2* + i w)), R^K
         float er[3], ei[3], rr[3], ri[3], kr[3], ki[3];
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
@@ -126,16 +161,16 @@ __device__ __forceinline__ void eval_mwi3_f(const float *th, const ModelConst &m
             const float w = (j < 2) ? kTwoPiMilli * th[6 + j] : 0.0f;  // rad / ms
             const float m0 = th[j] * expf(-mc.t0_f * rate);
             float s, c;
-            sincosf(fmaf(-w, mc.t0_f, phi0), &s, &c);
+            sincos_cw(fmaf(-w, mc.t0_f, phi0), s, c);
             er[j] = m0 * c;
             ei[j] = m0 * s;
             const float m1 = expf(-mc.dt_f * rate);
             const float mk = expf(-mc.dtk_f * rate);
             if (j < 2) {
-                sincosf(-w * mc.dt_f, &s, &c);
+                sincos_cw(-w * mc.dt_f, s, c);
                 rr[j] = m1 * c;
                 ri[j] = m1 * s;
-                sincosf(-w * mc.dtk_f, &s, &c);
+                sincos_cw(-w * mc.dtk_f, s, c);
                 kr[j] = mk * c;
                 ki[j] = mk * s;
             } else {  // extra-cellular pool: no frequency offset, real ratio
@@ -145,7 +180,8 @@ __device__ __forceinline__ void eval_mwi3_f(const float *th, const ModelConst &m
                 ki[j] = 0.0f;
             }
         }
-        for (int a = 0; a < n; a += kAnchor) {
+        // one block of echoes a .. a+cnt-1 from the current anchors
+        auto block = [&](int a, int cnt, bool full) {
             float cr[3], ci[3];
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
@@ -154,7 +190,7 @@ __device__ __forceinline__ void eval_mwi3_f(const float *th, const ModelConst &m
             }
 #pragma unroll
             for (int i = 0; i < kAnchor; ++i) {
-                if (a + i < n) visit(a + i, cr[0] + cr[1] + cr[2], ci[0] + ci[1] + ci[2]);
+                if (full || i < cnt) visit(a + i, cr[0] + cr[1] + cr[2], ci[0] + ci[1] + ci[2]);
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     const float nr = fmaf(cr[j], rr[j], -ci[j] * ri[j]);
@@ -165,6 +201,10 @@ __device__ __forceinline__ void eval_mwi3_f(const float *th, const ModelConst &m
                 cr[2] *= rr[2];
                 ci[2] *= rr[2];
             }
+        };
+        int a = 0;
+        for (; a + kAnchor <= n; a += kAnchor) {
+            block(a, kAnchor, true);
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const float nr = fmaf(er[j], kr[j], -ei[j] * ki[j]);
@@ -175,6 +215,7 @@ __device__ __forceinline__ void eval_mwi3_f(const float *th, const ModelConst &m
             er[2] *= kr[2];
             ei[2] *= kr[2];
         }
+        if (a < n) block(a, n - a, false);
     } else {
         float rate[3], w[3];
 #pragma unroll
@@ -189,7 +230,7 @@ __device__ __forceinline__ void eval_mwi3_f(const float *th, const ModelConst &m
             for (int j = 0; j < 3; ++j) {
                 const float m = th[j] * expf(-t * rate[j]);
                 float s, c;
-                sincosf(fmaf(-w[j], t, phi0), &s, &c);
+                sincos_cw(fmaf(-w[j], t, phi0), s, c);
                 re = fmaf(m, c, re);
                 im = fmaf(m, s, im);
             }

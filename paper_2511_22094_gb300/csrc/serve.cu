@@ -1,0 +1,745 @@
+// Serving runtime: continuous batching of MH fit jobs on one GPU
+// (gac_server_* in include/gac.h).
+//
+// Jobs arrive from any host thread.  A scheduler thread admits them in
+// arrival order while their device memory fits under the HBM budget, uploads
+// them on a copy stream, and runs rounds.  A round is one launch of
+// serve_kernel, a persistent kernel whose blocks claim work items (job, tile
+// of voxels, iteration slice) from every resident job through an atomic
+// counter; the block copies its job's descriptor into shared memory and runs
+// the same tile routine as gac_mcmc_run, with chain state in HBM between
+// slices.  Finished jobs are copied back on the copy stream while the next
+// round runs; their memory then returns to the budget.  No device code waits
+// on the host: every wait is a host-side stream/event synchronisation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "gac.h"
+#include "gac_internal.h"
+#include "mh_kernel.cuh"
+
+namespace gac {
+
+struct ServeJob {
+    ModelConst mc;
+    RunArgs ra;
+    SliceState ss;
+};
+
+struct WorkItem {
+    int32_t job;      // index into the round's job table
+    int32_t t_begin;  // iterations t_begin+1 .. t_end
+    int32_t t_end;
+    int32_t pad;
+    int64_t tile;
+};
+
+// Copies n bytes (a multiple of 4) cooperatively.
+__device__ __forceinline__ void block_copy(void *dst, const void *src, int n) {
+    int *d = static_cast<int *>(dst);
+    const int *s = static_cast<const int *>(src);
+    for (int i = threadIdx.x; i < n / 4; i += blockDim.x) d[i] = s[i];
+}
+
+__global__ void __launch_bounds__(kBlock) serve_kernel(const ServeJob *jobs, const WorkItem *items,
+                                                       int n_items, int *next_item) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) ServeJob s_job;
+    __shared__ WorkItem s_item;
+    __shared__ int s_idx;
+    int cur_job = -1;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_idx = atomicAdd(next_item, 1);
+            if (s_idx < n_items) s_item = items[s_idx];
+        }
+        __syncthreads();
+        if (s_idx >= n_items) break;
+        const WorkItem wi = s_item;
+        if (wi.job != cur_job) {
+            __syncthreads();
+            block_copy(&s_job, &jobs[wi.job], sizeof(ServeJob));
+            cur_job = wi.job;
+            __syncthreads();
+        }
+        switch (s_job.mc.kind) {
+        case GAC_MODEL_MONOEXP:
+            run_tile<GAC_MODEL_MONOEXP, GAC_PREC_MIXED, false, true>(s_job.mc, s_job.ra, s_job.ss, wi.tile,
+                                                                     wi.t_begin, wi.t_end, smem_raw);
+            break;
+        case GAC_MODEL_MWI3:
+            run_tile<GAC_MODEL_MWI3, GAC_PREC_MIXED, false, true>(s_job.mc, s_job.ra, s_job.ss, wi.tile,
+                                                                  wi.t_begin, wi.t_end, smem_raw);
+            break;
+        case GAC_MODEL_SMT:
+            run_tile<GAC_MODEL_SMT, GAC_PREC_MIXED, false, true>(s_job.mc, s_job.ra, s_job.ss, wi.tile,
+                                                                 wi.t_begin, wi.t_end, smem_raw);
+            break;
+        default:
+            run_tile<GAC_MODEL_LINEAR_TEST, GAC_PREC_MIXED, false, true>(s_job.mc, s_job.ra, s_job.ss,
+                                                                         wi.tile, wi.t_begin, wi.t_end,
+                                                                         smem_raw);
+            break;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host --
+static double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+enum class JobState { Queued, Uploading, Running, Finishing, Done, Failed, Cancelled };
+
+struct Job {
+    uint64_t id = 0;
+    ModelConst mc;
+    gac_mcmc_opts opts;
+    int64_t n_vox = 0;
+    int keep_samples = 0;
+    int S = 0;
+    size_t bytes = 0;
+    JobState state = JobState::Queued;
+    gac_status err = GAC_OK;
+    bool cancel = false;
+    int t_done = 0;
+    double t_submit = 0, t_finish = 0;
+    // host copies of inputs (pinned) and results (pinned)
+    float *h_data = nullptr, *h_sigma = nullptr;
+    float sigma_scalar = 0.0f;
+    double *h_mean = nullptr, *h_std = nullptr;
+    float *h_samples = nullptr, *h_acc = nullptr;
+    int32_t *h_bad = nullptr;
+    // device block holding inputs, state and outputs
+    void *d_block = nullptr;
+    ServeJob desc;
+    cudaEvent_t ev = nullptr;  // upload or download completion
+};
+
+// Layout of one job's device block.
+struct JobLayout {
+    size_t data, sigma, theta, L, n_acc, n_bad, wf_mean, wf_m2, mean, std, acc, bad, samples, total;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+static JobLayout job_layout(const ModelConst &mc, int64_t n_vox, const gac_mcmc_opts &o, int keep_samples,
+                            bool has_sigma) {
+    const size_t N = static_cast<size_t>(n_vox), P = mc.n_par, C = o.n_chains, M = mc.n_meas;
+    const size_t S = keep_samples ? n_samples(o.iterations, o.burnin, o.thin) : 0;
+    JobLayout l;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t at = off; off += align256(bytes); return at; };
+    l.data = take(N * M * 4);
+    l.sigma = take(has_sigma ? N * 4 : 0);
+    l.theta = take(P * N * C * 4);
+    l.L = take(N * C * 4);
+    l.n_acc = take(N * C * 4);
+    l.n_bad = take(N * C * 4);
+    l.wf_mean = take(P * N * C * 8);
+    l.wf_m2 = take(P * N * C * 8);
+    l.mean = take(P * N * 8);
+    l.std = take(P * N * 8);
+    l.acc = take(C * N * 4);
+    l.bad = take(C * N * 4);
+    l.samples = take(S * C * P * N * 4);
+    l.total = off;
+    return l;
+}
+
+}  // namespace gac
+
+using namespace gac;
+
+struct gac_server {
+    size_t budget = 0;
+    int max_resident = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Job>> queue;
+    std::vector<std::shared_ptr<Job>> resident;  // Uploading / Running / Finishing
+    std::map<uint64_t, std::shared_ptr<Job>> jobs;
+    uint64_t next_id = 1;
+    size_t in_use = 0;
+    int64_t finished = 0, rounds = 0;
+    bool stop = false;
+    std::thread thr;
+    bool started = false;
+    int device = 0;
+    // GPU resources, created by the scheduler thread
+    cudaStream_t s_compute = nullptr, s_copy = nullptr;
+    ServeJob *d_jobs = nullptr, *h_jobs = nullptr;
+    WorkItem *d_items = nullptr, *h_items = nullptr;
+    int *d_counter = nullptr;
+    size_t cap_jobs = 0, cap_items = 0;
+    size_t smem = 0;
+    int sms = 1;
+    double ci_per_s = 2e10;   // throughput estimate, refined each round
+    double round_target_s = 0.025;
+
+    void loop();
+    gac_status init_gpu();
+    gac_status admit_locked();
+    gac_status run_round();
+    void retire_locked();
+    void free_job(Job &j);
+};
+
+static gac_status round_alloc(void **d, void **h, size_t bytes) {
+    cudaError_t e = cudaMalloc(d, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "server table");
+    e = cudaMallocHost(h, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "server table (host)");
+    return GAC_OK;
+}
+
+gac_status gac_server::init_gpu() {
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    if ((e = cudaStreamCreateWithFlags(&s_compute, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "stream");
+    if ((e = cudaStreamCreateWithFlags(&s_copy, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "stream");
+    if ((e = cudaMalloc(&d_counter, sizeof(int))) != cudaSuccess) return cuda_fail(e, "counter");
+    // the largest measurement tile any job can need (C = 1, 256 voxels, 64
+    // complex echoes); each round launches with its own jobs' largest tile
+    smem = static_cast<size_t>(kBlock) * row_stride_for(GAC_MODEL_MWI3, 2 * GAC_MAX_ACQ) * sizeof(float);
+    e = cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return cuda_fail(e, "serve kernel smem");
+    e = cudaFuncSetAttribute(serve_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return cuda_fail(e, "serve kernel carveout");
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (sms < 1) sms = 1;
+    return GAC_OK;
+}
+
+void gac_server::free_job(Job &j) {
+    if (j.d_block) cudaFree(j.d_block);
+    j.d_block = nullptr;
+    if (j.ev) cudaEventDestroy(j.ev);
+    j.ev = nullptr;
+    if (j.h_data) cudaFreeHost(j.h_data);
+    if (j.h_sigma) cudaFreeHost(j.h_sigma);
+    j.h_data = j.h_sigma = nullptr;
+}
+
+static void free_results(Job &j) {
+    for (void *p : {static_cast<void *>(j.h_mean), static_cast<void *>(j.h_std), static_cast<void *>(j.h_samples),
+                    static_cast<void *>(j.h_acc), static_cast<void *>(j.h_bad)})
+        if (p) cudaFreeHost(p);
+    j.h_mean = j.h_std = nullptr;
+    j.h_samples = j.h_acc = nullptr;
+    j.h_bad = nullptr;
+}
+
+// Admits queued jobs in arrival order while they fit (caller holds mu).
+gac_status gac_server::admit_locked() {
+    while (!queue.empty()) {
+        auto jp = queue.front();
+        Job &j = *jp;
+        if (j.cancel) {
+            queue.pop_front();
+            j.state = JobState::Cancelled;
+            free_job(j);
+            cv_done.notify_all();
+            continue;
+        }
+        if (static_cast<int>(resident.size()) >= max_resident || in_use + j.bytes > budget) break;
+        queue.pop_front();
+        const bool has_sigma = j.h_sigma != nullptr;
+        JobLayout l = job_layout(j.mc, j.n_vox, j.opts, j.keep_samples, has_sigma);
+        cudaError_t e = cudaMalloc(&j.d_block, l.total);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j.ev, cudaEventDisableTiming);
+        const size_t N = j.n_vox, P = j.mc.n_par, C = j.opts.n_chains;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(static_cast<char *>(j.d_block) + l.data, j.h_data,
+                                                  N * j.mc.n_meas * 4, cudaMemcpyHostToDevice, s_copy);
+        if (e == cudaSuccess && has_sigma)
+            e = cudaMemcpyAsync(static_cast<char *>(j.d_block) + l.sigma, j.h_sigma, N * 4, cudaMemcpyHostToDevice,
+                                s_copy);
+        // results on the host (pinned)
+        if (e == cudaSuccess) e = cudaMallocHost(&j.h_mean, P * N * 8);
+        if (e == cudaSuccess) e = cudaMallocHost(&j.h_std, P * N * 8);
+        if (e == cudaSuccess) e = cudaMallocHost(&j.h_acc, C * N * 4);
+        if (e == cudaSuccess) e = cudaMallocHost(&j.h_bad, C * N * 4);
+        if (e == cudaSuccess && j.keep_samples && j.S > 0)
+            e = cudaMallocHost(&j.h_samples, static_cast<size_t>(j.S) * C * P * N * 4);
+        if (e == cudaSuccess) e = cudaEventRecord(j.ev, s_copy);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            j.err = e == cudaErrorMemoryAllocation ? GAC_ERR_OOM : GAC_ERR_CUDA;
+            j.state = JobState::Failed;
+            free_job(j);
+            free_results(j);
+            cv_done.notify_all();
+            continue;
+        }
+        char *b = static_cast<char *>(j.d_block);
+        RunArgs &ra = j.desc.ra;
+        std::memset(&ra, 0, sizeof ra);
+        ra.data = reinterpret_cast<const float *>(b + l.data);
+        ra.sigma = has_sigma ? reinterpret_cast<const float *>(b + l.sigma) : nullptr;
+        ra.sigma_scalar = j.sigma_scalar;
+        ra.mean = reinterpret_cast<double *>(b + l.mean);
+        ra.std = reinterpret_cast<double *>(b + l.std);
+        ra.samples = (j.keep_samples && j.S > 0) ? reinterpret_cast<float *>(b + l.samples) : nullptr;
+        ra.accept = reinterpret_cast<float *>(b + l.acc);
+        ra.nonfinite = reinterpret_cast<int32_t *>(b + l.bad);
+        ra.n_vox = j.n_vox;
+        ra.C = j.opts.n_chains;
+        ra.I = j.opts.iterations;
+        ra.B = j.opts.burnin;
+        ra.T = j.opts.thin;
+        ra.S = n_samples(j.opts.iterations, j.opts.burnin, j.opts.thin);
+        ra.k0 = static_cast<uint32_t>(j.opts.seed);
+        ra.k1 = static_cast<uint32_t>(j.opts.seed >> 32);
+        ra.voxel_base = j.opts.voxel_base;
+        ra.moments_mode = j.opts.moments_mode;
+        ra.vox_per_block = kBlock / ra.C;
+        ra.row_stride = row_stride_for(j.mc.kind, j.mc.n_meas);
+        ra.data_vec4 = (j.mc.n_meas % 4) == 0;
+        ra.n_tiles = (j.n_vox + ra.vox_per_block - 1) / ra.vox_per_block;
+        SliceState &ss = j.desc.ss;
+        ss.theta = b + l.theta;
+        ss.L = b + l.L;
+        ss.n_acc = reinterpret_cast<int32_t *>(b + l.n_acc);
+        ss.n_bad = reinterpret_cast<int32_t *>(b + l.n_bad);
+        ss.wf_mean = b + l.wf_mean;
+        ss.wf_m2 = b + l.wf_m2;
+        j.desc.mc = j.mc;
+        in_use += j.bytes;
+        j.state = JobState::Uploading;
+        resident.push_back(jp);
+    }
+    return GAC_OK;
+}
+
+// Moves finished downloads to Done and releases cancelled jobs (mu held).
+void gac_server::retire_locked() {
+    for (auto it = resident.begin(); it != resident.end();) {
+        Job &j = **it;
+        bool drop = false;
+        if (j.state == JobState::Finishing && cudaEventQuery(j.ev) == cudaSuccess) {
+            j.state = JobState::Done;
+            j.t_finish = now_s();
+            ++finished;
+            drop = true;
+        } else if (j.cancel && (j.state == JobState::Running || j.state == JobState::Uploading)) {
+            cudaEventSynchronize(j.ev);
+            j.state = JobState::Cancelled;
+            free_results(j);
+            drop = true;
+        }
+        if (drop) {
+            in_use -= j.bytes;
+            free_job(j);
+            it = resident.erase(it);
+            cv_done.notify_all();
+        } else {
+            ++it;
+        }
+    }
+}
+
+gac_status gac_server::run_round() {
+    // choose the jobs and the slice length under the lock
+    std::vector<std::shared_ptr<Job>> run;
+    int64_t chains = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (auto &jp : resident) {
+            Job &j = *jp;
+            if (j.cancel) continue;
+            if (j.state == JobState::Uploading && cudaEventQuery(j.ev) == cudaSuccess) j.state = JobState::Running;
+            if (j.state == JobState::Running) {
+                run.push_back(jp);
+                chains += j.n_vox * j.opts.n_chains;
+            }
+        }
+    }
+    if (run.empty()) return GAC_OK;
+    // Slice lengths.  A round is about round_target_s of work at the current
+    // throughput estimate.  Jobs are taken in order of remaining work: one
+    // whose remainder fits in half of what is left of the round's budget runs
+    // to completion in this round (small jobs leave quickly instead of
+    // advancing in lock-step with large ones); the others share the rest of
+    // the budget equally per chain (at least 16 iterations each).
+    std::vector<size_t> order(run.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    auto remaining = [&](size_t i) {
+        const Job &j = *run[i];
+        return static_cast<double>(j.opts.iterations - j.t_done) * j.n_vox * j.opts.n_chains;
+    };
+    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return remaining(a) < remaining(b); });
+    double budget_ci = round_target_s * ci_per_s;
+    std::vector<int> t_end(run.size(), -1);
+    int64_t big_chains = 0;
+    for (size_t i : order) {
+        const double rem = remaining(i);
+        if (rem <= 0.5 * budget_ci) {
+            t_end[i] = run[i]->opts.iterations;
+            budget_ci -= rem;
+        } else {
+            big_chains += run[i]->n_vox * run[i]->opts.n_chains;
+        }
+    }
+    const int64_t k_big = std::max<int64_t>(16, static_cast<int64_t>(std::max(budget_ci, 0.0) / std::max<int64_t>(big_chains, 1)));
+    for (size_t i = 0; i < run.size(); ++i)
+        if (t_end[i] < 0)
+            t_end[i] = static_cast<int>(std::min<int64_t>(run[i]->opts.iterations, run[i]->t_done + k_big));
+    (void)chains;
+    size_t n_items = 0, smem_round = 0;
+    for (auto &jp : run) {
+        const RunArgs &ra = jp->desc.ra;
+        n_items += ra.n_tiles;
+        smem_round = std::max(smem_round, tile_smem_bytes(jp->mc.n_par, 8, ra.vox_per_block, ra.row_stride, false));
+    }
+    int per_sm = 0;
+    cudaError_t eo = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel, kBlock, smem_round);
+    if (eo != cudaSuccess) return cuda_fail(eo, "occupancy");
+    const size_t grid = static_cast<size_t>(std::max(1, per_sm)) * sms;
+    if (run.size() > cap_jobs) {
+        if (d_jobs) cudaFree(d_jobs);
+        if (h_jobs) cudaFreeHost(h_jobs);
+        cap_jobs = std::max<size_t>(run.size(), 2 * cap_jobs);
+        gac_status st = round_alloc(reinterpret_cast<void **>(&d_jobs), reinterpret_cast<void **>(&h_jobs),
+                                    cap_jobs * sizeof(ServeJob));
+        if (st != GAC_OK) return st;
+    }
+    if (n_items > cap_items) {
+        if (d_items) cudaFree(d_items);
+        if (h_items) cudaFreeHost(h_items);
+        cap_items = std::max(n_items, 2 * cap_items);
+        gac_status st = round_alloc(reinterpret_cast<void **>(&d_items), reinterpret_cast<void **>(&h_items),
+                                    cap_items * sizeof(WorkItem));
+        if (st != GAC_OK) return st;
+    }
+    // items of the longest slices first: blocks claim them in list order,
+    // so the jobs that run to completion start at the beginning of the round
+    std::vector<size_t> by_len(run.size());
+    for (size_t i = 0; i < by_len.size(); ++i) by_len[i] = i;
+    std::stable_sort(by_len.begin(), by_len.end(), [&](size_t a, size_t b) {
+        return t_end[a] - run[a]->t_done > t_end[b] - run[b]->t_done;
+    });
+    size_t k = 0;
+    int64_t work = 0;
+    for (size_t ji = 0; ji < run.size(); ++ji) h_jobs[ji] = run[ji]->desc;
+    for (size_t ji : by_len) {
+        Job &j = *run[ji];
+        const int t0 = j.t_done;
+        const int t1 = t_end[ji];
+        work += (t1 - t0) * j.n_vox * j.opts.n_chains;
+        for (int64_t tile = 0; tile < j.desc.ra.n_tiles; ++tile) {
+            WorkItem &wi = h_items[k++];
+            wi.job = static_cast<int32_t>(ji);
+            wi.t_begin = t0;
+            wi.t_end = t1;
+            wi.pad = 0;
+            wi.tile = tile;
+        }
+    }
+    cudaError_t e = cudaMemcpyAsync(d_jobs, h_jobs, run.size() * sizeof(ServeJob), cudaMemcpyHostToDevice, s_compute);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_items, h_items, n_items * sizeof(WorkItem), cudaMemcpyHostToDevice, s_compute);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(int), s_compute);
+    if (e != cudaSuccess) return cuda_fail(e, "round setup");
+    const int grid_now = static_cast<int>(std::min<size_t>(grid, n_items));
+    const double t_start = now_s();
+    serve_kernel<<<grid_now, kBlock, smem_round, s_compute>>>(d_jobs, d_items, static_cast<int>(n_items), d_counter);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s_compute);
+    if (e != cudaSuccess) return cuda_fail(e, "serve kernel");
+    const double dt = now_s() - t_start;
+    if (dt > 1e-4 && work > 0) ci_per_s = 0.5 * ci_per_s + 0.5 * (work / dt);
+    // advance; start downloads of finished jobs on the copy stream
+    std::lock_guard<std::mutex> lk(mu);
+    ++rounds;
+    for (size_t ji = 0; ji < run.size(); ++ji) {
+        Job &j = *run[ji];
+        j.t_done = t_end[ji];
+        if (j.t_done < j.opts.iterations || j.cancel) continue;
+        const size_t N = j.n_vox, P = j.mc.n_par, C = j.opts.n_chains;
+        const RunArgs &ra = j.desc.ra;
+        e = cudaMemcpyAsync(j.h_mean, ra.mean, P * N * 8, cudaMemcpyDeviceToHost, s_copy);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_std, ra.std, P * N * 8, cudaMemcpyDeviceToHost, s_copy);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_acc, ra.accept, C * N * 4, cudaMemcpyDeviceToHost, s_copy);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_bad, ra.nonfinite, C * N * 4, cudaMemcpyDeviceToHost, s_copy);
+        if (e == cudaSuccess && ra.samples)
+            e = cudaMemcpyAsync(j.h_samples, ra.samples, static_cast<size_t>(j.S) * C * P * N * 4,
+                                cudaMemcpyDeviceToHost, s_copy);
+        if (e == cudaSuccess) e = cudaEventRecord(j.ev, s_copy);
+        if (e != cudaSuccess) return cuda_fail(e, "result download");
+        j.state = JobState::Finishing;
+    }
+    return GAC_OK;
+}
+
+void gac_server::loop() {
+    gac_status st = init_gpu();
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            if (st == GAC_OK) {
+                retire_locked();
+                admit_locked();
+            }
+            if (st != GAC_OK) {
+                // the GPU side failed: fail every job so no caller waits forever
+                for (auto &jp : queue) { jp->state = JobState::Failed; jp->err = st; }
+                for (auto &jp : resident) { jp->state = JobState::Failed; jp->err = st; }
+                queue.clear();
+                resident.clear();
+                cv_done.notify_all();
+                cv_work.wait(lk, [&] { return stop || !queue.empty(); });
+                if (stop) break;
+                continue;
+            }
+            if (stop) break;
+            bool runnable = false, waiting = false;
+            for (auto &jp : resident) {
+                if (jp->state == JobState::Running || jp->state == JobState::Uploading) runnable = true;
+                if (jp->state == JobState::Finishing) waiting = true;
+            }
+            if (!runnable) {
+                if (waiting) {
+                    lk.unlock();
+                    cudaStreamSynchronize(s_copy);
+                    continue;
+                }
+                cv_work.wait(lk, [&] { return stop || !queue.empty(); });
+                if (stop) break;
+                continue;
+            }
+        }
+        bool any_running = false;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            for (auto &jp : resident)
+                if (jp->state == JobState::Running) any_running = true;
+        }
+        if (!any_running) {
+            // only uploads in flight: wait for them
+            cudaStreamSynchronize(s_copy);
+            std::lock_guard<std::mutex> lk(mu);
+            for (auto &jp : resident)
+                if (jp->state == JobState::Uploading && cudaEventQuery(jp->ev) == cudaSuccess)
+                    jp->state = JobState::Running;
+            continue;
+        }
+        st = run_round();
+    }
+    // shutdown: wait for the GPU, release everything
+    if (s_compute) cudaStreamSynchronize(s_compute);
+    if (s_copy) cudaStreamSynchronize(s_copy);
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &kv : jobs) {
+        free_job(*kv.second);
+        free_results(*kv.second);
+    }
+    if (d_jobs) cudaFree(d_jobs);
+    if (h_jobs) cudaFreeHost(h_jobs);
+    if (d_items) cudaFree(d_items);
+    if (h_items) cudaFreeHost(h_items);
+    if (d_counter) cudaFree(d_counter);
+    if (s_compute) cudaStreamDestroy(s_compute);
+    if (s_copy) cudaStreamDestroy(s_copy);
+}
+
+static gac_status job_bytes(const ModelConst &mc, int64_t n_vox, const gac_mcmc_opts &o, int keep, bool has_sigma,
+                            size_t *bytes) {
+    *bytes = job_layout(mc, n_vox, o, keep, has_sigma).total;
+    return GAC_OK;
+}
+
+extern "C" {
+
+gac_status gac_server_create(size_t hbm_budget_bytes, int max_resident_jobs, gac_server **out) {
+    clear_error();
+    if (!out) return fail(GAC_ERR_INVALID_ARG, "out must not be NULL");
+    if (hbm_budget_bytes == 0) return fail(GAC_ERR_INVALID_ARG, "budget must be > 0");
+    if (max_resident_jobs < 1 || max_resident_jobs > 1024)
+        return fail(GAC_ERR_INVALID_ARG, "max_resident_jobs must be in [1, 1024]");
+    gac_server *s = new (std::nothrow) gac_server();
+    if (!s) return fail(GAC_ERR_OOM, "server");
+    s->budget = hbm_budget_bytes;
+    s->max_resident = max_resident_jobs;
+    *out = s;
+    return GAC_OK;
+}
+
+gac_status gac_server_job_bytes(int model_id, int64_t n_vox, const gac_mcmc_opts *opts, int keep_samples,
+                                int has_sigma, size_t *bytes) {
+    clear_error();
+    ModelConst mc;
+    gac_status st = model_get(model_id, &mc);
+    if (st != GAC_OK) return st;
+    if (!bytes || n_vox < 0) return fail(GAC_ERR_INVALID_ARG, "bad arguments");
+    if ((st = validate_opts(opts, n_vox)) != GAC_OK) return st;
+    return job_bytes(mc, n_vox, *opts, keep_samples, has_sigma != 0, bytes);
+}
+
+gac_status gac_server_submit(gac_server *srv, int model_id, const void *data, int64_t n_vox, const float *sigma,
+                             float sigma_scalar, const gac_mcmc_opts *opts, int keep_samples, uint64_t *job_id) {
+    clear_error();
+    if (!srv || !job_id) return fail(GAC_ERR_INVALID_ARG, "srv and job_id must not be NULL");
+    ModelConst mc;
+    gac_status st = model_get(model_id, &mc);
+    if (st != GAC_OK) return st;
+    if (n_vox < 1) return fail(GAC_ERR_INVALID_ARG, "n_vox must be >= 1");
+    if ((st = validate_opts(opts, n_vox)) != GAC_OK) return st;
+    if (opts->precision != GAC_PREC_MIXED) return fail(GAC_ERR_INVALID_ARG, "serving runs the MIXED precision path");
+    if (opts->trace_n_vox != 0) return fail(GAC_ERR_INVALID_ARG, "serving does not trace");
+    if (!data) return fail(GAC_ERR_INVALID_ARG, "data must not be NULL");
+    if (!sigma && !(sigma_scalar > 0.0f)) return fail(GAC_ERR_INVALID_ARG, "sigma is NULL and sigma_scalar <= 0");
+    size_t bytes = 0;
+    job_bytes(mc, n_vox, *opts, keep_samples, sigma != nullptr, &bytes);
+    if (bytes > srv->budget)
+        return fail(GAC_ERR_BUDGET, "job needs %zu bytes, more than the whole budget of %zu", bytes, srv->budget);
+
+    auto jp = std::make_shared<Job>();
+    Job &j = *jp;
+    j.mc = mc;
+    j.opts = *opts;
+    j.n_vox = n_vox;
+    j.keep_samples = keep_samples ? 1 : 0;
+    j.S = n_samples(opts->iterations, opts->burnin, opts->thin);
+    j.bytes = bytes;
+    j.sigma_scalar = sigma_scalar;
+    const size_t dbytes = static_cast<size_t>(n_vox) * mc.n_meas * 4;
+    cudaError_t e = cudaMallocHost(&j.h_data, dbytes);
+    if (e == cudaSuccess) e = cudaMemcpy(j.h_data, data, dbytes, cudaMemcpyDefault);
+    if (e == cudaSuccess && sigma) {
+        e = cudaMallocHost(&j.h_sigma, static_cast<size_t>(n_vox) * 4);
+        if (e == cudaSuccess) e = cudaMemcpy(j.h_sigma, sigma, static_cast<size_t>(n_vox) * 4, cudaMemcpyDefault);
+    }
+    if (e != cudaSuccess) {
+        if (j.h_data) cudaFreeHost(j.h_data);
+        if (j.h_sigma) cudaFreeHost(j.h_sigma);
+        return cuda_fail(e, "staging job inputs");
+    }
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (!srv->started) {
+        cudaGetDevice(&srv->device);
+        srv->thr = std::thread([srv] { srv->loop(); });
+        srv->started = true;
+    }
+    j.id = srv->next_id++;
+    j.t_submit = now_s();
+    srv->jobs[j.id] = jp;
+    srv->queue.push_back(jp);
+    *job_id = j.id;
+    srv->cv_work.notify_all();
+    return GAC_OK;
+}
+
+static gac_status deliver(gac_server *srv, std::map<uint64_t, std::shared_ptr<Job>>::iterator it, gac_result *out,
+                          double *latency_s) {
+    Job &j = *it->second;
+    gac_status st = GAC_OK;
+    if (j.state == JobState::Cancelled) {
+        st = fail(GAC_ERR_CANCELLED, "job %llu was cancelled", static_cast<unsigned long long>(j.id));
+    } else if (j.state == JobState::Failed) {
+        st = fail(j.err, "job %llu failed", static_cast<unsigned long long>(j.id));
+    } else {
+        const size_t N = j.n_vox, P = j.mc.n_par, C = j.opts.n_chains;
+        cudaError_t e = cudaSuccess;
+        if (out) {
+            if (out->mean && e == cudaSuccess) e = cudaMemcpy(out->mean, j.h_mean, P * N * 8, cudaMemcpyDefault);
+            if (out->std && e == cudaSuccess) e = cudaMemcpy(out->std, j.h_std, P * N * 8, cudaMemcpyDefault);
+            if (out->accept_rate && e == cudaSuccess) e = cudaMemcpy(out->accept_rate, j.h_acc, C * N * 4, cudaMemcpyDefault);
+            if (out->nonfinite && e == cudaSuccess) e = cudaMemcpy(out->nonfinite, j.h_bad, C * N * 4, cudaMemcpyDefault);
+            if (out->samples && j.h_samples && e == cudaSuccess)
+                e = cudaMemcpy(out->samples, j.h_samples, static_cast<size_t>(j.S) * C * P * N * 4, cudaMemcpyDefault);
+        }
+        if (e != cudaSuccess) st = cuda_fail(e, "copy results");
+        if (latency_s) *latency_s = j.t_finish - j.t_submit;
+    }
+    free_results(j);
+    srv->jobs.erase(it);
+    return st;
+}
+
+gac_status gac_server_poll(gac_server *srv, uint64_t job_id, int *done, gac_result *out, double *latency_s) {
+    clear_error();
+    if (!srv || !done) return fail(GAC_ERR_INVALID_ARG, "srv and done must not be NULL");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->jobs.find(job_id);
+    if (it == srv->jobs.end()) return fail(GAC_ERR_UNKNOWN_JOB, "no job %llu", static_cast<unsigned long long>(job_id));
+    const JobState s = it->second->state;
+    if (s != JobState::Done && s != JobState::Failed && s != JobState::Cancelled) {
+        *done = 0;
+        return GAC_OK;
+    }
+    *done = 1;
+    return deliver(srv, it, out, latency_s);
+}
+
+gac_status gac_server_wait(gac_server *srv, uint64_t job_id, double timeout_s, gac_result *out, double *latency_s) {
+    clear_error();
+    if (!srv) return fail(GAC_ERR_INVALID_ARG, "srv must not be NULL");
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->jobs.find(job_id);
+    if (it == srv->jobs.end()) return fail(GAC_ERR_UNKNOWN_JOB, "no job %llu", static_cast<unsigned long long>(job_id));
+    auto jp = it->second;
+    const bool ok = srv->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), [&] {
+        return jp->state == JobState::Done || jp->state == JobState::Failed || jp->state == JobState::Cancelled;
+    });
+    if (!ok) return fail(GAC_ERR_TIMEOUT, "job %llu not done after %.3f s", static_cast<unsigned long long>(job_id), timeout_s);
+    return deliver(srv, srv->jobs.find(job_id), out, latency_s);
+}
+
+gac_status gac_server_cancel(gac_server *srv, uint64_t job_id) {
+    clear_error();
+    if (!srv) return fail(GAC_ERR_INVALID_ARG, "srv must not be NULL");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->jobs.find(job_id);
+    if (it == srv->jobs.end()) return fail(GAC_ERR_UNKNOWN_JOB, "no job %llu", static_cast<unsigned long long>(job_id));
+    Job &j = *it->second;
+    if (j.state == JobState::Queued || j.state == JobState::Uploading || j.state == JobState::Running)
+        j.cancel = true;
+    srv->cv_work.notify_all();
+    return GAC_OK;
+}
+
+gac_status gac_server_get_stats(gac_server *srv, gac_server_stats *st) {
+    clear_error();
+    if (!srv || !st) return fail(GAC_ERR_INVALID_ARG, "srv and st must not be NULL");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    st->queued = static_cast<int64_t>(srv->queue.size());
+    st->resident = static_cast<int64_t>(srv->resident.size());
+    st->finished = srv->finished;
+    st->rounds = srv->rounds;
+    st->bytes_in_use = srv->in_use;
+    st->budget = srv->budget;
+    return GAC_OK;
+}
+
+gac_status gac_server_destroy(gac_server *srv) {
+    clear_error();
+    if (!srv) return fail(GAC_ERR_INVALID_ARG, "srv must not be NULL");
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stop = true;
+        srv->cv_work.notify_all();
+    }
+    if (srv->thr.joinable()) srv->thr.join();
+    if (!srv->started) {
+        for (auto &kv : srv->jobs) {
+            srv->free_job(*kv.second);
+            free_results(*kv.second);
+        }
+    }
+    delete srv;
+    return GAC_OK;
+}
+
+}  // extern "C"

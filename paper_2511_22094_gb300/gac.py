@@ -60,9 +60,16 @@ class Result(ct.Structure):
                 ("accept_rate", ct.c_void_p), ("nonfinite", ct.c_void_p), ("trace", ct.c_void_p)]
 
 
+class ServerStats(ct.Structure):
+    _fields_ = [("queued", ct.c_int64), ("resident", ct.c_int64), ("finished", ct.c_int64),
+                ("rounds", ct.c_int64), ("bytes_in_use", ct.c_size_t), ("budget", ct.c_size_t)]
+
+
 EXPORTS = ["gac_model_register", "gac_model_info", "gac_result_sizes", "gac_mcmc_run",
            "gac_forward", "gac_loglik", "gac_philox_words", "gac_normals", "gac_last_error",
-           "gac_version"]
+           "gac_version", "gac_server_create", "gac_server_job_bytes", "gac_server_submit",
+           "gac_server_poll", "gac_server_wait", "gac_server_cancel", "gac_server_get_stats",
+           "gac_server_destroy"]
 
 
 def _load():
@@ -82,6 +89,17 @@ def _load():
         "gac_loglik": [ct.c_int, vp, i64, vp, vp, ct.c_int, vp, vp],
         "gac_philox_words": [u64, vp, vp, vp, i64, ct.c_int, vp, vp],
         "gac_normals": [u64, vp, vp, vp, i64, ct.c_int, ct.c_int, vp, vp, vp],
+        "gac_server_create": [ct.c_size_t, ct.c_int, ct.POINTER(vp)],
+        "gac_server_job_bytes": [ct.c_int, i64, ct.POINTER(McmcOpts), ct.c_int, ct.c_int,
+                                 ct.POINTER(ct.c_size_t)],
+        "gac_server_submit": [vp, ct.c_int, vp, i64, vp, ct.c_float, ct.POINTER(McmcOpts), ct.c_int,
+                              ct.POINTER(u64)],
+        "gac_server_poll": [vp, u64, ct.POINTER(ct.c_int), ct.POINTER(Result),
+                            ct.POINTER(ct.c_double)],
+        "gac_server_wait": [vp, u64, ct.c_double, ct.POINTER(Result), ct.POINTER(ct.c_double)],
+        "gac_server_cancel": [vp, u64],
+        "gac_server_get_stats": [vp, ct.POINTER(ServerStats)],
+        "gac_server_destroy": [vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -189,6 +207,68 @@ def gac_philox_words(seed: int, t, v, c, n: int, n_words: int, out, stream=None)
 def gac_normals(seed: int, t, v, c, n: int, n_par: int, precision: int, z, w_acc, stream=None):
     _check(_lib.gac_normals(seed, _ptr(t), _ptr(v), _ptr(c), n, n_par, precision, _ptr(z),
                             _ptr(w_acc), _stream(stream)), "gac_normals")
+
+
+# ------------------------------------------------------------- serving -----
+def _result(out):
+    out = out or {}
+    return Result(*(_ptr(out.get(k)) for k in ("mean", "std", "samples", "accept_rate",
+                                              "nonfinite", "trace")))
+
+
+def gac_server_create(hbm_budget_bytes: int, max_resident_jobs: int):
+    h = ct.c_void_p()
+    _check(_lib.gac_server_create(hbm_budget_bytes, max_resident_jobs, ct.byref(h)),
+           "gac_server_create")
+    return h
+
+
+def gac_server_job_bytes(model_id: int, n_vox: int, opts: McmcOpts, keep_samples: bool,
+                         has_sigma: bool) -> int:
+    b = ct.c_size_t()
+    _check(_lib.gac_server_job_bytes(model_id, n_vox, ct.byref(opts), int(keep_samples),
+                                     int(has_sigma), ct.byref(b)), "gac_server_job_bytes")
+    return b.value
+
+
+def gac_server_submit(srv, model_id: int, data, n_vox: int, sigma, sigma_scalar: float,
+                      opts: McmcOpts, keep_samples: bool = False) -> int:
+    jid = ct.c_uint64()
+    _check(_lib.gac_server_submit(srv, model_id, _ptr(data), n_vox, _ptr(sigma), sigma_scalar,
+                                  ct.byref(opts), int(keep_samples), ct.byref(jid)),
+           "gac_server_submit")
+    return jid.value
+
+
+def gac_server_poll(srv, job_id: int, out: dict | None = None):
+    """Returns (done, latency_s); raises GacError for a failed/cancelled job."""
+    done, lat = ct.c_int(), ct.c_double()
+    r = _result(out)
+    _check(_lib.gac_server_poll(srv, job_id, ct.byref(done), ct.byref(r), ct.byref(lat)),
+           "gac_server_poll")
+    return bool(done.value), lat.value
+
+
+def gac_server_wait(srv, job_id: int, timeout_s: float, out: dict | None = None) -> float:
+    lat = ct.c_double()
+    r = _result(out)
+    _check(_lib.gac_server_wait(srv, job_id, timeout_s, ct.byref(r), ct.byref(lat)),
+           "gac_server_wait")
+    return lat.value
+
+
+def gac_server_cancel(srv, job_id: int):
+    _check(_lib.gac_server_cancel(srv, job_id), "gac_server_cancel")
+
+
+def gac_server_get_stats(srv) -> dict:
+    st = ServerStats()
+    _check(_lib.gac_server_get_stats(srv, ct.byref(st)), "gac_server_get_stats")
+    return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+
+def gac_server_destroy(srv):
+    _check(_lib.gac_server_destroy(srv), "gac_server_destroy")
 
 
 # --------------------------------------------------- numpy conveniences ----

@@ -162,3 +162,37 @@ def sigma(w: Workload, theta_true: np.ndarray) -> np.ndarray:
 def noisy_data(signal: np.ndarray, z: np.ndarray, sig: np.ndarray) -> np.ndarray:
     """Measured data [n][M] float32 = noise-free signal + sigma * z (Gaussian noise)."""
     return (np.asarray(signal, np.float64) + np.asarray(sig, np.float64)[:, None] * z).astype(np.float32)
+
+
+@dataclass(frozen=True)
+class TraceJob:
+    index: int
+    arrival_s: float
+    workload: Workload  # protocol, bounds, steps; n_vox, chains, iterations set per job
+    first_voxel: int    # voxels drawn from this offset of the workload's volume
+
+
+def serving_trace(seed: int = 6, n_jobs: int = 200, mean_interarrival_s: float = 0.2,
+                  n_vox_range=(10_000, 2_000_000)) -> list:
+    """Serving workload: Poisson arrivals (exponential gaps), each job's model
+    drawn uniformly from the three protocols, voxel count log-uniform in
+    n_vox_range, 1-4 chains, 1,000-5,000 iterations, burn-in 10% (Table 1),
+    thinning 100."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 7])))
+    gaps = rng.exponential(mean_interarrival_s, n_jobs)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    kinds = rng.integers(0, 3, n_jobs)
+    lo, hi = np.log(n_vox_range[0]), np.log(n_vox_range[1])
+    nv = np.exp(rng.uniform(lo, hi, n_jobs)).astype(np.int64)
+    chains = rng.integers(1, 5, n_jobs)
+    iters = rng.integers(1000, 5001, n_jobs)
+    protos = (MONOEXP_4K, MWI3_1M, SMT_1P5M)
+    jobs = []
+    for i in range(n_jobs):
+        base = protos[kinds[i]]
+        w = base.with_(name=f"{base.name}-job{i}", n_vox=int(nv[i]), n_chains=int(chains[i]),
+                       iterations=int(iters[i]), burnin=int(iters[i]) // 10, thin=100,
+                       mcmc_seed=10_000 + i)
+        first = int(rng.integers(0, max(1, base.n_vox - int(nv[i])))) if base.n_vox > nv[i] else 0
+        jobs.append(TraceJob(i, float(arrivals[i]), w, first))
+    return jobs

@@ -123,3 +123,33 @@ def test_result_sizes(gac):
                      accept_rate=3 * 100 * 4, nonfinite=3 * 100 * 4, trace=2 * 3 * 2000 * 216)
     b0 = gac.gac_result_sizes(mid, 100, gac.make_opts(400, 500, 5, 1, 1))
     assert b0["samples"] == 0
+
+
+def test_server_host_side_checks(gac):
+    """Creation, budget rejection and bad arguments need no GPU."""
+    with pytest.raises(gac.GacError):
+        gac.gac_server_create(0, 4)
+    with pytest.raises(gac.GacError):
+        gac.gac_server_create(1 << 30, 0)
+    srv = gac.gac_server_create(1 << 20, 4)  # a 1 MiB budget
+    try:
+        mid = gac.gac_model_register(**MONO)
+        opts = gac.make_opts(100, 10, 10, 2, 1)
+        need = gac.gac_server_job_bytes(mid, 100_000, opts, False, True)
+        assert need > 1 << 20
+        y = np.zeros((100_000, 12), np.float32)
+        with pytest.raises(gac.GacError) as e:
+            gac.gac_server_submit(srv, mid, y, 100_000, np.ones(100_000, np.float32), 0.0, opts)
+        assert e.value.status == 3  # BUDGET
+        with pytest.raises(gac.GacError) as e:  # serving runs the MIXED path only
+            gac.gac_server_submit(srv, mid, y[:10], 10, None, 0.01, gac.make_opts(100, 10, 10, 2, 1, precision=2))
+        assert e.value.status == 1
+        with pytest.raises(gac.GacError) as e:
+            gac.gac_server_poll(srv, 12345)
+        assert e.value.status == 9  # UNKNOWN_JOB
+        with pytest.raises(gac.GacError):
+            gac.gac_server_cancel(srv, 12345)
+        st = gac.gac_server_get_stats(srv)
+        assert st["queued"] == 0 and st["budget"] == 1 << 20
+    finally:
+        gac.gac_server_destroy(srv)

@@ -81,31 +81,35 @@ def test_smt_g_both_branches(gac, orc):
         assert np.abs(s[:, 0] - 1.0).max() <= (1e-6 if prec != gac.PREC_FP64 else 1e-15)
 
 
-@pytest.mark.parametrize("w", CASES + [W.MWI3_1M.with_(name="mwi3_snr300", snr=300.0),
-                                       W.MWI3_1M.with_(name="mwi3_snr50", snr=50.0)],
-                         ids=lambda w: w.name)
-def test_loglik_parity_at_posterior_typical_theta(gac, orc, w):
+LOGLIK = [(W.MONOEXP_4K, 1e-3), (W.MWI3_1M, 1e-3), (W.SMT_1P5M, 1e-3),
+          (W.MWI3_1M.with_(name="mwi3_snr50", snr=50.0), 1e-3),
+          (W.MWI3_1M.with_(name="mwi3_snr300", snr=300.0), 2e-3)]
+
+
+@pytest.mark.parametrize("w,tol", LOGLIK, ids=[c[0].name for c in LOGLIK])
+def test_loglik_parity_at_posterior_typical_theta(gac, orc, w, tol):
+    """|L_gpu - L_ref| at the true parameters, a typical posterior draw
+    (|L| ~ M/2).  The FP32 forward model carries a relative error of a few
+    1e-7 of |S|, i.e. ~SNR x 1e-7 in units of sigma per measurement, so the
+    bound grows with SNR: 1e-3 holds up to SNR 150; at SNR 300 the FP32
+    paths reach ~1.2e-3 (the FP64 path is exact to 1e-8)."""
     mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
-    n = 40_000
+    n = 100_000
     th, sig, y = make_voxels(orc, w, 0, n)
-    # the truth, and points about one posterior SD away along each axis
+    th = th.astype(np.float32).astype(np.float64)  # the FP32 state holds float parameters
+    ref = orc.loglik(w.kind, w.acq, th, y, sig)
+    # away from the posterior, errors scale with |L|: check them relatively
     rng = np.random.default_rng(7)
-    jitter = np.clip(th + 0.3 * np.array(w.step) * rng.standard_normal(th.shape), w.lb, w.ub)
-    th_all = np.concatenate([th, jitter])
-    # parameters rounded to float first, as the FP32 state holds them
-    th_all = th_all.astype(np.float32).astype(np.float64)
-    y_all = np.concatenate([y, y])
-    s_all = np.concatenate([sig, sig])
-    ref = orc.loglik(w.kind, w.acq, th_all, y_all, s_all)
+    far = np.clip(th + np.array(w.step) * rng.standard_normal(th.shape), w.lb, w.ub)
+    far = far.astype(np.float32).astype(np.float64)
+    ref_far = orc.loglik(w.kind, w.acq, far, y, sig)
     res = {}
-    for prec, tol in ((gac.PREC_MIXED, 1e-3), (gac.PREC_FP32, 2e-3), (gac.PREC_FP64, 1e-8)):
-        L = gac.loglik_host(mid, th_all, y_all, s_all, prec)
+    for prec, t in ((gac.PREC_MIXED, tol), (gac.PREC_FP32, tol), (gac.PREC_FP64, 1e-8)):
+        L = gac.loglik_host(mid, th, y, sig, prec)
         err = np.abs(L - ref)
-        typical = np.abs(ref) < 4 * w.n_meas  # posterior-typical: |L| of order M/2
-        res[prec] = (err[typical].max(), np.quantile(err[typical], 0.99))
-        assert typical.mean() > 0.5
-        assert err[typical].max() <= tol, (w.name, prec, res[prec])
-        # anywhere: relative error of a few FP32 ulps of |L|
-        if prec != gac.PREC_FP64:
-            assert (err / np.maximum(np.abs(ref), 1.0)).max() <= 5e-5
+        res[prec] = (err.max(), np.quantile(err, 0.999), np.quantile(err, 0.99))
+        assert err.max() <= t, (w.name, prec, res[prec])
+        Lf = gac.loglik_host(mid, far, y, sig, prec)
+        rel = np.abs(Lf - ref_far) / np.maximum(np.abs(ref_far), 1.0)
+        assert rel.max() <= (1e-12 if prec == gac.PREC_FP64 else 5e-5), (w.name, prec, rel.max())
     print(w.name, {k: tuple(f"{x:.2e}" for x in v) for k, v in res.items()})

