@@ -189,18 +189,19 @@ def run_ours(args, w):
     dev = torch.device(f"cuda:{local}")
     stream = torch.cuda.current_stream()
 
+    from paper_2511_22094_gb300 import shard
     N, C, P, M = w.n_vox, w.n_chains, w.n_par, w.n_meas
     S = w.n_samples
     mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
-    base = rank * N
+    base, _ = shard.weak_range(N, rank)  # this rank's slice of a volume of world * N voxels
 
     # synthetic inputs: seeded truths and noise; the signal from the library's
     # own forward model on the device
-    th = torch.from_numpy(W.truths(w, 0, N)).to(dev)
+    th = torch.from_numpy(W.truths(w, base, N)).to(dev)
     sig = torch.from_numpy(W.sigma(w, th.cpu().numpy())).to(dev)
     s = torch.empty((N, M), dtype=torch.float64, device=dev)
     gac.gac_forward(mid, th, N, gac.PREC_FP64, s, stream)
-    z = torch.from_numpy(W.noise(w, 0, N)).to(dev)
+    z = torch.from_numpy(W.noise(w, base, N)).to(dev)
     y = (s + sig.double()[:, None] * z).float().contiguous()
     del s, z, th
     out = dict(mean=torch.empty((P, N), dtype=torch.float64, device=dev),

@@ -47,7 +47,7 @@ namespace gac {
 constexpr int kBlock = 256;
 // Blocks per SM the FP32/MIXED kernels are compiled for (register cap).
 #ifndef GAC_MH_MIN_BLOCKS
-#define GAC_MH_MIN_BLOCKS 3
+#define GAC_MH_MIN_BLOCKS 2
 #endif
 
 struct RunArgs {

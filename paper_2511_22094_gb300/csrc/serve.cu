@@ -52,8 +52,12 @@ __device__ __forceinline__ void block_copy(void *dst, const void *src, int n) {
     for (int i = threadIdx.x; i < n / 4; i += blockDim.x) d[i] = s[i];
 }
 
-__global__ void __launch_bounds__(kBlock) serve_kernel(const ServeJob *jobs, const WorkItem *items,
-                                                       int n_items, int *next_item) {
+// One kernel per model kind, so that each runs at its own register
+// footprint; a round launches the kinds present concurrently on their own
+// streams, and their blocks share the SMs.
+template <int KIND>
+__global__ void __launch_bounds__(kBlock, 2) serve_kernel(const ServeJob *jobs, const WorkItem *items,
+                                                          int n_items, int *next_item) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(16) ServeJob s_job;
     __shared__ WorkItem s_item;
@@ -74,25 +78,33 @@ __global__ void __launch_bounds__(kBlock) serve_kernel(const ServeJob *jobs, con
             cur_job = wi.job;
             __syncthreads();
         }
-        switch (s_job.mc.kind) {
-        case GAC_MODEL_MONOEXP:
-            run_tile<GAC_MODEL_MONOEXP, GAC_PREC_MIXED, false, true>(s_job.mc, s_job.ra, s_job.ss, wi.tile,
-                                                                     wi.t_begin, wi.t_end, smem_raw);
-            break;
-        case GAC_MODEL_MWI3:
-            run_tile<GAC_MODEL_MWI3, GAC_PREC_MIXED, false, true>(s_job.mc, s_job.ra, s_job.ss, wi.tile,
-                                                                  wi.t_begin, wi.t_end, smem_raw);
-            break;
-        case GAC_MODEL_SMT:
-            run_tile<GAC_MODEL_SMT, GAC_PREC_MIXED, false, true>(s_job.mc, s_job.ra, s_job.ss, wi.tile,
-                                                                 wi.t_begin, wi.t_end, smem_raw);
-            break;
-        default:
-            run_tile<GAC_MODEL_LINEAR_TEST, GAC_PREC_MIXED, false, true>(s_job.mc, s_job.ra, s_job.ss,
-                                                                         wi.tile, wi.t_begin, wi.t_end,
-                                                                         smem_raw);
-            break;
-        }
+        run_tile<KIND, GAC_PREC_MIXED, false, true>(s_job.mc, s_job.ra, s_job.ss, wi.tile, wi.t_begin,
+                                                    wi.t_end, smem_raw);
+    }
+}
+
+constexpr int kKinds = 4;
+static const int kKindOf[kKinds] = {GAC_MODEL_MONOEXP, GAC_MODEL_MWI3, GAC_MODEL_SMT, GAC_MODEL_LINEAR_TEST};
+static int kind_slot(int kind) {
+    for (int i = 0; i < kKinds; ++i)
+        if (kKindOf[i] == kind) return i;
+    return -1;
+}
+static const void *serve_fn(int slot) {
+    switch (slot) {
+    case 0: return reinterpret_cast<const void *>(&serve_kernel<GAC_MODEL_MONOEXP>);
+    case 1: return reinterpret_cast<const void *>(&serve_kernel<GAC_MODEL_MWI3>);
+    case 2: return reinterpret_cast<const void *>(&serve_kernel<GAC_MODEL_SMT>);
+    default: return reinterpret_cast<const void *>(&serve_kernel<GAC_MODEL_LINEAR_TEST>);
+    }
+}
+static void launch_serve(int slot, int grid, size_t smem, cudaStream_t s, const ServeJob *jobs,
+                         const WorkItem *items, int n, int *counter) {
+    switch (slot) {
+    case 0: serve_kernel<GAC_MODEL_MONOEXP><<<grid, kBlock, smem, s>>>(jobs, items, n, counter); break;
+    case 1: serve_kernel<GAC_MODEL_MWI3><<<grid, kBlock, smem, s>>>(jobs, items, n, counter); break;
+    case 2: serve_kernel<GAC_MODEL_SMT><<<grid, kBlock, smem, s>>>(jobs, items, n, counter); break;
+    default: serve_kernel<GAC_MODEL_LINEAR_TEST><<<grid, kBlock, smem, s>>>(jobs, items, n, counter); break;
     }
 }
 
@@ -181,6 +193,8 @@ struct gac_server {
     int device = 0;
     // GPU resources, created by the scheduler thread
     cudaStream_t s_compute = nullptr, s_copy = nullptr;
+    cudaStream_t s_kind[kKinds] = {};
+    cudaEvent_t ev_setup = nullptr, ev_kind[kKinds] = {};
     ServeJob *d_jobs = nullptr, *h_jobs = nullptr;
     WorkItem *d_items = nullptr, *h_items = nullptr;
     int *d_counter = nullptr;
@@ -211,14 +225,21 @@ gac_status gac_server::init_gpu() {
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     if ((e = cudaStreamCreateWithFlags(&s_compute, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "stream");
     if ((e = cudaStreamCreateWithFlags(&s_copy, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "stream");
-    if ((e = cudaMalloc(&d_counter, sizeof(int))) != cudaSuccess) return cuda_fail(e, "counter");
+    if ((e = cudaMalloc(&d_counter, kKinds * sizeof(int))) != cudaSuccess) return cuda_fail(e, "counter");
+    if ((e = cudaEventCreateWithFlags(&ev_setup, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "event");
+    for (int i = 0; i < kKinds; ++i) {
+        if ((e = cudaStreamCreateWithFlags(&s_kind[i], cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "stream");
+        if ((e = cudaEventCreateWithFlags(&ev_kind[i], cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "event");
+    }
     // the largest measurement tile any job can need (C = 1, 256 voxels, 64
     // complex echoes); each round launches with its own jobs' largest tile
     smem = static_cast<size_t>(kBlock) * row_stride_for(GAC_MODEL_MWI3, 2 * GAC_MAX_ACQ) * sizeof(float);
-    e = cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return cuda_fail(e, "serve kernel smem");
-    e = cudaFuncSetAttribute(serve_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e != cudaSuccess) return cuda_fail(e, "serve kernel carveout");
+    for (int i = 0; i < kKinds; ++i) {
+        e = cudaFuncSetAttribute(serve_fn(i), cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return cuda_fail(e, "serve kernel smem");
+        e = cudaFuncSetAttribute(serve_fn(i), cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return cuda_fail(e, "serve kernel carveout");
+    }
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (sms < 1) sms = 1;
     return GAC_OK;
@@ -398,16 +419,8 @@ gac_status gac_server::run_round() {
         if (t_end[i] < 0)
             t_end[i] = static_cast<int>(std::min<int64_t>(run[i]->opts.iterations, run[i]->t_done + k_big));
     (void)chains;
-    size_t n_items = 0, smem_round = 0;
-    for (auto &jp : run) {
-        const RunArgs &ra = jp->desc.ra;
-        n_items += ra.n_tiles;
-        smem_round = std::max(smem_round, tile_smem_bytes(jp->mc.n_par, 8, ra.vox_per_block, ra.row_stride, false));
-    }
-    int per_sm = 0;
-    cudaError_t eo = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel, kBlock, smem_round);
-    if (eo != cudaSuccess) return cuda_fail(eo, "occupancy");
-    const size_t grid = static_cast<size_t>(std::max(1, per_sm)) * sms;
+    size_t n_items = 0;
+    for (auto &jp : run) n_items += jp->desc.ra.n_tiles;
     if (run.size() > cap_jobs) {
         if (d_jobs) cudaFree(d_jobs);
         if (h_jobs) cudaFreeHost(h_jobs);
@@ -424,8 +437,9 @@ gac_status gac_server::run_round() {
                                     cap_items * sizeof(WorkItem));
         if (st != GAC_OK) return st;
     }
-    // items of the longest slices first: blocks claim them in list order,
-    // so the jobs that run to completion start at the beginning of the round
+    // items grouped by model kind (one contiguous range per kind's kernel),
+    // within a kind the longest slices first: blocks claim items in list
+    // order, so the jobs that run to completion start at the beginning
     std::vector<size_t> by_len(run.size());
     for (size_t i = 0; i < by_len.size(); ++i) by_len[i] = i;
     std::stable_sort(by_len.begin(), by_len.end(), [&](size_t a, size_t b) {
@@ -433,31 +447,51 @@ gac_status gac_server::run_round() {
     });
     size_t k = 0;
     int64_t work = 0;
+    size_t first_item[kKinds] = {}, count_item[kKinds] = {}, smem_kind[kKinds] = {};
     for (size_t ji = 0; ji < run.size(); ++ji) h_jobs[ji] = run[ji]->desc;
-    for (size_t ji : by_len) {
-        Job &j = *run[ji];
-        const int t0 = j.t_done;
-        const int t1 = t_end[ji];
-        work += (t1 - t0) * j.n_vox * j.opts.n_chains;
-        for (int64_t tile = 0; tile < j.desc.ra.n_tiles; ++tile) {
-            WorkItem &wi = h_items[k++];
-            wi.job = static_cast<int32_t>(ji);
-            wi.t_begin = t0;
-            wi.t_end = t1;
-            wi.pad = 0;
-            wi.tile = tile;
+    for (int slot = 0; slot < kKinds; ++slot) {
+        first_item[slot] = k;
+        for (size_t ji : by_len) {
+            Job &j = *run[ji];
+            if (kind_slot(j.mc.kind) != slot) continue;
+            const RunArgs &ra = j.desc.ra;
+            smem_kind[slot] = std::max(smem_kind[slot], tile_smem_bytes(j.mc.n_par, 8, ra.vox_per_block, ra.row_stride, false));
+            const int t0 = j.t_done;
+            const int t1 = t_end[ji];
+            work += static_cast<int64_t>(t1 - t0) * j.n_vox * j.opts.n_chains;
+            for (int64_t tile = 0; tile < ra.n_tiles; ++tile) {
+                WorkItem &wi = h_items[k++];
+                wi.job = static_cast<int32_t>(ji);
+                wi.t_begin = t0;
+                wi.t_end = t1;
+                wi.pad = 0;
+                wi.tile = tile;
+            }
         }
+        count_item[slot] = k - first_item[slot];
     }
     cudaError_t e = cudaMemcpyAsync(d_jobs, h_jobs, run.size() * sizeof(ServeJob), cudaMemcpyHostToDevice, s_compute);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_items, h_items, n_items * sizeof(WorkItem), cudaMemcpyHostToDevice, s_compute);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(int), s_compute);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, kKinds * sizeof(int), s_compute);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_setup, s_compute);
     if (e != cudaSuccess) return cuda_fail(e, "round setup");
-    const int grid_now = static_cast<int>(std::min<size_t>(grid, n_items));
     const double t_start = now_s();
-    serve_kernel<<<grid_now, kBlock, smem_round, s_compute>>>(d_jobs, d_items, static_cast<int>(n_items), d_counter);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s_compute);
-    if (e != cudaSuccess) return cuda_fail(e, "serve kernel");
+    for (int slot = 0; slot < kKinds; ++slot) {
+        if (count_item[slot] == 0) continue;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_fn(slot), kBlock, smem_kind[slot]);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+        const size_t grid = std::min<size_t>(static_cast<size_t>(std::max(1, per_sm)) * sms, count_item[slot]);
+        if ((e = cudaStreamWaitEvent(s_kind[slot], ev_setup, 0)) != cudaSuccess) return cuda_fail(e, "wait");
+        launch_serve(slot, static_cast<int>(grid), smem_kind[slot], s_kind[slot], d_jobs, d_items + first_item[slot],
+                     static_cast<int>(count_item[slot]), d_counter + slot);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "serve kernel launch");
+        if ((e = cudaEventRecord(ev_kind[slot], s_kind[slot])) != cudaSuccess) return cuda_fail(e, "event");
+    }
+    for (int slot = 0; slot < kKinds; ++slot) {
+        if (count_item[slot] == 0) continue;
+        if ((e = cudaEventSynchronize(ev_kind[slot])) != cudaSuccess) return cuda_fail(e, "serve kernel");
+    }
     const double dt = now_s() - t_start;
     if (dt > 1e-4 && work > 0) ci_per_s = 0.5 * ci_per_s + 0.5 * (work / dt);
     // advance; start downloads of finished jobs on the copy stream
@@ -550,6 +584,12 @@ void gac_server::loop() {
     if (d_items) cudaFree(d_items);
     if (h_items) cudaFreeHost(h_items);
     if (d_counter) cudaFree(d_counter);
+    for (int i = 0; i < kKinds; ++i) {
+        if (s_kind[i]) cudaStreamSynchronize(s_kind[i]);
+        if (s_kind[i]) cudaStreamDestroy(s_kind[i]);
+        if (ev_kind[i]) cudaEventDestroy(ev_kind[i]);
+    }
+    if (ev_setup) cudaEventDestroy(ev_setup);
     if (s_compute) cudaStreamDestroy(s_compute);
     if (s_copy) cudaStreamDestroy(s_copy);
 }

@@ -23,6 +23,7 @@ def _jobs(orc, gac):
         (W.MONOEXP_4K, 257, 2, 1200, 120, 10),
         (W.MWI3_1M, 333, 1, 400, 40, 40),
         (W.SMT_1P5M, 64, 4, 350, 35, 7),
+        (W.MWI3_1M, 120_000, 4, 1500, 150, 50),  # large: sliced over many rounds
     ]
     jobs = []
     for i, (w, n, C, I, B, T) in enumerate(specs):
