@@ -187,6 +187,39 @@ gac_status gac_normals(uint64_t seed, const uint32_t *t, const uint32_t *v, cons
                        int64_t n, int n_par, int precision, double *z, uint32_t *w_acc,
                        void *stream);
 
+/* Allocation-free variant of gac_mcmc_run.  The paper has no counterpart to
+ * this entry point; it exists for callers that cannot allocate device
+ * memory: an application that has handed the GPU's memory to its own pool
+ * (a deep-learning framework's caching allocator, an on-scanner
+ * reconstruction pipeline with a fixed memory plan), or a latency-critical
+ * loop that must not pay the device-wide synchronisation that cudaMalloc and
+ * cudaFree imply.  It allocates nothing: it runs the same sampler in slices
+ * of slice_iterations iterations (one kernel launch each) and keeps the
+ * chains' state between slices in one fixed array of
+ * GAC_NOALLOC_STATE_BYTES that the library holds in device memory on every
+ * GPU where it is loaded, until the process exits.
+ *   - Every array (data, sigma, x0 and the result buffers) must be device
+ *     memory; host pointers are rejected with GAC_ERR_INVALID_ARG.
+ *   - The chain state needs about (20 P + 12) bytes per chain (P parameters):
+ *     n_vox * n_chains must stay within GAC_NOALLOC_STATE_BYTES of it (e.g.
+ *     ~349,000 chains of the 9-parameter model); larger runs are rejected
+ *     with GAC_ERR_INVALID_ARG and a message giving the limit.
+ *   - precision must be GAC_PREC_MIXED and trace_n_vox 0; results equal
+ *     gac_mcmc_run's for the same inputs.
+ *   - The first call on a device looks up the array's device address (a
+ *     one-time set-up per device); make that first call before any stream
+ *     capture.
+ *   - All calls share the one array, and it keeps the last call's contents
+ *     (each call initialises the state it uses, so nothing needs clearing).
+ *     Calls whose kernels overlap on the GPU -- on different streams or from
+ *     different threads -- race on it and must not be issued.
+ *   - Synchronous like gac_mcmc_run.  Errors: INVALID_ARG, UNKNOWN_MODEL,
+ *     CUDA. */
+#define GAC_NOALLOC_STATE_BYTES (64u << 20)
+gac_status gac_mcmc_run_noalloc(int model_id, const void *data, int64_t n_vox, const float *sigma,
+                                float sigma_scalar, const float *x0, const gac_mcmc_opts *opts,
+                                int slice_iterations, gac_result *out, void *stream);
+
 /* ------------------------------------------------------------------------
  * Serving: continuous batching of fit jobs on one GPU.
  *

@@ -69,7 +69,8 @@ EXPORTS = ["gac_model_register", "gac_model_info", "gac_result_sizes", "gac_mcmc
            "gac_forward", "gac_loglik", "gac_philox_words", "gac_normals", "gac_last_error",
            "gac_version", "gac_server_create", "gac_server_job_bytes", "gac_server_submit",
            "gac_server_poll", "gac_server_wait", "gac_server_cancel", "gac_server_get_stats",
-           "gac_server_destroy"]
+           "gac_server_destroy", "gac_mcmc_run_noalloc"]
+NOALLOC_STATE_BYTES = 64 << 20
 
 
 def _load():
@@ -89,6 +90,8 @@ def _load():
         "gac_loglik": [ct.c_int, vp, i64, vp, vp, ct.c_int, vp, vp],
         "gac_philox_words": [u64, vp, vp, vp, i64, ct.c_int, vp, vp],
         "gac_normals": [u64, vp, vp, vp, i64, ct.c_int, ct.c_int, vp, vp, vp],
+        "gac_mcmc_run_noalloc": [ct.c_int, vp, i64, vp, ct.c_float, vp, ct.POINTER(McmcOpts), ct.c_int,
+                                 ct.POINTER(Result), vp],
         "gac_server_create": [ct.c_size_t, ct.c_int, ct.POINTER(vp)],
         "gac_server_job_bytes": [ct.c_int, i64, ct.POINTER(McmcOpts), ct.c_int, ct.c_int,
                                  ct.POINTER(ct.c_size_t)],
@@ -187,6 +190,16 @@ def gac_mcmc_run(model_id: int, data, n_vox: int, sigma, sigma_scalar: float, x0
                                              "trace")))
     _check(_lib.gac_mcmc_run(model_id, _ptr(data), n_vox, _ptr(sigma), sigma_scalar, _ptr(x0),
                              ct.byref(opts), ct.byref(r), _stream(stream)), "gac_mcmc_run")
+
+
+def gac_mcmc_run_noalloc(model_id: int, data, n_vox: int, sigma, sigma_scalar: float, x0,
+                         opts: McmcOpts, slice_iterations: int, out: dict, stream=None):
+    """Allocation-free sampler run (device buffers only); see include/gac.h."""
+    r = Result(*(_ptr(out.get(k)) for k in ("mean", "std", "samples", "accept_rate", "nonfinite",
+                                             "trace")))
+    _check(_lib.gac_mcmc_run_noalloc(model_id, _ptr(data), n_vox, _ptr(sigma), sigma_scalar,
+                                     _ptr(x0), ct.byref(opts), slice_iterations, ct.byref(r),
+                                     _stream(stream)), "gac_mcmc_run_noalloc")
 
 
 def gac_forward(model_id: int, theta, n: int, precision: int, s, stream=None):
