@@ -209,7 +209,8 @@ def run_ours(args, w):
                samples=torch.empty((S, C, P, N), dtype=torch.float32, device=dev),
                accept_rate=torch.empty((C, N), dtype=torch.float32, device=dev),
                nonfinite=torch.empty((C, N), dtype=torch.int32, device=dev))
-    opts = gac.make_opts(w.iterations, w.burnin, w.thin, C, w.mcmc_seed, voxel_base=base)
+    prec = {"mixed": gac.PREC_MIXED, "fp32": gac.PREC_FP32, "fp64": gac.PREC_FP64}[args.precision]
+    opts = gac.make_opts(w.iterations, w.burnin, w.thin, C, w.mcmc_seed, voxel_base=base, precision=prec)
 
     def step():
         gac.gac_mcmc_run(mid, y, N, sig, 0.0, None, opts, out, stream)
@@ -288,11 +289,12 @@ def run_ours(args, w):
             "traffic": None, "kernel_ms": kernel_s * 1e3}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"mixed": "f32+f64", "fp32": "f32", "fp64": "f64"}[args.precision],
             "data": "synthetic (seeded truths + Gaussian noise, signal from the library's forward model)",
             "config": {"workload": w.name, "n_vox": N, "n_chains": C, "iterations": w.iterations,
                        "burnin": w.burnin, "thin": w.thin, "samples_stored": True,
-                       "precision": "mixed", "parallelism": f"voxel-shard x{world}",
+                       "precision": args.precision, "parallelism": f"voxel-shard x{world}",
                        "l2": f"inputs {y.numel() * 4 / 1e6:.0f} MB + samples {S * C * P * N * 4 / 1e9:.1f} GB written per step > 129 MB L2"},
             "roofline": roof, "clocks": clocks, "gpu_launches": args.steps,
             "wall_s": t_wall}
@@ -425,6 +427,9 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default="mwi3_1m", choices=sorted(W.WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", choices=("mixed", "fp32", "fp64"), default="mixed")
+    ap.add_argument("--n-vox", type=int, default=None, help="smaller case (profiling only)")
+    ap.add_argument("--iterations", type=int, default=None, help="smaller case (profiling only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true", help="run the serving trace instead")
     ap.add_argument("--serving-jobs", type=int, default=200)
@@ -434,6 +439,10 @@ def main():
         run_serving(args)
         return
     w = W.WORKLOADS[args.workload]
+    if args.n_vox is not None:
+        w = w.with_(n_vox=args.n_vox)
+    if args.iterations is not None:
+        w = w.with_(iterations=args.iterations, burnin=min(w.burnin, args.iterations // 5))
     if args.impl == "reference":
         run_reference(args, w)
     else:

@@ -187,6 +187,24 @@ gac_status gac_normals(uint64_t seed, const uint32_t *t, const uint32_t *v, cons
                        int64_t n, int n_par, int precision, double *z, uint32_t *w_acc,
                        void *stream);
 
+/* Affine-invariant ensemble sampler (the paper's second mcmc.m algorithm,
+ * Sec. 2.2.2: Nwalkers walkers and one stepSize for all parameters; Table 1:
+ * 50 walkers x 2000 iterations).  Goodman & Weare's stretch move with the
+ * two-halves parallel update: walkers 0..L/2-1 move against the other half,
+ * then walkers L/2..L-1 against the updated first half.  Walker k uses the
+ * Philox call (t, voxel, k << 8, 0): word 0 picks its partner j in the other
+ * half, word 1 the stretch z = ((a-1) u + 1)^2 / a (density ~ 1/sqrt(z) on
+ * [1/a, a], a = `stretch`), word 2 the acceptance uniform.  The proposal
+ * X_j + z (X_k - X_j) is rejected outside the prior box, otherwise accepted
+ * iff log u < (P-1) log z + L(Y) - L(X_k).
+ * Arguments, outputs and precision variants as gac_mcmc_run, with
+ * opts->n_chains = L walkers (even, 4..128) in place of chains; x0 is
+ * [n_vox][L][P]; step sizes of the registration are not used; trace records
+ * hold L' = NaN for proposals outside the box. */
+gac_status gac_ensemble_run(int model_id, const void *data, int64_t n_vox, const float *sigma,
+                            float sigma_scalar, const float *x0, const gac_mcmc_opts *opts,
+                            double stretch, gac_result *out, void *stream);
+
 /* Allocation-free variant of gac_mcmc_run.  The paper has no counterpart to
  * this entry point; it exists for callers that cannot allocate device
  * memory: an application that has handed the GPU's memory to its own pool

@@ -123,10 +123,13 @@ def _declare(L):
     L.orc_g.restype = ct.c_double
     L.orc_n_samples.argtypes = [ct.c_int, ct.c_int, ct.c_int]
     L.orc_n_samples.restype = ct.c_int
+    L.orc_stretch_z.argtypes = [ct.c_uint32, ct.c_double]
+    L.orc_stretch_z.restype = ct.c_double
     L.orc_max_threads.argtypes = []
     L.orc_max_threads.restype = ct.c_int
     for name in ("orc_forward_many", "orc_loglik_many", "orc_mcmc_run", "orc_chain_path",
-                 "orc_lockstep", "orc_words_many", "orc_normals_many"):
+                 "orc_lockstep", "orc_words_many", "orc_normals_many", "orc_ensemble_run",
+                 "orc_ensemble_path"):
         getattr(L, name).restype = ct.c_int
     return L
 
@@ -282,6 +285,55 @@ def chain_path(kind, acq, lb, ub, step, y, sigma, *, iterations, burnin=0, thin=
                               ct.c_uint64(voxel), ct.c_int(chain), _vp(path), ct.byref(acc))
     assert rc == 0
     return path, acc.value
+
+
+def ensemble_run(kind, acq, lb, ub, data, sigma, *, iterations, burnin, thin, n_walkers, seed,
+                 stretch=2.0, x0=None, sigma_scalar=0.0, voxel_base=0, moments_mode=0,
+                 n_threads=0, want_samples=True):
+    """Affine-invariant ensemble sampler; outputs as mcmc_run, walkers as chains."""
+    P = len(lb)
+    m, keep = _model(kind, acq, lb, ub, np.zeros(P))
+    data = np.ascontiguousarray(data, np.float32)
+    n_vox = data.shape[0]
+    sig = None if sigma is None else np.ascontiguousarray(sigma, np.float32)
+    x0a = None if x0 is None else np.ascontiguousarray(x0, np.float32)
+    S = n_samples(iterations, burnin, thin)
+    L = n_walkers
+    mean = np.full((P, n_vox), np.nan)
+    std = np.full((P, n_vox), np.nan)
+    samples = np.full((S, L, P, n_vox), np.nan) if want_samples else None
+    acc = np.zeros((L, n_vox))
+    bad = np.zeros((L, n_vox), np.int32)
+    used = ct.c_int(0)
+    o = _Opts(iterations, burnin, thin, L, seed, voxel_base, moments_mode, n_threads)
+    rc = lib().orc_ensemble_run(ct.byref(m), _vp(data), ct.c_int64(n_vox), _vp(sig),
+                                ct.c_float(sigma_scalar), _vp(x0a), ct.byref(o), ct.c_double(stretch),
+                                _vp(mean), _vp(std), _vp(samples), _vp(acc), _vp(bad), ct.byref(used))
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return dict(mean=mean, std=std, samples=samples, accept_rate=acc, nonfinite=bad,
+                threads=used.value)
+
+
+def ensemble_path(kind, acq, lb, ub, y, sigma, *, iterations, n_walkers, seed, stretch=2.0,
+                  voxel=0, x0=None, voxel_base=0):
+    """All walkers after each iteration of one voxel: [I+1][L][P] float64."""
+    P = len(lb)
+    m, keep = _model(kind, acq, lb, ub, np.zeros(P))
+    y = np.ascontiguousarray(y, np.float32)
+    x0a = None if x0 is None else np.ascontiguousarray(x0, np.float32)
+    path = np.zeros((iterations + 1, n_walkers, P))
+    acc = np.zeros((n_walkers, 1))
+    o = _Opts(iterations, 0, 1, n_walkers, seed, voxel_base, 0, 1)
+    rc = lib().orc_ensemble_path(ct.byref(m), _vp(y), ct.c_double(sigma), _vp(x0a), ct.byref(o),
+                                 ct.c_double(stretch), ct.c_uint64(voxel), _vp(path), _vp(acc))
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return path, acc[:, 0]
+
+
+def stretch_z(w: int, a: float) -> float:
+    return lib().orc_stretch_z(int(w), float(a))
 
 
 def lockstep(kind, acq, lb, ub, step, y, sigma, theta, prop, w_acc):

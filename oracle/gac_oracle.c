@@ -292,6 +292,29 @@ static void run_chain(const orc_model *m, const float *y, double sigma, const fl
     if (nonfinite) nonfinite[(size_t)c * n_vox + v] = (int32_t)n_bad;
 }
 
+/* Mean and SD (n-1 divisor) of the pooled values of C chains, stored chain
+ * after chain as [P][per_chain] blocks; n = 0 gives NaN, n = 1 an SD of 0. */
+static void pooled_moments(const double *pooled, int C, int per_chain, int P, int64_t v,
+                           int64_t n_vox, double *mean, double *std) {
+    size_t n_all = (size_t)C * per_chain;
+    for (int p = 0; p < P; ++p) {
+        double sum = 0.0;
+        for (int c = 0; c < C; ++c)
+            for (int i = 0; i < per_chain; ++i)
+                sum += pooled[(size_t)c * per_chain * P + (size_t)p * per_chain + i];
+        double mu = n_all > 0 ? sum / (double)n_all : NAN;
+        double ss = 0.0;
+        for (int c = 0; c < C; ++c)
+            for (int i = 0; i < per_chain; ++i) {
+                double d = pooled[(size_t)c * per_chain * P + (size_t)p * per_chain + i] - mu;
+                ss += d * d;
+            }
+        double sd = n_all > 1 ? sqrt(ss / (double)(n_all - 1)) : (n_all == 1 ? 0.0 : NAN);
+        if (mean) mean[(size_t)p * n_vox + v] = mu;
+        if (std) std[(size_t)p * n_vox + v] = sd;
+    }
+}
+
 /* Runs C chains for each of n_vox voxels.  data: [n_vox][n_meas] float (complex
  * data interleaved re, im); sigma: [n_vox] or NULL (then sigma_scalar);
  * x0: [n_vox][C][P] or NULL.  Outputs (each may be NULL):
@@ -332,23 +355,7 @@ int orc_mcmc_run(const orc_model *m, const float *data, int64_t n_vox, const flo
                       pooled + (size_t)c * per_chain * P, per_chain, accept_rate, nonfinite,
                       NULL);
         }
-        /* pooled holds, chain after chain, [P][per_chain] blocks */
-        for (int p = 0; p < P; ++p) {
-            double sum = 0.0;
-            for (int c = 0; c < C; ++c)
-                for (int i = 0; i < per_chain; ++i)
-                    sum += pooled[(size_t)c * per_chain * P + (size_t)p * per_chain + i];
-            double mu = n_all > 0 ? sum / (double)n_all : NAN;
-            double ss = 0.0;
-            for (int c = 0; c < C; ++c)
-                for (int i = 0; i < per_chain; ++i) {
-                    double d = pooled[(size_t)c * per_chain * P + (size_t)p * per_chain + i] - mu;
-                    ss += d * d;
-                }
-            double sd = n_all > 1 ? sqrt(ss / (double)(n_all - 1)) : (n_all == 1 ? 0.0 : NAN);
-            if (mean) mean[(size_t)p * n_vox + v] = mu;
-            if (std) std[(size_t)p * n_vox + v] = sd;
-        }
+        pooled_moments(pooled, C, per_chain, P, v, n_vox, mean, std);
         free(pooled);
     }
     return 0;
@@ -435,5 +442,147 @@ int orc_words_many(uint64_t seed, const uint32_t *t, const uint32_t *v, const ui
 int orc_normals_many(const uint32_t *words, int64_t n, int nw, int n_par, double *z) {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) orc_normals_from_words(words + (size_t)i * nw, n_par, z + (size_t)i * n_par);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Affine-invariant ensemble sampler (the paper's second mcmc.m algorithm,   */
+/* Sec. 2.2.2: Nwalkers walkers, one stepSize for all parameters).           */
+/* Goodman & Weare's stretch move (CAMCoS 5, 2010) with the two-halves       */
+/* parallel update of Foreman-Mackey et al. (PASP 125, 2013):                */
+/*   walkers 0..L/2-1 form half 0, L/2..L-1 half 1; iteration t moves every  */
+/*   walker of half 0 against the current half 1, then every walker of       */
+/*   half 1 against the updated half 0.                                      */
+/* Walker k draws one Philox call, counter (t, voxel, k<<8, 0):              */
+/*   word 0 picks its partner j in the other half, j = floor(w0 (L/2) 2^-32);*/
+/*   word 1 gives the stretch z = ((a-1) u + 1)^2 / a, u = u01(w1), whose    */
+/*   density is proportional to 1/sqrt(z) on [1/a, a] (a = stepSize);        */
+/*   word 2 is the acceptance uniform.                                       */
+/* Proposal Y = X_j + z (X_k - X_j).  Y outside the prior box has prior 0    */
+/* and is rejected; otherwise accept iff log u < (P-1) log z + L(Y) - L(X_k).*/
+/* Thinning, moments and outputs are those of the MH sampler, with walkers   */
+/* in place of chains.                                                       */
+/* ------------------------------------------------------------------------ */
+
+/* Stretch factor from a word: inverse CDF of g(z) ~ 1/sqrt(z) on [1/a, a]. */
+double orc_stretch_z(uint32_t w, double a) {
+    double s = (a - 1.0) * orc_u01(w) + 1.0;
+    return s * s / a;
+}
+
+static void ensemble_voxel(const orc_model *m, const float *y, double sigma, const float *x0v,
+                           const orc_opts *o, double a, uint32_t vg, int64_t v, int64_t n_vox,
+                           double *samples, double *pooled, int per_chain, double *accept_rate,
+                           int32_t *nonfinite, double *path) {
+    int P = m->n_par, L = o->n_chains, H = L / 2, I = o->iterations, B = o->burnin, T = o->thin;
+    int S = orc_n_samples(I, B, T);
+    double *X = (double *)malloc(sizeof(double) * (size_t)L * P);
+    double *LL = (double *)malloc(sizeof(double) * L);
+    long *acc = (long *)calloc((size_t)L, sizeof(long));
+    long *bad = (long *)calloc((size_t)L, sizeof(long));
+    int *npool = (int *)calloc((size_t)L, sizeof(int));
+    uint32_t w[64];
+    double Yp[64];
+
+    for (int k = 0; k < L; ++k) {
+        double *xk = X + (size_t)k * P;
+        if (x0v) {
+            for (int p = 0; p < P; ++p) xk[p] = clampd((double)x0v[(size_t)k * P + p], m->lb[p], m->ub[p]);
+        } else {
+            orc_words(o->seed, ORC_INIT_ITER, vg, (uint32_t)k, P, w);
+            for (int p = 0; p < P; ++p) xk[p] = m->lb[p] + (m->ub[p] - m->lb[p]) * orc_u01(w[p]);
+        }
+        LL[k] = orc_loglik(m->kind, m->acq, m->n_acq, xk, y, sigma);
+    }
+    if (path) memcpy(path, X, sizeof(double) * (size_t)L * P);
+    for (int t = 1; t <= I; ++t) {
+        for (int h = 0; h < 2; ++h) {
+            int other = (1 - h) * H;
+            for (int i = 0; i < H; ++i) {
+                int k = h * H + i;
+                orc_words(o->seed, (uint32_t)t, vg, (uint32_t)k, 3, w);
+                int j = other + (int)(((uint64_t)w[0] * (uint64_t)H) >> 32);
+                double z = orc_stretch_z(w[1], a);
+                const double *xk = X + (size_t)k * P, *xj = X + (size_t)j * P;
+                int inside = 1;
+                for (int p = 0; p < P; ++p) {
+                    Yp[p] = xj[p] + z * (xk[p] - xj[p]);
+                    if (!(Yp[p] >= m->lb[p] && Yp[p] <= m->ub[p])) inside = 0;
+                }
+                if (!inside) continue;
+                double Ly = orc_loglik(m->kind, m->acq, m->n_acq, Yp, y, sigma);
+                if (!isfinite(Ly)) ++bad[k];
+                double log_u = log(orc_u01(w[2]));
+                if (log_u < (double)(P - 1) * log(z) + Ly - LL[k]) {
+                    memcpy(X + (size_t)k * P, Yp, sizeof(double) * P);
+                    LL[k] = Ly;
+                    ++acc[k];
+                }
+            }
+        }
+        if (path) memcpy(path + (size_t)t * L * P, X, sizeof(double) * (size_t)L * P);
+        int on_grid = (t > B) && ((t - B) % T == 0);
+        int take = (o->moments_mode == 1) ? (t > B) : on_grid;
+        for (int k = 0; k < L; ++k) {
+            const double *xk = X + (size_t)k * P;
+            if (on_grid && samples) {
+                int idx = (t - B) / T - 1;
+                if (idx < S)
+                    for (int p = 0; p < P; ++p) samples[(((size_t)idx * L + k) * P + p) * n_vox + v] = xk[p];
+            }
+            if (take && pooled && npool[k] < per_chain) {
+                double *blk = pooled + (size_t)k * per_chain * P;
+                for (int p = 0; p < P; ++p) blk[(size_t)p * per_chain + npool[k]] = xk[p];
+                ++npool[k];
+            }
+        }
+    }
+    for (int k = 0; k < L; ++k) {
+        if (accept_rate) accept_rate[(size_t)k * n_vox + v] = I > 0 ? (double)acc[k] / (double)I : 0.0;
+        if (nonfinite) nonfinite[(size_t)k * n_vox + v] = (int32_t)bad[k];
+    }
+    free(X); free(LL); free(acc); free(bad); free(npool);
+}
+
+/* Ensemble run over n_vox voxels; o->n_chains = walkers L (even, >= 4),
+ * a = stepSize > 1.  Same inputs and outputs as orc_mcmc_run. */
+int orc_ensemble_run(const orc_model *m, const float *data, int64_t n_vox, const float *sigma,
+                     float sigma_scalar, const float *x0, const orc_opts *o, double a, double *mean,
+                     double *std, double *samples, double *accept_rate, int32_t *nonfinite,
+                     int *threads_used) {
+    int P = m->n_par;
+    if (P != orc_n_par(m->kind) || P > 64 || o->n_chains < 4 || (o->n_chains & 1) ||
+        o->n_chains > 256 || o->iterations < 0 || o->burnin < 0 || o->thin < 1 || n_vox < 0 || !(a > 1.0))
+        return -1;
+    int M = orc_n_meas(m->kind, m->n_acq);
+    int L = o->n_chains, I = o->iterations, B = o->burnin;
+    int S = orc_n_samples(I, B, o->thin);
+    int per_chain = (o->moments_mode == 1) ? (I > B ? I - B : 0) : S;
+    int nt = 1;
+#ifdef _OPENMP
+    nt = o->n_threads > 0 ? o->n_threads : omp_get_max_threads();
+#endif
+    if (threads_used) *threads_used = nt;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int64_t v = 0; v < n_vox; ++v) {
+        size_t n_all = (size_t)L * per_chain;
+        double *pooled = (double *)malloc(sizeof(double) * (n_all * P + 1));
+        ensemble_voxel(m, data + (size_t)v * M, sigma ? (double)sigma[v] : (double)sigma_scalar,
+                       x0 ? x0 + (size_t)v * L * P : NULL, o, a,
+                       (uint32_t)(o->voxel_base + (uint64_t)v), v, n_vox, samples, pooled, per_chain,
+                       accept_rate, nonfinite, NULL);
+        pooled_moments(pooled, L, per_chain, P, v, n_vox, mean, std);
+        free(pooled);
+    }
+    return 0;
+}
+
+/* Every walker's state after each iteration t = 0..I of one voxel: path
+ * [I+1][L][P]. */
+int orc_ensemble_path(const orc_model *m, const float *y, double sigma, const float *x0v,
+                      const orc_opts *o, double a, uint64_t voxel, double *path, double *accept_rate) {
+    if (m->n_par != orc_n_par(m->kind) || o->n_chains < 4 || (o->n_chains & 1) || !(a > 1.0)) return -1;
+    ensemble_voxel(m, y, sigma, x0v, o, a, (uint32_t)(o->voxel_base + voxel), 0, 1, NULL, NULL, 0,
+                   accept_rate, NULL, path);
     return 0;
 }

@@ -1,0 +1,257 @@
+// Affine-invariant ensemble sampler (the paper's second mcmc.m algorithm,
+// Sec. 2.2.2: Nwalkers walkers, one stepSize).  Goodman & Weare's stretch
+// move with the two-halves parallel update (Foreman-Mackey et al. 2013):
+// walkers 0..H-1 (H = L/2) form half 0 and H..L-1 half 1; iteration t moves
+// every walker of half 0 against the current half 1, then every walker of
+// half 1 against the updated half 0.  Walker k uses one Philox call with
+// counter (t, voxel, k << 8, 0): word 0 picks its partner j in the other half
+// (floor(w0 H / 2^32)), word 1 the stretch z = ((a-1) u + 1)^2 / a, word 2 the
+// acceptance uniform.  Proposal Y = X_j + z (X_k - X_j); outside the prior
+// box it is rejected, otherwise accepted iff log u < (P-1) log z + L(Y) - L(X_k).
+//
+// Layout: a block holds VB = floor(256 / H) voxels x H threads; thread i of
+// voxel lv owns walkers i and H + i.  The walkers' positions and
+// log-likelihoods live in shared memory ([VB][L][P] and [VB][L]); the two
+// half-steps of an iteration are separated by block barriers, so a half
+// reads only positions the other half finished writing.  The measurement
+// tile, the likelihood, the precision variants, thinning and the Welford
+// moments are those of the MH kernel.
+#pragma once
+#include "mh_kernel.cuh"
+
+namespace gac {
+
+struct EnsArgs {
+    float stretch;    // a > 1
+    double stretch_d;
+    int H;            // walkers per half
+};
+
+__host__ __device__ inline size_t ens_smem_bytes(int P, size_t r_bytes, size_t w_bytes, int VB, int L,
+                                                 int row_stride) {
+    return 2 * static_cast<size_t>(P) * VB * L * w_bytes  // Welford per walker
+           + static_cast<size_t>(VB) * L * P * r_bytes     // positions
+           + static_cast<size_t>(VB) * L * r_bytes         // log-likelihoods
+           + static_cast<size_t>(VB) * row_stride * sizeof(float);
+}
+
+template <int KIND, int PREC, bool TRACE>
+__global__ void __launch_bounds__(kBlock) ens_kernel(const ModelConst mc, const RunArgs ra, const EnsArgs ea) {
+    using R = typename PrecTraits<PREC>::R;
+    using W = typename PrecTraits<PREC>::W;
+    constexpr int P = model_n_par(KIND);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+
+    const int L = ra.C, H = ea.H, VB = ra.vox_per_block, M = mc.n_meas;
+    const int nw = VB * L;  // walkers per block
+    W *wf_mean = reinterpret_cast<W *>(smem_raw);   // [P][nw]
+    W *wf_m2 = wf_mean + P * nw;                     // [P][nw]
+    R *X = reinterpret_cast<R *>(wf_m2 + P * nw);    // [VB][L][P]
+    R *LL = X + nw * P;                              // [VB][L]
+    float *ytile = reinterpret_cast<float *>(LL + nw);
+
+    const int tid = threadIdx.x;
+    const int lv = tid / H;
+    const int i = tid - lv * H;
+    const bool lane_used = tid < VB * H;
+
+    for (int64_t tile = blockIdx.x; tile < ra.n_tiles; tile += gridDim.x) {
+        const int64_t v0 = tile * VB;
+        const int64_t left = ra.n_vox - v0;
+        const int nv = left < VB ? static_cast<int>(left) : VB;
+        __syncthreads();
+        {
+            const float *src = ra.data + v0 * M;
+            for (int e = tid; e < nv * M; e += blockDim.x) {
+                const int row = e / M, col = e - row * M;
+                ytile[row * ra.row_stride + col] = __ldg(src + e);
+            }
+        }
+        __syncthreads();
+        const bool active = lane_used && lv < nv;
+        const int64_t v = v0 + lv;
+        const uint32_t vg = static_cast<uint32_t>(ra.voxel_base + static_cast<uint64_t>(active ? v : 0));
+        const float *y = ytile + lv * ra.row_stride;
+        R inv_s2 = R(1);
+        if (active) {
+            const float sig = ra.sigma ? __ldg(ra.sigma + v) : ra.sigma_scalar;
+            inv_s2 = R(1) / (R(sig) * R(sig));
+        }
+        int n_acc[2] = {0, 0}, n_bad[2] = {0, 0};
+
+        // initial walkers (prior draw at counter iteration 0xFFFFFFFF, or x0)
+        if (active) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = h * H + i;
+                R *xk = X + (lv * L + k) * P;
+                if (ra.x0) {
+                    const float *x0 = ra.x0 + (v * L + k) * P;
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        if constexpr (PREC == GAC_PREC_FP64)
+                            xk[p] = fmin(fmax(static_cast<double>(x0[p]), mc.lb_d[p]), mc.ub_d[p]);
+                        else
+                            xk[p] = fminf(fmaxf(x0[p], mc.lb_f[p]), mc.ub_f[p]);
+                    }
+                } else {
+                    uint32_t w0[4 * ((P + 3) / 4)];
+                    draw_words(w0, kInitIteration, vg, static_cast<uint32_t>(k), ra.k0, ra.k1);
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        if constexpr (PREC == GAC_PREC_FP64)
+                            xk[p] = mc.lb_d[p] + (mc.ub_d[p] - mc.lb_d[p]) * u01_d(w0[p]);
+                        else
+                            xk[p] = fmaf(mc.ub_f[p] - mc.lb_f[p], u01_f(w0[p]), mc.lb_f[p]);
+                    }
+                }
+                R th[P];
+#pragma unroll
+                for (int p = 0; p < P; ++p) th[p] = xk[p];
+                LL[lv * L + k] = loglik_any<KIND, PREC>(th, y, inv_s2, mc);
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    wf_mean[p * nw + lv * L + k] = W(0);
+                    wf_m2[p * nw + lv * L + k] = W(0);
+                }
+            }
+        }
+        const bool all_mode = ra.moments_mode == GAC_MOMENTS_ALL_POSTBURNIN;
+        int n_mom = 0;
+        int to_thin = ra.B + ra.T;
+        for (int t = 1; t <= ra.I; ++t) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                __syncthreads();  // the other half's positions are final
+                if (active) {
+                    const int k = h * H + i;
+                    uint32_t w[4];
+                    draw_words(w, static_cast<uint32_t>(t), vg, static_cast<uint32_t>(k), ra.k0, ra.k1);
+                    const int j = (1 - h) * H + static_cast<int>((static_cast<uint64_t>(w[0]) * H) >> 32);
+                    R z;
+                    if constexpr (PREC == GAC_PREC_FP64) {
+                        const double s = (ea.stretch_d - 1.0) * u01_d(w[1]) + 1.0;
+                        z = s * s / ea.stretch_d;
+                    } else {
+                        const float s = fmaf(ea.stretch - 1.0f, u01_f(w[1]), 1.0f);
+                        z = s * s / ea.stretch;
+                    }
+                    const R *xk = X + (lv * L + k) * P;
+                    const R *xj = X + (lv * L + j) * P;
+                    R th[P], prop[P];
+                    bool inside = true;
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        th[p] = xk[p];
+                        const R xjp = xj[p];
+                        if constexpr (PREC == GAC_PREC_FP64) {
+                            prop[p] = fma(z, th[p] - xjp, xjp);
+                            inside = inside && prop[p] >= mc.lb_d[p] && prop[p] <= mc.ub_d[p];
+                        } else {
+                            prop[p] = fmaf(z, th[p] - xjp, xjp);
+                            inside = inside && prop[p] >= mc.lb_f[p] && prop[p] <= mc.ub_f[p];
+                        }
+                    }
+                    const R Lk = LL[lv * L + k];
+                    R Lp = R(0);
+                    bool acc = false;
+                    if (inside) {
+                        Lp = loglik_any<KIND, PREC>(prop, y, inv_s2, mc);
+                        n_bad[h] += !isfinite(Lp);
+                        // log u < (P - 1) log z + L(Y) - L(X_k): the z factor
+                        // enters as an offset of the likelihood difference
+                        R logz_term;
+                        if constexpr (PREC == GAC_PREC_FP64) logz_term = (P - 1) * log(z);
+                        else logz_term = static_cast<float>(P - 1) * logf(z);
+                        acc = accept_step<PREC>(Lp + logz_term, Lk, w[2]);
+                    }
+                    if constexpr (TRACE) {
+                        if (v < ra.trace_n) {
+                            gac_trace_rec *rec = ra.trace + (v * L + k) * static_cast<int64_t>(ra.I) + (t - 1);
+#pragma unroll
+                            for (int p = 0; p < P; ++p) {
+                                rec->theta[p] = static_cast<double>(th[p]);
+                                rec->prop[p] = static_cast<double>(prop[p]);
+                            }
+                            rec->L = static_cast<double>(Lk);
+                            rec->Lp = inside ? static_cast<double>(Lp) : __longlong_as_double(0x7ff8000000000000ll);
+                            rec->w_acc = w[2];
+                            rec->accepted = acc ? 1 : 0;
+                        }
+                    }
+                    if (acc) {
+                        R *xw = X + (lv * L + k) * P;
+#pragma unroll
+                        for (int p = 0; p < P; ++p) xw[p] = prop[p];
+                        LL[lv * L + k] = Lp;
+                        ++n_acc[h];
+                    }
+                }
+            }
+            // thinning grid and moments (own walkers' positions are final)
+            const bool on_grid = (t == to_thin);
+            if (on_grid) to_thin += ra.T;
+            const bool take = all_mode ? (t > ra.B) : on_grid;
+            if (active && (on_grid || take)) {
+                if (take) ++n_mom;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = h * H + i;
+                    const R *xk = X + (lv * L + k) * P;
+                    if (on_grid && ra.samples) {
+                        const int s = (t - ra.B) / ra.T - 1;
+                        float *dst = ra.samples + ((static_cast<int64_t>(s) * L + k) * P) * ra.n_vox + v;
+#pragma unroll
+                        for (int p = 0; p < P; ++p) dst[p * ra.n_vox] = static_cast<float>(xk[p]);
+                    }
+                    if (take) {
+                        const W inv_n = W(1) / W(n_mom);
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            const W x = static_cast<W>(xk[p]);
+                            const int q = p * nw + lv * L + k;
+                            W m = wf_mean[q];
+                            const W d = x - m;
+                            m += d * inv_n;
+                            wf_mean[q] = m;
+                            wf_m2[q] += d * (x - m);
+                        }
+                    }
+                }
+            }
+        }
+        if (active) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = h * H + i;
+                if (ra.accept) ra.accept[k * ra.n_vox + v] = ra.I > 0 ? float(n_acc[h]) / float(ra.I) : 0.0f;
+                if (ra.nonfinite) ra.nonfinite[k * ra.n_vox + v] = n_bad[h];
+            }
+        }
+        __syncthreads();
+        // pool the walkers of each voxel in walker order
+        if (active && i == 0 && (ra.mean || ra.std)) {
+            const int n_each = all_mode ? max(ra.I - ra.B, 0) : ra.S;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const int q0 = p * nw + lv * L;
+                W mu = wf_mean[q0];
+                W m2 = wf_m2[q0];
+                double n = n_each;
+                for (int k = 1; k < L; ++k) {
+                    const double ntot = n + n_each;
+                    const W delta = wf_mean[q0 + k] - mu;
+                    mu += delta * W(n_each / ntot);
+                    m2 += wf_m2[q0 + k] + delta * delta * W(n * n_each / ntot);
+                    n = ntot;
+                }
+                const double nan = __longlong_as_double(0x7ff8000000000000ll);
+                if (ra.mean) ra.mean[p * ra.n_vox + v] = n > 0 ? static_cast<double>(mu) : nan;
+                if (ra.std)
+                    ra.std[p * ra.n_vox + v] = n > 1 ? sqrt(static_cast<double>(m2) / (n - 1.0)) : (n == 1 ? 0.0 : nan);
+            }
+        }
+    }
+}
+
+}  // namespace gac

@@ -110,6 +110,31 @@ gac_status DevBuf::copy_out() {
 
 int n_samples(int I, int B, int T) { return (T > 0 && I > B) ? (I - B) / T : 0; }
 
+// Host buffers are staged through the device's default stream-ordered
+// memory pool.  Let the pool keep what a call frees (instead of returning it
+// to the driver at every synchronisation), so that repeated calls with host
+// buffers do not map gigabytes of staging memory anew each time.  Done once
+// per device; a caller that needs the memory back can call cudaMemPoolTrimTo
+// on the device's default pool.
+void keep_staging_pool() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done[dev] = true;
+}
+
 // ----------------------------------------------------- launch sizing -------
 static int sm_count() {
     static int n = 0;
@@ -283,13 +308,25 @@ gac_status gac_model_register(const gac_model_desc *d, int *model_id) {
             mc.dtk_f = static_cast<float>(kAnchor * dt);
         }
     }
-    // g(-y) = sum_n y^n / (n! (2n+1)) rewritten in u = y / 12: c_n = 12^n / (n! (2n+1))
+    // g(-y) = sum_n y^n / (n! (2n+1)) rewritten in u = y / y_max: c_n = y_max^n / (n! (2n+1)),
+    // y_max = the largest -x = -b (De_par - De_perp) or -b Da the bounds allow
     {
-        double pw = 1.0;  // 12^n / n!
+        double ymax = 1e-3;
+        if (d->kind == GAC_MODEL_SMT)
+            for (int k = 0; k < d->n_acq; ++k)
+                ymax = std::max({ymax, d->acq[k] * (d->ub[3] - d->lb[2]), d->acq[k] * (-d->lb[1])});
+        double pw = 1.0, sum = 0.0;  // y_max^n / n!
+        double c[kSeriesDegree + 1];
         for (int n = 0; n <= kSeriesDegree; ++n) {
-            if (n > 0) pw *= static_cast<double>(kSeriesYMax) / n;
-            mc.gser_f[n] = static_cast<float>(pw / (2.0 * n + 1.0));
+            if (n > 0) pw *= ymax / n;
+            c[n] = pw / (2.0 * n + 1.0);
+            sum += c[n];
         }
+        int deg = kSeriesDegree;
+        while (deg > 1 && c[deg] < 1e-9 * sum) --deg;
+        for (int n = 0; n <= kSeriesDegree; ++n) mc.gser_f[n] = n <= deg ? static_cast<float>(c[n]) : 0.0f;
+        mc.gser_inv_ymax = static_cast<float>(1.0 / ymax);
+        mc.gser_degree = deg;
     }
     std::lock_guard<std::mutex> lk(g_reg_mu);
     if (g_models.size() >= GAC_MAX_MODELS)
@@ -346,6 +383,7 @@ gac_status gac_mcmc_run(int model_id, const void *data, int64_t n_vox, const flo
     if (n_vox == 0) return GAC_OK;
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    keep_staging_pool();
     const int P = mc.n_par, C = o->n_chains, M = mc.n_meas;
     const int S = n_samples(o->iterations, o->burnin, o->thin);
     const size_t N = static_cast<size_t>(n_vox);

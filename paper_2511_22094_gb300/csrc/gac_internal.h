@@ -17,6 +17,7 @@ bool is_device_ptr(const void *p);
 int n_samples(int I, int B, int T);
 gac_status validate_opts(const gac_mcmc_opts *o, int64_t n_vox);
 int row_stride_for(int kind, int M);
+void keep_staging_pool();
 
 // Device view of a caller buffer (see DevBuf::make in gac.cu).
 struct DevBuf {

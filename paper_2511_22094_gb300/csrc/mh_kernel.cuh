@@ -45,10 +45,13 @@
 namespace gac {
 
 constexpr int kBlock = 256;
-// Blocks per SM the FP32/MIXED kernels are compiled for (register cap).
-#ifndef GAC_MH_MIN_BLOCKS
-#define GAC_MH_MIN_BLOCKS 2
-#endif
+// Blocks per SM each kernel is compiled for (a register cap): the 3-pool
+// model needs ~118 registers (2 blocks of 256), the lighter models fit 3
+// blocks; FP64 paths are left uncapped.
+template <int KIND, int PREC>
+constexpr int mh_min_blocks() {
+    return PREC == GAC_PREC_FP64 ? 1 : (KIND == GAC_MODEL_MWI3 ? 2 : 3);
+}
 
 struct RunArgs {
     const float *data;   // [N][M]
@@ -389,7 +392,7 @@ __device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra
 
 // One job, one launch: every tile runs all I iterations.
 template <int KIND, int PREC, bool TRACE>
-__global__ void __launch_bounds__(kBlock, PREC == GAC_PREC_FP64 ? 1 : GAC_MH_MIN_BLOCKS)
+__global__ void __launch_bounds__(kBlock, mh_min_blocks<KIND, PREC>())
     mh_kernel(const ModelConst mc, const RunArgs ra) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SliceState none{};

@@ -28,7 +28,7 @@ namespace gac {
 
 constexpr int kAnchor = 6;
 constexpr float kSinCosMaxArg = 6000.0f;  // |x| bound of sincos_cw (registration checks it)
-constexpr int kSeriesDegree = 40;     // g(x) series for x < 0 in u = -x / kSeriesYMax
+constexpr int kSeriesDegree = 40;     // max degree of the g(x) series for x < 0
 constexpr float kSeriesYMax = 12.0f;  // registration keeps -x <= 12
 
 struct ModelConst {
@@ -42,8 +42,12 @@ struct ModelConst {
     double acq_d[GAC_MAX_ACQ];
     float lb_f[GAC_MAX_PAR], ub_f[GAC_MAX_PAR], step_f[GAC_MAX_PAR];
     double lb_d[GAC_MAX_PAR], ub_d[GAC_MAX_PAR], step_d[GAC_MAX_PAR];
-    // coefficients of g(-y) = sum_n c_n (y / kSeriesYMax)^n, c_n = 12^n / (n! (2n+1))
+    // g(-y) = sum_n c_n (y / y_max)^n, c_n = y_max^n / (n! (2n+1)), for
+    // 0 <= y <= y_max (the largest negative argument the bounds allow);
+    // terms above gser_degree are below 1e-9 of the sum and stored as 0
     float gser_f[kSeriesDegree + 1];
+    float gser_inv_ymax;
+    int gser_degree;
 };
 
 __host__ __device__ constexpr int model_n_par(int kind) {
@@ -63,14 +67,17 @@ constexpr double kSqrtPiHalfD = 0.886226925452758014;
 __device__ __forceinline__ float smt_g_f(float x, const ModelConst &mc) {
     if (x > 0.0f) {
         if (x < 1e-30f) return 1.0f;
-        const float s = sqrtf(x);
-        return kSqrtPiHalf * erff(s) / s;
+        // sqrt(pi)/2 erf(s)/s with s = sqrt(x): one reciprocal square root
+        // (SFU, ~2 ulp) gives both s = x rsqrt(x) and 1/s
+        const float rs = rsqrtf(x);
+        return kSqrtPiHalf * erff(x * rs) * rs;
     }
-    // x <= 0: all-positive power series, Horner in u = -x / 12 in [0, 1]
-    const float u = -x * (1.0f / kSeriesYMax);
-    float p = mc.gser_f[kSeriesDegree];
-#pragma unroll 8
-    for (int n = kSeriesDegree - 1; n >= 0; --n) p = fmaf(p, u, mc.gser_f[n]);
+    // x <= 0: all-positive power series of g(-y), Horner in u = -x / y_max
+    // in [0, 1] with the degree the registered range needs
+    const float u = -x * mc.gser_inv_ymax;
+    float p = mc.gser_f[mc.gser_degree];
+#pragma unroll 4
+    for (int n = mc.gser_degree - 1; n >= 0; --n) p = fmaf(p, u, mc.gser_f[n]);
     return p;
 }
 
@@ -119,6 +126,35 @@ __device__ __forceinline__ void sincos_cw(float x, float &sn, float &cs) {
     cs = ((n + 1) & 2) ? -b : b;
 }
 
+// Paired FP32 arithmetic (Blackwell's two-lane FFMA2/FADD2/FMUL2): each lane
+// performs exactly the operation of the scalar code, so results are
+// bit-identical while two values take one instruction.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// sincos_cw on both lanes of x.
+__device__ __forceinline__ void sincos_cw2(float2 x, float2 &sn, float2 &cs) {
+    const float2 qx = __fmul2_rn(x, f2(0.636619772367581343f));
+    const float2 q = make_float2(rintf(qx.x), rintf(qx.y));
+    float2 r = __ffma2_rn(q, f2(-1.5703125f), x);
+    r = __ffma2_rn(q, f2(-4.837512969970703125e-4f), r);
+    r = __ffma2_rn(q, f2(-7.549790126404332e-8f), r);
+    const float2 r2 = __fmul2_rn(r, r);
+    float2 ps = __ffma2_rn(r2, f2(2.75573192e-6f), f2(-1.98412698e-4f));
+    ps = __ffma2_rn(ps, r2, f2(8.33333333e-3f));
+    ps = __ffma2_rn(ps, r2, f2(-1.66666667e-1f));
+    const float2 sr = __ffma2_rn(__fmul2_rn(ps, r2), r, r);
+    float2 pc = __ffma2_rn(r2, f2(-2.75573192e-7f), f2(2.48015873e-5f));
+    pc = __ffma2_rn(pc, r2, f2(-1.38888889e-3f));
+    pc = __ffma2_rn(pc, r2, f2(4.16666667e-2f));
+    pc = __ffma2_rn(pc, r2, f2(-0.5f));
+    const float2 cr = __ffma2_rn(pc, r2, f2(1.0f));
+    const int n0 = static_cast<int>(q.x), n1 = static_cast<int>(q.y);
+    const float a0 = (n0 & 1) ? cr.x : sr.x, b0 = (n0 & 1) ? sr.x : cr.x;
+    const float a1 = (n1 & 1) ? cr.y : sr.y, b1 = (n1 & 1) ? sr.y : cr.y;
+    sn = make_float2((n0 & 2) ? -a0 : a0, (n1 & 2) ? -a1 : a1);
+    cs = make_float2(((n0 + 1) & 2) ? -b0 : b0, ((n1 + 1) & 2) ? -b1 : b1);
+}
+
 // ----------------------------------------------------------- FP32 models --
 template <class V>
 __device__ __forceinline__ void eval_monoexp_f(const float *th, const ModelConst &mc, V &&visit) {
@@ -153,67 +189,50 @@ __device__ __forceinline__ void eval_mwi3_f(const float *th, const ModelConst &m
     const float phi0 = th[8];
     const int n = mc.n_acq;
     if (mc.even) {
-        // per pool: E_0 = A exp(-t0/T2*) e^{i(phi0 - w t0)}, R = exp(-dt (1/T2* + i w)), R^K
-        float er[3], ei[3], rr[3], ri[3], kr[3], ki[3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const float rate = 1.0f / th[3 + j];
-            const float w = (j < 2) ? kTwoPiMilli * th[6 + j] : 0.0f;  // rad / ms
-            const float m0 = th[j] * expf(-mc.t0_f * rate);
-            float s, c;
-            sincos_cw(fmaf(-w, mc.t0_f, phi0), s, c);
-            er[j] = m0 * c;
-            ei[j] = m0 * s;
-            const float m1 = expf(-mc.dt_f * rate);
-            const float mk = expf(-mc.dtk_f * rate);
-            if (j < 2) {
-                sincos_cw(-w * mc.dt_f, s, c);
-                rr[j] = m1 * c;
-                ri[j] = m1 * s;
-                sincos_cw(-w * mc.dtk_f, s, c);
-                kr[j] = mk * c;
-                ki[j] = mk * s;
-            } else {  // extra-cellular pool: no frequency offset, real ratio
-                rr[j] = m1;
-                ri[j] = 0.0f;
-                kr[j] = mk;
-                ki[j] = 0.0f;
-            }
-        }
+        // Per pool: E_0 = A exp(-t0/T2*) e^{i(phi0 - w t0)}, R = exp(-dt (1/T2* + i w))
+        // and R^K.  The myelin- and intra-axonal pools (which have frequency
+        // offsets) are carried as lane pairs: X = (Re E_MW, Re E_IW),
+        // Y = (Im E_MW, Im E_IW); the extra-cellular pool, whose ratio R is
+        // real, as Z = (Re E_EW, Im E_EW).
+        const float rate0 = 1.0f / th[3], rate1 = 1.0f / th[4], rate2 = 1.0f / th[5];
+        const float2 w = make_float2(kTwoPiMilli * th[6], kTwoPiMilli * th[7]);  // rad / ms
+        const float2 m0 = make_float2(th[0] * expf(-mc.t0_f * rate0), th[1] * expf(-mc.t0_f * rate1));
+        const float2 m1 = make_float2(expf(-mc.dt_f * rate0), expf(-mc.dt_f * rate1));
+        const float2 mk = make_float2(expf(-mc.dtk_f * rate0), expf(-mc.dtk_f * rate1));
+        float2 s, c;
+        sincos_cw2(__ffma2_rn(make_float2(-w.x, -w.y), f2(mc.t0_f), f2(phi0)), s, c);
+        float2 X = __fmul2_rn(m0, c), Y = __fmul2_rn(m0, s);
+        sincos_cw2(__fmul2_rn(make_float2(-w.x, -w.y), f2(mc.dt_f)), s, c);
+        const float2 RR = __fmul2_rn(m1, c), RI = __fmul2_rn(m1, s);
+        const float2 NRI = make_float2(-RI.x, -RI.y);
+        sincos_cw2(__fmul2_rn(make_float2(-w.x, -w.y), f2(mc.dtk_f)), s, c);
+        const float2 KR = __fmul2_rn(mk, c), KI = __fmul2_rn(mk, s);
+        const float2 NKI = make_float2(-KI.x, -KI.y);
+        float se, ce;
+        sincos_cw(phi0, se, ce);
+        const float m2 = th[2] * expf(-mc.t0_f * rate2);
+        float2 Z = make_float2(m2 * ce, m2 * se);
+        const float2 R2 = f2(expf(-mc.dt_f * rate2));
+        const float2 K2 = f2(expf(-mc.dtk_f * rate2));
         // one block of echoes a .. a+cnt-1 from the current anchors
         auto block = [&](int a, int cnt, bool full) {
-            float cr[3], ci[3];
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                cr[j] = er[j];
-                ci[j] = ei[j];
-            }
+            float2 x = X, y = Y, z = Z;
 #pragma unroll
             for (int i = 0; i < kAnchor; ++i) {
-                if (full || i < cnt) visit(a + i, cr[0] + cr[1] + cr[2], ci[0] + ci[1] + ci[2]);
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const float nr = fmaf(cr[j], rr[j], -ci[j] * ri[j]);
-                    const float ni = fmaf(cr[j], ri[j], ci[j] * rr[j]);
-                    cr[j] = nr;
-                    ci[j] = ni;
-                }
-                cr[2] *= rr[2];
-                ci[2] *= rr[2];
+                if (full || i < cnt) visit(a + i, x.x + x.y + z.x, y.x + y.y + z.y);
+                const float2 xn = __ffma2_rn(x, RR, __fmul2_rn(y, NRI));
+                y = __ffma2_rn(x, RI, __fmul2_rn(y, RR));
+                x = xn;
+                z = __fmul2_rn(z, R2);
             }
         };
         int a = 0;
         for (; a + kAnchor <= n; a += kAnchor) {
             block(a, kAnchor, true);
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const float nr = fmaf(er[j], kr[j], -ei[j] * ki[j]);
-                const float ni = fmaf(er[j], ki[j], ei[j] * kr[j]);
-                er[j] = nr;
-                ei[j] = ni;
-            }
-            er[2] *= kr[2];
-            ei[2] *= kr[2];
+            const float2 xn = __ffma2_rn(X, KR, __fmul2_rn(Y, NKI));
+            Y = __ffma2_rn(X, KI, __fmul2_rn(Y, KR));
+            X = xn;
+            Z = __fmul2_rn(Z, K2);
         }
         if (a < n) block(a, n - a, false);
     } else {
@@ -245,6 +264,10 @@ __device__ __forceinline__ void eval_smt_f(const float *th, const ModelConst &mc
     const float ddiff = dpar - dperp;
     for (int k = 0; k < mc.n_acq; ++k) {
         const float b = mc.acq_f[k];
+        if (b == 0.0f) {  // S(b = 0) = S0 = 1 (same b for every thread: no divergence)
+            visit(k, 1.0f);
+            continue;
+        }
         const float intra = smt_g_f(b * da, mc);
         const float extra = expf(-b * dperp) * smt_g_f(b * ddiff, mc);
         visit(k, fmaf(f, intra, (1.0f - f) * extra));
@@ -344,9 +367,8 @@ __device__ __forceinline__ float loglik_f(const float *th, const float *y, float
     if constexpr (model_complex(KIND)) {
         eval_f<KIND>(th, mc, [&](int k, float sr, float si) {
             const float2 yk = reinterpret_cast<const float2 *>(y)[k];
-            const float dr = yk.x - sr;
-            const float di = yk.y - si;
-            acc.add(fmaf(dr, dr, di * di));
+            const float2 d = __ffma2_rn(make_float2(sr, si), f2(-1.0f), yk);  // y - s, both parts
+            acc.add(fmaf(d.x, d.x, d.y * d.y));
         });
     } else {
         eval_f<KIND>(th, mc, [&](int k, float s) {

@@ -69,7 +69,7 @@ EXPORTS = ["gac_model_register", "gac_model_info", "gac_result_sizes", "gac_mcmc
            "gac_forward", "gac_loglik", "gac_philox_words", "gac_normals", "gac_last_error",
            "gac_version", "gac_server_create", "gac_server_job_bytes", "gac_server_submit",
            "gac_server_poll", "gac_server_wait", "gac_server_cancel", "gac_server_get_stats",
-           "gac_server_destroy", "gac_mcmc_run_noalloc"]
+           "gac_server_destroy", "gac_mcmc_run_noalloc", "gac_ensemble_run"]
 NOALLOC_STATE_BYTES = 64 << 20
 
 
@@ -90,6 +90,8 @@ def _load():
         "gac_loglik": [ct.c_int, vp, i64, vp, vp, ct.c_int, vp, vp],
         "gac_philox_words": [u64, vp, vp, vp, i64, ct.c_int, vp, vp],
         "gac_normals": [u64, vp, vp, vp, i64, ct.c_int, ct.c_int, vp, vp, vp],
+        "gac_ensemble_run": [ct.c_int, vp, i64, vp, ct.c_float, vp, ct.POINTER(McmcOpts), ct.c_double,
+                             ct.POINTER(Result), vp],
         "gac_mcmc_run_noalloc": [ct.c_int, vp, i64, vp, ct.c_float, vp, ct.POINTER(McmcOpts), ct.c_int,
                                  ct.POINTER(Result), vp],
         "gac_server_create": [ct.c_size_t, ct.c_int, ct.POINTER(vp)],
@@ -190,6 +192,16 @@ def gac_mcmc_run(model_id: int, data, n_vox: int, sigma, sigma_scalar: float, x0
                                              "trace")))
     _check(_lib.gac_mcmc_run(model_id, _ptr(data), n_vox, _ptr(sigma), sigma_scalar, _ptr(x0),
                              ct.byref(opts), ct.byref(r), _stream(stream)), "gac_mcmc_run")
+
+
+def gac_ensemble_run(model_id: int, data, n_vox: int, sigma, sigma_scalar: float, x0,
+                     opts: McmcOpts, stretch: float, out: dict, stream=None):
+    """Affine-invariant ensemble sampler; opts.n_chains = walkers."""
+    r = Result(*(_ptr(out.get(k)) for k in ("mean", "std", "samples", "accept_rate", "nonfinite",
+                                             "trace")))
+    _check(_lib.gac_ensemble_run(model_id, _ptr(data), n_vox, _ptr(sigma), sigma_scalar, _ptr(x0),
+                                 ct.byref(opts), stretch, ct.byref(r), _stream(stream)),
+           "gac_ensemble_run")
 
 
 def gac_mcmc_run_noalloc(model_id: int, data, n_vox: int, sigma, sigma_scalar: float, x0,
@@ -308,6 +320,28 @@ def run_host(model_id: int, data: np.ndarray, sigma, *, iterations, burnin, thin
     opts = make_opts(iterations, burnin, thin, n_chains, seed, voxel_base, precision, moments_mode,
                      trace_n_vox)
     gac_mcmc_run(model_id, data, N, sig, sigma_scalar, x0a, opts, out)
+    return out
+
+
+def run_ensemble_host(model_id: int, data: np.ndarray, sigma, *, iterations, burnin, thin,
+                      n_walkers, seed, stretch=2.0, x0=None, sigma_scalar=0.0, voxel_base=0,
+                      precision=PREC_MIXED, moments_mode=MOMENTS_THINNED, trace_n_vox=0,
+                      want_samples=True):
+    """Ensemble sampler on host numpy inputs; host numpy outputs."""
+    P, M = gac_model_info(model_id)
+    data = np.ascontiguousarray(data, np.float32)
+    N = data.shape[0]
+    S = n_samples(iterations, burnin, thin)
+    L = n_walkers
+    out = dict(mean=np.full((P, N), np.nan), std=np.full((P, N), np.nan),
+               samples=np.full((S, L, P, N), np.nan, np.float32) if (want_samples and S) else None,
+               accept_rate=np.zeros((L, N), np.float32), nonfinite=np.zeros((L, N), np.int32),
+               trace=np.zeros((trace_n_vox, L, iterations), TRACE_DTYPE) if trace_n_vox else None)
+    sig = None if sigma is None else np.ascontiguousarray(sigma, np.float32)
+    x0a = None if x0 is None else np.ascontiguousarray(x0, np.float32)
+    opts = make_opts(iterations, burnin, thin, n_walkers, seed, voxel_base, precision, moments_mode,
+                     trace_n_vox)
+    gac_ensemble_run(model_id, data, N, sig, sigma_scalar, x0a, opts, stretch, out)
     return out
 
 

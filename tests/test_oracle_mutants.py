@@ -7,6 +7,7 @@ that kind of mistake.  A pin that still passed would not be pinning anything.
 import numpy as np
 import pytest
 
+import test_oracle_ensemble as E
 import test_oracle_models as M
 import test_oracle_rng as R
 import test_oracle_sampler as S
@@ -63,6 +64,14 @@ CASES = [
      S.test_thinning_grid_and_moments),
     ("MH without acceptance test", "if (log_u < Lp - L) {", "if (1) {",
      S.test_linear_gaussian_posterior),
+    ("ensemble z exponent", "(double)(P - 1) * log(z)", "(double)P * log(z)", E.test_every_walker_move),
+    ("ensemble partner from own half", "int other = (1 - h) * H;", "int other = h * H;",
+     E.test_every_walker_move),
+    ("ensemble stretch law", "double s = (a - 1.0) * orc_u01(w) + 1.0;",
+     "double s = (a - 1.0) * orc_u01(w) + 0.5;", lambda orc: E.test_stretch_distribution(orc, 2.0)),
+    ("ensemble prior box ignored", "if (!inside) continue;", "(void)inside;", E.test_every_walker_move),
+    ("ensemble stationary law (z^P)", "(double)(P - 1) * log(z)", "(double)P * log(z)",
+     E.test_linear_gaussian_posterior),
 ]
 
 
