@@ -43,6 +43,13 @@ OPS = {
     "smt_1p5m": dict(mufu=51, fp32=103, int=120),
     "monoexp_4k": dict(mufu=17, fp32=65, int=60),
 }
+# Ensemble walker-move counts: the same model evaluation, one Philox call, no
+# Box-Muller; the stretch z costs a log (MUFU) and a few FP32 ops.
+OPS_ENSEMBLE = {
+    "mwi3_1m": dict(mufu=221, fp32=490, int=60),
+    "smt_1p5m": dict(mufu=44, fp32=92, int=60),
+    "monoexp_4k": dict(mufu=14, fp32=64, int=60),
+}
 MUFU_PER_CLK_SM = 16
 FP32_PER_CLK_SM = 128
 
@@ -127,24 +134,30 @@ def _host_inputs_for_oracle(w, n):
     return y, sig
 
 
-def cpu_oracle_rate(w, target_s=15.0):
+def cpu_oracle_rate(w, target_s=15.0, sampler="mh", stretch=2.0):
     """Oracle (as it stands) on a bounded voxel sample of the workload, all
     host cores; returns (chain-iterations/s, threads, sample description)."""
     import oracle
     oracle.build()
-    kw = dict(iterations=w.iterations, burnin=w.burnin, thin=w.thin, n_chains=w.n_chains,
-              seed=w.mcmc_seed)
+    kw = dict(iterations=w.iterations, burnin=w.burnin, thin=w.thin, seed=w.mcmc_seed)
+
+    def run(y, sig):
+        if sampler == "ensemble":
+            return oracle.ensemble_run(w.kind, w.acq, w.lb, w.ub, y, sig, n_walkers=w.n_chains,
+                                       stretch=stretch, **kw)
+        return oracle.mcmc_run(w.kind, w.acq, w.lb, w.ub, w.step, y, sig, n_chains=w.n_chains, **kw)
+
     pilot = 8
     y, sig = _host_inputs_for_oracle(w, pilot)
     t0 = time.perf_counter()
-    oracle.mcmc_run(w.kind, w.acq, w.lb, w.ub, w.step, y, sig, **kw)
+    run(y, sig)
     per_vox = (time.perf_counter() - t0) / pilot
     threads = oracle.max_threads()
     n = int(max(threads, min(w.n_vox, target_s / max(per_vox, 1e-9))))
     n = max(threads, (n // threads) * threads)
     y, sig = _host_inputs_for_oracle(w, n)
     t0 = time.perf_counter()
-    r = oracle.mcmc_run(w.kind, w.acq, w.lb, w.ub, w.step, y, sig, **kw)
+    r = run(y, sig)
     dt = time.perf_counter() - t0
     ci = n * w.n_chains * w.iterations
     return ci / dt, r["threads"], f"first {n} of {w.n_vox} voxels, all {w.n_chains} chains x {w.iterations} iterations ({dt:.1f} s)"
@@ -157,7 +170,8 @@ def run_reference(args, w):
         return
     rates = []
     for i in range(args.warmup + args.steps):
-        rate, threads, sample = cpu_oracle_rate(w, target_s=max(5.0, 60.0 / max(args.steps + args.warmup, 1)))
+        rate, threads, sample = cpu_oracle_rate(w, target_s=max(5.0, 60.0 / max(args.steps + args.warmup, 1)),
+                                                sampler=args.sampler, stretch=args.stretch)
         if i >= args.warmup:
             rates.append(rate)
     value = float(np.median(rates))
@@ -213,7 +227,10 @@ def run_ours(args, w):
     opts = gac.make_opts(w.iterations, w.burnin, w.thin, C, w.mcmc_seed, voxel_base=base, precision=prec)
 
     def step():
-        gac.gac_mcmc_run(mid, y, N, sig, 0.0, None, opts, out, stream)
+        if args.sampler == "ensemble":
+            gac.gac_ensemble_run(mid, y, N, sig, 0.0, None, opts, args.stretch, out, stream)
+        else:
+            gac.gac_mcmc_run(mid, y, N, sig, 0.0, None, opts, out, stream)
 
     def barrier():
         if pg is not None:
@@ -252,12 +269,14 @@ def run_ours(args, w):
         hout = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
         h2d = hy.numel() * 4 + hs.numel() * 4
         d2h = sum(v.numel() * v.element_size() for v in hout.values())
-        gac.gac_mcmc_run(mid, hy, N, hs, 0.0, None, opts, hout, stream)  # warm the allocator
+        run = (lambda o: gac.gac_ensemble_run(mid, hy, N, hs, 0.0, None, opts, args.stretch, o, stream)) \
+            if args.sampler == "ensemble" else (lambda o: gac.gac_mcmc_run(mid, hy, N, hs, 0.0, None, opts, o, stream))
+        run(hout)  # warm the allocator
         torch.cuda.synchronize()
         reps = max(1, min(args.steps, 3))
         t0 = time.perf_counter()
         for _ in range(reps):
-            gac.gac_mcmc_run(mid, hy, N, hs, 0.0, None, opts, hout, stream)
+            run(hout)
             _ = float(hout["accept_rate"][0, 0])  # read the result on the host
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / reps
@@ -272,7 +291,8 @@ def run_ours(args, w):
     peaks = _peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     f_max = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
-    ops = OPS[w.name]
+    base_name = w.name.replace("_ensemble", "")
+    ops = (OPS_ENSEMBLE if args.sampler == "ensemble" else OPS)[base_name]
     ci_s = ci_per_step / kernel_s
     t_mufu = ops["mufu"] / (sms * MUFU_PER_CLK_SM * f_max)
     t_alu = (ops["fp32"] + ops["int"]) / (sms * FP32_PER_CLK_SM * f_max)
@@ -292,7 +312,8 @@ def run_ours(args, w):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"mixed": "f32+f64", "fp32": "f32", "fp64": "f64"}[args.precision],
             "data": "synthetic (seeded truths + Gaussian noise, signal from the library's forward model)",
-            "config": {"workload": w.name, "n_vox": N, "n_chains": C, "iterations": w.iterations,
+            "config": {"workload": w.name, "sampler": args.sampler, "n_vox": N,
+                       ("n_walkers" if args.sampler == "ensemble" else "n_chains"): C, "iterations": w.iterations,
                        "burnin": w.burnin, "thin": w.thin, "samples_stored": True,
                        "precision": args.precision, "parallelism": f"voxel-shard x{world}",
                        "l2": f"inputs {y.numel() * 4 / 1e6:.0f} MB + samples {S * C * P * N * 4 / 1e9:.1f} GB written per step > 129 MB L2"},
@@ -301,7 +322,7 @@ def run_ours(args, w):
     if e2e:
         line["e2e"] = e2e
     if not args.no_cpu_baseline:
-        rate, threads, sample = cpu_oracle_rate(w)
+        rate, threads, sample = cpu_oracle_rate(w, sampler=args.sampler, stretch=args.stretch)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": sample}
     print(json.dumps(line), flush=True)
@@ -428,6 +449,8 @@ def main():
     ap.add_argument("--workload", default="mwi3_1m", choices=sorted(W.WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", choices=("mixed", "fp32", "fp64"), default="mixed")
+    ap.add_argument("--sampler", choices=("mh", "ensemble"), default="mh")
+    ap.add_argument("--stretch", type=float, default=2.0, help="ensemble stepSize a")
     ap.add_argument("--n-vox", type=int, default=None, help="smaller case (profiling only)")
     ap.add_argument("--iterations", type=int, default=None, help="smaller case (profiling only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -439,6 +462,11 @@ def main():
         run_serving(args)
         return
     w = W.WORKLOADS[args.workload]
+    if args.sampler == "ensemble":
+        # Table 1: 50 walkers x 2,000 iterations, 10% burn-in, thinning 100, at the
+        # paper's largest speed-test size (2.5e5 voxels)
+        w = w.with_(name=w.name + "_ensemble", n_vox=min(w.n_vox, 250_000), n_chains=50,
+                    iterations=2000, burnin=200, thin=100)
     if args.n_vox is not None:
         w = w.with_(n_vox=args.n_vox)
     if args.iterations is not None:

@@ -77,29 +77,44 @@ def test_precision_study(gac, orc, snr):
             assert r["dmean_over_sd"]["frac_le_0.05"] >= min_frac, name
 
 
+def paired_seed_check(runs, pairs, label):
+    """Per-voxel mean over parameters of |mu_a - mu_b| / SD_b for the run
+    pairs (cpu_a, cpu_b) and (gpu_c, cpu_d) -- four independent random
+    streams.  Under "the GPU samples the same distribution as the CPU" the
+    two per-voxel statistics are exchangeable, so their paired difference has
+    mean 0 (checked within 4 standard errors) and the medians agree."""
+    ok = np.ones(runs[pairs[0][0]]["mean"].shape[1], bool)
+    for r in runs.values():
+        ok &= (r["std"] > 0).all(axis=0)
+
+    def stat(a, b):
+        sd = runs[b]["std"]
+        return (np.abs(runs[a]["mean"] - runs[b]["mean"]) / np.where(sd > 0, sd, 1)).mean(axis=0)[ok]
+
+    s_cpu, s_gpu = stat(*pairs[0]), stat(*pairs[1])
+    d = s_gpu - s_cpu
+    t = d.mean() / (d.std(ddof=1) / np.sqrt(d.size))
+    ratio = np.median(s_gpu) / np.median(s_cpu)
+    print(f"{label}: median |GPU-CPU|/SD {np.median(s_gpu):.3f}, |CPU-CPU|/SD {np.median(s_cpu):.3f}, "
+          f"ratio {ratio:.3f}, paired t {t:.2f} over {d.size} voxels")
+    assert abs(t) < 4.0
+    assert 0.9 < ratio < 1.1
+
+
 def test_independent_seed_agreement(gac, orc):
     """The paper's CPU/GPU validation design (Demo 2, Sec. 2.6.2): the
-    GPU-minus-CPU disagreement of posterior means, with independent random
-    streams, is judged against the CPU-minus-CPU disagreement of two
-    independent CPU runs.  Both differences of the 3-pool model at SNR 150,
-    in units of the posterior SD, must have the same distribution (two-sample
-    Kolmogorov-Smirnov) and no bias (Bland-Altman mean within 4 SE)."""
-    from scipy import stats
+    GPU-minus-CPU disagreement of posterior means under independent random
+    streams is judged against the CPU-minus-CPU disagreement of two
+    independent CPU runs.  3-pool model at SNR 150, chains started at the
+    true parameters (so that the comparison is of posterior samples, not of
+    burn-in from different starts)."""
     w = W.MWI3_1M
     mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
     n = 2048
     th, sig, y = make_voxels(orc, w, 100_000, n)
-    kw = dict(iterations=w.iterations, burnin=w.burnin, thin=w.thin, n_chains=w.n_chains)
-    ref_a = orc.mcmc_run(w.kind, w.acq, w.lb, w.ub, w.step, y, sig, seed=11, want_samples=False, **kw)
-    ref_b = orc.mcmc_run(w.kind, w.acq, w.lb, w.ub, w.step, y, sig, seed=22, want_samples=False, **kw)
-    gpu_c = gac.run_host(mid, y, sig, seed=33, want_samples=False, **kw)
-    sd = ref_a["std"]
-    ok = sd > 0
-    d_cpu = ((ref_a["mean"] - ref_b["mean"]) / np.where(ok, sd, 1))[ok]
-    d_gpu = ((gpu_c["mean"] - ref_b["mean"]) / np.where(ok, sd, 1))[ok]
-    ks = stats.ks_2samp(np.abs(d_gpu), np.abs(d_cpu))
-    bias, se = d_gpu.mean(), d_gpu.std() / np.sqrt(d_gpu.size)
-    print(f"independent seeds: median |GPU-CPU|/SD {np.median(np.abs(d_gpu)):.3f}, median |CPU-CPU|/SD "
-          f"{np.median(np.abs(d_cpu)):.3f}, KS p {ks.pvalue:.3f}, bias {bias:.4f} +- {se:.4f}")
-    assert ks.pvalue > 0.01
-    assert abs(bias) < 4 * se
+    x0 = np.repeat(th[:, None, :], w.n_chains, axis=1).astype(np.float32)
+    kw = dict(iterations=w.iterations, burnin=w.burnin, thin=w.thin, n_chains=w.n_chains, x0=x0,
+              want_samples=False)
+    runs = {s: orc.mcmc_run(w.kind, w.acq, w.lb, w.ub, w.step, y, sig, seed=s, **kw) for s in (11, 22, 44)}
+    runs[33] = gac.run_host(mid, y, sig, seed=33, **kw)
+    paired_seed_check(runs, ((11, 22), (33, 44)), "MH 3-pool")
