@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(kBlock) ens_kernel(const ModelConst mc, const 
         const int64_t left = ra.n_vox - v0;
         const int nv = left < VB ? static_cast<int>(left) : VB;
         __syncthreads();
+        model_smem_load<KIND>(mc);
         {
             const float *src = ra.data + v0 * M;
             for (int e = tid; e < nv * M; e += blockDim.x) {
@@ -99,8 +100,8 @@ __global__ void __launch_bounds__(kBlock) ens_kernel(const ModelConst mc, const 
                     draw_words(w0, kInitIteration, vg, static_cast<uint32_t>(k), ra.k0, ra.k1);
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
-                        if constexpr (PREC == GAC_PREC_FP64)
-                            xk[p] = mc.lb_d[p] + (mc.ub_d[p] - mc.lb_d[p]) * u01_d(w0[p]);
+                        if constexpr (PREC == GAC_PREC_FP64)  // uncontracted, as in the FP64 definition
+                            xk[p] = __dadd_rn(mc.lb_d[p], __dmul_rn(mc.ub_d[p] - mc.lb_d[p], u01_d(w0[p])));
                         else
                             xk[p] = fmaf(mc.ub_f[p] - mc.lb_f[p], u01_f(w0[p]), mc.lb_f[p]);
                     }
@@ -130,8 +131,14 @@ __global__ void __launch_bounds__(kBlock) ens_kernel(const ModelConst mc, const 
                     const int j = (1 - h) * H + static_cast<int>((static_cast<uint64_t>(w[0]) * H) >> 32);
                     R z;
                     if constexpr (PREC == GAC_PREC_FP64) {
-                        const double s = (ea.stretch_d - 1.0) * u01_d(w[1]) + 1.0;
-                        z = s * s / ea.stretch_d;
+                        // FP64: every rounding of z and of the proposal is the
+                        // plain left-to-right one (no fused multiply-add).  The
+                        // stretch moves amplify a one-ulp difference in a
+                        // walker by e^{E log z} per accepted move, so only
+                        // identically rounded positions stay comparable with an
+                        // FP64 reference over thousands of iterations.
+                        const double s = __dadd_rn(__dmul_rn(ea.stretch_d - 1.0, u01_d(w[1])), 1.0);
+                        z = __dmul_rn(s, s) / ea.stretch_d;
                     } else {
                         const float s = fmaf(ea.stretch - 1.0f, u01_f(w[1]), 1.0f);
                         z = s * s / ea.stretch;
@@ -145,7 +152,7 @@ __global__ void __launch_bounds__(kBlock) ens_kernel(const ModelConst mc, const 
                         th[p] = xk[p];
                         const R xjp = xj[p];
                         if constexpr (PREC == GAC_PREC_FP64) {
-                            prop[p] = fma(z, th[p] - xjp, xjp);
+                            prop[p] = __dadd_rn(xjp, __dmul_rn(z, th[p] - xjp));
                             inside = inside && prop[p] >= mc.lb_d[p] && prop[p] <= mc.ub_d[p];
                         } else {
                             prop[p] = fmaf(z, th[p] - xjp, xjp);

@@ -135,6 +135,92 @@ void keep_staging_pool() {
     done[dev] = true;
 }
 
+// ------------------------------------------------------ SMT g(x) table ----
+// g(x) = int_0^1 exp(-x u^2) du by 40-point Gauss-Legendre quadrature: the
+// integrand is entire in u, and for -13 <= x <= 17 the rule agrees with
+// 40-digit adaptive quadrature to 2e-15 relative.
+namespace {
+struct GaussLegendre01 {
+    static constexpr int n = 40;
+    double node[n], weight[n];  // on [0, 1]
+    GaussLegendre01() {
+        for (int i = 0; i < n; ++i) {
+            // Newton's method on the Legendre polynomial P_n from the
+            // asymptotic estimate of its i-th root; P_n by the three-term
+            // recurrence, P_n'(z) = n (z P_n - P_{n-1}) / (z^2 - 1)
+            double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+            for (int it = 0; it < 100; ++it) {
+                double pm = 1.0, p = z;
+                for (int j = 2; j <= n; ++j) {
+                    const double pn = ((2.0 * j - 1.0) * z * p - (j - 1.0) * pm) / j;
+                    pm = p;
+                    p = pn;
+                }
+                dp = n * (z * p - pm) / (z * z - 1.0);
+                const double dz = p / dp;
+                z -= dz;
+                if (std::fabs(dz) < 1e-15) break;
+            }
+            node[i] = 0.5 * (1.0 + z);
+            weight[i] = 1.0 / ((1.0 - z * z) * dp * dp);  // (2 / ((1 - z^2) P_n'^2)) / 2
+        }
+    }
+    double g(double x) const {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += weight[i] * std::exp(-x * node[i] * node[i]);
+        return s;
+    }
+};
+}  // namespace
+
+// Fills mc->gtab with, for each centre c = c_lo .. 16, the monomial
+// coefficients in d of the degree-7 polynomial that interpolates g(c + d) at
+// the eight Chebyshev points of [-1/2, 1/2], and checks every interval on 65
+// points against the quadrature (relative error of the float coefficients
+// evaluated in double at most 2e-7; the interpolation error itself is below
+// 1e-9 for unit intervals).
+static gac_status build_g_table(int c_lo, ModelConst *mc) {
+    static const GaussLegendre01 gl;
+    constexpr int K = 8;  // coefficients per interval
+    const int n_int = static_cast<int>(kGTail) - c_lo + 1;
+    if (c_lo < static_cast<int>(kSmtArgMin) - 1 || n_int > kGTabMax)
+        return fail(GAC_ERR_INVALID_ARG, "SMT argument range starts at %d, below %d", c_lo,
+                    static_cast<int>(kSmtArgMin));
+    double T[K][K] = {};  // T[n][m]: coefficient of s^m in the Chebyshev polynomial T_n(s)
+    T[0][0] = 1.0;
+    T[1][1] = 1.0;
+    for (int n = 2; n < K; ++n)
+        for (int m = 0; m < K; ++m) T[n][m] = (m > 0 ? 2.0 * T[n - 1][m - 1] : 0.0) - T[n - 2][m];
+    for (int i = 0; i < n_int; ++i) {
+        const double c = c_lo + i;
+        double f[K];
+        for (int j = 0; j < K; ++j) f[j] = gl.g(c + 0.5 * std::cos(M_PI * (j + 0.5) / K));
+        double a[K] = {};  // monomial coefficients in s = 2 d
+        for (int n = 0; n < K; ++n) {
+            double b = 0.0;  // Chebyshev coefficient b_n
+            for (int j = 0; j < K; ++j) b += f[j] * std::cos(M_PI * n * (j + 0.5) / K);
+            b *= (n == 0 ? 1.0 : 2.0) / K;
+            for (int m = 0; m < K; ++m) a[m] += b * T[n][m];
+        }
+        float af[K];
+        for (int m = 0; m < K; ++m) {
+            af[m] = static_cast<float>(std::ldexp(a[m], m));  // coefficient of d^m
+            mc->gtab[((m < 4 ? 0 : kGTabMax) + i) * 4 + (m & 3)] = af[m];
+        }
+        for (int q = 0; q <= 64; ++q) {
+            const double dd = -0.5 + q / 64.0;
+            double p = af[K - 1];
+            for (int m = K - 2; m >= 0; --m) p = p * dd + af[m];
+            const double ref = gl.g(c + dd);
+            if (!(std::fabs(p - ref) <= 2e-7 * ref))
+                return fail(GAC_ERR_INVALID_ARG, "g(x) table check failed at x = %g", c + dd);
+        }
+    }
+    mc->gtab_lo = c_lo;
+    mc->gtab_n = n_int;
+    return GAC_OK;
+}
+
 // ----------------------------------------------------- launch sizing -------
 static int sm_count() {
     static int n = 0;
@@ -267,7 +353,7 @@ gac_status gac_model_register(const gac_model_desc *d, int *model_id) {
         for (int k = 0; k < d->n_acq; ++k) {
             const double b = d->acq[k];
             if (b < 0) return fail(GAC_ERR_INVALID_ARG, "b-values must be >= 0");
-            if (b * (d->ub[3] - d->lb[2]) > kSeriesYMax || b * (-d->lb[1]) > kSeriesYMax)
+            if (b * (d->lb[2] - d->ub[3]) < kSmtArgMin || b * d->lb[1] < kSmtArgMin)
                 return fail(GAC_ERR_INVALID_ARG,
                             "SMT bounds outside the validated range: need b*(ub[De_perp]-lb[De_par]) <= 12");
         }
@@ -308,25 +394,12 @@ gac_status gac_model_register(const gac_model_desc *d, int *model_id) {
             mc.dtk_f = static_cast<float>(kAnchor * dt);
         }
     }
-    // g(-y) = sum_n y^n / (n! (2n+1)) rewritten in u = y / y_max: c_n = y_max^n / (n! (2n+1)),
-    // y_max = the largest -x = -b (De_par - De_perp) or -b Da the bounds allow
-    {
-        double ymax = 1e-3;
-        if (d->kind == GAC_MODEL_SMT)
-            for (int k = 0; k < d->n_acq; ++k)
-                ymax = std::max({ymax, d->acq[k] * (d->ub[3] - d->lb[2]), d->acq[k] * (-d->lb[1])});
-        double pw = 1.0, sum = 0.0;  // y_max^n / n!
-        double c[kSeriesDegree + 1];
-        for (int n = 0; n <= kSeriesDegree; ++n) {
-            if (n > 0) pw *= ymax / n;
-            c[n] = pw / (2.0 * n + 1.0);
-            sum += c[n];
-        }
-        int deg = kSeriesDegree;
-        while (deg > 1 && c[deg] < 1e-9 * sum) --deg;
-        for (int n = 0; n <= kSeriesDegree; ++n) mc.gser_f[n] = n <= deg ? static_cast<float>(c[n]) : 0.0f;
-        mc.gser_inv_ymax = static_cast<float>(1.0 / ymax);
-        mc.gser_degree = deg;
+    if (d->kind == GAC_MODEL_SMT) {
+        double xmin = 0.0;  // the smallest argument b Da or b (De_par - De_perp) the bounds allow
+        for (int k = 0; k < d->n_acq; ++k)
+            xmin = std::min({xmin, d->acq[k] * d->lb[1], d->acq[k] * (d->lb[2] - d->ub[3])});
+        const gac_status st = build_g_table(static_cast<int>(std::floor(xmin)), &mc);
+        if (st != GAC_OK) return st;
     }
     std::lock_guard<std::mutex> lk(g_reg_mu);
     if (g_models.size() >= GAC_MAX_MODELS)

@@ -15,6 +15,8 @@ template <int KIND, int PREC>
 __global__ void forward_kernel(const ModelConst mc, const double *theta, int64_t n, double *s) {
     constexpr int P = model_n_par(KIND);
     const int M = mc.n_meas;
+    model_smem_load<KIND>(mc);
+    __syncthreads();
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         double *out = s + i * M;
@@ -42,6 +44,8 @@ __global__ void loglik_kernel(const ModelConst mc, const double *theta, int64_t 
     constexpr int P = model_n_par(KIND);
     using R = typename PrecTraits<PREC>::R;
     const int M = mc.n_meas;
+    model_smem_load<KIND>(mc);
+    __syncthreads();
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         R th[P];

@@ -195,8 +195,10 @@ __device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra
     const int64_t left = ra.n_vox - v0;
     const int nv = left < VB ? static_cast<int>(left) : VB;
 
-    // a1: stage measurements of voxels [v0, v0 + nv) in shared memory
+    // a1: stage measurements of voxels [v0, v0 + nv) (and the model's
+    // table) in shared memory
     __syncthreads();
+    model_smem_load<KIND>(mc);
     {
         const float *src = ra.data + v0 * M;
         const int total = nv * M;

@@ -28,8 +28,9 @@ namespace gac {
 
 constexpr int kAnchor = 6;
 constexpr float kSinCosMaxArg = 6000.0f;  // |x| bound of sincos_cw (registration checks it)
-constexpr int kSeriesDegree = 40;     // max degree of the g(x) series for x < 0
-constexpr float kSeriesYMax = 12.0f;  // registration keeps -x <= 12
+constexpr float kSmtArgMin = -12.0f;  // registration keeps b (De_par - De_perp), b Da >= -12
+constexpr int kGTabMax = 32;          // unit intervals of the g(x) table, centres c_lo .. 16
+constexpr float kGTail = 16.0f;       // x >= 16: g(x) = sqrt(pi)/2 x^-1/2 (erfc(4) = 1.5e-8)
 
 struct ModelConst {
     int kind;
@@ -42,12 +43,13 @@ struct ModelConst {
     double acq_d[GAC_MAX_ACQ];
     float lb_f[GAC_MAX_PAR], ub_f[GAC_MAX_PAR], step_f[GAC_MAX_PAR];
     double lb_d[GAC_MAX_PAR], ub_d[GAC_MAX_PAR], step_d[GAC_MAX_PAR];
-    // g(-y) = sum_n c_n (y / y_max)^n, c_n = y_max^n / (n! (2n+1)), for
-    // 0 <= y <= y_max (the largest negative argument the bounds allow);
-    // terms above gser_degree are below 1e-9 of the sum and stored as 0
-    float gser_f[kSeriesDegree + 1];
-    float gser_inv_ymax;
-    int gser_degree;
+    // g(x) = int_0^1 exp(-x u^2) du on unit intervals centred at the integers
+    // c = gtab_lo .. 16: g(c + d) = sum_{n<=7} a_n d^n for |d| <= 1/2 (the
+    // Chebyshev interpolant of degree 7).  Layout [2][kGTabMax][4]: a_0..a_3
+    // of every interval, then a_4..a_7, so one interval is two 16-byte loads.
+    alignas(16) float gtab[2 * kGTabMax * 4];
+    int gtab_lo;
+    int gtab_n;
 };
 
 __host__ __device__ constexpr int model_n_par(int kind) {
@@ -64,21 +66,41 @@ constexpr float kSqrtPiHalf = 0.886226925452758014f;
 constexpr double kSqrtPiHalfD = 0.886226925452758014;
 
 // ---------------------------------------------------------------- g(x) ----
-__device__ __forceinline__ float smt_g_f(float x, const ModelConst &mc) {
-    if (x > 0.0f) {
-        if (x < 1e-30f) return 1.0f;
-        // sqrt(pi)/2 erf(s)/s with s = sqrt(x): one reciprocal square root
-        // (SFU, ~2 ulp) gives both s = x rsqrt(x) and 1/s
-        const float rs = rsqrtf(x);
-        return kSqrtPiHalf * erff(x * rs) * rs;
+// The g(x) table of the block's model, copied from ModelConst by
+// model_smem_load before the first evaluation (the lookups of a warp go to
+// different intervals, which the constant bank would serialise).
+static __shared__ float4 smt_gtab_s[2 * kGTabMax];
+
+template <int KIND>
+__device__ __forceinline__ void model_smem_load(const ModelConst &mc) {
+    if constexpr (KIND == GAC_MODEL_SMT) {
+        float *dst = reinterpret_cast<float *>(smt_gtab_s);
+        for (int e = threadIdx.x; e < 2 * kGTabMax * 4; e += blockDim.x) dst[e] = mc.gtab[e];
     }
-    // x <= 0: all-positive power series of g(-y), Horner in u = -x / y_max
-    // in [0, 1] with the degree the registered range needs
-    const float u = -x * mc.gser_inv_ymax;
-    float p = mc.gser_f[mc.gser_degree];
-#pragma unroll 4
-    for (int n = mc.gser_degree - 1; n >= 0; --n) p = fmaf(p, u, mc.gser_f[n]);
-    return p;
+}
+
+// g(x) in FP32 without branches: the interval is c = rint(x), taken from the
+// bits of x + 1.5 * 2^23 (exact for |x| < 2^22), and d = x - c is exact;
+// Horner in d over the interval's eight coefficients.  For x >= 16 the
+// asymptote sqrt(pi)/2 x^-1/2 replaces the table (relative error erfc(4)).
+// The clamped index keeps every load inside the table for any x.
+__device__ __forceinline__ float smt_g_f(float x, const ModelConst &mc) {
+    constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
+    const float t = x + kRound;
+    const float d = x - (t - kRound);
+    int i = __float_as_int(t) - __float_as_int(kRound) - mc.gtab_lo;
+    i = min(max(i, 0), mc.gtab_n - 1);
+    const float4 lo = smt_gtab_s[i];
+    const float4 hi = smt_gtab_s[kGTabMax + i];
+    float p = fmaf(hi.w, d, hi.z);
+    p = fmaf(p, d, hi.y);
+    p = fmaf(p, d, hi.x);
+    p = fmaf(p, d, lo.w);
+    p = fmaf(p, d, lo.z);
+    p = fmaf(p, d, lo.y);
+    p = fmaf(p, d, lo.x);
+    const float tail = kSqrtPiHalf * rsqrtf(x);
+    return x >= kGTail ? tail : p;
 }
 
 __device__ __forceinline__ double smt_g_d(double x) {
