@@ -16,6 +16,7 @@ the data path; the barrier and max-over-ranks timing use the process group).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -37,7 +38,7 @@ UNIT = "chain-iter/s"
 # model (every echo evaluated with its own exp / sin / cos), counted from the
 # oracle's expression tree: MUFU = exp, log, sin, cos, sqrt, reciprocal;
 # FP32 = add/mul/fma/min/max; INT = Philox (10 rounds x (2 wide multiplies,
-# 2 three-input xors, 2 key adds) per call).  See DESIGN.md, "Roofline".
+# 2 three-input xors, 2 key adds) per call).
 OPS = {
     "mwi3_1m": dict(mufu=240, fp32=520, int=180),
     "smt_1p5m": dict(mufu=51, fp32=103, int=120),
@@ -52,6 +53,34 @@ OPS_ENSEMBLE = {
 }
 MUFU_PER_CLK_SM = 16
 FP32_PER_CLK_SM = 128
+ISSUE_PER_CLK_SM = 4  # warp-instructions
+
+# From the ncu captures summarised under profiles/: DRAM bytes of one full
+# launch of the sampler kernel (read + write) and executed warp instructions
+# per 32 chain-iterations.  Reported only while the kernel's sources hash to
+# the value they were measured with (otherwise null).
+KERNEL_SOURCES = ("include/gac.h", "paper_2511_22094_gb300/csrc/mh_kernel.cuh",
+                  "paper_2511_22094_gb300/csrc/models.cuh", "paper_2511_22094_gb300/csrc/philox.cuh")
+KIND_SOURCE = {"mwi3_1m": "mh_mwi3.cu", "smt_1p5m": "mh_smt.cu", "monoexp_4k": "mh_monoexp.cu"}
+MEASURED = {
+    "mwi3_1m": dict(sources="8558c16b51c6b58f", traffic_bytes=292.6e6 + 6623.0e6, warp_instr=990.0),
+    "smt_1p5m": dict(sources="cd1636cf11cf4662", traffic_bytes=None, warp_instr=684.7),
+}
+
+
+def _sources_hash(workload: str) -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES + ("paper_2511_22094_gb300/csrc/" + KIND_SOURCE[workload],):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _measured(workload: str, sampler: str) -> dict:
+    m = MEASURED.get(workload) if sampler == "mh" else None
+    if not m or m["sources"] != _sources_hash(workload):
+        return {}
+    return m
 
 
 def _peaks():
@@ -302,11 +331,18 @@ def run_ours(args, w):
         pipe, achieved = "fp32+int", (ops["fp32"] + ops["int"]) * ci_s / 1e9
         peak = sms * FP32_PER_CLK_SM * f_max / 1e9
     f_med = (clocks.get("sm_mhz") or 0) * 1e6
+    meas = _measured(base_name, args.sampler) if (world == 1 and args.precision == "mixed") else {}
     roof = {"bound": "alu", "pipe": pipe, "count": "direct-form", "achieved": achieved,
             "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
             "peak_basis": f"{sms} SMs x {MUFU_PER_CLK_SM if pipe == 'mufu' else FP32_PER_CLK_SM}/clk x {f_max / 1e6:.0f} MHz (max SM clock)",
             "frac_at_sampled_clock": (achieved / peak * f_max / f_med) if f_med else None,
-            "traffic": None, "kernel_ms": kernel_s * 1e3}
+            "traffic": meas.get("traffic_bytes") if N == W.WORKLOADS[base_name].n_vox else None,
+            "kernel_ms": kernel_s * 1e3}
+    if meas.get("warp_instr"):
+        issue_peak = sms * ISSUE_PER_CLK_SM * f_max
+        roof["executed"] = {"warp_instr_per_32_units": meas["warp_instr"],
+                            "issue_frac": meas["warp_instr"] * ci_s / 32 / issue_peak,
+                            "basis": f"{sms} SMs x {ISSUE_PER_CLK_SM} warp-instr/clk x {f_max / 1e6:.0f} MHz"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -67,7 +67,7 @@ typedef enum {
 
 #define GAC_MAX_PAR 12
 #define GAC_MAX_ACQ 64
-#define GAC_MAX_MODELS 64
+#define GAC_MAX_MODELS 4096
 
 typedef struct {
     int kind;           /* gac_model_kind */
@@ -82,17 +82,19 @@ typedef struct {
 /* Registers a forward model with its acquisition parameters, prior bounds and
  * proposal steps (Sec. 2.3.1: users supply the forward model, bounds and
  * options; Sec. 2.2.2: xStepSize).  Copies every array.  Single-precision
- * paths round acq/lb/ub/step to float.  Returns a model id >= 1 in *model_id.
+ * paths round acq/lb/ub/step to float.  Returns a model id >= 1 in *model_id;
+ * registering a description equal to an earlier one returns the earlier id.
  * Errors: INVALID_ARG (NULL, sizes, lb > ub, negative step, non-finite
  * values, SMT range), UNKNOWN_MODEL (kind), and INVALID_ARG when
- * GAC_MAX_MODELS are registered already.  Thread-safe. */
+ * GAC_MAX_MODELS distinct models are registered already.  Thread-safe. */
 gac_status gac_model_register(const gac_model_desc *desc, int *model_id);
 
 /* Parameter count and real measurements per voxel of a registered model. */
 gac_status gac_model_info(int model_id, int *n_par, int *n_meas);
 
 /* Arithmetic of the sampler.  MIXED (default): forward model and residuals in
- * FP32 with a compensated (Kahan) likelihood sum, the acceptance decision
+ * FP32, the likelihood summed in FP32 within blocks of six acquisitions and
+ * the block sums added with Kahan's compensation, the acceptance decision
  * taken with FP64 semantics, FP64 moment accumulators.  FP32: everything in
  * FP32, plain sums.  FP64: everything in FP64. */
 enum { GAC_PREC_MIXED = 0, GAC_PREC_FP32 = 1, GAC_PREC_FP64 = 2 };
@@ -112,7 +114,21 @@ typedef struct {
     int moments_mode;    /* GAC_MOMENTS_* */
     int trace_n_vox;     /* >0: record every step of the chains of voxels
                             [0, trace_n_vox) into gac_result.trace */
+    int adapt_window;    /* 0 (default): fixed steps, as in the paper.  W > 0:
+                            adapt each chain's steps during burn-in (below) */
+    double adapt_target; /* target acceptance rate of the adaptation, in (0, 1) */
 } gac_mcmc_opts;
+
+/* Step adaptation during burn-in (an extension; the paper has no
+ * counterpart: its xStepSize steps are fixed).  Each chain proposes with
+ * xStepSize * 2^(e/4) for an integer e starting at 0.  After each iteration t
+ * with t % W == 0 and t <= B, with a = the proposals the chain accepted in
+ * iterations t-W+1 .. t: e += 1 if a > adapt_target * W, e -= 1 if
+ * a < adapt_target * W, kept within [GAC_ADAPT_EMIN, GAC_ADAPT_EMAX].  The
+ * steps are fixed after burn-in, so the post-burn-in states are those of a
+ * Metropolis-Hastings chain with a fixed proposal.  MH only. */
+#define GAC_ADAPT_EMIN (-48)
+#define GAC_ADAPT_EMAX 16
 
 /* One recorded MH step (lock-step parity checks): state before the step,
  * the clamped proposal, both log-likelihoods, the acceptance word and the
@@ -135,12 +151,20 @@ typedef struct {
     float *accept_rate;   /* [C][N] accepted proposals / I */
     int32_t *nonfinite;   /* [C][N] steps whose proposal likelihood was not finite */
     gac_trace_rec *trace; /* [trace_n_vox][C][I] */
+    double *rhat;         /* [P][N] R-hat of the C chains over the values that
+                             enter the moments (Gelman & Rubin 1992, no
+                             splitting): sqrt(((n-1)/n W + B/n) / W), W the
+                             mean within-chain variance, B/n the variance of
+                             the chain means.  NaN if C < 2 or n < 2 (and if
+                             W = B = 0), +inf if W = 0 < B.  MH only. */
+    float *step_scale;    /* [C][N] final step multiplier 2^(e/4) (1 without
+                             adaptation).  MH only. */
 } gac_result;
 
 /* Bytes of each gac_result buffer in the order mean, std, samples,
- * accept_rate, nonfinite, trace (bytes[6]). */
+ * accept_rate, nonfinite, trace, rhat, step_scale (bytes[8]). */
 gac_status gac_result_sizes(int model_id, int64_t n_vox, const gac_mcmc_opts *opts,
-                            size_t bytes[6]);
+                            size_t bytes[8]);
 
 /* Runs C Metropolis-Hastings chains for each of n_vox voxels (Sec. 2.2.2):
  * per iteration a Gaussian random-walk proposal clamped to [lb, ub], the
@@ -200,7 +224,8 @@ gac_status gac_normals(uint64_t seed, const uint32_t *t, const uint32_t *v, cons
  * Arguments, outputs and precision variants as gac_mcmc_run, with
  * opts->n_chains = L walkers (even, 4..128) in place of chains; x0 is
  * [n_vox][L][P]; step sizes of the registration are not used; trace records
- * hold L' = NaN for proposals outside the box. */
+ * hold L' = NaN for proposals outside the box.  INVALID_ARG for
+ * opts->adapt_window != 0 or non-NULL out->rhat / out->step_scale (MH only). */
 gac_status gac_ensemble_run(int model_id, const void *data, int64_t n_vox, const float *sigma,
                             float sigma_scalar, const float *x0, const gac_mcmc_opts *opts,
                             double stretch, gac_result *out, void *stream);
@@ -218,9 +243,9 @@ gac_status gac_ensemble_run(int model_id, const void *data, int64_t n_vox, const
  * GPU where it is loaded, until the process exits.
  *   - Every array (data, sigma, x0 and the result buffers) must be device
  *     memory; host pointers are rejected with GAC_ERR_INVALID_ARG.
- *   - The chain state needs about (20 P + 12) bytes per chain (P parameters):
+ *   - The chain state needs about (20 P + 20) bytes per chain (P parameters):
  *     n_vox * n_chains must stay within GAC_NOALLOC_STATE_BYTES of it (e.g.
- *     ~349,000 chains of the 9-parameter model); larger runs are rejected
+ *     ~335,000 chains of the 9-parameter model); larger runs are rejected
  *     with GAC_ERR_INVALID_ARG and a message giving the limit.
  *   - precision must be GAC_PREC_MIXED and trace_n_vox 0; results equal
  *     gac_mcmc_run's for the same inputs.

@@ -89,7 +89,8 @@ class _Model(ct.Structure):
 class _Opts(ct.Structure):
     _fields_ = [("iterations", ct.c_int), ("burnin", ct.c_int), ("thin", ct.c_int),
                 ("n_chains", ct.c_int), ("seed", ct.c_uint64), ("voxel_base", ct.c_uint64),
-                ("moments_mode", ct.c_int), ("n_threads", ct.c_int)]
+                ("moments_mode", ct.c_int), ("n_threads", ct.c_int), ("adapt_window", ct.c_int),
+                ("adapt_target", ct.c_double)]
 
 
 def lib():
@@ -125,6 +126,8 @@ def _declare(L):
     L.orc_n_samples.restype = ct.c_int
     L.orc_stretch_z.argtypes = [ct.c_uint32, ct.c_double]
     L.orc_stretch_z.restype = ct.c_double
+    L.orc_rhat.argtypes = [f64, ct.c_int, ct.c_int, ct.c_size_t]
+    L.orc_rhat.restype = ct.c_double
     L.orc_max_threads.argtypes = []
     L.orc_max_threads.restype = ct.c_int
     for name in ("orc_forward_many", "orc_loglik_many", "orc_mcmc_run", "orc_chain_path",
@@ -245,7 +248,7 @@ def _model(kind, acq, lb, ub, step):
 
 def mcmc_run(kind, acq, lb, ub, step, data, sigma, *, iterations, burnin, thin, n_chains, seed,
              x0=None, sigma_scalar=0.0, voxel_base=0, moments_mode=0, n_threads=0,
-             want_samples=True):
+             want_samples=True, adapt_window=0, adapt_target=0.0):
     """Runs the oracle sampler; returns a dict of numpy arrays (float64)."""
     m, keep = _model(kind, acq, lb, ub, step)
     P = len(keep.lb)
@@ -260,31 +263,45 @@ def mcmc_run(kind, acq, lb, ub, step, data, sigma, *, iterations, burnin, thin, 
     samples = np.full((S, C, P, n_vox), np.nan) if want_samples else None
     acc = np.zeros((C, n_vox))
     bad = np.zeros((C, n_vox), np.int32)
+    rhat = np.full((P, n_vox), np.nan)
+    scale = np.zeros((C, n_vox))
     used = ct.c_int(0)
-    o = _Opts(iterations, burnin, thin, n_chains, seed, voxel_base, moments_mode, n_threads)
+    o = _Opts(iterations, burnin, thin, n_chains, seed, voxel_base, moments_mode, n_threads,
+              adapt_window, adapt_target)
     rc = lib().orc_mcmc_run(ct.byref(m), _vp(data), ct.c_int64(n_vox), _vp(sig),
                             ct.c_float(sigma_scalar), _vp(x0a), ct.byref(o), _vp(mean), _vp(std),
-                            _vp(samples), _vp(acc), _vp(bad), ct.byref(used))
+                            _vp(samples), _vp(acc), _vp(bad), _vp(rhat), _vp(scale), ct.byref(used))
     if rc != 0:
         raise ValueError("oracle rejected the arguments")
-    return dict(mean=mean, std=std, samples=samples, accept_rate=acc, nonfinite=bad,
-                threads=used.value)
+    return dict(mean=mean, std=std, samples=samples, accept_rate=acc, nonfinite=bad, rhat=rhat,
+                step_scale=scale, threads=used.value)
+
+
+def rhat(chains):
+    """R-hat of chains [C][n] (float64)."""
+    x = np.ascontiguousarray(chains, np.float64)
+    return lib().orc_rhat(x.reshape(-1) if x.size else np.zeros(1), x.shape[0], x.shape[1], x.shape[1])
 
 
 def chain_path(kind, acq, lb, ub, step, y, sigma, *, iterations, burnin=0, thin=1, seed,
-               voxel=0, chain=0, x0=None, voxel_base=0):
-    """State after each iteration t = 0..I of one chain, [I+1][P] float64."""
+               voxel=0, chain=0, x0=None, voxel_base=0, adapt_window=0, adapt_target=0.0,
+               want_scale=False):
+    """State after each iteration t = 0..I of one chain, [I+1][P] float64, and
+    the acceptance rate (and the final step multiplier if want_scale)."""
     m, keep = _model(kind, acq, lb, ub, step)
     P = len(keep.lb)
     y = np.ascontiguousarray(y, np.float32)
     x0a = None if x0 is None else np.ascontiguousarray(x0, np.float32)
     path = np.zeros((iterations + 1, P))
     acc = ct.c_double(0)
-    o = _Opts(iterations, burnin, thin, chain + 1, seed, voxel_base, 0, 1)
+    scale = ct.c_double(0)
+    o = _Opts(iterations, burnin, thin, chain + 1, seed, voxel_base, 0, 1, adapt_window, adapt_target)
     rc = lib().orc_chain_path(ct.byref(m), _vp(y), ct.c_double(sigma), _vp(x0a), ct.byref(o),
-                              ct.c_uint64(voxel), ct.c_int(chain), _vp(path), ct.byref(acc))
-    assert rc == 0
-    return path, acc.value
+                              ct.c_uint64(voxel), ct.c_int(chain), _vp(path), ct.byref(acc),
+                              ct.byref(scale))
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return (path, acc.value, scale.value) if want_scale else (path, acc.value)
 
 
 def ensemble_run(kind, acq, lb, ub, data, sigma, *, iterations, burnin, thin, n_walkers, seed,
@@ -305,7 +322,7 @@ def ensemble_run(kind, acq, lb, ub, data, sigma, *, iterations, burnin, thin, n_
     acc = np.zeros((L, n_vox))
     bad = np.zeros((L, n_vox), np.int32)
     used = ct.c_int(0)
-    o = _Opts(iterations, burnin, thin, L, seed, voxel_base, moments_mode, n_threads)
+    o = _Opts(iterations, burnin, thin, L, seed, voxel_base, moments_mode, n_threads, 0, 0.0)
     rc = lib().orc_ensemble_run(ct.byref(m), _vp(data), ct.c_int64(n_vox), _vp(sig),
                                 ct.c_float(sigma_scalar), _vp(x0a), ct.byref(o), ct.c_double(stretch),
                                 _vp(mean), _vp(std), _vp(samples), _vp(acc), _vp(bad), ct.byref(used))
@@ -324,7 +341,7 @@ def ensemble_path(kind, acq, lb, ub, y, sigma, *, iterations, n_walkers, seed, s
     x0a = None if x0 is None else np.ascontiguousarray(x0, np.float32)
     path = np.zeros((iterations + 1, n_walkers, P))
     acc = np.zeros((n_walkers, 1))
-    o = _Opts(iterations, 0, 1, n_walkers, seed, voxel_base, 0, 1)
+    o = _Opts(iterations, 0, 1, n_walkers, seed, voxel_base, 0, 1, 0, 0.0)
     rc = lib().orc_ensemble_path(ct.byref(m), _vp(y), ct.c_double(sigma), _vp(x0a), ct.byref(o),
                                  ct.c_double(stretch), ct.c_uint64(voxel), _vp(path), _vp(acc))
     if rc != 0:

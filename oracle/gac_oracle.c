@@ -226,7 +226,20 @@ typedef struct {
     uint64_t voxel_base;  /* global index of voxel 0, used in the counter */
     int moments_mode;     /* 0: thinned samples, 1: every post-burn-in state */
     int n_threads;        /* 0: all available */
+    int adapt_window;     /* 0: fixed steps; > 0: burn-in adaptation window (below) */
+    double adapt_target;  /* target acceptance rate of the adaptation, in (0, 1) */
 } orc_opts;
+
+/* Step adaptation during burn-in (an extension: the paper's steps are fixed).
+ * Each chain carries an integer exponent e, starting at 0, and proposes with
+ * the steps xStepSize * 2^(e/4).  After iteration t with t % W == 0 and
+ * t <= B (W = adapt_window), let a be the number of proposals the chain
+ * accepted in iterations t-W+1 .. t: e rises by one if a > target * W and
+ * falls by one if a < target * W, within [ORC_ADAPT_EMIN, ORC_ADAPT_EMAX].
+ * After burn-in the steps stay fixed, so the states that enter the moments
+ * come from a Metropolis-Hastings chain with a fixed proposal. */
+#define ORC_ADAPT_EMIN (-48)
+#define ORC_ADAPT_EMAX 16
 
 /* Number of thinned samples per chain: t in {B+T, B+2T, ...} <= I. */
 int orc_n_samples(int iterations, int burnin, int thin) {
@@ -242,7 +255,7 @@ static double clampd(double x, double lo, double hi) { return fmin(fmax(x, lo), 
 static void run_chain(const orc_model *m, const float *y, double sigma, const float *x0,
                       const orc_opts *o, uint32_t vg, uint32_t c, int64_t v, int64_t n_vox,
                       double *samples, double *pooled, int per_chain, double *accept_rate,
-                      int32_t *nonfinite, double *path) {
+                      int32_t *nonfinite, double *step_scale, double *path) {
     int P = m->n_par, I = o->iterations, B = o->burnin, T = o->thin;
     int S = orc_n_samples(I, B, T);
     int nw = orc_n_words(P);
@@ -258,12 +271,15 @@ static void run_chain(const orc_model *m, const float *y, double sigma, const fl
     double L = orc_loglik(m->kind, m->acq, m->n_acq, theta, y, sigma);
     if (path) memcpy(path, theta, sizeof(double) * P);
 
-    long n_acc = 0, n_bad = 0;
+    long n_acc = 0, n_bad = 0, n_acc_window_start = 0;
     int n_pooled = 0;
+    int e = 0;            /* adaptation exponent */
+    double lambda = 1.0;  /* step multiplier 2^(e/4) */
     for (int t = 1; t <= I; ++t) {
         orc_words(o->seed, (uint32_t)t, vg, c, nw, w);
         orc_normals_from_words(w, P, z);
-        for (int p = 0; p < P; ++p) prop[p] = clampd(theta[p] + m->step[p] * z[p], m->lb[p], m->ub[p]);
+        for (int p = 0; p < P; ++p)
+            prop[p] = clampd(theta[p] + m->step[p] * (lambda * z[p]), m->lb[p], m->ub[p]);
         double Lp = orc_loglik(m->kind, m->acq, m->n_acq, prop, y, sigma);
         if (!isfinite(Lp)) ++n_bad;
         double log_u = log(orc_u01(w[nw - 1]));
@@ -271,6 +287,14 @@ static void run_chain(const orc_model *m, const float *y, double sigma, const fl
             memcpy(theta, prop, sizeof(double) * P);
             L = Lp;
             ++n_acc;
+        }
+        if (o->adapt_window > 0 && t <= B && t % o->adapt_window == 0) {
+            double a = (double)(n_acc - n_acc_window_start);
+            double target = o->adapt_target * (double)o->adapt_window;
+            if (a > target && e < ORC_ADAPT_EMAX) ++e;
+            if (a < target && e > ORC_ADAPT_EMIN) --e;
+            lambda = exp2(0.25 * (double)e);
+            n_acc_window_start = n_acc;
         }
         if (path) memcpy(path + (size_t)t * P, theta, sizeof(double) * P);
         int on_grid = (t > B) && T > 0 && ((t - B) % T == 0);
@@ -290,12 +314,48 @@ static void run_chain(const orc_model *m, const float *y, double sigma, const fl
     }
     if (accept_rate) accept_rate[(size_t)c * n_vox + v] = I > 0 ? (double)n_acc / (double)I : 0.0;
     if (nonfinite) nonfinite[(size_t)c * n_vox + v] = (int32_t)n_bad;
+    if (step_scale) step_scale[(size_t)c * n_vox + v] = lambda;
+}
+
+/* Potential scale reduction factor of C chains of n values each (x[c * stride
+ * + i], i < n), Gelman & Rubin (1992) without chain splitting:
+ *   W = mean over chains of the within-chain variances (n-1 divisor),
+ *   B/n = variance of the chain means (C-1 divisor),
+ *   R-hat = sqrt(((n-1)/n W + B/n) / W).
+ * NaN for C < 2 or n < 2 (and for W = B = 0); +inf for W = 0 < B. */
+double orc_rhat(const double *x, int C, int n, size_t stride) {
+    if (C < 2 || n < 2) return NAN;
+    double mean_of_means = 0.0;
+    for (int c = 0; c < C; ++c) {
+        double sum = 0.0;
+        for (int i = 0; i < n; ++i) sum += x[(size_t)c * stride + i];
+        mean_of_means += sum / n;
+    }
+    mean_of_means /= C;
+    double W = 0.0, B_over_n = 0.0;
+    for (int c = 0; c < C; ++c) {
+        double sum = 0.0;
+        for (int i = 0; i < n; ++i) sum += x[(size_t)c * stride + i];
+        double chain_mean = sum / n;
+        double ss = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double d = x[(size_t)c * stride + i] - chain_mean;
+            ss += d * d;
+        }
+        W += ss / (n - 1);
+        B_over_n += (chain_mean - mean_of_means) * (chain_mean - mean_of_means);
+    }
+    W /= C;
+    B_over_n /= (C - 1);
+    double var_plus = (double)(n - 1) / n * W + B_over_n;
+    return sqrt(var_plus / W);
 }
 
 /* Mean and SD (n-1 divisor) of the pooled values of C chains, stored chain
- * after chain as [P][per_chain] blocks; n = 0 gives NaN, n = 1 an SD of 0. */
+ * after chain as [P][per_chain] blocks; n = 0 gives NaN, n = 1 an SD of 0;
+ * R-hat of the chains per parameter. */
 static void pooled_moments(const double *pooled, int C, int per_chain, int P, int64_t v,
-                           int64_t n_vox, double *mean, double *std) {
+                           int64_t n_vox, double *mean, double *std, double *rhat) {
     size_t n_all = (size_t)C * per_chain;
     for (int p = 0; p < P; ++p) {
         double sum = 0.0;
@@ -312,6 +372,9 @@ static void pooled_moments(const double *pooled, int C, int per_chain, int P, in
         double sd = n_all > 1 ? sqrt(ss / (double)(n_all - 1)) : (n_all == 1 ? 0.0 : NAN);
         if (mean) mean[(size_t)p * n_vox + v] = mu;
         if (std) std[(size_t)p * n_vox + v] = sd;
+        if (rhat)
+            rhat[(size_t)p * n_vox + v] =
+                orc_rhat(pooled + (size_t)p * per_chain, C, per_chain, (size_t)per_chain * P);
     }
 }
 
@@ -321,16 +384,19 @@ static void pooled_moments(const double *pooled, int C, int per_chain, int P, in
  *   mean, std   [P][n_vox]      pooled over chains (two-pass, n-1 divisor);
  *   samples     [S][C][P][n_vox];
  *   accept_rate [C][n_vox]      accepted / I;
- *   nonfinite   [C][n_vox]      iterations with a non-finite proposal likelihood.
+ *   nonfinite   [C][n_vox]      iterations with a non-finite proposal likelihood;
+ *   rhat        [P][n_vox]      R-hat over the chains of the moment values;
+ *   step_scale  [C][n_vox]      final step multiplier 2^(e/4) (1 without adaptation).
  * Moments of n = 0 values are NaN; the SD of one value is 0.
  * Returns 0, or -1 on invalid arguments; *threads_used = OpenMP threads. */
 int orc_mcmc_run(const orc_model *m, const float *data, int64_t n_vox, const float *sigma,
                  float sigma_scalar, const float *x0, const orc_opts *o, double *mean,
                  double *std, double *samples, double *accept_rate, int32_t *nonfinite,
-                 int *threads_used) {
+                 double *rhat, double *step_scale, int *threads_used) {
     int P = m->n_par;
     if (P != orc_n_par(m->kind) || P > 64 || o->n_chains < 1 || o->iterations < 0 ||
-        o->burnin < 0 || o->thin < 1 || n_vox < 0)
+        o->burnin < 0 || o->thin < 1 || n_vox < 0 || o->adapt_window < 0 ||
+        (o->adapt_window > 0 && !(o->adapt_target > 0.0 && o->adapt_target < 1.0)))
         return -1;
     int M = orc_n_meas(m->kind, m->n_acq);
     int C = o->n_chains, I = o->iterations, B = o->burnin;
@@ -353,9 +419,9 @@ int orc_mcmc_run(const orc_model *m, const float *data, int64_t n_vox, const flo
             const float *x0v = x0 ? x0 + ((size_t)v * C + c) * P : NULL;
             run_chain(m, y, sig, x0v, o, vg, (uint32_t)c, v, n_vox, samples,
                       pooled + (size_t)c * per_chain * P, per_chain, accept_rate, nonfinite,
-                      NULL);
+                      step_scale, NULL);
         }
-        pooled_moments(pooled, C, per_chain, P, v, n_vox, mean, std);
+        pooled_moments(pooled, C, per_chain, P, v, n_vox, mean, std, rhat);
         free(pooled);
     }
     return 0;
@@ -365,19 +431,22 @@ int orc_mcmc_run(const orc_model *m, const float *data, int64_t n_vox, const flo
  * tests of the thinning grid and of the sampler's stationary distribution. */
 int orc_chain_path(const orc_model *m, const float *y, double sigma, const float *x0,
                    const orc_opts *o, uint64_t voxel, int chain, double *path,
-                   double *accept_rate) {
-    if (m->n_par != orc_n_par(m->kind) || m->n_par > 64 || o->iterations < 0) return -1;
+                   double *accept_rate, double *step_scale) {
+    if (m->n_par != orc_n_par(m->kind) || m->n_par > 64 || o->iterations < 0 ||
+        o->adapt_window < 0 || (o->adapt_window > 0 && !(o->adapt_target > 0.0 && o->adapt_target < 1.0)))
+        return -1;
     orc_opts one = *o;
     one.n_chains = chain + 1;
     double acc = 0.0;
     int32_t bad = 0;
     /* accept_rate/nonfinite are indexed [c][v] with n_vox = 1, v = 0 */
-    double acc_buf[256];
+    double acc_buf[256], scale_buf[256];
     int32_t bad_buf[256];
     if (chain >= 256) return -1;
     run_chain(m, y, sigma, x0, &one, (uint32_t)(o->voxel_base + voxel), (uint32_t)chain, 0, 1,
-              NULL, NULL, 0, acc_buf, bad_buf, path);
+              NULL, NULL, 0, acc_buf, bad_buf, scale_buf, path);
     acc = acc_buf[chain];
+    if (step_scale) *step_scale = scale_buf[chain];
     bad = bad_buf[chain];
     (void)bad;
     if (accept_rate) *accept_rate = acc;
@@ -571,7 +640,7 @@ int orc_ensemble_run(const orc_model *m, const float *data, int64_t n_vox, const
                        x0 ? x0 + (size_t)v * L * P : NULL, o, a,
                        (uint32_t)(o->voxel_base + (uint64_t)v), v, n_vox, samples, pooled, per_chain,
                        accept_rate, nonfinite, NULL);
-        pooled_moments(pooled, L, per_chain, P, v, n_vox, mean, std);
+        pooled_moments(pooled, L, per_chain, P, v, n_vox, mean, std, NULL);
         free(pooled);
     }
     return 0;

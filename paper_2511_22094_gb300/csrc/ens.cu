@@ -74,6 +74,8 @@ extern "C" gac_status gac_ensemble_run(int model_id, const void *data, int64_t n
     if (n_vox > 0 && !data) return fail(GAC_ERR_INVALID_ARG, "data must not be NULL");
     if (!sigma && !(sigma_scalar > 0.0f)) return fail(GAC_ERR_INVALID_ARG, "sigma is NULL and sigma_scalar <= 0");
     if (o->trace_n_vox > 0 && !out->trace) return fail(GAC_ERR_INVALID_ARG, "trace_n_vox > 0 needs out->trace");
+    if (o->adapt_window != 0 || out->rhat || out->step_scale)
+        return fail(GAC_ERR_INVALID_ARG, "step adaptation, rhat and step_scale belong to the MH sampler");
     if (n_vox == 0) return GAC_OK;
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -73,21 +73,33 @@ DevBuf::~DevBuf() {
     if (owned && ptr) cudaFreeAsync(ptr, stream);
 }
 
-// Makes a device view of a caller buffer: device pointers are used in place,
-// host pointers get a stream-ordered device allocation (copied in if `in`).
+// Makes a device view of a caller buffer: device pointers are used in place;
+// page-locked host memory is mapped into the device's address space, so the
+// kernels read and write it in place (over NVLink-C2C on a Grace-Blackwell
+// node: the data crosses once, while the kernel runs, with no staging copy);
+// pageable host memory gets a stream-ordered device allocation (copied in
+// if `in`, out by copy_out).
 gac_status DevBuf::make(void *user, size_t nbytes, bool in, cudaStream_t s, const char *name) {
     stream = s;
     bytes = nbytes;
     host = user;
+    owned = false;
     if (!user || nbytes == 0) {
         ptr = nullptr;
-        owned = false;
         return GAC_OK;
     }
-    if (is_device_ptr(user)) {
-        ptr = user;
-        owned = false;
-        return GAC_OK;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, user) == cudaSuccess) {
+        if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+            ptr = user;
+            return GAC_OK;
+        }
+        if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+            ptr = a.devicePointer;
+            return GAC_OK;
+        }
+    } else {
+        cudaGetLastError();
     }
     cudaError_t e = cudaMallocAsync(&ptr, nbytes, s);
     if (e != cudaSuccess) {
@@ -305,6 +317,9 @@ gac_status validate_opts(const gac_mcmc_opts *o, int64_t n_vox) {
         return fail(GAC_ERR_INVALID_ARG, "unknown moments_mode %d", o->moments_mode);
     if (o->trace_n_vox < 0 || o->trace_n_vox > n_vox)
         return fail(GAC_ERR_INVALID_ARG, "trace_n_vox must be in [0, n_vox]");
+    if (o->adapt_window < 0) return fail(GAC_ERR_INVALID_ARG, "adapt_window must be >= 0");
+    if (o->adapt_window > 0 && !(o->adapt_target > 0.0 && o->adapt_target < 1.0))
+        return fail(GAC_ERR_INVALID_ARG, "adapt_target must be in (0, 1)");
     if (o->voxel_base > (1ull << 32) || static_cast<uint64_t>(n_vox) > (1ull << 32) - o->voxel_base)
         return fail(GAC_ERR_INVALID_ARG, "voxel_base + n_vox must be <= 2^32 (32-bit counter word)");
     return GAC_OK;
@@ -402,6 +417,11 @@ gac_status gac_model_register(const gac_model_desc *d, int *model_id) {
         if (st != GAC_OK) return st;
     }
     std::lock_guard<std::mutex> lk(g_reg_mu);
+    for (size_t i = 0; i < g_models.size(); ++i)  // ModelConst is zero-filled before it is set
+        if (std::memcmp(&g_models[i], &mc, sizeof mc) == 0) {
+            *model_id = static_cast<int>(i + 1);
+            return GAC_OK;
+        }
     if (g_models.size() >= GAC_MAX_MODELS)
         return fail(GAC_ERR_INVALID_ARG, "at most %d models can be registered", GAC_MAX_MODELS);
     g_models.push_back(mc);
@@ -419,7 +439,7 @@ gac_status gac_model_info(int model_id, int *n_par, int *n_meas) {
     return GAC_OK;
 }
 
-gac_status gac_result_sizes(int model_id, int64_t n_vox, const gac_mcmc_opts *o, size_t bytes[6]) {
+gac_status gac_result_sizes(int model_id, int64_t n_vox, const gac_mcmc_opts *o, size_t bytes[8]) {
     clear_error();
     ModelConst mc;
     gac_status st = model_get(model_id, &mc);
@@ -435,6 +455,8 @@ gac_status gac_result_sizes(int model_id, int64_t n_vox, const gac_mcmc_opts *o,
     bytes[3] = C * N * sizeof(float);
     bytes[4] = C * N * sizeof(int32_t);
     bytes[5] = static_cast<size_t>(o->trace_n_vox) * C * o->iterations * sizeof(gac_trace_rec);
+    bytes[6] = P * N * sizeof(double);
+    bytes[7] = C * N * sizeof(float);
     return GAC_OK;
 }
 
@@ -461,7 +483,7 @@ gac_status gac_mcmc_run(int model_id, const void *data, int64_t n_vox, const flo
     const int S = n_samples(o->iterations, o->burnin, o->thin);
     const size_t N = static_cast<size_t>(n_vox);
 
-    DevBuf d_data, d_sigma, d_x0, d_mean, d_std, d_samples, d_acc, d_bad, d_trace;
+    DevBuf d_data, d_sigma, d_x0, d_mean, d_std, d_samples, d_acc, d_bad, d_trace, d_rhat, d_scale;
     if ((st = d_data.make(const_cast<void *>(data), N * M * sizeof(float), true, s, "data")) != GAC_OK) return st;
     if ((st = d_sigma.make(const_cast<float *>(sigma), sigma ? N * sizeof(float) : 0, true, s, "sigma")) != GAC_OK) return st;
     if ((st = d_x0.make(const_cast<float *>(x0), x0 ? N * C * P * sizeof(float) : 0, true, s, "x0")) != GAC_OK) return st;
@@ -471,6 +493,8 @@ gac_status gac_mcmc_run(int model_id, const void *data, int64_t n_vox, const flo
     if ((st = d_acc.make(out->accept_rate, C * N * sizeof(float), false, s, "accept_rate")) != GAC_OK) return st;
     if ((st = d_bad.make(out->nonfinite, C * N * sizeof(int32_t), false, s, "nonfinite")) != GAC_OK) return st;
     if ((st = d_trace.make(out->trace, static_cast<size_t>(o->trace_n_vox) * C * o->iterations * sizeof(gac_trace_rec), false, s, "trace")) != GAC_OK) return st;
+    if ((st = d_rhat.make(out->rhat, P * N * sizeof(double), false, s, "rhat")) != GAC_OK) return st;
+    if ((st = d_scale.make(out->step_scale, C * N * sizeof(float), false, s, "step_scale")) != GAC_OK) return st;
 
     const bool trace = o->trace_n_vox > 0;
     LaunchCfg cfg;
@@ -506,10 +530,13 @@ gac_status gac_mcmc_run(int model_id, const void *data, int64_t n_vox, const flo
     ra.row_stride = row_stride_for(mc.kind, M);
     ra.data_vec4 = (M % 4 == 0) && ((reinterpret_cast<uintptr_t>(ra.data) & 15) == 0);
     ra.n_tiles = n_tiles;
+    set_adaptation(ra, o);
+    ra.rhat = static_cast<double *>(d_rhat.ptr);
+    ra.step_scale = static_cast<float *>(d_scale.ptr);
 
     cudaError_t e = launch_mh(mc.kind, o->precision, trace, mc, ra, cfg);
     if (e != cudaSuccess) return cuda_fail(e, "MH kernel launch");
-    for (DevBuf *b : {&d_mean, &d_std, &d_samples, &d_acc, &d_bad, &d_trace})
+    for (DevBuf *b : {&d_mean, &d_std, &d_samples, &d_acc, &d_bad, &d_trace, &d_rhat, &d_scale})
         if ((st = b->copy_out()) != GAC_OK) return st;
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "MH kernel");

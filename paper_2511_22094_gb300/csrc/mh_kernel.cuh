@@ -9,7 +9,8 @@
 //   a2  draws or loads its initial state and evaluates its likelihood
 //       (or, when resuming a slice, reloads theta, L and its counters),
 //   a3  per iteration draws Philox words for (t, voxel, chain),
-//   a4  proposes theta' = clamp(theta + step * z, lb, ub),
+//   a4  proposes theta' = clamp(theta + step * z, lb, ub) (step scaled by
+//       2^(e/4) when burn-in adaptation is on; e changes at window ends),
 //   a5  evaluates the forward model at every acquisition and
 //   a6  accumulates the Gaussian log-likelihood in registers,
 //   a7  accepts iff log u < L' - L,
@@ -17,8 +18,8 @@
 //       updates Welford accumulators,
 // and after the last iteration
 //   a9  merges the C chains' accumulators of each voxel in chain order
-//       (Chan et al.'s pairwise update) and writes mean, SD, acceptance
-//       rate and the non-finite count.
+//       (Chan et al.'s pairwise update) and writes mean, SD, R-hat,
+//       acceptance rate, the non-finite count and the step multiplier.
 // Nothing but thinned samples touches HBM inside the iteration loop.
 //
 // Two drivers share this tile routine: mh_kernel runs one job in one launch
@@ -29,13 +30,16 @@
 // voxel, chain)).
 //
 // Precision variants (template PREC):
-//   MIXED  FP32 model and residuals, Kahan-compensated sum, acceptance with
+//   MIXED  FP32 model and residuals, FP32 block sums of six acquisitions
+//          added with Kahan's compensation, acceptance with
 //          FP64 semantics (an FP32 test with a proven error margin decides
 //          almost every step; steps inside the margin are decided in FP64
 //          from the same L, L' and acceptance word), FP64 Welford.
 //   FP32   FP32 everywhere (plain sum, FP32 decision, FP32 Welford).
 //   FP64   FP64 everywhere.
 #pragma once
+#include <climits>
+#include <cmath>
 #include <cstdint>
 
 #include "gac.h"
@@ -74,6 +78,12 @@ struct RunArgs {
     int row_stride;      // shared-memory floats per voxel row (padded)
     int data_vec4;       // rows are whole float4s and data is 16-byte aligned
     int64_t n_tiles;
+    // burn-in step adaptation: window W (0 = off); e rises when a window's
+    // acceptances a > adapt_hi (= floor(target W)), falls when a < adapt_lo
+    // (= ceil(target W))
+    int adapt_window, adapt_lo, adapt_hi;
+    double *rhat;        // [P][N] or nullptr
+    float *step_scale;   // [C][N] or nullptr
 };
 
 // Chain state kept in HBM between slices, structure of arrays over the
@@ -85,7 +95,26 @@ struct SliceState {
     int32_t *n_bad;  // [N*C]
     void *wf_mean;   // [P][N*C] of W
     void *wf_m2;     // [P][N*C] of W
+    int32_t *adapt;  // [2][N*C]: adaptation exponent e, accepted count at the window start
 };
+
+// Host: the adaptation fields of RunArgs.  a > target W <=> a > floor(target W)
+// and a < target W <=> a < ceil(target W) for integer a.
+inline void set_adaptation(RunArgs &ra, const gac_mcmc_opts *o) {
+    ra.adapt_window = o->adapt_window;
+    const double x = o->adapt_target * static_cast<double>(o->adapt_window);
+    ra.adapt_lo = o->adapt_window > 0 ? static_cast<int>(std::ceil(x)) : 0;
+    ra.adapt_hi = o->adapt_window > 0 ? static_cast<int>(std::floor(x)) : 0;
+}
+
+// Step multiplier s = 2^(e/4) of the adaptation, as the Box-Muller radius
+// factor k: -2 s^2 = -2^(e/2 + 1) against ln u (FP64), times ln 2 against
+// log2 u (FP32).
+template <class R>
+__device__ __forceinline__ R adapt_bm_scale(int e) {
+    if constexpr (sizeof(R) == 8) return -exp2(0.5 * e + 1.0);
+    else return exp2f(0.5f * static_cast<float>(e)) * kNeg2Ln2;
+}
 
 template <int PREC>
 struct PrecTraits;
@@ -236,12 +265,15 @@ __device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra
         R th[P];
         R L;
         int n_acc = 0, n_bad = 0;
+        int ad_e = 0, ad_acc0 = 0;  // adaptation exponent, n_acc at the window start
         if (SLICED && t_begin > 0) {
 #pragma unroll
             for (int p = 0; p < P; ++p) th[p] = static_cast<const R *>(ss.theta)[p * nchains + ch];
             L = static_cast<const R *>(ss.L)[ch];
             n_acc = ss.n_acc[ch];
             n_bad = ss.n_bad[ch];
+            ad_e = ss.adapt[ch];
+            ad_acc0 = ss.adapt[nchains + ch];
         } else {
             if (ra.x0) {
                 const float *x0 = ra.x0 + ch * P;
@@ -275,100 +307,122 @@ __device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra
         const bool all_mode = ra.moments_mode == GAC_MOMENTS_ALL_POSTBURNIN;
         int n_mom = all_mode ? max(t_begin - ra.B, 0) : (t_begin > ra.B ? (t_begin - ra.B) / ra.T : 0);
         int to_thin = t_begin < ra.B ? ra.B + ra.T : ra.B + ((t_begin - ra.B) / ra.T + 1) * ra.T;
+        // next window end of the burn-in adaptation (INT_MAX: none left)
+        const int W_ad = ra.adapt_window;
+        int to_adapt = INT_MAX;
+        if (W_ad > 0 && (t_begin / W_ad + 1) <= ra.B / W_ad) to_adapt = (t_begin / W_ad + 1) * W_ad;
+        R bm_k = adapt_bm_scale<R>(ad_e);
 
-        for (int t = t_begin + 1; t <= t_end; ++t) {
-            // a3: random words for (t, voxel, chain)
-            uint32_t w[NWA];
-            draw_words(w, static_cast<uint32_t>(t), vg, cu, ra.k0, ra.k1);
-            // a4: proposal
-            R prop[P];
+        // iterations run in segments that end at the adaptation windows, so
+        // the loop itself carries no adaptation test
+        for (int t_seg = t_begin; t_seg < t_end;) {
+            const int seg_end = to_adapt < t_end ? to_adapt : t_end;
+            for (int t = t_seg + 1; t <= seg_end; ++t) {
+                // a3: random words for (t, voxel, chain)
+                uint32_t w[NWA];
+                draw_words(w, static_cast<uint32_t>(t), vg, cu, ra.k0, ra.k1);
+                // a4: proposal
+                R prop[P];
 #pragma unroll
-            for (int j = 0; 2 * j < P; ++j) {
-                R z0, z1;
-                if constexpr (PREC == GAC_PREC_FP64) box_muller_d(w[2 * j], w[2 * j + 1], z0, z1);
-                else box_muller_f(w[2 * j], w[2 * j + 1], z0, z1);
-                if constexpr (PREC == GAC_PREC_FP64) {
-                    prop[2 * j] = fmin(fmax(fma(mc.step_d[2 * j], z0, th[2 * j]), mc.lb_d[2 * j]),
-                                       mc.ub_d[2 * j]);
-                    if (2 * j + 1 < P)
-                        prop[2 * j + 1] = fmin(fmax(fma(mc.step_d[2 * j + 1], z1, th[2 * j + 1]),
-                                                    mc.lb_d[2 * j + 1]), mc.ub_d[2 * j + 1]);
-                } else {
-                    prop[2 * j] = fminf(fmaxf(fmaf(mc.step_f[2 * j], z0, th[2 * j]), mc.lb_f[2 * j]),
-                                        mc.ub_f[2 * j]);
-                    if (2 * j + 1 < P)
-                        prop[2 * j + 1] = fminf(fmaxf(fmaf(mc.step_f[2 * j + 1], z1, th[2 * j + 1]),
-                                                      mc.lb_f[2 * j + 1]), mc.ub_f[2 * j + 1]);
+                for (int j = 0; 2 * j < P; ++j) {
+                    R z0, z1;
+                    if constexpr (PREC == GAC_PREC_FP64) box_muller_d(w[2 * j], w[2 * j + 1], z0, z1, bm_k);
+                    else box_muller_f(w[2 * j], w[2 * j + 1], z0, z1, bm_k);
+                    if constexpr (PREC == GAC_PREC_FP64) {
+                        prop[2 * j] = fmin(fmax(fma(mc.step_d[2 * j], z0, th[2 * j]), mc.lb_d[2 * j]),
+                                           mc.ub_d[2 * j]);
+                        if (2 * j + 1 < P)
+                            prop[2 * j + 1] = fmin(fmax(fma(mc.step_d[2 * j + 1], z1, th[2 * j + 1]),
+                                                        mc.lb_d[2 * j + 1]), mc.ub_d[2 * j + 1]);
+                    } else {
+                        prop[2 * j] = fminf(fmaxf(fmaf(mc.step_f[2 * j], z0, th[2 * j]), mc.lb_f[2 * j]),
+                                            mc.ub_f[2 * j]);
+                        if (2 * j + 1 < P)
+                            prop[2 * j + 1] = fminf(fmaxf(fmaf(mc.step_f[2 * j + 1], z1, th[2 * j + 1]),
+                                                          mc.lb_f[2 * j + 1]), mc.ub_f[2 * j + 1]);
+                    }
                 }
-            }
-            // a5 + a6: forward model and likelihood
-            const R Lp = loglik_any<KIND, PREC>(prop, y, inv_s2, mc);
-            // a7: accept / reject
-            const uint32_t w_acc = w[NW - 1];
-            const bool acc = accept_step<PREC>(Lp, L, w_acc);
-            n_bad += !isfinite(Lp);
-            if constexpr (TRACE) {
-                if (v < ra.trace_n) {
-                    gac_trace_rec *rec = ra.trace + ch * static_cast<int64_t>(ra.I) + (t - 1);
+                // a5 + a6: forward model and likelihood
+                const R Lp = loglik_any<KIND, PREC>(prop, y, inv_s2, mc);
+                // a7: accept / reject
+                const uint32_t w_acc = w[NW - 1];
+                const bool acc = accept_step<PREC>(Lp, L, w_acc);
+                n_bad += !isfinite(Lp);
+                if constexpr (TRACE) {
+                    if (v < ra.trace_n) {
+                        gac_trace_rec *rec = ra.trace + ch * static_cast<int64_t>(ra.I) + (t - 1);
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            rec->theta[p] = static_cast<double>(th[p]);
+                            rec->prop[p] = static_cast<double>(prop[p]);
+                        }
+                        rec->L = static_cast<double>(L);
+                        rec->Lp = static_cast<double>(Lp);
+                        rec->w_acc = w_acc;
+                        rec->accepted = acc ? 1 : 0;
+                    }
+                }
+                if (acc) {
+#pragma unroll
+                    for (int p = 0; p < P; ++p) th[p] = prop[p];
+                    L = Lp;
+                    ++n_acc;
+                }
+                // a8: thinning grid t = B + T, B + 2T, ... and moments
+                const bool on_grid = (t == to_thin);
+                if (on_grid) {
+                    to_thin += ra.T;
+                    if (ra.samples) {
+                        const int s = (t - ra.B) / ra.T - 1;
+                        float *dst = ra.samples + ((static_cast<int64_t>(s) * C + c) * P) * ra.n_vox + v;
+#pragma unroll
+                        for (int p = 0; p < P; ++p) dst[p * ra.n_vox] = static_cast<float>(th[p]);
+                    }
+                }
+                if (all_mode ? (t > ra.B) : on_grid) {
+                    ++n_mom;
+                    const W inv_n = W(1) / W(n_mom);
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
-                        rec->theta[p] = static_cast<double>(th[p]);
-                        rec->prop[p] = static_cast<double>(prop[p]);
+                        const W x = static_cast<W>(th[p]);
+                        W m = wf_mean[p * wf_stride + wf_idx];
+                        const W d = x - m;
+                        m += d * inv_n;
+                        wf_mean[p * wf_stride + wf_idx] = m;
+                        wf_m2[p * wf_stride + wf_idx] += d * (x - m);
                     }
-                    rec->L = static_cast<double>(L);
-                    rec->Lp = static_cast<double>(Lp);
-                    rec->w_acc = w_acc;
-                    rec->accepted = acc ? 1 : 0;
                 }
             }
-            if (acc) {
-#pragma unroll
-                for (int p = 0; p < P; ++p) th[p] = prop[p];
-                L = Lp;
-                ++n_acc;
-            }
-            // a8: thinning grid t = B + T, B + 2T, ... and moments
-            const bool on_grid = (t == to_thin);
-            if (on_grid) {
-                to_thin += ra.T;
-                if (ra.samples) {
-                    const int s = (t - ra.B) / ra.T - 1;
-                    float *dst = ra.samples + ((static_cast<int64_t>(s) * C + c) * P) * ra.n_vox + v;
-#pragma unroll
-                    for (int p = 0; p < P; ++p) dst[p * ra.n_vox] = static_cast<float>(th[p]);
-                }
-            }
-            if (all_mode ? (t > ra.B) : on_grid) {
-                ++n_mom;
-                const W inv_n = W(1) / W(n_mom);
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    const W x = static_cast<W>(th[p]);
-                    W m = wf_mean[p * wf_stride + wf_idx];
-                    const W d = x - m;
-                    m += d * inv_n;
-                    wf_mean[p * wf_stride + wf_idx] = m;
-                    wf_m2[p * wf_stride + wf_idx] += d * (x - m);
-                }
+            t_seg = seg_end;
+            if (t_seg == to_adapt) {  // a window ends (the same t for every thread)
+                const int a = n_acc - ad_acc0;
+                ad_e += (a > ra.adapt_hi && ad_e < GAC_ADAPT_EMAX) - (a < ra.adapt_lo && ad_e > GAC_ADAPT_EMIN);
+                ad_acc0 = n_acc;
+                bm_k = adapt_bm_scale<R>(ad_e);
+                to_adapt = (W_ad <= ra.B - t_seg) ? t_seg + W_ad : INT_MAX;
             }
         }
         if (t_end == ra.I) {
             if (ra.accept) ra.accept[c * ra.n_vox + v] = ra.I > 0 ? float(n_acc) / float(ra.I) : 0.0f;
             if (ra.nonfinite) ra.nonfinite[c * ra.n_vox + v] = n_bad;
+            if (ra.step_scale) ra.step_scale[c * ra.n_vox + v] = exp2f(0.25f * static_cast<float>(ad_e));
         } else if constexpr (SLICED) {
 #pragma unroll
             for (int p = 0; p < P; ++p) static_cast<R *>(ss.theta)[p * nchains + ch] = th[p];
             static_cast<R *>(ss.L)[ch] = L;
             ss.n_acc[ch] = n_acc;
             ss.n_bad[ch] = n_bad;
+            ss.adapt[ch] = ad_e;
+            ss.adapt[nchains + ch] = ad_acc0;
         }
     }
 
     // a9: pool the C chains of each voxel in chain order
     if (t_end != ra.I) return;
     __syncthreads();
-    if (active && c == 0 && (ra.mean || ra.std)) {
+    if (active && c == 0 && (ra.mean || ra.std || ra.rhat)) {
         const int n_each = (ra.moments_mode == GAC_MOMENTS_ALL_POSTBURNIN) ? max(ra.I - ra.B, 0) : ra.S;
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             W mu = wf_mean[p * wf_stride + wf_idx];
@@ -383,11 +437,30 @@ __device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra
                 m2 += m2b + delta * delta * W(n * n_each / ntot);
                 n = ntot;
             }
-            const double nan = __longlong_as_double(0x7ff8000000000000ll);
             const double mean_out = n > 0 ? static_cast<double>(mu) : nan;
             const double sd_out = n > 1 ? sqrt(static_cast<double>(m2) / (n - 1.0)) : (n == 1 ? 0.0 : nan);
             if (ra.mean) ra.mean[p * ra.n_vox + v] = mean_out;
             if (ra.std) ra.std[p * ra.n_vox + v] = sd_out;
+            if (ra.rhat) {
+                // R-hat from the per-chain accumulators, in FP64: W = mean of
+                // the within-chain variances, B/n = variance of the chain means
+                double r = nan;
+                if (C >= 2 && n_each >= 2) {
+                    double mbar = 0.0;
+                    for (int c2 = 0; c2 < C; ++c2) mbar += static_cast<double>(wf_mean[p * wf_stride + wf_idx + c2]);
+                    mbar /= C;
+                    double w_in = 0.0, b_n = 0.0;
+                    for (int c2 = 0; c2 < C; ++c2) {
+                        const double d = static_cast<double>(wf_mean[p * wf_stride + wf_idx + c2]) - mbar;
+                        w_in += static_cast<double>(wf_m2[p * wf_stride + wf_idx + c2]) / (n_each - 1);
+                        b_n += d * d;
+                    }
+                    w_in /= C;
+                    b_n /= (C - 1);
+                    r = sqrt(((n_each - 1.0) / n_each * w_in + b_n) / w_in);
+                }
+                ra.rhat[p * ra.n_vox + v] = r;
+            }
         }
     }
 }

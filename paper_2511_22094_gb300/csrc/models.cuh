@@ -178,6 +178,15 @@ __device__ __forceinline__ void sincos_cw2(float2 x, float2 &sn, float2 &cs) {
 }
 
 // ----------------------------------------------------------- FP32 models --
+// Tells a visitor that a block of echoes of a recurrence is complete, if it
+// wants to know (visitors without block_end() ignore it).
+template <class V>
+__device__ __forceinline__ auto end_block(V &v, int) -> decltype(v.block_end(), void()) {
+    v.block_end();
+}
+template <class V>
+__device__ __forceinline__ void end_block(V &, long) {}
+
 template <class V>
 __device__ __forceinline__ void eval_monoexp_f(const float *th, const ModelConst &mc, V &&visit) {
     const float s0 = th[0];
@@ -195,6 +204,7 @@ __device__ __forceinline__ void eval_monoexp_f(const float *th, const ModelConst
                 visit(a + i, e);
                 e *= r1;
             }
+            end_block(visit, 0);
             anchor *= rk;
         }
         for (float e = anchor; a < n; ++a) {  // last, partial block
@@ -202,7 +212,11 @@ __device__ __forceinline__ void eval_monoexp_f(const float *th, const ModelConst
             e *= r1;
         }
     } else {
-        for (int k = 0; k < n; ++k) visit(k, s0 * expf(-mc.acq_f[k] * rate));
+        for (int k0 = 0; k0 < n; k0 += kAnchor) {
+            const int k1 = min(k0 + kAnchor, n);
+            for (int k = k0; k < k1; ++k) visit(k, s0 * expf(-mc.acq_f[k] * rate));
+            end_block(visit, 0);
+        }
     }
 }
 
@@ -251,6 +265,7 @@ __device__ __forceinline__ void eval_mwi3_f(const float *th, const ModelConst &m
         int a = 0;
         for (; a + kAnchor <= n; a += kAnchor) {
             block(a, kAnchor, true);
+            end_block(visit, 0);
             const float2 xn = __ffma2_rn(X, KR, __fmul2_rn(Y, NKI));
             Y = __ffma2_rn(X, KI, __fmul2_rn(Y, KR));
             X = xn;
@@ -264,18 +279,22 @@ __device__ __forceinline__ void eval_mwi3_f(const float *th, const ModelConst &m
             rate[j] = 1.0f / th[3 + j];
             w[j] = (j < 2) ? kTwoPiMilli * th[6 + j] : 0.0f;
         }
-        for (int k = 0; k < n; ++k) {
-            const float t = mc.acq_f[k];
-            float re = 0.0f, im = 0.0f;
+        for (int k0 = 0; k0 < n; k0 += kAnchor) {
+            const int k1 = min(k0 + kAnchor, n);
+            for (int k = k0; k < k1; ++k) {
+                const float t = mc.acq_f[k];
+                float re = 0.0f, im = 0.0f;
 #pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const float m = th[j] * expf(-t * rate[j]);
-                float s, c;
-                sincos_cw(fmaf(-w[j], t, phi0), s, c);
-                re = fmaf(m, c, re);
-                im = fmaf(m, s, im);
+                for (int j = 0; j < 3; ++j) {
+                    const float m = th[j] * expf(-t * rate[j]);
+                    float s, c;
+                    sincos_cw(fmaf(-w[j], t, phi0), s, c);
+                    re = fmaf(m, c, re);
+                    im = fmaf(m, s, im);
+                }
+                visit(k, re, im);
             }
-            visit(k, re, im);
+            end_block(visit, 0);
         }
     }
 }
@@ -284,15 +303,20 @@ template <class V>
 __device__ __forceinline__ void eval_smt_f(const float *th, const ModelConst &mc, V &&visit) {
     const float f = th[0], da = th[1], dpar = th[2], dperp = th[3];
     const float ddiff = dpar - dperp;
-    for (int k = 0; k < mc.n_acq; ++k) {
-        const float b = mc.acq_f[k];
-        if (b == 0.0f) {  // S(b = 0) = S0 = 1 (same b for every thread: no divergence)
-            visit(k, 1.0f);
-            continue;
+    const int n = mc.n_acq;
+    for (int k0 = 0; k0 < n; k0 += kAnchor) {
+        const int k1 = min(k0 + kAnchor, n);
+        for (int k = k0; k < k1; ++k) {
+            const float b = mc.acq_f[k];
+            if (b == 0.0f) {  // S(b = 0) = S0 = 1 (same b for every thread: no divergence)
+                visit(k, 1.0f);
+                continue;
+            }
+            const float intra = smt_g_f(b * da, mc);
+            const float extra = expf(-b * dperp) * smt_g_f(b * ddiff, mc);
+            visit(k, fmaf(f, intra, (1.0f - f) * extra));
         }
-        const float intra = smt_g_f(b * da, mc);
-        const float extra = expf(-b * dperp) * smt_g_f(b * ddiff, mc);
-        visit(k, fmaf(f, intra, (1.0f - f) * extra));
+        end_block(visit, 0);
     }
 }
 
@@ -359,20 +383,37 @@ __device__ __forceinline__ void eval_d(const double *th, const ModelConst &mc, V
 
 // ----------------------------------------------------- likelihood sums -----
 // Kahan-compensated FP32 sum (MIXED path).
+// Sums of squared residuals.  Complex rows feed (d_re, d_im) pairs, squared
+// and accumulated lane-wise by one paired FMA; real rows feed single
+// residuals.  The models call block_end() after each block of echoes of
+// their recurrences (end_block below).
+//
+// MIXED: plain FP32 inside a block of kAnchor acquisitions (at most
+// 2 kAnchor terms), the block sums added with Kahan's compensation.
 struct KahanSum {
+    float2 p = make_float2(0.0f, 0.0f);
     float s = 0.0f, c = 0.0f;
-    __device__ __forceinline__ void add(float x) {
-        const float y = x - c;
+    __device__ __forceinline__ void add2(float2 d) { p = __ffma2_rn(d, d, p); }
+    __device__ __forceinline__ void add(float d) { p.x = fmaf(d, d, p.x); }
+    __device__ __forceinline__ void block_end() {
+        const float y = (p.x + p.y) - c;
         const float t = s + y;
         c = (t - s) - y;
         s = t;
+        p = make_float2(0.0f, 0.0f);
     }
-    __device__ __forceinline__ float value() const { return s; }
+    __device__ __forceinline__ float value() {
+        block_end();
+        return s;
+    }
 };
+// FP32: one plain FP32 sum per lane.
 struct PlainSumF {
-    float s = 0.0f;
-    __device__ __forceinline__ void add(float x) { s += x; }
-    __device__ __forceinline__ float value() const { return s; }
+    float2 p = make_float2(0.0f, 0.0f);
+    __device__ __forceinline__ void add2(float2 d) { p = __ffma2_rn(d, d, p); }
+    __device__ __forceinline__ void add(float d) { p.x = fmaf(d, d, p.x); }
+    __device__ __forceinline__ void block_end() {}
+    __device__ __forceinline__ float value() const { return p.x + p.y; }
 };
 struct PlainSumD {
     double s = 0.0;
@@ -382,22 +423,23 @@ struct PlainSumD {
 
 // -1/2 * sum_m (y_m - s_m)^2 / sigma^2, with y read from `y` (row of the
 // voxel; complex rows as re, im pairs).  ACC = KahanSum or PlainSumF.
+template <class ACC>
+struct ResidualVisitor {
+    ACC &acc;
+    const float *y;
+    __device__ __forceinline__ void operator()(int k, float sr, float si) const {
+        const float2 yk = reinterpret_cast<const float2 *>(y)[k];
+        acc.add2(__ffma2_rn(make_float2(sr, si), f2(-1.0f), yk));  // y - s, both parts
+    }
+    __device__ __forceinline__ void operator()(int k, float s) const { acc.add(y[k] - s); }
+    __device__ __forceinline__ void block_end() const { acc.block_end(); }
+};
+
 template <int KIND, class ACC>
 __device__ __forceinline__ float loglik_f(const float *th, const float *y, float inv_s2,
                                           const ModelConst &mc) {
     ACC acc;
-    if constexpr (model_complex(KIND)) {
-        eval_f<KIND>(th, mc, [&](int k, float sr, float si) {
-            const float2 yk = reinterpret_cast<const float2 *>(y)[k];
-            const float2 d = __ffma2_rn(make_float2(sr, si), f2(-1.0f), yk);  // y - s, both parts
-            acc.add(fmaf(d.x, d.x, d.y * d.y));
-        });
-    } else {
-        eval_f<KIND>(th, mc, [&](int k, float s) {
-            const float d = y[k] - s;
-            acc.add(d * d);
-        });
-    }
+    eval_f<KIND>(th, mc, ResidualVisitor<ACC>{acc, y});
     return -0.5f * acc.value() * inv_s2;
 }
 

@@ -17,7 +17,8 @@
 namespace gac {
 
 // Chain state of one call: theta [P][N*C] f32, L [N*C] f32, accepted and
-// non-finite counters [N*C] i32, Welford mean and M2 [P][N*C] f64.  Every
+// non-finite counters [N*C] i32, adaptation state [2][N*C] i32, Welford mean
+// and M2 [P][N*C] f64.  Every
 // GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_state[GAC_NOALLOC_STATE_BYTES];
 
@@ -94,16 +95,19 @@ extern "C" gac_status gac_mcmc_run_noalloc(int model_id, const void *data, int64
 
     const size_t P = mc.n_par, NC = static_cast<size_t>(n_vox) * o->n_chains;
     const size_t off_L = up256(P * NC * 4), off_acc = off_L + up256(NC * 4), off_bad = off_acc + up256(NC * 4);
-    const size_t off_wm = off_bad + up256(NC * 4), off_w2 = off_wm + up256(P * NC * 8);
+    const size_t off_ad = off_bad + up256(NC * 4);
+    const size_t off_wm = off_ad + up256(2 * NC * 4), off_w2 = off_wm + up256(P * NC * 8);
     const size_t need = off_w2 + up256(P * NC * 8);
     if (need > GAC_NOALLOC_STATE_BYTES)
         return fail(GAC_ERR_INVALID_ARG,
                     "%lld voxels x %d chains need %zu bytes of chain state; this entry point holds at most %zu",
                     static_cast<long long>(n_vox), o->n_chains, need, static_cast<size_t>(GAC_NOALLOC_STATE_BYTES));
     // every array must already be on the device: staging would allocate
-    const void *ptrs[] = {data, sigma, x0, out->mean, out->std, out->samples, out->accept_rate, out->nonfinite};
-    const char *names[] = {"data", "sigma", "x0", "mean", "std", "samples", "accept_rate", "nonfinite"};
-    for (int i = 0; i < 8; ++i)
+    const void *ptrs[] = {data, sigma, x0, out->mean, out->std, out->samples, out->accept_rate, out->nonfinite,
+                          out->rhat, out->step_scale};
+    const char *names[] = {"data", "sigma", "x0", "mean", "std", "samples", "accept_rate", "nonfinite",
+                           "rhat", "step_scale"};
+    for (int i = 0; i < 10; ++i)
         if (ptrs[i] && !is_device_ptr(ptrs[i]))
             return fail(GAC_ERR_INVALID_ARG, "%s must be device memory", names[i]);
 
@@ -115,6 +119,7 @@ extern "C" gac_status gac_mcmc_run_noalloc(int model_id, const void *data, int64
     ss.L = b + off_L;
     ss.n_acc = reinterpret_cast<int32_t *>(b + off_acc);
     ss.n_bad = reinterpret_cast<int32_t *>(b + off_bad);
+    ss.adapt = reinterpret_cast<int32_t *>(b + off_ad);
     ss.wf_mean = b + off_wm;
     ss.wf_m2 = b + off_w2;
 
@@ -143,6 +148,9 @@ extern "C" gac_status gac_mcmc_run_noalloc(int model_id, const void *data, int64
     ra.row_stride = row_stride_for(mc.kind, mc.n_meas);
     ra.data_vec4 = (mc.n_meas % 4 == 0) && ((reinterpret_cast<uintptr_t>(data) & 15) == 0);
     ra.n_tiles = (n_vox + ra.vox_per_block - 1) / ra.vox_per_block;
+    set_adaptation(ra, o);
+    ra.rhat = out->rhat;
+    ra.step_scale = out->step_scale;
 
     const void *fn = noalloc_fn(mc.kind);
     const size_t smem = tile_smem_bytes(mc.n_par, 8, ra.vox_per_block, ra.row_stride, false);

@@ -74,7 +74,7 @@ __device__ __forceinline__ double u01_d(uint32_t w) {
 }
 
 // Box-Muller in FP32 on the special-function unit.  Radius
-// sqrt(-2 ln u1) from the hardware log2 (absolute error ~4e-7 near u1 = 1,
+// sqrt(-2 ln u1) from the hardware log2 (absolute error ~2e-7 near u1 = 1,
 // 3 ulp elsewhere) and reciprocal square root, guarded so that a log that
 // rounds to >= 0 gives radius ~0 rather than NaN; angle 2 pi u2 taken
 // through the signed word, 2 pi ((int32) w + 1/2) 2^-32 in [-pi, pi) -- the
@@ -82,8 +82,13 @@ __device__ __forceinline__ double u01_d(uint32_t w) {
 // The pair stays rotationally symmetric, so the proposal stays symmetric
 // and the Metropolis rule exact; the deviation from exact Box-Muller normals
 // is ~1e-6 (up to ~1e-3 only when u1 is within 1e-6 of 1).
-__device__ __forceinline__ void box_muller_f(uint32_t w1, uint32_t w2, float &z0, float &z1) {
-    const float x = fmaxf(-2.0f * __logf(u01_f(w1)), 1e-30f);
+// The radius is taken as sqrt(k log2 u1) with k = -2 ln 2 s^2, which scales
+// both normals by s > 0 (the MH step multiplier) at no extra cost; the
+// default k gives the standard pair (s = 1).
+constexpr float kNeg2Ln2 = -1.38629436111989061883f;  // -2 ln 2
+__device__ __forceinline__ void box_muller_f(uint32_t w1, uint32_t w2, float &z0, float &z1,
+                                             float k = kNeg2Ln2) {
+    const float x = fmaxf(k * __log2f(u01_f(w1)), 1e-30f);
     const float r = x * rsqrtf(x);
     const float ang = fmaf(static_cast<float>(static_cast<int32_t>(w2)), 1.46291807926715968e-9f,
                            7.31459039633579840e-10f);  // 2 pi 2^-32, pi 2^-32
@@ -93,10 +98,12 @@ __device__ __forceinline__ void box_muller_f(uint32_t w1, uint32_t w2, float &z0
     z1 = r * s;
 }
 
-__device__ __forceinline__ void box_muller_d(uint32_t w1, uint32_t w2, double &z0, double &z1) {
+// k = -2 s^2 scales both normals by s > 0; -2 gives the standard pair.
+__device__ __forceinline__ void box_muller_d(uint32_t w1, uint32_t w2, double &z0, double &z1,
+                                             double k = -2.0) {
     const double u1 = u01_d(w1);
     const double u2 = u01_d(w2);
-    const double r = sqrt(-2.0 * log(u1));
+    const double r = sqrt(k * log(u1));
     double s, c;
     sincospi(2.0 * u2, &s, &c);
     z0 = r * c;

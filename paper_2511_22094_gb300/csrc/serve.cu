@@ -132,8 +132,8 @@ struct Job {
     // host copies of inputs (pinned) and results (pinned)
     float *h_data = nullptr, *h_sigma = nullptr;
     float sigma_scalar = 0.0f;
-    double *h_mean = nullptr, *h_std = nullptr;
-    float *h_samples = nullptr, *h_acc = nullptr;
+    double *h_mean = nullptr, *h_std = nullptr, *h_rhat = nullptr;
+    float *h_samples = nullptr, *h_acc = nullptr, *h_scale = nullptr;
     int32_t *h_bad = nullptr;
     // device block holding inputs, state and outputs
     void *d_block = nullptr;
@@ -143,7 +143,8 @@ struct Job {
 
 // Layout of one job's device block.
 struct JobLayout {
-    size_t data, sigma, theta, L, n_acc, n_bad, wf_mean, wf_m2, mean, std, acc, bad, samples, total;
+    size_t data, sigma, theta, L, n_acc, n_bad, adapt, wf_mean, wf_m2, mean, std, acc, bad, rhat, scale, samples,
+        total;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
@@ -161,12 +162,15 @@ static JobLayout job_layout(const ModelConst &mc, int64_t n_vox, const gac_mcmc_
     l.L = take(N * C * 4);
     l.n_acc = take(N * C * 4);
     l.n_bad = take(N * C * 4);
+    l.adapt = take(2 * N * C * 4);
     l.wf_mean = take(P * N * C * 8);
     l.wf_m2 = take(P * N * C * 8);
     l.mean = take(P * N * 8);
     l.std = take(P * N * 8);
     l.acc = take(C * N * 4);
     l.bad = take(C * N * 4);
+    l.rhat = take(P * N * 8);
+    l.scale = take(C * N * 4);
     l.samples = take(S * C * P * N * 4);
     l.total = off;
     return l;
@@ -257,10 +261,11 @@ void gac_server::free_job(Job &j) {
 
 static void free_results(Job &j) {
     for (void *p : {static_cast<void *>(j.h_mean), static_cast<void *>(j.h_std), static_cast<void *>(j.h_samples),
-                    static_cast<void *>(j.h_acc), static_cast<void *>(j.h_bad)})
+                    static_cast<void *>(j.h_acc), static_cast<void *>(j.h_bad), static_cast<void *>(j.h_rhat),
+                    static_cast<void *>(j.h_scale)})
         if (p) cudaFreeHost(p);
-    j.h_mean = j.h_std = nullptr;
-    j.h_samples = j.h_acc = nullptr;
+    j.h_mean = j.h_std = j.h_rhat = nullptr;
+    j.h_samples = j.h_acc = j.h_scale = nullptr;
     j.h_bad = nullptr;
 }
 
@@ -293,6 +298,8 @@ gac_status gac_server::admit_locked() {
         if (e == cudaSuccess) e = cudaMallocHost(&j.h_std, P * N * 8);
         if (e == cudaSuccess) e = cudaMallocHost(&j.h_acc, C * N * 4);
         if (e == cudaSuccess) e = cudaMallocHost(&j.h_bad, C * N * 4);
+        if (e == cudaSuccess) e = cudaMallocHost(&j.h_rhat, P * N * 8);
+        if (e == cudaSuccess) e = cudaMallocHost(&j.h_scale, C * N * 4);
         if (e == cudaSuccess && j.keep_samples && j.S > 0)
             e = cudaMallocHost(&j.h_samples, static_cast<size_t>(j.S) * C * P * N * 4);
         if (e == cudaSuccess) e = cudaEventRecord(j.ev, s_copy);
@@ -330,11 +337,15 @@ gac_status gac_server::admit_locked() {
         ra.row_stride = row_stride_for(j.mc.kind, j.mc.n_meas);
         ra.data_vec4 = (j.mc.n_meas % 4) == 0;
         ra.n_tiles = (j.n_vox + ra.vox_per_block - 1) / ra.vox_per_block;
+        set_adaptation(ra, &j.opts);
+        ra.rhat = reinterpret_cast<double *>(b + l.rhat);
+        ra.step_scale = reinterpret_cast<float *>(b + l.scale);
         SliceState &ss = j.desc.ss;
         ss.theta = b + l.theta;
         ss.L = b + l.L;
         ss.n_acc = reinterpret_cast<int32_t *>(b + l.n_acc);
         ss.n_bad = reinterpret_cast<int32_t *>(b + l.n_bad);
+        ss.adapt = reinterpret_cast<int32_t *>(b + l.adapt);
         ss.wf_mean = b + l.wf_mean;
         ss.wf_m2 = b + l.wf_m2;
         j.desc.mc = j.mc;
@@ -507,6 +518,8 @@ gac_status gac_server::run_round() {
         if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_std, ra.std, P * N * 8, cudaMemcpyDeviceToHost, s_copy);
         if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_acc, ra.accept, C * N * 4, cudaMemcpyDeviceToHost, s_copy);
         if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_bad, ra.nonfinite, C * N * 4, cudaMemcpyDeviceToHost, s_copy);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_rhat, ra.rhat, P * N * 8, cudaMemcpyDeviceToHost, s_copy);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_scale, ra.step_scale, C * N * 4, cudaMemcpyDeviceToHost, s_copy);
         if (e == cudaSuccess && ra.samples)
             e = cudaMemcpyAsync(j.h_samples, ra.samples, static_cast<size_t>(j.S) * C * P * N * 4,
                                 cudaMemcpyDeviceToHost, s_copy);
@@ -697,6 +710,9 @@ static gac_status deliver(gac_server *srv, std::map<uint64_t, std::shared_ptr<Jo
             if (out->std && e == cudaSuccess) e = cudaMemcpy(out->std, j.h_std, P * N * 8, cudaMemcpyDefault);
             if (out->accept_rate && e == cudaSuccess) e = cudaMemcpy(out->accept_rate, j.h_acc, C * N * 4, cudaMemcpyDefault);
             if (out->nonfinite && e == cudaSuccess) e = cudaMemcpy(out->nonfinite, j.h_bad, C * N * 4, cudaMemcpyDefault);
+            if (out->rhat && e == cudaSuccess) e = cudaMemcpy(out->rhat, j.h_rhat, P * N * 8, cudaMemcpyDefault);
+            if (out->step_scale && e == cudaSuccess)
+                e = cudaMemcpy(out->step_scale, j.h_scale, C * N * 4, cudaMemcpyDefault);
             if (out->samples && j.h_samples && e == cudaSuccess)
                 e = cudaMemcpy(out->samples, j.h_samples, static_cast<size_t>(j.S) * C * P * N * 4, cudaMemcpyDefault);
         }

@@ -40,7 +40,8 @@ class ModelDesc(ct.Structure):
 class McmcOpts(ct.Structure):
     _fields_ = [("iterations", ct.c_int), ("burnin", ct.c_int), ("thin", ct.c_int),
                 ("n_chains", ct.c_int), ("seed", ct.c_uint64), ("voxel_base", ct.c_uint64),
-                ("precision", ct.c_int), ("moments_mode", ct.c_int), ("trace_n_vox", ct.c_int)]
+                ("precision", ct.c_int), ("moments_mode", ct.c_int), ("trace_n_vox", ct.c_int),
+                ("adapt_window", ct.c_int), ("adapt_target", ct.c_double)]
 
 
 class TraceRec(ct.Structure):
@@ -55,9 +56,11 @@ TRACE_DTYPE = np.dtype([("theta", np.float64, MAX_PAR), ("prop", np.float64, MAX
 assert TRACE_DTYPE.itemsize == ct.sizeof(TraceRec)
 
 
+RESULT_KEYS = ("mean", "std", "samples", "accept_rate", "nonfinite", "trace", "rhat", "step_scale")
+
+
 class Result(ct.Structure):
-    _fields_ = [("mean", ct.c_void_p), ("std", ct.c_void_p), ("samples", ct.c_void_p),
-                ("accept_rate", ct.c_void_p), ("nonfinite", ct.c_void_p), ("trace", ct.c_void_p)]
+    _fields_ = [(k, ct.c_void_p) for k in RESULT_KEYS]
 
 
 class ServerStats(ct.Structure):
@@ -83,7 +86,7 @@ def _load():
     sig = {
         "gac_model_register": [ct.POINTER(ModelDesc), ct.POINTER(ct.c_int)],
         "gac_model_info": [ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)],
-        "gac_result_sizes": [ct.c_int, i64, ct.POINTER(McmcOpts), ct.POINTER(ct.c_size_t * 6)],
+        "gac_result_sizes": [ct.c_int, i64, ct.POINTER(McmcOpts), ct.POINTER(ct.c_size_t * len(RESULT_KEYS))],
         "gac_mcmc_run": [ct.c_int, vp, i64, vp, ct.c_float, vp, ct.POINTER(McmcOpts),
                          ct.POINTER(Result), vp],
         "gac_forward": [ct.c_int, vp, i64, ct.c_int, vp, vp],
@@ -173,23 +176,23 @@ def gac_model_info(model_id: int):
 
 
 def make_opts(iterations, burnin, thin, n_chains, seed, voxel_base=0, precision=PREC_MIXED,
-              moments_mode=MOMENTS_THINNED, trace_n_vox=0) -> McmcOpts:
+              moments_mode=MOMENTS_THINNED, trace_n_vox=0, adapt_window=0,
+              adapt_target=0.0) -> McmcOpts:
     return McmcOpts(iterations, burnin, thin, n_chains, seed, voxel_base, precision, moments_mode,
-                    trace_n_vox)
+                    trace_n_vox, adapt_window, adapt_target)
 
 
 def gac_result_sizes(model_id: int, n_vox: int, opts: McmcOpts):
-    b = (ct.c_size_t * 6)()
+    b = (ct.c_size_t * len(RESULT_KEYS))()
     _check(_lib.gac_result_sizes(model_id, n_vox, ct.byref(opts), ct.byref(b)), "gac_result_sizes")
-    return dict(zip(("mean", "std", "samples", "accept_rate", "nonfinite", "trace"), list(b)))
+    return dict(zip(RESULT_KEYS, list(b)))
 
 
 def gac_mcmc_run(model_id: int, data, n_vox: int, sigma, sigma_scalar: float, x0,
                  opts: McmcOpts, out: dict, stream=None):
-    """out: dict with any of mean, std, samples, accept_rate, nonfinite, trace
-    (caller-allocated numpy arrays or tensors, host or device)."""
-    r = Result(*(_ptr(out.get(k)) for k in ("mean", "std", "samples", "accept_rate", "nonfinite",
-                                             "trace")))
+    """out: dict with any of RESULT_KEYS (caller-allocated numpy arrays or
+    tensors, host or device)."""
+    r = _result(out)
     _check(_lib.gac_mcmc_run(model_id, _ptr(data), n_vox, _ptr(sigma), sigma_scalar, _ptr(x0),
                              ct.byref(opts), ct.byref(r), _stream(stream)), "gac_mcmc_run")
 
@@ -197,8 +200,7 @@ def gac_mcmc_run(model_id: int, data, n_vox: int, sigma, sigma_scalar: float, x0
 def gac_ensemble_run(model_id: int, data, n_vox: int, sigma, sigma_scalar: float, x0,
                      opts: McmcOpts, stretch: float, out: dict, stream=None):
     """Affine-invariant ensemble sampler; opts.n_chains = walkers."""
-    r = Result(*(_ptr(out.get(k)) for k in ("mean", "std", "samples", "accept_rate", "nonfinite",
-                                             "trace")))
+    r = _result(out)
     _check(_lib.gac_ensemble_run(model_id, _ptr(data), n_vox, _ptr(sigma), sigma_scalar, _ptr(x0),
                                  ct.byref(opts), stretch, ct.byref(r), _stream(stream)),
            "gac_ensemble_run")
@@ -207,8 +209,7 @@ def gac_ensemble_run(model_id: int, data, n_vox: int, sigma, sigma_scalar: float
 def gac_mcmc_run_noalloc(model_id: int, data, n_vox: int, sigma, sigma_scalar: float, x0,
                          opts: McmcOpts, slice_iterations: int, out: dict, stream=None):
     """Allocation-free sampler run (device buffers only); see include/gac.h."""
-    r = Result(*(_ptr(out.get(k)) for k in ("mean", "std", "samples", "accept_rate", "nonfinite",
-                                             "trace")))
+    r = _result(out)
     _check(_lib.gac_mcmc_run_noalloc(model_id, _ptr(data), n_vox, _ptr(sigma), sigma_scalar,
                                      _ptr(x0), ct.byref(opts), slice_iterations, ct.byref(r),
                                      _stream(stream)), "gac_mcmc_run_noalloc")
@@ -237,8 +238,7 @@ def gac_normals(seed: int, t, v, c, n: int, n_par: int, precision: int, z, w_acc
 # ------------------------------------------------------------- serving -----
 def _result(out):
     out = out or {}
-    return Result(*(_ptr(out.get(k)) for k in ("mean", "std", "samples", "accept_rate",
-                                              "nonfinite", "trace")))
+    return Result(*(_ptr(out.get(k)) for k in RESULT_KEYS))
 
 
 def gac_server_create(hbm_budget_bytes: int, max_resident_jobs: int):
@@ -303,7 +303,8 @@ def n_samples(iterations: int, burnin: int, thin: int) -> int:
 
 def run_host(model_id: int, data: np.ndarray, sigma, *, iterations, burnin, thin, n_chains, seed,
              x0=None, sigma_scalar=0.0, voxel_base=0, precision=PREC_MIXED,
-             moments_mode=MOMENTS_THINNED, trace_n_vox=0, want_samples=True):
+             moments_mode=MOMENTS_THINNED, trace_n_vox=0, want_samples=True, adapt_window=0,
+             adapt_target=0.0):
     """Runs the sampler on host numpy inputs (the library stages them through
     device memory) and returns host numpy outputs."""
     P, M = gac_model_info(model_id)
@@ -314,11 +315,12 @@ def run_host(model_id: int, data: np.ndarray, sigma, *, iterations, burnin, thin
     out = dict(mean=np.full((P, N), np.nan), std=np.full((P, N), np.nan),
                samples=np.full((S, C, P, N), np.nan, np.float32) if (want_samples and S) else None,
                accept_rate=np.zeros((C, N), np.float32), nonfinite=np.zeros((C, N), np.int32),
-               trace=np.zeros((trace_n_vox, C, iterations), TRACE_DTYPE) if trace_n_vox else None)
+               trace=np.zeros((trace_n_vox, C, iterations), TRACE_DTYPE) if trace_n_vox else None,
+               rhat=np.full((P, N), np.nan), step_scale=np.zeros((C, N), np.float32))
     sig = None if sigma is None else np.ascontiguousarray(sigma, np.float32)
     x0a = None if x0 is None else np.ascontiguousarray(x0, np.float32)
     opts = make_opts(iterations, burnin, thin, n_chains, seed, voxel_base, precision, moments_mode,
-                     trace_n_vox)
+                     trace_n_vox, adapt_window, adapt_target)
     gac_mcmc_run(model_id, data, N, sig, sigma_scalar, x0a, opts, out)
     return out
 

@@ -93,6 +93,8 @@ def test_run_argument_validation(gac):
     cases = [
         dict(iterations=-1), dict(burnin=-1), dict(thin=0), dict(n_chains=0), dict(n_chains=65),
         dict(precision=3), dict(moments_mode=2), dict(trace_n_vox=5),
+        dict(adapt_window=-1), dict(adapt_window=10, adapt_target=0.0),
+        dict(adapt_window=10, adapt_target=1.0), dict(adapt_window=10, adapt_target=float("nan")),
     ]
     for c in cases:
         kw = dict(iterations=10, burnin=0, thin=1, n_chains=1, seed=1)
@@ -120,7 +122,8 @@ def test_result_sizes(gac):
     opts = gac.make_opts(2000, 500, 5, 3, 1, trace_n_vox=2)
     b = gac.gac_result_sizes(mid, 100, opts)
     assert b == dict(mean=2 * 100 * 8, std=2 * 100 * 8, samples=300 * 3 * 2 * 100 * 4,
-                     accept_rate=3 * 100 * 4, nonfinite=3 * 100 * 4, trace=2 * 3 * 2000 * 216)
+                     accept_rate=3 * 100 * 4, nonfinite=3 * 100 * 4, trace=2 * 3 * 2000 * 216,
+                     rhat=2 * 100 * 8, step_scale=3 * 100 * 4)
     b0 = gac.gac_result_sizes(mid, 100, gac.make_opts(400, 500, 5, 1, 1))
     assert b0["samples"] == 0
 
@@ -153,3 +156,23 @@ def test_server_host_side_checks(gac):
         assert st["queued"] == 0 and st["budget"] == 1 << 20
     finally:
         gac.gac_server_destroy(srv)
+
+
+def test_ensemble_rejects_mh_only_options(gac):
+    mid = gac.gac_model_register(**MONO)
+    y = np.zeros((4, 12), np.float32)
+    for opts, out in ((gac.make_opts(10, 0, 1, 8, 1, adapt_window=5, adapt_target=0.3), {}),
+                      (gac.make_opts(10, 0, 1, 8, 1), {"rhat": np.zeros((2, 4))}),
+                      (gac.make_opts(10, 0, 1, 8, 1), {"step_scale": np.zeros((8, 4), np.float32)})):
+        with pytest.raises(gac.GacError) as e:
+            gac.gac_ensemble_run(mid, y, 4, None, 0.01, None, opts, 2.0, out)
+        assert e.value.status == 1 and "MH sampler" in gac.last_error()
+
+
+def test_register_same_description_returns_same_id(gac):
+    a = gac.gac_model_register(**MONO)
+    b = gac.gac_model_register(**MONO)
+    d = dict(MONO)
+    d["step"] = [0.02, 1.0]
+    c = gac.gac_model_register(**d)
+    assert a == b and c != a

@@ -186,6 +186,16 @@ def test_determinism_tiling_split_and_pointer_kinds(gac, orc):
     torch.cuda.synchronize()
     np.testing.assert_array_equal(out["mean"].cpu().numpy(), a["mean"])
     np.testing.assert_array_equal(out["samples"].cpu().numpy(), a["samples"])
+    # page-locked host buffers (read and written in place by the kernel) too
+    hy = torch.from_numpy(y).pin_memory()
+    hs = torch.from_numpy(sig).pin_memory()
+    hout = dict(mean=torch.empty((P, n), dtype=torch.float64).pin_memory(),
+                std=torch.empty((P, n), dtype=torch.float64).pin_memory(),
+                samples=torch.empty((S, C, P, n), dtype=torch.float32).pin_memory(),
+                accept_rate=torch.empty((C, n), dtype=torch.float32).pin_memory())
+    gac.gac_mcmc_run(mid, hy, n, hs, 0.0, None, opts, hout, torch.cuda.current_stream())
+    for k, v in hout.items():
+        np.testing.assert_array_equal(v.numpy(), a[k], err_msg=f"pinned {k}")
 
 
 def test_degenerate_options(gac, orc):

@@ -16,27 +16,28 @@ pytestmark = pytest.mark.gpu
 
 
 def _jobs(orc, gac):
-    specs = [
-        (W.MONOEXP_4K, 3000, 1, 700, 100, 5),
-        (W.MWI3_1M, 1500, 4, 600, 60, 20),
-        (W.SMT_1P5M, 2500, 3, 900, 90, 30),
-        (W.MONOEXP_4K, 257, 2, 1200, 120, 10),
-        (W.MWI3_1M, 333, 1, 400, 40, 40),
-        (W.SMT_1P5M, 64, 4, 350, 35, 7),
-        (W.MWI3_1M, 120_000, 4, 1500, 150, 50),  # large: sliced over many rounds
+    specs = [  # (workload, voxels, chains, I, B, T, burn-in adaptation window)
+        (W.MONOEXP_4K, 3000, 1, 700, 100, 5, 0),
+        (W.MWI3_1M, 1500, 4, 600, 60, 20, 15),
+        (W.SMT_1P5M, 2500, 3, 900, 90, 30, 0),
+        (W.MONOEXP_4K, 257, 2, 1200, 120, 10, 0),
+        (W.MWI3_1M, 333, 1, 400, 40, 40, 0),
+        (W.SMT_1P5M, 64, 4, 350, 35, 7, 5),
+        (W.MWI3_1M, 120_000, 4, 1500, 150, 50, 25),  # large: sliced over many rounds
     ]
     jobs = []
-    for i, (w, n, C, I, B, T) in enumerate(specs):
+    for i, (w, n, C, I, B, T, Wa) in enumerate(specs):
         mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
         th, sig, y = make_voxels(orc, w, 1000 * i, n)
-        opts = gac.make_opts(I, B, T, C, 77 + i)
+        opts = gac.make_opts(I, B, T, C, 77 + i, adapt_window=Wa, adapt_target=0.3 if Wa else 0.0)
         jobs.append((w, mid, y, sig, opts))
     return jobs
 
 
 def _alone(gac, mid, y, sig, opts):
     return gac.run_host(mid, y, sig, iterations=opts.iterations, burnin=opts.burnin, thin=opts.thin,
-                        n_chains=opts.n_chains, seed=opts.seed)
+                        n_chains=opts.n_chains, seed=opts.seed, adapt_window=opts.adapt_window,
+                        adapt_target=opts.adapt_target)
 
 
 def _out_like(ref):
@@ -54,10 +55,11 @@ def test_mix_equals_alone(gac, orc):
             out = _out_like(ref)
             lat = gac.gac_server_wait(srv, jid, 300.0, out)
             assert lat > 0
-            for k in ("samples", "accept_rate", "nonfinite"):
+            for k in ("samples", "accept_rate", "nonfinite", "step_scale"):
                 np.testing.assert_array_equal(out[k], ref[k], err_msg=k)
             np.testing.assert_allclose(out["mean"], ref["mean"], rtol=1e-12, atol=0)
             np.testing.assert_allclose(out["std"], ref["std"], rtol=1e-9, atol=0)
+            np.testing.assert_allclose(out["rhat"], ref["rhat"], rtol=1e-9, atol=0)
         st = gac.gac_server_get_stats(srv)
         assert st["finished"] == len(jobs) and st["rounds"] > 1 and st["bytes_in_use"] == 0
     finally:

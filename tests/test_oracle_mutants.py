@@ -7,6 +7,7 @@ that kind of mistake.  A pin that still passed would not be pinning anything.
 import numpy as np
 import pytest
 
+import test_oracle_adapt as A
 import test_oracle_ensemble as E
 import test_oracle_models as M
 import test_oracle_rng as R
@@ -58,8 +59,8 @@ CASES = [
      S.test_thinning_grid_and_moments),
     ("acceptance sign", "if (log_u < Lp - L)", "if (log_u < L - Lp)",
      S.test_chain_init_and_every_transition),
-    ("no clamp", "prop[p] = clampd(theta[p] + m->step[p] * z[p], m->lb[p], m->ub[p]);",
-     "prop[p] = theta[p] + m->step[p] * z[p];", S.test_degenerate_runs),
+    ("no clamp", "prop[p] = clampd(theta[p] + m->step[p] * (lambda * z[p]), m->lb[p], m->ub[p]);",
+     "prop[p] = theta[p] + m->step[p] * (lambda * z[p]);", S.test_degenerate_runs),
     ("SD divisor n", "sqrt(ss / (double)(n_all - 1))", "sqrt(ss / (double)n_all)",
      S.test_thinning_grid_and_moments),
     ("MH without acceptance test", "if (log_u < Lp - L) {", "if (1) {",
@@ -72,6 +73,17 @@ CASES = [
     ("ensemble prior box ignored", "if (!inside) continue;", "(void)inside;", E.test_every_walker_move),
     ("ensemble stationary law (z^P)", "(double)(P - 1) * log(z)", "(double)P * log(z)",
      E.test_linear_gaussian_posterior),
+    ("R-hat chain-mean divisor", "B_over_n /= (C - 1);", "B_over_n /= C;", A.test_rhat_hand_examples),
+    ("R-hat within-chain divisor", "W += ss / (n - 1);", "W += ss / n;", A.test_rhat_hand_examples),
+    ("adaptation after burn-in", "t <= B && t % o->adapt_window == 0", "t % o->adapt_window == 0",
+     lambda orc: A.test_adaptation_when_every_proposal_is_accepted(orc, 100, 10, 10)),
+    ("adaptation direction", "if (a > target && e < ORC_ADAPT_EMAX) ++e;",
+     "if (a > target && e < ORC_ADAPT_EMAX) --e;",
+     lambda orc: A.test_adaptation_when_every_proposal_is_accepted(orc, 100, 10, 10)),
+    ("adaptation multiplier", "lambda = exp2(0.25 * (double)e);", "lambda = exp2(0.5 * (double)e);",
+     lambda orc: A.test_adaptation_when_every_proposal_is_accepted(orc, 100, 10, 10)),
+    ("adaptation floor", "if (a < target && e > ORC_ADAPT_EMIN) --e;", "if (a < target) --e;",
+     lambda orc: A.test_adaptation_when_every_proposal_is_rejected(orc, 700, -48)),
 ]
 
 
