@@ -43,6 +43,9 @@ OPS = {
     "mwi3_1m": dict(mufu=240, fp32=520, int=180),
     "smt_1p5m": dict(mufu=51, fp32=103, int=120),
     "monoexp_4k": dict(mufu=17, fp32=65, int=60),
+    # 2 timings x 18 cylinder-series terms x (3 exp + 12 FP32) + 16 b-values x
+    # (2 exp + 2 g at 4 MUFU + 8 FP32 each + 10 FP32)
+    "axcal_250k": dict(mufu=275, fp32=888, int=120),
 }
 # Ensemble walker-move counts: the same model evaluation, one Philox call, no
 # Box-Muller; the stretch z costs a log (MUFU) and a few FP32 ops.
@@ -50,6 +53,7 @@ OPS_ENSEMBLE = {
     "mwi3_1m": dict(mufu=221, fp32=490, int=60),
     "smt_1p5m": dict(mufu=44, fp32=92, int=60),
     "monoexp_4k": dict(mufu=14, fp32=64, int=60),
+    "axcal_250k": dict(mufu=269, fp32=874, int=60),
 }
 MUFU_PER_CLK_SM = 16
 FP32_PER_CLK_SM = 128
@@ -61,7 +65,8 @@ ISSUE_PER_CLK_SM = 4  # warp-instructions
 # the value they were measured with (otherwise null).
 KERNEL_SOURCES = ("include/gac.h", "paper_2511_22094_gb300/csrc/mh_kernel.cuh",
                   "paper_2511_22094_gb300/csrc/models.cuh", "paper_2511_22094_gb300/csrc/philox.cuh")
-KIND_SOURCE = {"mwi3_1m": "mh_mwi3.cu", "smt_1p5m": "mh_smt.cu", "monoexp_4k": "mh_monoexp.cu"}
+KIND_SOURCE = {"mwi3_1m": "mh_mwi3.cu", "smt_1p5m": "mh_smt.cu", "monoexp_4k": "mh_monoexp.cu",
+               "axcal_250k": "mh_axcal.cu"}
 MEASURED = {
     "mwi3_1m": dict(sources="8558c16b51c6b58f", traffic_bytes=292.6e6 + 6623.0e6, warp_instr=990.0),
     "smt_1p5m": dict(sources="cd1636cf11cf4662", traffic_bytes=None, warp_instr=684.7),

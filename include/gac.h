@@ -62,6 +62,7 @@ typedef enum {
     GAC_MODEL_MONOEXP = 1,
     GAC_MODEL_MWI3 = 2,
     GAC_MODEL_SMT = 3,
+    GAC_MODEL_AXCAL_SMT = 4,
     GAC_MODEL_LINEAR_TEST = 100
 } gac_model_kind;
 

@@ -126,6 +126,10 @@ def _declare(L):
     L.orc_n_samples.restype = ct.c_int
     L.orc_stretch_z.argtypes = [ct.c_uint32, ct.c_double]
     L.orc_stretch_z.restype = ct.c_double
+    L.orc_j1p_zero.argtypes = [ct.c_int]
+    L.orc_j1p_zero.restype = ct.c_double
+    L.orc_cyl_kappa.argtypes = [ct.c_double] * 5
+    L.orc_cyl_kappa.restype = ct.c_double
     L.orc_rhat.argtypes = [f64, ct.c_int, ct.c_int, ct.c_size_t]
     L.orc_rhat.restype = ct.c_double
     L.orc_max_threads.argtypes = []
@@ -275,6 +279,16 @@ def mcmc_run(kind, acq, lb, ub, step, data, sigma, *, iterations, burnin, thin, 
         raise ValueError("oracle rejected the arguments")
     return dict(mean=mean, std=std, samples=samples, accept_rate=acc, nonfinite=bad, rhat=rhat,
                 step_scale=scale, threads=used.value)
+
+
+def j1p_zero(m):
+    """m-th positive zero of J1' (m >= 1)."""
+    return lib().orc_j1p_zero(m)
+
+
+def cyl_kappa(b, Delta, delta, R, D):
+    """-ln of the perpendicular signal of a cylinder (Gaussian phase approximation)."""
+    return lib().orc_cyl_kappa(b, Delta, delta, R, D)
 
 
 def rhat(chains):

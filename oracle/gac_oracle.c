@@ -29,6 +29,7 @@
  * quadrature, cuRAND's host Philox), exact linear-Gaussian posteriors and
  * brute-force grid posteriors.  No function is "parity unpinned".
  */
+#define _XOPEN_SOURCE 700 /* j0, j1 */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -40,6 +41,7 @@
 #define ORC_MONOEXP 1
 #define ORC_MWI3 2
 #define ORC_SMT 3
+#define ORC_AXCAL 4
 #define ORC_LINEAR 100
 
 #define ORC_INIT_ITER 0xFFFFFFFFu
@@ -113,14 +115,17 @@ int orc_n_par(int kind) {
     case ORC_MONOEXP: return 2;
     case ORC_MWI3: return 9;
     case ORC_SMT: return 4;
+    case ORC_AXCAL: return 4;
     case ORC_LINEAR: return 2;
     default: return -1;
     }
 }
 
-/* Real-valued measurements per voxel: complex models count re and im. */
+/* Real-valued measurements per voxel: complex models count re and im;
+ * AxCaliberSMT takes (b, Delta, delta) triplets. */
 int orc_n_meas(int kind, int n_acq) {
     if (kind == ORC_MWI3) return 2 * n_acq;
+    if (kind == ORC_AXCAL) return (n_acq % 3 == 0) ? n_acq / 3 : -1;
     if (orc_n_par(kind) < 0) return -1;
     return n_acq;
 }
@@ -145,6 +150,67 @@ double orc_g(double x) {
     return sum;
 }
 
+/* m-th positive zero (m >= 1) of J1'(x) = J0(x) - J1(x)/x, by bisection on
+ * [(m - 1/4) pi - 1, (m - 1/4) pi + 0.2], which holds exactly one zero
+ * (McMahon: the zeros lie just below (m - 1/4) pi). */
+double orc_j1p_zero(int m) {
+    double lo = (m - 0.25) * ORC_PI - 1.0, hi = (m - 0.25) * ORC_PI + 0.2;
+    if (lo < 0.5) lo = 0.5;
+    double flo = j0(lo) - j1(lo) / lo;
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        double fm = j0(mid) - j1(mid) / mid;
+        if ((fm < 0.0) == (flo < 0.0)) {
+            lo = mid;
+            flo = fm;
+        } else {
+            hi = mid;
+        }
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* e^{-y} - 1 + y, without the cancellation of the plain form for small y. */
+static double e_minus_one_plus(double y) { return expm1(-y) + y; }
+
+/* -ln E_perp of a cylinder of radius R [um] with intrinsic diffusivity D
+ * [um^2/ms] under a pulsed-gradient pair (b [ms/um^2], separation Delta,
+ * duration delta [ms]) in the Gaussian phase approximation (Neuman 1974;
+ * van Gelderen et al. 1994):
+ *   kappa = 2 gamma^2 G^2 sum_m R^6 / (D^2 x_m^6 (x_m^2 - 1)) N_m,
+ *   N_m = 2 delta q - 2 + 2 e^{-q delta} + 2 e^{-q Delta}
+ *         - e^{-q (Delta - delta)} - e^{-q (Delta + delta)},  q = x_m^2 D / R^2,
+ * x_m the zeros of J1', gamma^2 G^2 = b / (delta^2 (Delta - delta/3)).  N_m
+ * is summed as 2E(q delta) + 2E(q Delta) - E(q (Delta - delta)) -
+ * E(q (Delta + delta)) with E(y) = e^{-y} - 1 + y (the same sum; the linear
+ * and constant terms cancel exactly).  ORC_AX_TERMS zeros. */
+#define ORC_AX_TERMS 100
+static double orc_zeros[ORC_AX_TERMS];
+__attribute__((constructor)) static void orc_init_zeros(void) {
+    for (int m = 0; m < ORC_AX_TERMS; ++m) orc_zeros[m] = orc_j1p_zero(m + 1);
+}
+
+double orc_cyl_kappa(double b, double Delta, double delta, double R, double D) {
+    const double *zeros = orc_zeros;
+    double g2 = b / (delta * delta * (Delta - delta / 3.0));
+    double sum = 0.0;
+    for (int m = 0; m < ORC_AX_TERMS; ++m) {
+        double x = zeros[m], x2 = x * x;
+        double q = x2 * D / (R * R);
+        double N = 2.0 * e_minus_one_plus(q * delta) + 2.0 * e_minus_one_plus(q * Delta) -
+                   e_minus_one_plus(q * (Delta - delta)) - e_minus_one_plus(q * (Delta + delta));
+        double r2 = R * R;
+        sum += (r2 * r2 * r2) / (D * D * x2 * x2 * x2 * (x2 - 1.0)) * N;
+    }
+    return 2.0 * g2 * sum;
+}
+
+/* AxCaliberSMT's fixed diffusivities [um^2/ms] (Sec. 2.5): intra-axonal and
+ * extra-axonal parallel 1.7, free water 3. */
+#define ORC_AX_DA 1.7
+#define ORC_AX_DEPAR 1.7
+#define ORC_AX_DCSF 3.0
+
 /* Evaluates the forward model at theta; writes n_meas(kind, n_acq) reals.
  *  MONOEXP (Eq. 3):  s_k = S0 exp(-R2* TE_k), theta = (S0, R2* [1/s]),
  *                    acq = TE [ms].
@@ -153,6 +219,13 @@ double orc_g(double x) {
  *         phi0 [rad]), df_EW = 0, acq = TE [ms]; output (re, im) per echo.
  *  SMT:   s(b) = f g(b Da) + (1 - f) exp(-b De_perp) g(b (De_par - De_perp)), S0 = 1,
  *         theta = (f, Da, De_par, De_perp) [um^2/ms], acq = b [ms/um^2].
+ *  AXCAL: AxCaliberSMT (Sec. 2.5, after Fan et al. 2020), S0 = 1:
+ *         s = (1 - f_csf) [f_n e^{-k} g(b Da - k) + (1 - f_n) e^{-b De_R} g(b (De_par - De_R))]
+ *             + f_csf e^{-b D_csf},  k = orc_cyl_kappa(b, Delta, delta, a/2, Da),
+ *         the restricted cylinder's spherical mean being the orientation
+ *         average of e^{-b Da u^2 - k (1 - u^2)};
+ *         theta = (a [um, axon diameter], f_n, f_csf, De_R [um^2/ms]),
+ *         acq = (b [ms/um^2], Delta [ms], delta [ms]) per measurement.
  *  LINEAR: s_k = a + c t_k, theta = (a, c), acq = t. */
 int orc_forward(int kind, const double *acq, int n_acq, const double *theta, double *s) {
     switch (kind) {
@@ -182,6 +255,18 @@ int orc_forward(int kind, const double *acq, int n_acq, const double *theta, dou
             s[k] = f * intra + (1.0 - f) * extra;
         }
         return 0;
+    case ORC_AXCAL: {
+        if (n_acq % 3 != 0) return -1;
+        double R = 0.5 * theta[0], fn = theta[1], fcsf = theta[2], der = theta[3];
+        for (int k = 0; k < n_acq / 3; ++k) {
+            double b = acq[3 * k], Delta = acq[3 * k + 1], delta = acq[3 * k + 2];
+            double kap = orc_cyl_kappa(b, Delta, delta, R, ORC_AX_DA);
+            double restricted = exp(-kap) * orc_g(b * ORC_AX_DA - kap);
+            double hindered = exp(-b * der) * orc_g(b * (ORC_AX_DEPAR - der));
+            s[k] = (1.0 - fcsf) * (fn * restricted + (1.0 - fn) * hindered) + fcsf * exp(-b * ORC_AX_DCSF);
+        }
+        return 0;
+    }
     case ORC_LINEAR:
         for (int k = 0; k < n_acq; ++k) s[k] = theta[0] + theta[1] * acq[k];
         return 0;

@@ -50,6 +50,7 @@ static cudaError_t ens_dispatch(int kind, int prec, bool trace, int grid, size_t
     case GAC_MODEL_MONOEXP: return ens_by_prec<GAC_MODEL_MONOEXP>(prec, trace, grid, smem, s, mc, ra, ea, fn);
     case GAC_MODEL_MWI3: return ens_by_prec<GAC_MODEL_MWI3>(prec, trace, grid, smem, s, mc, ra, ea, fn);
     case GAC_MODEL_SMT: return ens_by_prec<GAC_MODEL_SMT>(prec, trace, grid, smem, s, mc, ra, ea, fn);
+    case GAC_MODEL_AXCAL_SMT: return ens_by_prec<GAC_MODEL_AXCAL_SMT>(prec, trace, grid, smem, s, mc, ra, ea, fn);
     default: return ens_by_prec<GAC_MODEL_LINEAR_TEST>(prec, trace, grid, smem, s, mc, ra, ea, fn);
     }
 }
@@ -122,6 +123,7 @@ extern "C" gac_status gac_ensemble_run(int model_id, const void *data, int64_t n
     ra.n_tiles = (n_vox + ra.vox_per_block - 1) / ra.vox_per_block;
     EnsArgs ea;
     ea.stretch = static_cast<float>(stretch);
+    ea.inv_stretch = static_cast<float>(1.0 / stretch);
     ea.stretch_d = stretch;
     ea.H = H;
 
@@ -132,6 +134,10 @@ extern "C" gac_status gac_ensemble_run(int model_id, const void *data, int64_t n
     ens_dispatch(mc.kind, o->precision, trace, 0, 0, s, mc, ra, ea, &fn);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return cuda_fail(e, "ensemble kernel smem");
+    // the walkers' positions and Welford accumulators live in shared memory:
+    // prefer the largest carveout, so that the register limit (2 blocks) binds
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return cuda_fail(e, "ensemble kernel carveout");
     int per_sm = 0, sms = 0, dev = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, smem)) != cudaSuccess)
         return cuda_fail(e, "occupancy");

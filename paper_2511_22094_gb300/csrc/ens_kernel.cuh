@@ -23,6 +23,7 @@ namespace gac {
 
 struct EnsArgs {
     float stretch;    // a > 1
+    float inv_stretch;
     double stretch_d;
     int H;            // walkers per half
 };
@@ -36,7 +37,7 @@ __host__ __device__ inline size_t ens_smem_bytes(int P, size_t r_bytes, size_t w
 }
 
 template <int KIND, int PREC, bool TRACE>
-__global__ void __launch_bounds__(kBlock) ens_kernel(const ModelConst mc, const RunArgs ra, const EnsArgs ea) {
+__global__ void __launch_bounds__(kBlock, 2) ens_kernel(const ModelConst mc, const RunArgs ra, const EnsArgs ea) {
     using R = typename PrecTraits<PREC>::R;
     using W = typename PrecTraits<PREC>::W;
     constexpr int P = model_n_par(KIND);
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(kBlock) ens_kernel(const ModelConst mc, const 
                         z = __dmul_rn(s, s) / ea.stretch_d;
                     } else {
                         const float s = fmaf(ea.stretch - 1.0f, u01_f(w[1]), 1.0f);
-                        z = s * s / ea.stretch;
+                        z = s * s * ea.inv_stretch;
                     }
                     const R *xk = X + (lv * L + k) * P;
                     const R *xj = X + (lv * L + j) * P;
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(kBlock) ens_kernel(const ModelConst mc, const 
                         // enters as an offset of the likelihood difference
                         R logz_term;
                         if constexpr (PREC == GAC_PREC_FP64) logz_term = (P - 1) * log(z);
-                        else logz_term = static_cast<float>(P - 1) * logf(z);
+                        else logz_term = static_cast<float>(P - 1) * __logf(z);  // z in [1/a, a]
                         acc = accept_step<PREC>(Lp + logz_term, Lk, w[2]);
                     }
                     if constexpr (TRACE) {
@@ -236,27 +237,13 @@ __global__ void __launch_bounds__(kBlock) ens_kernel(const ModelConst mc, const 
             }
         }
         __syncthreads();
-        // pool the walkers of each voxel in walker order
-        if (active && i == 0 && (ra.mean || ra.std)) {
+        // pool the walkers of each voxel; its threads take the parameters in turn
+        if (active && (ra.mean || ra.std)) {
             const int n_each = all_mode ? max(ra.I - ra.B, 0) : ra.S;
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                const int q0 = p * nw + lv * L;
-                W mu = wf_mean[q0];
-                W m2 = wf_m2[q0];
-                double n = n_each;
-                for (int k = 1; k < L; ++k) {
-                    const double ntot = n + n_each;
-                    const W delta = wf_mean[q0 + k] - mu;
-                    mu += delta * W(n_each / ntot);
-                    m2 += wf_m2[q0 + k] + delta * delta * W(n * n_each / ntot);
-                    n = ntot;
-                }
-                const double nan = __longlong_as_double(0x7ff8000000000000ll);
-                if (ra.mean) ra.mean[p * ra.n_vox + v] = n > 0 ? static_cast<double>(mu) : nan;
-                if (ra.std)
-                    ra.std[p * ra.n_vox + v] = n > 1 ? sqrt(static_cast<double>(m2) / (n - 1.0)) : (n == 1 ? 0.0 : nan);
-            }
+            for (int p = i; p < P; p += H)
+                pool_chains(wf_mean + p * nw + lv * L, wf_m2 + p * nw + lv * L, L, n_each,
+                            ra.mean ? ra.mean + p * ra.n_vox + v : nullptr, ra.std ? ra.std + p * ra.n_vox + v : nullptr,
+                            static_cast<double *>(nullptr));
         }
     }
 }

@@ -233,6 +233,92 @@ static gac_status build_g_table(int c_lo, ModelConst *mc) {
     return GAC_OK;
 }
 
+// ------------------------------------------------- AxCaliberSMT constants --
+// m-th positive zero of J1' (m >= 1): Newton's method on J1'(x) = J0(x) -
+// J1(x)/x, with J1''(x) = -J1'(x)/x - (1 - 1/x^2) J1(x) from Bessel's
+// equation, from McMahon's estimate (m - 1/4) pi - 7 / (8 (m - 1/4) pi).
+static double j1p_zero(int m) {
+    const double beta = (m - 0.25) * M_PI;
+    double x = beta - 7.0 / (8.0 * beta);
+    for (int it = 0; it < 50; ++it) {
+        const double j0 = std::cyl_bessel_j(0.0, x), j1 = std::cyl_bessel_j(1.0, x);
+        const double d1 = j0 - j1 / x;
+        const double d2 = -d1 / x - (1.0 - 1.0 / (x * x)) * j1;
+        const double step = d1 / d2;
+        x -= step;
+        if (std::fabs(step) < 1e-15 * x) break;
+    }
+    return x;
+}
+
+// N_m of the cylinder series in double (see ax_n_series_f for the forms).
+static double ax_n_host(double q, double dl, double DL) {
+    const double a = q * dl;
+    if (a < 1.0) return 2.0 * (std::expm1(-a) + a) - std::exp(-q * DL) * (std::expm1(a) + std::expm1(-a));
+    return 2.0 * a - 2.0 + 2.0 * (std::exp(-a) + std::exp(-q * DL)) - std::exp(-q * (DL - dl)) - std::exp(-q * (DL + dl));
+}
+
+// Per-measurement constants, distinct timings, series coefficients and the
+// number of terms: the FP32 evaluation keeps the terms whose tail stays below
+// 2e-8 of the sum for every timing at 64 radii spanning the prior box; the
+// FP64 evaluation keeps all kAxMaxTerms.
+static gac_status build_axcal(const gac_model_desc *d, ModelConst *mc) {
+    AxConst &ax = mc->ax;
+    const int K = d->n_acq / 3;
+    if (K > kAxMaxMeas) return fail(GAC_ERR_INVALID_ARG, "at most %d AxCaliberSMT measurements", kAxMaxMeas);
+    ax.n_timing = 0;
+    for (int k = 0; k < K; ++k) {
+        const double b = d->acq[3 * k], Delta = d->acq[3 * k + 1], delta = d->acq[3 * k + 2];
+        int t = 0;
+        while (t < ax.n_timing && !(ax.Delta_d[t] == Delta && ax.delta_d[t] == delta)) ++t;
+        if (t == ax.n_timing) {
+            if (t == kAxMaxTiming) return fail(GAC_ERR_INVALID_ARG, "at most %d distinct (Delta, delta)", kAxMaxTiming);
+            ax.Delta_d[t] = Delta;
+            ax.delta_d[t] = delta;
+            ax.Delta_f[t] = static_cast<float>(Delta);
+            ax.delta_f[t] = static_cast<float>(delta);
+            ++ax.n_timing;
+        }
+        ax.t[k] = t;
+        const double g2 = b / (delta * delta * (Delta - delta / 3.0));
+        ax.b_d[k] = b;
+        ax.g2_d[k] = g2;
+        ax.csf_d[k] = std::exp(-b * kAxDcsfD);
+        ax.b_f[k] = static_cast<float>(b);
+        ax.g2_f[k] = static_cast<float>(g2);
+        ax.csf_f[k] = static_cast<float>(ax.csf_d[k]);
+    }
+    double x2d[kAxMaxTerms], c[kAxMaxTerms];
+    for (int m = 0; m < kAxMaxTerms; ++m) {
+        const double x = j1p_zero(m + 1), x2 = x * x;
+        x2d[m] = x2 * kAxDaD;
+        c[m] = 2.0 / (kAxDaD * kAxDaD * x2 * x2 * x2 * (x2 - 1.0));
+        ax.x2d_d[m] = x2d[m];
+        ax.c_d[m] = c[m];
+        ax.x2d_f[m] = static_cast<float>(x2d[m]);
+        ax.c_f[m] = static_cast<float>(c[m]);
+    }
+    ax.terms_d = kAxMaxTerms;
+    const double r_lo = 0.5 * d->lb[0], r_hi = 0.5 * d->ub[0];
+    int terms = 1;
+    for (int t = 0; t < ax.n_timing; ++t)
+        for (int i = 0; i < 64; ++i) {
+            const double R = r_lo * std::pow(r_hi / r_lo, i / 63.0), r2 = R * R;
+            double term[kAxMaxTerms], total = 0.0;
+            for (int m = 0; m < kAxMaxTerms; ++m) total += term[m] = c[m] * ax_n_host(x2d[m] / r2, ax.delta_d[t], ax.Delta_d[t]);
+            double tail = total;
+            int need = 0;
+            while (need < kAxMaxTerms && tail > 2e-8 * total) tail -= term[need++];
+            terms = std::max(terms, need);
+        }
+    ax.terms_f = terms;
+    double dmin = ax.delta_d[0];
+    for (int t = 1; t < ax.n_timing; ++t) dmin = std::min(dmin, ax.delta_d[t]);
+    ax.careful_f = 0;
+    while (ax.careful_f < ax.terms_f && x2d[ax.careful_f] / (r_hi * r_hi) * dmin < 1.0) ++ax.careful_f;
+    return GAC_OK;
+}
+
 // ----------------------------------------------------- launch sizing -------
 static int sm_count() {
     static int n = 0;
@@ -262,6 +348,7 @@ const void *mh_kernel_ptr(int kind, int prec, bool trace) {
     case GAC_MODEL_MONOEXP: return mh_ptr_monoexp(prec, trace);
     case GAC_MODEL_MWI3: return mh_ptr_mwi3(prec, trace);
     case GAC_MODEL_SMT: return mh_ptr_smt(prec, trace);
+    case GAC_MODEL_AXCAL_SMT: return mh_ptr_axcal(prec, trace);
     case GAC_MODEL_LINEAR_TEST: return mh_ptr_linear(prec, trace);
     default: return nullptr;
     }
@@ -273,6 +360,7 @@ cudaError_t launch_mh(int kind, int prec, bool trace, const ModelConst &mc, cons
     case GAC_MODEL_MONOEXP: return launch_mh_monoexp(prec, trace, mc, ra, cfg);
     case GAC_MODEL_MWI3: return launch_mh_mwi3(prec, trace, mc, ra, cfg);
     case GAC_MODEL_SMT: return launch_mh_smt(prec, trace, mc, ra, cfg);
+    case GAC_MODEL_AXCAL_SMT: return launch_mh_axcal(prec, trace, mc, ra, cfg);
     case GAC_MODEL_LINEAR_TEST: return launch_mh_linear(prec, trace, mc, ra, cfg);
     default: return cudaErrorInvalidValue;
     }
@@ -374,12 +462,24 @@ gac_status gac_model_register(const gac_model_desc *d, int *model_id) {
         }
     }
 
+    if (d->kind == GAC_MODEL_AXCAL_SMT) {
+        if (d->n_acq % 3 != 0) return fail(GAC_ERR_INVALID_ARG, "AxCaliberSMT takes (b, Delta, delta) triplets");
+        for (int k = 0; k < d->n_acq / 3; ++k) {
+            const double b = d->acq[3 * k], Delta = d->acq[3 * k + 1], delta = d->acq[3 * k + 2];
+            if (b < 0 || !(delta > 0) || !(Delta >= delta))
+                return fail(GAC_ERR_INVALID_ARG, "measurement %d: need b >= 0, delta > 0, Delta >= delta", k);
+            if (b * (d->ub[3] - kAxDeParD) > -kSmtArgMin)
+                return fail(GAC_ERR_INVALID_ARG, "AxCaliberSMT bounds outside the validated range: b*(ub[De_R]-1.7) <= 12");
+        }
+        if (!(d->lb[0] > 0)) return fail(GAC_ERR_INVALID_ARG, "the axon diameter's lower bound must be > 0");
+    }
+
     ModelConst mc;
     std::memset(&mc, 0, sizeof mc);
     mc.kind = d->kind;
     mc.n_par = P;
     mc.n_acq = d->n_acq;
-    mc.n_meas = model_complex(d->kind) ? 2 * d->n_acq : d->n_acq;
+    mc.n_meas = model_complex(d->kind) ? 2 * d->n_acq : (d->kind == GAC_MODEL_AXCAL_SMT ? d->n_acq / 3 : d->n_acq);
     for (int k = 0; k < d->n_acq; ++k) {
         mc.acq_d[k] = d->acq[k];
         mc.acq_f[k] = static_cast<float>(d->acq[k]);
@@ -415,6 +515,14 @@ gac_status gac_model_register(const gac_model_desc *d, int *model_id) {
             xmin = std::min({xmin, d->acq[k] * d->lb[1], d->acq[k] * (d->lb[2] - d->ub[3])});
         const gac_status st = build_g_table(static_cast<int>(std::floor(xmin)), &mc);
         if (st != GAC_OK) return st;
+    }
+    if (d->kind == GAC_MODEL_AXCAL_SMT) {
+        gac_status st = build_axcal(d, &mc);
+        if (st != GAC_OK) return st;
+        // g arguments: b Da - kappa >= 0 (up to rounding) and b (1.7 - De_R)
+        double xmin = -1.0;
+        for (int k = 0; k < mc.n_meas; ++k) xmin = std::min(xmin, d->acq[3 * k] * (kAxDeParD - d->ub[3]));
+        if ((st = build_g_table(static_cast<int>(std::floor(xmin)), &mc)) != GAC_OK) return st;
     }
     std::lock_guard<std::mutex> lk(g_reg_mu);
     for (size_t i = 0; i < g_models.size(); ++i)  // ModelConst is zero-filled before it is set

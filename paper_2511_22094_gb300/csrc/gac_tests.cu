@@ -153,6 +153,7 @@ gac_status gac_forward(int model_id, const double *theta, int64_t n, int precisi
     case GAC_MODEL_MONOEXP: e = launch_forward<GAC_MODEL_MONOEXP>(precision, mc, th, n, out, cs); break;
     case GAC_MODEL_MWI3: e = launch_forward<GAC_MODEL_MWI3>(precision, mc, th, n, out, cs); break;
     case GAC_MODEL_SMT: e = launch_forward<GAC_MODEL_SMT>(precision, mc, th, n, out, cs); break;
+    case GAC_MODEL_AXCAL_SMT: e = launch_forward<GAC_MODEL_AXCAL_SMT>(precision, mc, th, n, out, cs); break;
     default: e = launch_forward<GAC_MODEL_LINEAR_TEST>(precision, mc, th, n, out, cs); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "forward kernel launch");
@@ -186,6 +187,7 @@ gac_status gac_loglik(int model_id, const double *theta, int64_t n, const float 
     case GAC_MODEL_MONOEXP: e = launch_loglik<GAC_MODEL_MONOEXP>(precision, mc, th, n, y, sg, out, cs); break;
     case GAC_MODEL_MWI3: e = launch_loglik<GAC_MODEL_MWI3>(precision, mc, th, n, y, sg, out, cs); break;
     case GAC_MODEL_SMT: e = launch_loglik<GAC_MODEL_SMT>(precision, mc, th, n, y, sg, out, cs); break;
+    case GAC_MODEL_AXCAL_SMT: e = launch_loglik<GAC_MODEL_AXCAL_SMT>(precision, mc, th, n, y, sg, out, cs); break;
     default: e = launch_loglik<GAC_MODEL_LINEAR_TEST>(precision, mc, th, n, y, sg, out, cs); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "loglik kernel launch");

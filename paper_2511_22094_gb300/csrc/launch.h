@@ -22,10 +22,12 @@ cudaError_t launch_mh(int kind, int prec, bool trace, const ModelConst &mc, cons
 const void *mh_ptr_monoexp(int prec, bool trace);
 const void *mh_ptr_mwi3(int prec, bool trace);
 const void *mh_ptr_smt(int prec, bool trace);
+const void *mh_ptr_axcal(int prec, bool trace);
 const void *mh_ptr_linear(int prec, bool trace);
 cudaError_t launch_mh_monoexp(int prec, bool trace, const ModelConst &mc, const RunArgs &ra, const LaunchCfg &cfg);
 cudaError_t launch_mh_mwi3(int prec, bool trace, const ModelConst &mc, const RunArgs &ra, const LaunchCfg &cfg);
 cudaError_t launch_mh_smt(int prec, bool trace, const ModelConst &mc, const RunArgs &ra, const LaunchCfg &cfg);
+cudaError_t launch_mh_axcal(int prec, bool trace, const ModelConst &mc, const RunArgs &ra, const LaunchCfg &cfg);
 cudaError_t launch_mh_linear(int prec, bool trace, const ModelConst &mc, const RunArgs &ra, const LaunchCfg &cfg);
 
 }  // namespace gac

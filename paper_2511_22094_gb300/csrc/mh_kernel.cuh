@@ -17,8 +17,8 @@
 //   a8  on the thinning grid stores the state (coalesced over voxels) and
 //       updates Welford accumulators,
 // and after the last iteration
-//   a9  merges the C chains' accumulators of each voxel in chain order
-//       (Chan et al.'s pairwise update) and writes mean, SD, R-hat,
+//   a9  pools the C chains' accumulators of each voxel (Chan et al.'s
+//       update for equal counts, one parameter per thread) and writes mean, SD, R-hat,
 //       acceptance rate, the non-finite count and the step multiplier.
 // Nothing but thinned samples touches HBM inside the iteration loop.
 //
@@ -177,6 +177,41 @@ __host__ __device__ inline size_t tile_smem_bytes(int P, size_t w_bytes, int VB,
                                                   bool welford_in_smem) {
     return (welford_in_smem ? 2 * static_cast<size_t>(P) * kBlock * w_bytes : 0) +
            static_cast<size_t>(VB) * row_stride * sizeof(float);
+}
+
+// Pools one parameter of C chains that each hold n values, from their
+// Welford means and sums of squared deviations (mean_k[k], m2_k[k]): with
+// equal counts the pooled mean is the mean of the chain means, and the pooled
+// sum of squares is sum_k M2_k + n sum_k (mean_k - mean)^2 (Chan et al.'s
+// update, applied to all chains at once).  Writes the mean and the SD (n-1
+// divisor; NaN for no values, 0 for one) and R-hat: W = mean within-chain
+// variance, B/n = variance of the chain means, R-hat = sqrt(((n-1)/n W +
+// B/n) / W), NaN for C < 2 or n < 2.  Any output may be nullptr.  FP64.
+template <class W>
+__device__ __forceinline__ void pool_chains(const W *mean_k, const W *m2_k, int C, int n, double *mean_out,
+                                            double *sd_out, double *rhat_out) {
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    double mu = 0.0;
+    for (int k = 0; k < C; ++k) mu += static_cast<double>(mean_k[k]);
+    mu /= C;
+    double ss_within = 0.0, ss_between = 0.0;
+    for (int k = 0; k < C; ++k) {
+        const double d = static_cast<double>(mean_k[k]) - mu;
+        ss_within += static_cast<double>(m2_k[k]);
+        ss_between += d * d;
+    }
+    const double n_all = static_cast<double>(C) * n;
+    if (mean_out) *mean_out = n > 0 ? mu : nan;
+    if (sd_out) *sd_out = n_all > 1 ? sqrt((ss_within + n * ss_between) / (n_all - 1.0)) : (n_all == 1 ? 0.0 : nan);
+    if (rhat_out) {
+        double r = nan;
+        if (C >= 2 && n >= 2) {
+            const double w_in = ss_within / (static_cast<double>(C) * (n - 1));
+            const double b_n = ss_between / (C - 1);
+            r = sqrt(((n - 1.0) / n * w_in + b_n) / w_in);
+        }
+        *rhat_out = r;
+    }
 }
 
 // Runs iterations t_begin+1 .. t_end of the chains of one tile of voxels.
@@ -417,51 +452,16 @@ __device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra
         }
     }
 
-    // a9: pool the C chains of each voxel in chain order
+    // a9: pool the C chains of each voxel; the voxel's threads take its
+    // parameters in turn
     if (t_end != ra.I) return;
     __syncthreads();
-    if (active && c == 0 && (ra.mean || ra.std || ra.rhat)) {
+    if (active && (ra.mean || ra.std || ra.rhat)) {
         const int n_each = (ra.moments_mode == GAC_MOMENTS_ALL_POSTBURNIN) ? max(ra.I - ra.B, 0) : ra.S;
-        const double nan = __longlong_as_double(0x7ff8000000000000ll);
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            W mu = wf_mean[p * wf_stride + wf_idx];
-            W m2 = wf_m2[p * wf_stride + wf_idx];
-            double n = n_each;
-            for (int c2 = 1; c2 < C; ++c2) {
-                const W mb = wf_mean[p * wf_stride + wf_idx + c2];
-                const W m2b = wf_m2[p * wf_stride + wf_idx + c2];
-                const double ntot = n + n_each;
-                const W delta = mb - mu;
-                mu += delta * W(n_each / ntot);
-                m2 += m2b + delta * delta * W(n * n_each / ntot);
-                n = ntot;
-            }
-            const double mean_out = n > 0 ? static_cast<double>(mu) : nan;
-            const double sd_out = n > 1 ? sqrt(static_cast<double>(m2) / (n - 1.0)) : (n == 1 ? 0.0 : nan);
-            if (ra.mean) ra.mean[p * ra.n_vox + v] = mean_out;
-            if (ra.std) ra.std[p * ra.n_vox + v] = sd_out;
-            if (ra.rhat) {
-                // R-hat from the per-chain accumulators, in FP64: W = mean of
-                // the within-chain variances, B/n = variance of the chain means
-                double r = nan;
-                if (C >= 2 && n_each >= 2) {
-                    double mbar = 0.0;
-                    for (int c2 = 0; c2 < C; ++c2) mbar += static_cast<double>(wf_mean[p * wf_stride + wf_idx + c2]);
-                    mbar /= C;
-                    double w_in = 0.0, b_n = 0.0;
-                    for (int c2 = 0; c2 < C; ++c2) {
-                        const double d = static_cast<double>(wf_mean[p * wf_stride + wf_idx + c2]) - mbar;
-                        w_in += static_cast<double>(wf_m2[p * wf_stride + wf_idx + c2]) / (n_each - 1);
-                        b_n += d * d;
-                    }
-                    w_in /= C;
-                    b_n /= (C - 1);
-                    r = sqrt(((n_each - 1.0) / n_each * w_in + b_n) / w_in);
-                }
-                ra.rhat[p * ra.n_vox + v] = r;
-            }
-        }
+        for (int p = c; p < P; p += C)
+            pool_chains(wf_mean + p * wf_stride + (wf_idx - c), wf_m2 + p * wf_stride + (wf_idx - c), C, n_each,
+                        ra.mean ? ra.mean + p * ra.n_vox + v : nullptr, ra.std ? ra.std + p * ra.n_vox + v : nullptr,
+                        ra.rhat ? ra.rhat + p * ra.n_vox + v : nullptr);
     }
 }
 

@@ -32,6 +32,29 @@ constexpr float kSmtArgMin = -12.0f;  // registration keeps b (De_par - De_perp)
 constexpr int kGTabMax = 32;          // unit intervals of the g(x) table, centres c_lo .. 16
 constexpr float kGTail = 16.0f;       // x >= 16: g(x) = sqrt(pi)/2 x^-1/2 (erfc(4) = 1.5e-8)
 
+// AxCaliberSMT (Sec. 2.5, after Fan et al. 2020): measurements are
+// (b, Delta, delta) triplets; the cylinder series runs over the zeros of J1'.
+constexpr int kAxMaxMeas = GAC_MAX_ACQ / 3;
+constexpr int kAxMaxTiming = 4;   // distinct (Delta, delta) pairs
+constexpr int kAxMaxTerms = 64;   // zeros of J1' in the series
+constexpr float kAxDa = 1.7f, kAxDePar = 1.7f, kAxDcsf = 3.0f;  // um^2/ms (fixed, Sec. 2.5)
+constexpr double kAxDaD = 1.7, kAxDeParD = 1.7, kAxDcsfD = 3.0;
+
+struct AxConst {
+    int n_timing;       // distinct (Delta, delta)
+    int terms_f;        // series terms of the FP32 evaluation (tail < 2e-8 on the prior box)
+    int terms_d;        // of the FP64 evaluation
+    int careful_f;      // leading terms whose q delta can fall below 1 on the prior box
+    int t[kAxMaxMeas];  // timing of measurement k
+    float b_f[kAxMaxMeas], g2_f[kAxMaxMeas], csf_f[kAxMaxMeas];  // b, gamma^2 G^2, e^{-b D_csf}
+    double b_d[kAxMaxMeas], g2_d[kAxMaxMeas], csf_d[kAxMaxMeas];
+    float delta_f[kAxMaxTiming], Delta_f[kAxMaxTiming];
+    double delta_d[kAxMaxTiming], Delta_d[kAxMaxTiming];
+    // term m: c_m = 2 / (Da^2 x_m^6 (x_m^2 - 1)), x_m^2 Da (q = x_m^2 Da / R^2)
+    float c_f[kAxMaxTerms], x2d_f[kAxMaxTerms];
+    double c_d[kAxMaxTerms], x2d_d[kAxMaxTerms];
+};
+
 struct ModelConst {
     int kind;
     int n_par;
@@ -50,12 +73,14 @@ struct ModelConst {
     alignas(16) float gtab[2 * kGTabMax * 4];
     int gtab_lo;
     int gtab_n;
+    AxConst ax;  // GAC_MODEL_AXCAL_SMT only
 };
 
 __host__ __device__ constexpr int model_n_par(int kind) {
     return kind == GAC_MODEL_MONOEXP ? 2
          : kind == GAC_MODEL_MWI3 ? 9
          : kind == GAC_MODEL_SMT ? 4
+         : kind == GAC_MODEL_AXCAL_SMT ? 4
          : kind == GAC_MODEL_LINEAR_TEST ? 2 : -1;
 }
 __host__ __device__ constexpr bool model_complex(int kind) { return kind == GAC_MODEL_MWI3; }
@@ -73,7 +98,7 @@ static __shared__ float4 smt_gtab_s[2 * kGTabMax];
 
 template <int KIND>
 __device__ __forceinline__ void model_smem_load(const ModelConst &mc) {
-    if constexpr (KIND == GAC_MODEL_SMT) {
+    if constexpr (KIND == GAC_MODEL_SMT || KIND == GAC_MODEL_AXCAL_SMT) {
         float *dst = reinterpret_cast<float *>(smt_gtab_s);
         for (int e = threadIdx.x; e < 2 * kGTabMax * 4; e += blockDim.x) dst[e] = mc.gtab[e];
     }
@@ -320,6 +345,78 @@ __device__ __forceinline__ void eval_smt_f(const float *th, const ModelConst &mc
     }
 }
 
+// The cylinder's Gaussian-phase attenuation (Neuman 1974; van Gelderen et al.
+// 1994) is kappa = gamma^2 G^2 R^6 sum_m c_m N_m with
+//   N_m = 2 delta q - 2 + 2 e^{-q delta} + 2 e^{-q Delta} - e^{-q (Delta - delta)}
+//         - e^{-q (Delta + delta)},   q = x_m^2 Da / R^2,
+// which also equals 2 E(a) - e^{-q Delta} H(a) with a = q delta,
+// E(a) = e^{-a} - 1 + a and H(a) = e^{a} + e^{-a} - 2.  For a >= 1 the direct
+// form loses at most ~3 bits; for a < 1 (wide cylinders, leading terms only)
+// E and H come from their Taylor series, whose leading orders would cancel in
+// the direct form.
+__device__ __forceinline__ float ax_n_direct_f(float q, float dl, float DL) {
+    const float A = __expf(-q * dl), B = __expf(-q * DL), C = __expf(-q * (DL - dl));
+    return fmaf(2.0f * dl, q, -2.0f) + 2.0f * (A + B) - C - A * B;
+}
+__device__ __forceinline__ float ax_n_series_f(float q, float dl, float DL) {
+    const float a = q * dl, a2 = a * a;
+    // E(a) / a^2 = sum_k (-a)^k / (k+2)!, k <= 9 (next term < 3e-9 of the sum)
+    float e = fmaf(a, 2.50521084e-8f, -2.75573192e-7f);
+    e = fmaf(e, a, 2.75573192e-6f);
+    e = fmaf(e, a, -2.48015873e-5f);
+    e = fmaf(e, a, 1.98412698e-4f);
+    e = fmaf(e, a, -1.38888889e-3f);
+    e = fmaf(e, a, 8.33333333e-3f);
+    e = fmaf(e, a, -4.16666667e-2f);
+    e = fmaf(e, a, 1.66666667e-1f);
+    e = fmaf(e, -a, 0.5f);
+    // H(a) / a^2 = sum_k 2 a^(2k) / (2k+2)!, k <= 4 (next term < 5e-9)
+    float h = fmaf(a2, 5.51146384e-7f, 4.96031746e-5f);
+    h = fmaf(h, a2, 2.77777778e-3f);
+    h = fmaf(h, a2, 8.33333333e-2f);
+    h = fmaf(h, a2, 1.0f);
+    return a2 * fmaf(2.0f, e, -__expf(-q * DL) * h);
+}
+
+template <class V>
+__device__ __forceinline__ void eval_axcal_f(const float *th, const ModelConst &mc, V &&visit) {
+    const AxConst &ax = mc.ax;
+    const float R = 0.5f * th[0], fn = th[1], fcsf = th[2], der = th[3];
+    const float R2 = R * R, inv_r2 = 1.0f / R2, r6 = R2 * R2 * R2;
+    float phi[kAxMaxTiming];
+#pragma unroll
+    for (int j = 0; j < kAxMaxTiming; ++j) {
+        phi[j] = 0.0f;
+        if (j < ax.n_timing) {  // the same for every thread
+            const float dl = ax.delta_f[j], DL = ax.Delta_f[j];
+            float acc = 0.0f;
+            int m = 0;
+            for (; m < ax.careful_f; ++m) {
+                const float q = ax.x2d_f[m] * inv_r2;
+                const float n = (q * dl < 1.0f) ? ax_n_series_f(q, dl, DL) : ax_n_direct_f(q, dl, DL);
+                acc = fmaf(ax.c_f[m], n, acc);
+            }
+            for (; m < ax.terms_f; ++m) acc = fmaf(ax.c_f[m], ax_n_direct_f(ax.x2d_f[m] * inv_r2, dl, DL), acc);
+            phi[j] = acc * r6;
+        }
+    }
+    const float w_r = (1.0f - fcsf) * fn, w_h = (1.0f - fcsf) * (1.0f - fn), dh = kAxDePar - der;
+    const int n = mc.n_meas;
+    for (int k0 = 0; k0 < n; k0 += kAnchor) {
+        const int k1 = min(k0 + kAnchor, n);
+        for (int k = k0; k < k1; ++k) {
+            const float b = ax.b_f[k];
+            const int t = ax.t[k];
+            const float ph = t == 0 ? phi[0] : (t == 1 ? phi[1] : (t == 2 ? phi[2] : phi[3]));
+            const float kap = ax.g2_f[k] * ph;
+            const float sr = __expf(-kap) * smt_g_f(fmaf(b, kAxDa, -kap), mc);
+            const float sh = __expf(-b * der) * smt_g_f(b * dh, mc);
+            visit(k, fmaf(w_r, sr, fmaf(w_h, sh, fcsf * ax.csf_f[k])));
+        }
+        end_block(visit, 0);
+    }
+}
+
 template <class V>
 __device__ __forceinline__ void eval_linear_f(const float *th, const ModelConst &mc, V &&visit) {
     for (int k = 0; k < mc.n_acq; ++k) visit(k, fmaf(th[1], mc.acq_f[k], th[0]));
@@ -360,6 +457,44 @@ __device__ __forceinline__ void eval_smt_d(const double *th, const ModelConst &m
 }
 
 template <class V>
+__device__ __forceinline__ void eval_axcal_d(const double *th, const ModelConst &mc, V &&visit) {
+    const AxConst &ax = mc.ax;
+    const double R = 0.5 * th[0], fn = th[1], fcsf = th[2], der = th[3];
+    const double R2 = R * R, r6 = R2 * R2 * R2;
+    double phi[kAxMaxTiming];
+#pragma unroll
+    for (int j = 0; j < kAxMaxTiming; ++j) {
+        phi[j] = 0.0;
+        if (j < ax.n_timing) {
+            const double dl = ax.delta_d[j], DL = ax.Delta_d[j];
+            double acc = 0.0;
+            for (int m = 0; m < ax.terms_d; ++m) {
+                const double q = ax.x2d_d[m] / R2, a = q * dl;
+                double n;
+                if (a < 1.0) {  // 2 E(a) - e^{-q Delta} H(a) (see ax_n_series_f)
+                    const double em = expm1(-a), ep = expm1(a);
+                    n = 2.0 * (em + a) - exp(-q * DL) * (ep + em);
+                } else {
+                    const double A = exp(-a), B = exp(-q * DL), C = exp(-q * (DL - dl));
+                    n = 2.0 * a - 2.0 + 2.0 * (A + B) - C - A * B;
+                }
+                acc += ax.c_d[m] * n;
+            }
+            phi[j] = acc * r6;
+        }
+    }
+    for (int k = 0; k < mc.n_meas; ++k) {
+        const double b = ax.b_d[k];
+        const int t = ax.t[k];
+        const double ph = t == 0 ? phi[0] : (t == 1 ? phi[1] : (t == 2 ? phi[2] : phi[3]));
+        const double kap = ax.g2_d[k] * ph;
+        const double sr = exp(-kap) * smt_g_d(b * kAxDaD - kap);
+        const double sh = exp(-b * der) * smt_g_d(b * (kAxDeParD - der));
+        visit(k, (1.0 - fcsf) * (fn * sr + (1.0 - fn) * sh) + fcsf * ax.csf_d[k]);
+    }
+}
+
+template <class V>
 __device__ __forceinline__ void eval_linear_d(const double *th, const ModelConst &mc, V &&visit) {
     for (int k = 0; k < mc.n_acq; ++k) visit(k, th[0] + th[1] * mc.acq_d[k]);
 }
@@ -370,6 +505,7 @@ __device__ __forceinline__ void eval_f(const float *th, const ModelConst &mc, V 
     if constexpr (KIND == GAC_MODEL_MONOEXP) eval_monoexp_f(th, mc, visit);
     else if constexpr (KIND == GAC_MODEL_MWI3) eval_mwi3_f(th, mc, visit);
     else if constexpr (KIND == GAC_MODEL_SMT) eval_smt_f(th, mc, visit);
+    else if constexpr (KIND == GAC_MODEL_AXCAL_SMT) eval_axcal_f(th, mc, visit);
     else eval_linear_f(th, mc, visit);
 }
 
@@ -378,6 +514,7 @@ __device__ __forceinline__ void eval_d(const double *th, const ModelConst &mc, V
     if constexpr (KIND == GAC_MODEL_MONOEXP) eval_monoexp_d(th, mc, visit);
     else if constexpr (KIND == GAC_MODEL_MWI3) eval_mwi3_d(th, mc, visit);
     else if constexpr (KIND == GAC_MODEL_SMT) eval_smt_d(th, mc, visit);
+    else if constexpr (KIND == GAC_MODEL_AXCAL_SMT) eval_axcal_d(th, mc, visit);
     else eval_linear_d(th, mc, visit);
 }
 

@@ -35,6 +35,7 @@ static const void *noalloc_fn(int kind) {
     case GAC_MODEL_MONOEXP: return reinterpret_cast<const void *>(&noalloc_kernel<GAC_MODEL_MONOEXP>);
     case GAC_MODEL_MWI3: return reinterpret_cast<const void *>(&noalloc_kernel<GAC_MODEL_MWI3>);
     case GAC_MODEL_SMT: return reinterpret_cast<const void *>(&noalloc_kernel<GAC_MODEL_SMT>);
+    case GAC_MODEL_AXCAL_SMT: return reinterpret_cast<const void *>(&noalloc_kernel<GAC_MODEL_AXCAL_SMT>);
     default: return reinterpret_cast<const void *>(&noalloc_kernel<GAC_MODEL_LINEAR_TEST>);
     }
 }
@@ -45,6 +46,7 @@ static void noalloc_launch(int kind, int grid, size_t smem, cudaStream_t s, cons
     case GAC_MODEL_MONOEXP: noalloc_kernel<GAC_MODEL_MONOEXP><<<grid, kBlock, smem, s>>>(mc, ra, ss, t0, t1); break;
     case GAC_MODEL_MWI3: noalloc_kernel<GAC_MODEL_MWI3><<<grid, kBlock, smem, s>>>(mc, ra, ss, t0, t1); break;
     case GAC_MODEL_SMT: noalloc_kernel<GAC_MODEL_SMT><<<grid, kBlock, smem, s>>>(mc, ra, ss, t0, t1); break;
+    case GAC_MODEL_AXCAL_SMT: noalloc_kernel<GAC_MODEL_AXCAL_SMT><<<grid, kBlock, smem, s>>>(mc, ra, ss, t0, t1); break;
     default: noalloc_kernel<GAC_MODEL_LINEAR_TEST><<<grid, kBlock, smem, s>>>(mc, ra, ss, t0, t1); break;
     }
 }
@@ -156,6 +158,8 @@ extern "C" gac_status gac_mcmc_run_noalloc(int model_id, const void *data, int64
     const size_t smem = tile_smem_bytes(mc.n_par, 8, ra.vox_per_block, ra.row_stride, false);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(carveout)");
     int per_sm = 0, sms = 0, dev = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, smem)) != cudaSuccess)
         return cuda_fail(e, "occupancy");

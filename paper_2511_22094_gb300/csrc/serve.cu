@@ -83,8 +83,9 @@ __global__ void __launch_bounds__(kBlock, 2) serve_kernel(const ServeJob *jobs, 
     }
 }
 
-constexpr int kKinds = 4;
-static const int kKindOf[kKinds] = {GAC_MODEL_MONOEXP, GAC_MODEL_MWI3, GAC_MODEL_SMT, GAC_MODEL_LINEAR_TEST};
+constexpr int kKinds = 5;
+static const int kKindOf[kKinds] = {GAC_MODEL_MONOEXP, GAC_MODEL_MWI3, GAC_MODEL_SMT, GAC_MODEL_AXCAL_SMT,
+                                    GAC_MODEL_LINEAR_TEST};
 static int kind_slot(int kind) {
     for (int i = 0; i < kKinds; ++i)
         if (kKindOf[i] == kind) return i;
@@ -95,6 +96,7 @@ static const void *serve_fn(int slot) {
     case 0: return reinterpret_cast<const void *>(&serve_kernel<GAC_MODEL_MONOEXP>);
     case 1: return reinterpret_cast<const void *>(&serve_kernel<GAC_MODEL_MWI3>);
     case 2: return reinterpret_cast<const void *>(&serve_kernel<GAC_MODEL_SMT>);
+    case 3: return reinterpret_cast<const void *>(&serve_kernel<GAC_MODEL_AXCAL_SMT>);
     default: return reinterpret_cast<const void *>(&serve_kernel<GAC_MODEL_LINEAR_TEST>);
     }
 }
@@ -104,6 +106,7 @@ static void launch_serve(int slot, int grid, size_t smem, cudaStream_t s, const 
     case 0: serve_kernel<GAC_MODEL_MONOEXP><<<grid, kBlock, smem, s>>>(jobs, items, n, counter); break;
     case 1: serve_kernel<GAC_MODEL_MWI3><<<grid, kBlock, smem, s>>>(jobs, items, n, counter); break;
     case 2: serve_kernel<GAC_MODEL_SMT><<<grid, kBlock, smem, s>>>(jobs, items, n, counter); break;
+    case 3: serve_kernel<GAC_MODEL_AXCAL_SMT><<<grid, kBlock, smem, s>>>(jobs, items, n, counter); break;
     default: serve_kernel<GAC_MODEL_LINEAR_TEST><<<grid, kBlock, smem, s>>>(jobs, items, n, counter); break;
     }
 }

@@ -25,7 +25,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-MONOEXP, MWI3, SMT, LINEAR = 1, 2, 3, 100
+MONOEXP, MWI3, SMT, AXCAL, LINEAR = 1, 2, 3, 4, 100
 BLOCK = 65536
 _STREAM_TRUTH, _STREAM_NOISE = 1, 2
 
@@ -34,7 +34,7 @@ _STREAM_TRUTH, _STREAM_NOISE = 1, 2
 class Workload:
     name: str
     kind: int
-    acq: tuple            # TE [ms] or b [ms/um^2]
+    acq: tuple            # TE [ms], b [ms/um^2], or (b, Delta, delta) triplets (AxCaliberSMT)
     lb: tuple
     ub: tuple
     step: tuple
@@ -54,7 +54,9 @@ class Workload:
 
     @property
     def n_meas(self) -> int:
-        return 2 * len(self.acq) if self.kind == MWI3 else len(self.acq)
+        if self.kind == MWI3:
+            return 2 * len(self.acq)
+        return len(self.acq) // 3 if self.kind == AXCAL else len(self.acq)
 
     @property
     def n_samples(self) -> int:
@@ -103,7 +105,22 @@ SMT_1P5M = Workload(
     n_vox=1_500_000, n_chains=4, iterations=5000, burnin=500, thin=100, snr=50.0,
     data_seed=3, mcmc_seed=1003, par_names=("f", "Da", "De_par", "De_perp"))
 
-WORKLOADS = {w.name: w for w in (MONOEXP_4K, MWI3_1M, SMT_1P5M)}
+#: AxCaliberSMT, the paper's own speed-test model (Sec. 2.5): 250,000 voxels
+#: (its largest sample count), the 16 b-values of Supplementary Table S1
+#: (8 at Delta = 13 ms, 8 at Delta = 30 ms; pulse width delta = 6 ms, not
+#: printed: chosen so that the largest b of each Delta needs 460-500 mT/m,
+#: the scanner's gradient limit), SNR 30 at b = 0, and Table 1's MH settings
+#: (4 chains x 25,000 iterations, 10% burn-in, thinning 100: 900 samples).
+_AX_B13 = (0.05, 0.35, 0.8, 1.5, 2.4, 3.45, 4.75, 6.0)
+_AX_B30 = (0.2, 0.95, 2.3, 4.25, 6.75, 9.85, 13.5, 17.8)
+AXCAL_250K = Workload(
+    name="axcal_250k", kind=AXCAL,
+    acq=tuple(x for b in _AX_B13 for x in (b, 13.0, 6.0)) + tuple(x for b in _AX_B30 for x in (b, 30.0, 6.0)),
+    lb=(0.2, 0.0, 0.0, 0.05), ub=(16.0, 1.0, 1.0, 1.7), step=(0.4, 0.02, 0.01, 0.04),
+    n_vox=250_000, n_chains=4, iterations=25_000, burnin=2_500, thin=100, snr=30.0,
+    data_seed=4, mcmc_seed=1004, par_names=("diameter", "f_neurite", "f_csf", "De_R"))
+
+WORKLOADS = {w.name: w for w in (MONOEXP_4K, MWI3_1M, SMT_1P5M, AXCAL_250K)}
 
 
 def _block_rng(seed: int, stream: int, block: int) -> np.random.Generator:
@@ -133,6 +150,11 @@ def truths(w: Workload, first: int = 0, n: int | None = None) -> np.ndarray:
             a_mw = mwf * (a_iw + a_ew) / (1.0 - mwf)
             rest = [rng.uniform(lo, hi, m) for lo, hi in zip(w.lb[3:], w.ub[3:])]
             return np.stack([a_mw, a_iw, a_ew] + rest, axis=1)
+        if w.kind == AXCAL:
+            # inside the prior box: diameter ~ U(1, 10) um, f_neurite ~ U(0.3, 0.8),
+            # f_csf ~ U(0, 0.2), De_R ~ U(0.3, 1.2) um^2/ms
+            return np.stack([rng.uniform(1.0, 10.0, m), rng.uniform(0.3, 0.8, m), rng.uniform(0.0, 0.2, m),
+                             rng.uniform(0.3, 1.2, m)], axis=1)
         return np.stack([rng.uniform(lo, hi, m) for lo, hi in zip(w.lb, w.ub)], axis=1)
 
     return _draw(w, first, n, _STREAM_TRUTH, w.n_par, fill)
@@ -148,7 +170,8 @@ def noise(w: Workload, first: int = 0, n: int | None = None) -> np.ndarray:
 def sigma(w: Workload, theta_true: np.ndarray) -> np.ndarray:
     """Per-voxel noise SD [n] (float32) from the workload's SNR at TE = 0 / b = 0:
     S0/SNR (mono-exponential), (A_MW + A_IW + A_EW)/SNR per real and imaginary
-    channel (3-pool), 1/SNR (Standard Model, signal normalised to S(b=0) = 1)."""
+    channel (3-pool), 1/SNR (Standard Model and AxCaliberSMT, signals
+    normalised to S(b=0) = 1)."""
     th = np.asarray(theta_true)
     if w.kind == MONOEXP:
         s = th[:, 0] / w.snr

@@ -5,7 +5,8 @@ voxel (||s_gpu - s_ref|| / ||s_ref||, because elementwise relative error is
 undefined where a complex component crosses zero); log-likelihood absolute
 error <= 1e-3 at posterior-typical parameters (the truth and one-sigma
 neighbourhoods of it, where |L| ~ M/2).  The FP64 variant is held to 1e-12
-and 1e-8.
+and 1e-8 (AxCaliberSMT: 1e-10 and 1e-7, its FP64 cylinder series stops at
+64 terms where the oracle takes 100).
 """
 import numpy as np
 import pytest
@@ -15,7 +16,9 @@ from paper_2511_22094_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-CASES = [W.MONOEXP_4K, W.MWI3_1M, W.SMT_1P5M]
+CASES = [W.MONOEXP_4K, W.MWI3_1M, W.SMT_1P5M, W.AXCAL_250K]
+FP64_DEFAULT = (1e-12, 1e-8, 1e-12)   # forward, log-likelihood at the truth, relative far from it
+FP64_TOL = {W.AXCAL: (1e-10, 1e-7, 1e-9)}
 
 
 def _edge_thetas(w, rng, n):
@@ -38,7 +41,8 @@ def test_forward_parity(gac, orc, w):
     ref = orc.forward(w.kind, w.acq, th)
     norm = np.linalg.norm(ref, axis=1)
     keep = norm > 1e-6 * norm.max()  # an all-zero signal (every amplitude 0) has no relative error
-    for prec, tol in ((gac.PREC_MIXED, 1e-5), (gac.PREC_FP32, 1e-5), (gac.PREC_FP64, 1e-12)):
+    for prec, tol in ((gac.PREC_MIXED, 1e-5), (gac.PREC_FP32, 1e-5),
+                      (gac.PREC_FP64, FP64_TOL.get(w.kind, FP64_DEFAULT)[0])):
         s = gac.forward_host(mid, th, prec)
         rel = np.linalg.norm(s - ref, axis=1)[keep] / norm[keep]
         assert rel.max() <= tol, (w.name, prec, rel.max(), np.median(rel))
@@ -81,7 +85,7 @@ def test_smt_g_both_branches(gac, orc):
         assert np.abs(s[:, 0] - 1.0).max() <= (1e-6 if prec != gac.PREC_FP64 else 1e-15)
 
 
-LOGLIK = [(W.MONOEXP_4K, 1e-3), (W.MWI3_1M, 1e-3), (W.SMT_1P5M, 1e-3),
+LOGLIK = [(W.MONOEXP_4K, 1e-3), (W.MWI3_1M, 1e-3), (W.SMT_1P5M, 1e-3), (W.AXCAL_250K, 1e-3),
           (W.MWI3_1M.with_(name="mwi3_snr50", snr=50.0), 1e-3),
           (W.MWI3_1M.with_(name="mwi3_snr300", snr=300.0), 2e-3)]
 
@@ -104,12 +108,34 @@ def test_loglik_parity_at_posterior_typical_theta(gac, orc, w, tol):
     far = far.astype(np.float32).astype(np.float64)
     ref_far = orc.loglik(w.kind, w.acq, far, y, sig)
     res = {}
-    for prec, t in ((gac.PREC_MIXED, tol), (gac.PREC_FP32, tol), (gac.PREC_FP64, 1e-8)):
+    _, t64, t64_far = FP64_TOL.get(w.kind, FP64_DEFAULT)
+    for prec, t in ((gac.PREC_MIXED, tol), (gac.PREC_FP32, tol), (gac.PREC_FP64, t64)):
         L = gac.loglik_host(mid, th, y, sig, prec)
         err = np.abs(L - ref)
         res[prec] = (err.max(), np.quantile(err, 0.999), np.quantile(err, 0.99))
         assert err.max() <= t, (w.name, prec, res[prec])
         Lf = gac.loglik_host(mid, far, y, sig, prec)
         rel = np.abs(Lf - ref_far) / np.maximum(np.abs(ref_far), 1.0)
-        assert rel.max() <= (1e-12 if prec == gac.PREC_FP64 else 5e-5), (w.name, prec, rel.max())
+        assert rel.max() <= (t64_far if prec == gac.PREC_FP64 else 5e-5), (w.name, prec, rel.max())
     print(w.name, {k: tuple(f"{x:.2e}" for x in v) for k, v in res.items()})
+
+
+def test_axcal_cylinder_regimes(gac, orc):
+    """Axon diameters across the prior box, including the wide cylinders whose
+    leading series terms take the Taylor forms (q delta < 1), with Delta =
+    delta and Delta >> delta timings, and b = 0."""
+    w = W.AXCAL_250K
+    acq = np.array([[0.0, 13.0, 6.0], [1.5, 6.0, 6.0], [6.0, 13.0, 6.0], [17.8, 30.0, 6.0],
+                    [3.0, 60.0, 4.0], [9.85, 30.0, 6.0]]).ravel()
+    mid = gac.gac_model_register(w.kind, acq, w.lb, w.ub, w.step)
+    rng = np.random.default_rng(11)
+    n = 40_000
+    th = np.stack([np.exp(rng.uniform(np.log(0.2), np.log(16.0), n)), rng.uniform(0, 1, n),
+                   rng.uniform(0, 1, n), rng.uniform(0.05, 1.7, n)], 1)
+    ref = orc.forward(w.kind, acq, th)
+    for prec, tol in ((gac.PREC_MIXED, 1e-5), (gac.PREC_FP64, 1e-10)):
+        s = gac.forward_host(mid, th, prec)
+        rel = np.linalg.norm(s - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        print(f"axcal regimes prec={prec}: max {rel.max():.2e} median {np.median(rel):.2e}")
+        assert rel.max() <= tol, (prec, rel.max())
+        assert np.abs(s[:, 0] - 1.0).max() <= (1e-6 if prec != gac.PREC_FP64 else 1e-15)

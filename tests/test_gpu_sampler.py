@@ -59,7 +59,9 @@ def _lockstep_check(gac, orc, w, tr, y, sig, seed, prec, n_tr, C, I, B, min_agre
             typical = np.abs(Lp) <= w.n_meas
             dL.append(np.abs(rec["Lp"] - Lp)[typical])
             rel = np.abs(rec["Lp"] - Lp) / np.maximum(np.abs(Lp), 1.0)
-            assert rel.max() <= (1e-12 if prec == gac.PREC_FP64 else 1e-4), (v, c, rel.max())
+            # FP64: 1e-12 (AxCaliberSMT: its series stops at 64 terms, the oracle's at 100)
+            tol64 = 1e-9 if w.kind == W.AXCAL else 1e-12
+            assert rel.max() <= (tol64 if prec == gac.PREC_FP64 else 1e-4), (v, c, rel.max())
     dL = np.concatenate(dL) if dL else np.zeros(1)
     frac = agree / total
     print(f"{w.name} prec={prec}: agreement {agree}/{total} = {frac:.6f}; posterior-typical "
@@ -72,6 +74,8 @@ LOCKSTEP = [
     (W.MONOEXP_4K, 4096, 64, 0, 0.999),
     (W.MWI3_1M, 256, 8, 0, 0.999),
     (W.SMT_1P5M, 256, 8, 0, 0.999),
+    (W.AXCAL_250K.with_(name="axcal_2k", iterations=2000, burnin=200, thin=20), 256, 8, 0, 0.999),
+    (W.AXCAL_250K.with_(name="axcal_1k", iterations=1000, burnin=100, thin=20), 64, 4, 2, 0.9999),
     (W.MWI3_1M, 64, 4, 2, 0.9999),
     (W.MONOEXP_4K, 256, 32, 2, 0.9999),
     (W.MWI3_1M.with_(name="mwi3_fp32"), 64, 4, 1, 0.99),
@@ -104,7 +108,8 @@ def _posterior_gap(gpu, ref):
     return np.abs(gpu["mean"] - ref["mean"])[ok] / sd[ok]
 
 
-FREE = [(W.MONOEXP_4K, 4096), (W.MWI3_1M, 512), (W.SMT_1P5M, 512)]
+FREE = [(W.MONOEXP_4K, 4096), (W.MWI3_1M, 512), (W.SMT_1P5M, 512),
+        (W.AXCAL_250K.with_(name="axcal_3k", iterations=3000, burnin=300, thin=30), 512)]
 
 
 @pytest.mark.parametrize("w,n", FREE, ids=[c[0].name for c in FREE])

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import test_oracle_adapt as A
+import test_oracle_axcal as X
 import test_oracle_ensemble as E
 import test_oracle_models as M
 import test_oracle_rng as R
@@ -82,6 +83,20 @@ CASES = [
      lambda orc: A.test_adaptation_when_every_proposal_is_accepted(orc, 100, 10, 10)),
     ("adaptation multiplier", "lambda = exp2(0.25 * (double)e);", "lambda = exp2(0.5 * (double)e);",
      lambda orc: A.test_adaptation_when_every_proposal_is_accepted(orc, 100, 10, 10)),
+    ("cylinder radius power", "sum += (r2 * r2 * r2) / (D * D * x2 * x2 * x2 * (x2 - 1.0)) * N;",
+     "sum += (r2 * r2) / (D * D * x2 * x2 * x2 * (x2 - 1.0)) * N;", X.test_free_diffusion_bound_and_limit),
+    ("cylinder zero factor", "sum += (r2 * r2 * r2) / (D * D * x2 * x2 * x2 * (x2 - 1.0)) * N;",
+     "sum += (r2 * r2 * r2) / (D * D * x2 * x2 * x2 * x2) * N;", lambda orc: X.test_wide_pulse_limit(orc, 1.0)),
+    ("cylinder pulse-pair sign", "e_minus_one_plus(q * (Delta - delta)) - e_minus_one_plus(q * (Delta + delta));",
+     "e_minus_one_plus(q * (Delta - delta)) + e_minus_one_plus(q * (Delta + delta));",
+     X.test_free_diffusion_bound_and_limit),
+    ("cylinder gradient timing", "double g2 = b / (delta * delta * (Delta - delta / 3.0));",
+     "double g2 = b / (delta * delta * Delta);", lambda orc: X.test_wide_pulse_limit(orc, 2.0)),
+    ("restricted orientation average", "double restricted = exp(-kap) * orc_g(b * ORC_AX_DA - kap);",
+     "double restricted = exp(-kap) * orc_g(b * ORC_AX_DA);",
+     X.test_restricted_spherical_mean_against_orientation_quadrature),
+    ("free-water diffusivity", "fcsf * exp(-b * ORC_AX_DCSF);", "fcsf * exp(-b * ORC_AX_DA);",
+     X.test_compartment_reductions),
     ("adaptation floor", "if (a < target && e > ORC_ADAPT_EMIN) --e;", "if (a < target) --e;",
      lambda orc: A.test_adaptation_when_every_proposal_is_rejected(orc, 700, -48)),
 ]
