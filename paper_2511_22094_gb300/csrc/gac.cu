@@ -185,6 +185,40 @@ struct GaussLegendre01 {
 };
 }  // namespace
 
+// Monomial coefficients af[0..7] (float) in d of the degree-7 polynomial that
+// interpolates f(d) at the eight Chebyshev points of [-1/2, 1/2], and the
+// largest relative error of that float polynomial, evaluated in double, on 65
+// points of the interval.
+template <class F>
+static double cheb8_fit(F &&f, float af[8]) {
+    constexpr int K = 8;
+    double T[K][K] = {};  // T[n][m]: coefficient of s^m in the Chebyshev polynomial T_n(s)
+    T[0][0] = 1.0;
+    T[1][1] = 1.0;
+    for (int n = 2; n < K; ++n)
+        for (int m = 0; m < K; ++m) T[n][m] = (m > 0 ? 2.0 * T[n - 1][m - 1] : 0.0) - T[n - 2][m];
+    double fv[K];
+    for (int j = 0; j < K; ++j) fv[j] = f(0.5 * std::cos(M_PI * (j + 0.5) / K));
+    double a[K] = {};  // monomial coefficients in s = 2 d
+    for (int n = 0; n < K; ++n) {
+        double b = 0.0;  // Chebyshev coefficient b_n
+        for (int j = 0; j < K; ++j) b += fv[j] * std::cos(M_PI * n * (j + 0.5) / K);
+        b *= (n == 0 ? 1.0 : 2.0) / K;
+        for (int m = 0; m < K; ++m) a[m] += b * T[n][m];
+    }
+    for (int m = 0; m < K; ++m) af[m] = static_cast<float>(std::ldexp(a[m], m));  // coefficient of d^m
+    double worst = 0.0;
+    for (int q = 0; q <= 64; ++q) {
+        const double dd = -0.5 + q / 64.0;
+        double p = af[K - 1];
+        for (int m = K - 2; m >= 0; --m) p = p * dd + af[m];
+        const double ref = f(dd);
+        const double rel = std::fabs(p - ref) / std::fabs(ref);
+        worst = (rel > worst || rel != rel) ? rel : worst;
+    }
+    return worst;
+}
+
 // Fills mc->gtab with, for each centre c = c_lo .. 16, the monomial
 // coefficients in d of the degree-7 polynomial that interpolates g(c + d) at
 // the eight Chebyshev points of [-1/2, 1/2], and checks every interval on 65
@@ -193,40 +227,16 @@ struct GaussLegendre01 {
 // 1e-9 for unit intervals).
 static gac_status build_g_table(int c_lo, ModelConst *mc) {
     static const GaussLegendre01 gl;
-    constexpr int K = 8;  // coefficients per interval
     const int n_int = static_cast<int>(kGTail) - c_lo + 1;
     if (c_lo < static_cast<int>(kSmtArgMin) - 1 || n_int > kGTabMax)
         return fail(GAC_ERR_INVALID_ARG, "SMT argument range starts at %d, below %d", c_lo,
                     static_cast<int>(kSmtArgMin));
-    double T[K][K] = {};  // T[n][m]: coefficient of s^m in the Chebyshev polynomial T_n(s)
-    T[0][0] = 1.0;
-    T[1][1] = 1.0;
-    for (int n = 2; n < K; ++n)
-        for (int m = 0; m < K; ++m) T[n][m] = (m > 0 ? 2.0 * T[n - 1][m - 1] : 0.0) - T[n - 2][m];
     for (int i = 0; i < n_int; ++i) {
         const double c = c_lo + i;
-        double f[K];
-        for (int j = 0; j < K; ++j) f[j] = gl.g(c + 0.5 * std::cos(M_PI * (j + 0.5) / K));
-        double a[K] = {};  // monomial coefficients in s = 2 d
-        for (int n = 0; n < K; ++n) {
-            double b = 0.0;  // Chebyshev coefficient b_n
-            for (int j = 0; j < K; ++j) b += f[j] * std::cos(M_PI * n * (j + 0.5) / K);
-            b *= (n == 0 ? 1.0 : 2.0) / K;
-            for (int m = 0; m < K; ++m) a[m] += b * T[n][m];
-        }
-        float af[K];
-        for (int m = 0; m < K; ++m) {
-            af[m] = static_cast<float>(std::ldexp(a[m], m));  // coefficient of d^m
-            mc->gtab[((m < 4 ? 0 : kGTabMax) + i) * 4 + (m & 3)] = af[m];
-        }
-        for (int q = 0; q <= 64; ++q) {
-            const double dd = -0.5 + q / 64.0;
-            double p = af[K - 1];
-            for (int m = K - 2; m >= 0; --m) p = p * dd + af[m];
-            const double ref = gl.g(c + dd);
-            if (!(std::fabs(p - ref) <= 2e-7 * ref))
-                return fail(GAC_ERR_INVALID_ARG, "g(x) table check failed at x = %g", c + dd);
-        }
+        float af[8];
+        const double err = cheb8_fit([&](double d) { return gl.g(c + d); }, af);
+        for (int m = 0; m < 8; ++m) mc->gtab[((m < 4 ? 0 : kGTabMax) + i) * 4 + (m & 3)] = af[m];
+        if (!(err <= 2e-7)) return fail(GAC_ERR_INVALID_ARG, "g(x) table check failed near x = %g", c);
     }
     mc->gtab_lo = c_lo;
     mc->gtab_n = n_int;
@@ -316,6 +326,30 @@ static gac_status build_axcal(const gac_model_desc *d, ModelConst *mc) {
     for (int t = 1; t < ax.n_timing; ++t) dmin = std::min(dmin, ax.delta_d[t]);
     ax.careful_f = 0;
     while (ax.careful_f < ax.terms_f && x2d[ax.careful_f] / (r_hi * r_hi) * dmin < 1.0) ++ax.careful_f;
+    // the FP32 table of phi_j(R) = R^6 sum_m c_m N_m in u = log2 R: intervals
+    // of width <= 1/2 over the prior box (at most kAxTabMax, widened if the
+    // box is wider), each checked on 65 points; if any check exceeds 3e-7 the
+    // kernels sum the series instead
+    const double u_lo = std::log2(r_lo), u_hi = std::log2(r_hi);
+    const int n_int = std::min(kAxTabMax, std::max(1, static_cast<int>(std::ceil((u_hi - u_lo) / 0.5))));
+    const double w = std::max(u_hi - u_lo, 1e-3) / n_int;
+    bool ok = true;
+    for (int t = 0; t < ax.n_timing && ok; ++t)
+        for (int i = 0; i < n_int && ok; ++i) {
+            const double uc = u_lo + (i + 0.5) * w;
+            auto phi = [&](double dd) {
+                const double R = std::exp2(uc + dd * w), r2 = R * R;
+                double sum = 0.0;
+                for (int m = 0; m < kAxMaxTerms; ++m) sum += c[m] * ax_n_host(x2d[m] / r2, ax.delta_d[t], ax.Delta_d[t]);
+                return r2 * r2 * r2 * sum;
+            };
+            float af[8];
+            ok = cheb8_fit(phi, af) <= 3e-7;
+            for (int m = 0; m < 8; ++m) ax.tab[((2 * t + (m < 4 ? 0 : 1)) * kAxTabMax + i) * 4 + (m & 3)] = af[m];
+        }
+    ax.tab_n = ok ? n_int : 0;
+    ax.tab_inv_w = static_cast<float>(1.0 / w);
+    ax.tab_off = static_cast<float>(-u_lo / w - 0.5);
     return GAC_OK;
 }
 

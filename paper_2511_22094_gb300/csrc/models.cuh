@@ -37,6 +37,7 @@ constexpr float kGTail = 16.0f;       // x >= 16: g(x) = sqrt(pi)/2 x^-1/2 (erfc
 constexpr int kAxMaxMeas = GAC_MAX_ACQ / 3;
 constexpr int kAxMaxTiming = 4;   // distinct (Delta, delta) pairs
 constexpr int kAxMaxTerms = 64;   // zeros of J1' in the series
+constexpr int kAxTabMax = 16;     // intervals of the FP32 table of the series in log2 R
 constexpr float kAxDa = 1.7f, kAxDePar = 1.7f, kAxDcsf = 3.0f;  // um^2/ms (fixed, Sec. 2.5)
 constexpr double kAxDaD = 1.7, kAxDeParD = 1.7, kAxDcsfD = 3.0;
 
@@ -53,6 +54,14 @@ struct AxConst {
     // term m: c_m = 2 / (Da^2 x_m^6 (x_m^2 - 1)), x_m^2 Da (q = x_m^2 Da / R^2)
     float c_f[kAxMaxTerms], x2d_f[kAxMaxTerms];
     double c_d[kAxMaxTerms], x2d_d[kAxMaxTerms];
+    // FP32 path: phi_j(R) = R^6 sum_m c_m N_m per timing j as a piecewise
+    // degree-7 polynomial in log2 R (intervals of width 1/tab_inv_w from
+    // log2 of the smallest radius; centred coordinate in [-1/2, 1/2]), used
+    // when tab_n > 0 (registration checks it against the series).  Layout
+    // [timing][2][kAxTabMax][4]: a_0..a_3 of every interval, then a_4..a_7.
+    int tab_n;
+    float tab_off, tab_inv_w;  // t = log2 R * tab_inv_w + tab_off; interval rint(t), d = t - rint(t)
+    alignas(16) float tab[kAxMaxTiming * 2 * kAxTabMax * 4];
 };
 
 struct ModelConst {
@@ -96,11 +105,18 @@ constexpr double kSqrtPiHalfD = 0.886226925452758014;
 // different intervals, which the constant bank would serialise).
 static __shared__ float4 smt_gtab_s[2 * kGTabMax];
 
+// The AxCaliberSMT series table of the block's model (FP32 path).
+static __shared__ float4 ax_tab_s[kAxMaxTiming * 2 * kAxTabMax];
+
 template <int KIND>
 __device__ __forceinline__ void model_smem_load(const ModelConst &mc) {
     if constexpr (KIND == GAC_MODEL_SMT || KIND == GAC_MODEL_AXCAL_SMT) {
         float *dst = reinterpret_cast<float *>(smt_gtab_s);
         for (int e = threadIdx.x; e < 2 * kGTabMax * 4; e += blockDim.x) dst[e] = mc.gtab[e];
+    }
+    if constexpr (KIND == GAC_MODEL_AXCAL_SMT) {
+        float *dst = reinterpret_cast<float *>(ax_tab_s);
+        for (int e = threadIdx.x; e < kAxMaxTiming * 2 * kAxTabMax * 4; e += blockDim.x) dst[e] = mc.ax.tab[e];
     }
 }
 
@@ -378,12 +394,9 @@ __device__ __forceinline__ float ax_n_series_f(float q, float dl, float DL) {
     return a2 * fmaf(2.0f, e, -__expf(-q * DL) * h);
 }
 
-template <class V>
-__device__ __forceinline__ void eval_axcal_f(const float *th, const ModelConst &mc, V &&visit) {
-    const AxConst &ax = mc.ax;
-    const float R = 0.5f * th[0], fn = th[1], fcsf = th[2], der = th[3];
+// phi_j(R) = R^6 sum_m c_m N_m for every timing j, summed term by term.
+__device__ __forceinline__ void ax_phi_series_f(float R, const AxConst &ax, float (&phi)[kAxMaxTiming]) {
     const float R2 = R * R, inv_r2 = 1.0f / R2, r6 = R2 * R2 * R2;
-    float phi[kAxMaxTiming];
 #pragma unroll
     for (int j = 0; j < kAxMaxTiming; ++j) {
         phi[j] = 0.0f;
@@ -400,6 +413,41 @@ __device__ __forceinline__ void eval_axcal_f(const float *th, const ModelConst &
             phi[j] = acc * r6;
         }
     }
+}
+
+// The same from the shared-memory table: interval rint(t) of t = log2 R *
+// tab_inv_w + tab_off (clamped, so every load stays in the table), Horner in
+// d = t - interval.
+__device__ __forceinline__ void ax_phi_table_f(float R, const AxConst &ax, float (&phi)[kAxMaxTiming]) {
+    constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
+    const float t = fmaf(log2f(R), ax.tab_inv_w, ax.tab_off);  // once per evaluation: the accurate log2
+    int i = static_cast<int>((t + kRound) - kRound);
+    i = min(max(i, 0), ax.tab_n - 1);
+    const float d = t - static_cast<float>(i);
+#pragma unroll
+    for (int j = 0; j < kAxMaxTiming; ++j) {
+        phi[j] = 0.0f;
+        if (j < ax.n_timing) {
+            const float4 lo = ax_tab_s[(2 * j) * kAxTabMax + i];
+            const float4 hi = ax_tab_s[(2 * j + 1) * kAxTabMax + i];
+            float p = fmaf(hi.w, d, hi.z);
+            p = fmaf(p, d, hi.y);
+            p = fmaf(p, d, hi.x);
+            p = fmaf(p, d, lo.w);
+            p = fmaf(p, d, lo.z);
+            p = fmaf(p, d, lo.y);
+            phi[j] = fmaf(p, d, lo.x);
+        }
+    }
+}
+
+template <class V>
+__device__ __forceinline__ void eval_axcal_f(const float *th, const ModelConst &mc, V &&visit) {
+    const AxConst &ax = mc.ax;
+    const float R = 0.5f * th[0], fn = th[1], fcsf = th[2], der = th[3];
+    float phi[kAxMaxTiming];
+    if (ax.tab_n > 0) ax_phi_table_f(R, ax, phi);  // the same branch for every thread
+    else ax_phi_series_f(R, ax, phi);
     const float w_r = (1.0f - fcsf) * fn, w_h = (1.0f - fcsf) * (1.0f - fn), dh = kAxDePar - der;
     const int n = mc.n_meas;
     for (int k0 = 0; k0 < n; k0 += kAnchor) {
