@@ -197,6 +197,126 @@ def cpu_oracle_rate(w, target_s=15.0, sampler="mh", stretch=2.0):
     return ci / dt, r["threads"], f"first {n} of {w.n_vox} voxels, all {w.n_chains} chains x {w.iterations} iterations ({dt:.1f} s)"
 
 
+FIT_METRIC = "whole-volume fit voxel-iterations/s"
+FIT_UNIT = "voxel-iter/s"
+# Direct-form counts per voxel-iteration of the 3-pool fit (24 echoes x 3
+# pools: exp, sin, cos and 18 Jacobian entries per echo; Adam on 9 parameters)
+FIT_OPS = dict(mufu=24 * 3 * 3, fp32=24 * (3 * 14 + 2 * 9 * 2) + 9 * 12)
+
+
+def _fit_problem(w, shape):
+    """The workload's volume as a grid, its truths' data, a start at the
+    centre of the prior box, and a mask without the outer layer of voxels."""
+    N = int(np.prod(shape))
+    th = W.truths(w, 0, N)
+    y = None  # built on the device by the caller
+    theta0 = np.tile(0.5 * (np.array(w.lb) + np.array(w.ub)), (N, 1))
+    x, yy, z = np.meshgrid(np.arange(shape[0]), np.arange(shape[1]), np.arange(shape[2]), indexing="ij")
+    inner = ((x > 0) & (x < shape[0] - 1) & (yy > 0) & (yy < shape[1] - 1) & (z > 0) & (z < shape[2] - 1))
+    mask = inner.transpose(2, 1, 0).reshape(-1).astype(np.uint8)  # voxel v = x + nx (y + ny z)
+    return th, y, theta0, mask
+
+
+def run_fit(args):
+    """Whole-volume Adam fit (askadam.m, Sec. 2.2.1) of the 3-pool model on a
+    100^3 grid (the 1M-voxel volume): L1 loss, Adam (lr 0.01), 3D total
+    variation on the myelin-water amplitude (lambda 1e-3), `--fit-iterations`
+    updates per step from the same start."""
+    import torch
+    from paper_2511_22094_gb300 import build
+    build.build()
+    from paper_2511_22094_gb300 import gac
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    stream = torch.cuda.current_stream()
+    w = W.MWI3_1M
+    shape = (100, 100, 100)
+    N, P, M = int(np.prod(shape)), w.n_par, w.n_meas
+    it = args.fit_iterations
+    mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
+    th_true, _, theta0, mask = _fit_problem(w, shape)
+    th = torch.from_numpy(th_true).to(dev)
+    sig = torch.from_numpy(W.sigma(w, th_true)).to(dev)
+    s = torch.empty((N, M), dtype=torch.float64, device=dev)
+    gac.gac_forward(mid, th, N, gac.PREC_FP64, s, stream)
+    z = torch.from_numpy(W.noise(w, 0, N)).to(dev)
+    y = (s + sig.double()[:, None] * z).float().contiguous()
+    del s, z, th
+    mk = torch.from_numpy(mask).to(dev)
+    wt = (1.0 / sig).float().contiguous()  # volumetric weights ~ SNR (Eq. 1)
+    th0 = torch.from_numpy(theta0).to(dev)
+    theta = torch.empty_like(th0)
+    hist = torch.empty(it, dtype=torch.float64, device=dev)
+    opts = gac.make_fit_opts(shape, loss=gac.FIT_L1, iterations=it, learning_rate=0.01, tv_lambda=1e-3,
+                             tv_params=0b1, tv_dims=3, precision=gac.PREC_FP32)
+
+    def step():
+        theta.copy_(th0)
+        return gac.gac_fit_run(mid, y, mk, wt, opts, theta, hist, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        for e0, e1 in ev:
+            e0.record(stream)
+            done = step()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    t_total = sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3
+    vi = N * it
+    value = vi * args.steps / t_total
+    # end to end: host (pinned) buffers in and out through the same call
+    hy, hmk, hwt = y.cpu().pin_memory(), mk.cpu().pin_memory(), wt.cpu().pin_memory()
+    hth = torch.empty((N, P), dtype=torch.float64).pin_memory()
+    hh = torch.empty(it, dtype=torch.float64).pin_memory()
+    h0 = torch.from_numpy(theta0)
+    reps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        hth.copy_(h0)
+        gac.gac_fit_run(mid, hy, hmk, hwt, opts, hth, hh, stream)
+    e2e_s = (time.perf_counter() - t0) / reps
+    clocks = clk.summary()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    f_max = (_peaks().get("sm_max_mhz") or 2070.0) * 1e6
+    vi_s = vi / (t_total / args.steps)
+    peak = sms * FP32_PER_CLK_SM * f_max / 1e9
+    achieved = FIT_OPS["fp32"] * vi_s / 1e9
+    line = {"metric": FIT_METRIC, "value": value, "unit": FIT_UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "mwi3_1m as a 100^3 grid", "loss": "L1", "optimiser": "Adam lr 0.01",
+                       "tv": "3D, A_MW, lambda 1e-3", "mask": "inner 98^3", "iterations_per_step": it,
+                       "updates_done": done},
+            "roofline": {"bound": "alu", "pipe": "fp32", "count": "direct-form", "achieved": achieved,
+                         "peak": peak, "unit": "Gop/s", "frac": achieved / peak, "traffic": None},
+            "e2e": {"value": vi / e2e_s, "unit": FIT_UNIT, "h2d_bytes_per_step": y.numel() * 4 + N * (1 + 4 + 8 * P),
+                    "d2h_bytes_per_step": N * 8 * P + it * 8},
+            "clocks": clocks, "gpu_launches": args.steps * (2 * it + 2), "wall_s": t_wall}
+    if not args.no_cpu_baseline:
+        import oracle
+        sub = (16, 16, 16)
+        ns = int(np.prod(sub))
+        th_s, _, theta0_s, mask_s = _fit_problem(w, sub)
+        ys = W.noisy_data(oracle.forward(w.kind, w.acq, th_s), W.noise(w, 0, ns), W.sigma(w, th_s))
+        its = 10
+        t0 = time.perf_counter()
+        oracle.fit_run(w.kind, w.acq, w.lb, w.ub, ys, theta0_s, shape=sub, mask=mask_s,
+                       weight=1.0 / W.sigma(w, th_s), loss=1, iterations=its, lr=0.01, lam=1e-3, tv_params=1,
+                       tv_dims=3)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": ns * its / dt, "unit": FIT_UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"16^3 voxels x {its} updates ({dt:.1f} s)"}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, w):
     """Reference arm: the FP64 CPU oracle, timed on the host cores."""
     world, rank, _ = _dist()
@@ -498,9 +618,14 @@ def main():
     ap.add_argument("--serving", action="store_true", help="run the serving trace instead")
     ap.add_argument("--serving-jobs", type=int, default=200)
     ap.add_argument("--serving-saturated", action="store_true")
+    ap.add_argument("--fit", action="store_true", help="whole-volume Adam fit instead of MCMC")
+    ap.add_argument("--fit-iterations", type=int, default=100)
     args = ap.parse_args()
     if args.serving:
         run_serving(args)
+        return
+    if args.fit:
+        run_fit(args)
         return
     w = W.WORKLOADS[args.workload]
     if args.sampler == "ensemble":

@@ -231,6 +231,49 @@ gac_status gac_ensemble_run(int model_id, const void *data, int64_t n_vox, const
                             float sigma_scalar, const float *x0, const gac_mcmc_opts *opts,
                             double stretch, gac_result *out, void *stream);
 
+/* Whole-volume gradient fit (askadam.m, Sec. 2.2.1; Eq. 2, 4, 5): Adam over
+ * all voxels of an nx x ny x nz grid (voxel v = x + nx (y + ny z)) at once.
+ * The optimiser works on normalised parameters u = (theta - lb) / (ub - lb),
+ * clamped to [0, 1] after every update.  Iteration t evaluates, at the
+ * current parameters, the loss
+ *   (1 / (n_mask M)) sum_{v in mask} sum_m rho(w_v (y_vm - s_vm)),
+ *       rho(r) = |r| (L1) or r^2 (L2),
+ *   + (tv_lambda / n_mask) sum_{p in tv_params} sum_{d < tv_dims}
+ *       sum_{v, v + e_d in mask} |u_p(v + e_d) - u_p(v)|
+ * and its (sub)gradient (sign(0) = 0), takes one Adam step (bias-corrected
+ * moments, learning_rate, beta1, beta2, epsilon), records the loss, and
+ * stops if the loss < tol (tol > 0) or if t >= convergence_window and the
+ * least-squares slope of the last convergence_window losses is below
+ * convergence_value in magnitude (convergence_value > 0).  Models: mono-
+ * exponential, 3-pool, Standard Model and the linear test model (analytic
+ * Jacobians); AxCaliberSMT is rejected. */
+enum { GAC_FIT_L1 = 1, GAC_FIT_L2 = 2 };
+typedef struct {
+    int nx, ny, nz;
+    int loss;                 /* GAC_FIT_L1 | GAC_FIT_L2 */
+    int iterations;           /* maximum number of updates */
+    double learning_rate, beta1, beta2, epsilon;
+    double tol;
+    double convergence_value;
+    int convergence_window;   /* 2..4096 when convergence_value > 0 */
+    double tv_lambda;
+    uint32_t tv_params;       /* bit p: total variation on parameter p */
+    int tv_dims;              /* 2 (x, y) or 3 (x, y, z) */
+    int precision;            /* GAC_PREC_FP32 or GAC_PREC_FP64 */
+} gac_fit_opts;
+
+/*   data     [N][n_meas] float32 (host or device)
+ *   mask     [N] uint8 (nonzero = fitted) or NULL for every voxel
+ *   weight   [N] float32 w_v or NULL for 1
+ *   theta    [N][P] double: initial parameters in, fitted parameters out
+ *            (voxels outside the mask keep theirs)
+ *   loss_history [iterations] double or NULL: the loss of each iteration
+ *   *iterations_done: the number of updates taken
+ * Synchronous.  Errors: INVALID_ARG, UNKNOWN_MODEL, OOM, CUDA. */
+gac_status gac_fit_run(int model_id, const void *data, const uint8_t *mask, const float *weight,
+                       const gac_fit_opts *opts, double *theta, double *loss_history, int *iterations_done,
+                       void *stream);
+
 /* Allocation-free variant of gac_mcmc_run.  The paper has no counterpart to
  * this entry point; it exists for callers that cannot allocate device
  * memory: an application that has handed the GPU's memory to its own pool

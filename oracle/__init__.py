@@ -130,6 +130,12 @@ def _declare(L):
     L.orc_j1p_zero.restype = ct.c_double
     L.orc_cyl_kappa.argtypes = [ct.c_double] * 5
     L.orc_cyl_kappa.restype = ct.c_double
+    L.orc_dg.argtypes = [ct.c_double]
+    L.orc_dg.restype = ct.c_double
+    L.orc_window_slope.argtypes = [ct.POINTER(ct.c_double), ct.c_int]
+    L.orc_window_slope.restype = ct.c_double
+    L.orc_jacobian.restype = ct.c_int
+    L.orc_fit_run.restype = ct.c_int
     L.orc_rhat.argtypes = [f64, ct.c_int, ct.c_int, ct.c_size_t]
     L.orc_rhat.restype = ct.c_double
     L.orc_max_threads.argtypes = []
@@ -279,6 +285,55 @@ def mcmc_run(kind, acq, lb, ub, step, data, sigma, *, iterations, burnin, thin, 
         raise ValueError("oracle rejected the arguments")
     return dict(mean=mean, std=std, samples=samples, accept_rate=acc, nonfinite=bad, rhat=rhat,
                 step_scale=scale, threads=used.value)
+
+
+class _FitOpts(ct.Structure):
+    _fields_ = [("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int), ("loss", ct.c_int),
+                ("iterations", ct.c_int), ("lr", ct.c_double), ("beta1", ct.c_double),
+                ("beta2", ct.c_double), ("eps", ct.c_double), ("tol", ct.c_double),
+                ("conv_value", ct.c_double), ("conv_window", ct.c_int), ("lam", ct.c_double),
+                ("tv_params", ct.c_uint32), ("tv_dims", ct.c_int)]
+
+
+def dg(x):
+    """d/dx of g(x) = int_0^1 exp(-x u^2) du."""
+    return lib().orc_dg(x)
+
+
+def jacobian(kind, acq, theta):
+    """theta [P] -> (s [M], J [M][P])."""
+    acq = np.ascontiguousarray(acq, np.float64)
+    th = np.ascontiguousarray(theta, np.float64)
+    M, P = n_meas(kind, len(acq)), n_par(kind)
+    s, J = np.zeros(M), np.zeros((M, P))
+    if lib().orc_jacobian(kind, _dptr(acq), len(acq), _dptr(th), _dptr(s), _dptr(J)) != 0:
+        raise ValueError("no Jacobian for this kind")
+    return s, J
+
+
+def window_slope(y):
+    y = np.ascontiguousarray(y, np.float64)
+    return lib().orc_window_slope(_dptr(y), len(y))
+
+
+def fit_run(kind, acq, lb, ub, data, theta0, *, shape, mask=None, weight=None, loss=1, iterations=100,
+            lr=0.01, beta1=0.9, beta2=0.999, eps=1e-8, tol=0.0, conv_value=0.0, conv_window=20,
+            lam=0.0, tv_params=0, tv_dims=3):
+    """Whole-volume Adam fit; returns (theta [N][P], loss history, updates done)."""
+    m, keep = _model(kind, acq, lb, ub, np.zeros(len(lb)))
+    data = np.ascontiguousarray(data, np.float32)
+    th = np.array(theta0, np.float64, copy=True, order="C")
+    mk = None if mask is None else np.ascontiguousarray(mask, np.uint8)
+    wt = None if weight is None else np.ascontiguousarray(weight, np.float32)
+    hist = np.full(max(iterations, 1), np.nan)
+    done = ct.c_int(0)
+    o = _FitOpts(shape[0], shape[1], shape[2], loss, iterations, lr, beta1, beta2, eps, tol, conv_value,
+                 conv_window, lam, tv_params, tv_dims)
+    rc = lib().orc_fit_run(ct.byref(m), _vp(data), _vp(mk), _vp(wt), ct.byref(o), _dptr(th), _dptr(hist),
+                           ct.byref(done))
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return th, hist[:done.value], done.value
 
 
 def j1p_zero(m):

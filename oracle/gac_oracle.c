@@ -740,3 +740,220 @@ int orc_ensemble_path(const orc_model *m, const float *y, double sigma, const fl
                    accept_rate, NULL, path);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Whole-volume gradient fit (askadam.m, Sec. 2.2.1, Eq. 2, 4, 5)            */
+/* ------------------------------------------------------------------------ */
+
+/* dg/dx of g(x) = int_0^1 exp(-x u^2) du: -int_0^1 u^2 exp(-x u^2) du, which
+ * integration by parts turns into (exp(-x) - g(x)) / (2x); for |x| <= 1 the
+ * term-wise derivative of the power series, sum_n n (-x)^(n-1) (-1) / (n! (2n+1)). */
+double orc_dg(double x) {
+    if (fabs(x) > 1.0) return (exp(-x) - orc_g(x)) / (2.0 * x);
+    double term = 1.0; /* (-x)^(n-1) / (n-1)! */
+    double sum = 0.0;
+    for (int n = 1; n < 400; ++n) {
+        if (n > 1) term *= -x / (double)(n - 1);
+        double add = -term / (double)(2 * n + 1);
+        sum += add;
+        if (fabs(add) <= 1e-18 * fabs(sum)) break;
+    }
+    return sum;
+}
+
+/* Forward model s [M] and its Jacobian J [M][P] (J[m][p] = ds_m / dtheta_p),
+ * differentiated by hand from the forms of orc_forward (MONOEXP, MWI3, SMT,
+ * LINEAR).  Returns 0, or -1 for a kind without a Jacobian. */
+int orc_jacobian(int kind, const double *acq, int n_acq, const double *theta, double *s, double *J) {
+    int P = orc_n_par(kind);
+    if (orc_forward(kind, acq, n_acq, theta, s) != 0) return -1;
+    switch (kind) {
+    case ORC_MONOEXP:
+        for (int k = 0; k < n_acq; ++k) {
+            double decay = exp(-1e-3 * acq[k] * theta[1]);
+            J[k * P + 0] = decay;
+            J[k * P + 1] = -1e-3 * acq[k] * theta[0] * decay;
+        }
+        return 0;
+    case ORC_MWI3:
+        for (int k = 0; k < n_acq; ++k) {
+            double tk = acq[k];
+            double *Jr = J + (size_t)(2 * k) * P, *Ji = J + (size_t)(2 * k + 1) * P;
+            for (int p = 0; p < P; ++p) Jr[p] = Ji[p] = 0.0;
+            for (int j = 0; j < 3; ++j) {
+                double decay = exp(-tk / theta[3 + j]);
+                double dfj = j < 2 ? theta[6 + j] : 0.0;
+                double phase = theta[8] - 2.0 * ORC_PI * 1e-3 * dfj * tk;
+                double c = cos(phase), sn = sin(phase);
+                double amp = theta[j] * decay;
+                Jr[j] = decay * c; /* d/dA_j */
+                Ji[j] = decay * sn;
+                double dT = amp * tk / (theta[3 + j] * theta[3 + j]); /* d/dT2*_j */
+                Jr[3 + j] = dT * c;
+                Ji[3 + j] = dT * sn;
+                if (j < 2) { /* d phase / d df = -2 pi t 1e-3 */
+                    double w = 2.0 * ORC_PI * 1e-3 * tk;
+                    Jr[6 + j] = amp * w * sn;
+                    Ji[6 + j] = -amp * w * c;
+                }
+            }
+            Jr[8] = -s[2 * k + 1]; /* d/dphi0 of S: i S */
+            Ji[8] = s[2 * k];
+        }
+        return 0;
+    case ORC_SMT:
+        for (int k = 0; k < n_acq; ++k) {
+            double bk = acq[k];
+            double f = theta[0], da = theta[1], dpar = theta[2], dperp = theta[3];
+            double g_in = orc_g(bk * da), ex = exp(-bk * dperp), g_ex = orc_g(bk * (dpar - dperp));
+            double dg_ex = orc_dg(bk * (dpar - dperp));
+            J[k * P + 0] = g_in - ex * g_ex;
+            J[k * P + 1] = f * bk * orc_dg(bk * da);
+            J[k * P + 2] = (1.0 - f) * ex * bk * dg_ex;
+            J[k * P + 3] = -(1.0 - f) * bk * ex * (g_ex + dg_ex);
+        }
+        return 0;
+    case ORC_LINEAR:
+        for (int k = 0; k < n_acq; ++k) {
+            J[k * P + 0] = 1.0;
+            J[k * P + 1] = acq[k];
+        }
+        return 0;
+    default:
+        return -1;
+    }
+}
+
+/* Least-squares slope of y[0..n-1] against 0..n-1. */
+double orc_window_slope(const double *y, int n) {
+    double xm = 0.5 * (n - 1), ym = 0.0, sxy = 0.0, sxx = 0.0;
+    for (int i = 0; i < n; ++i) ym += y[i];
+    ym /= n;
+    for (int i = 0; i < n; ++i) {
+        sxy += (i - xm) * (y[i] - ym);
+        sxx += (i - xm) * (i - xm);
+    }
+    return sxx > 0.0 ? sxy / sxx : 0.0;
+}
+
+typedef struct {
+    int nx, ny, nz;         /* voxel grid, N = nx ny nz, voxel v = x + nx (y + ny z) */
+    int loss;               /* 1: L1, 2: L2 */
+    int iterations;         /* maximum number of updates */
+    double lr, beta1, beta2, eps;   /* Adam (Kingma & Ba) */
+    double tol;             /* stop once the loss is below tol (0: off) */
+    double conv_value;      /* stop once |slope| of the last conv_window losses < conv_value (0: off) */
+    int conv_window;
+    double lambda;          /* total-variation weight (Eq. 4) */
+    uint32_t tv_params;     /* bit p: total variation on parameter p */
+    int tv_dims;            /* 2 or 3 (x, y[, z]) */
+} orc_fit_opts;
+
+static double sgn(double x) { return (x > 0.0) - (x < 0.0); }
+
+/* Adam on the whole volume.  The optimiser works on normalised parameters
+ * u = (theta - lb) / (ub - lb), clamped to [0, 1] after every update.  The
+ * loss at iteration t, evaluated at the current parameters, is
+ *   D = (1 / (n_mask M)) sum_{v in mask} sum_m rho(w_v (y_vm - s_vm)),
+ *       rho = |r| (L1) or r^2 (L2)                                   (Eq. 2)
+ *   + (lambda / n_mask) sum_{p in tv} sum_{v, v + e_d in mask} |u_p(v + e_d) - u_p(v)|
+ *                                                                   (Eq. 4, 5)
+ * with subgradient sign(0) = 0; then the Adam step (bias-corrected moments)
+ * updates every masked voxel.  After the update the loop stops if the loss is
+ * below tol, or if t >= conv_window and the least-squares slope of the last
+ * conv_window losses is below conv_value in magnitude.  theta [N][P] holds the
+ * initial parameters on entry and the fitted ones on return; loss_hist[t-1]
+ * receives the loss of iteration t; *iters_done the number of updates. */
+int orc_fit_run(const orc_model *m, const float *data, const uint8_t *mask, const float *weight,
+                const orc_fit_opts *o, double *theta, double *loss_hist, int *iters_done) {
+    int P = m->n_par, M = orc_n_meas(m->kind, m->n_acq);
+    int64_t N = (int64_t)o->nx * o->ny * o->nz;
+    if (P != orc_n_par(m->kind) || M < 1 || N < 1 || (o->loss != 1 && o->loss != 2) || o->iterations < 0 ||
+        (o->tv_dims != 2 && o->tv_dims != 3) || M > 512)
+        return -1;
+    double *u = (double *)malloc(sizeof(double) * N * P);
+    double *mom1 = (double *)calloc((size_t)N * P, sizeof(double));
+    double *mom2 = (double *)calloc((size_t)N * P, sizeof(double));
+    double *grad = (double *)malloc(sizeof(double) * N * P);
+    double *hist = (double *)malloc(sizeof(double) * (o->iterations + 1));
+    if (!u || !mom1 || !mom2 || !grad || !hist) return -1;
+    int64_t n_mask = 0;
+    for (int64_t v = 0; v < N; ++v) n_mask += mask ? (mask[v] != 0) : 1;
+    for (int64_t v = 0; v < N; ++v)
+        for (int p = 0; p < P; ++p) {
+            double range = m->ub[p] - m->lb[p];
+            u[v * P + p] = range > 0.0 ? (theta[v * P + p] - m->lb[p]) / range : 0.0;
+        }
+    int done = 0;
+    for (int t = 1; t <= o->iterations; ++t) {
+        double data_loss = 0.0, tv_loss = 0.0;
+        /* data term and its gradient, voxel by voxel */
+        for (int64_t v = 0; v < N; ++v) {
+            for (int p = 0; p < P; ++p) grad[v * P + p] = 0.0;
+            if (mask && !mask[v]) continue;
+            double th[64], s[512], J[512 * 12];
+            for (int p = 0; p < P; ++p) th[p] = m->lb[p] + u[v * P + p] * (m->ub[p] - m->lb[p]);
+            orc_jacobian(m->kind, m->acq, m->n_acq, th, s, J);
+            double w = weight ? (double)weight[v] : 1.0;
+            for (int k = 0; k < M; ++k) {
+                double r = w * ((double)data[v * M + k] - s[k]);
+                double drho_ds = (o->loss == 1) ? -w * sgn(r) : -2.0 * w * r;
+                data_loss += (o->loss == 1) ? fabs(r) : r * r;
+                for (int p = 0; p < P; ++p) grad[v * P + p] += drho_ds * J[k * P + p];
+            }
+        }
+        double scale = 1.0 / ((double)n_mask * M);
+        for (int64_t v = 0; v < N; ++v)
+            for (int p = 0; p < P; ++p) grad[v * P + p] *= scale * (m->ub[p] - m->lb[p]); /* d/du */
+        data_loss *= scale;
+        /* total variation over pairs of neighbouring masked voxels */
+        for (int p = 0; p < P && o->lambda != 0.0; ++p) {
+            if (!((o->tv_params >> p) & 1u)) continue;
+            for (int64_t v = 0; v < N; ++v) {
+                if (mask && !mask[v]) continue;
+                int x = (int)(v % o->nx), y = (int)((v / o->nx) % o->ny), z = (int)(v / ((int64_t)o->nx * o->ny));
+                int nb[3] = {x + 1 < o->nx, y + 1 < o->ny, z + 1 < o->nz};
+                int64_t step[3] = {1, o->nx, (int64_t)o->nx * o->ny};
+                for (int d = 0; d < o->tv_dims; ++d) {
+                    if (!nb[d]) continue;
+                    int64_t w2 = v + step[d];
+                    if (mask && !mask[w2]) continue;
+                    double diff = u[w2 * P + p] - u[v * P + p];
+                    tv_loss += fabs(diff);
+                    grad[w2 * P + p] += o->lambda / (double)n_mask * sgn(diff);
+                    grad[v * P + p] -= o->lambda / (double)n_mask * sgn(diff);
+                }
+            }
+        }
+        double loss = data_loss + o->lambda / (double)n_mask * tv_loss;
+        /* Adam */
+        double c1 = 1.0 - pow(o->beta1, t), c2 = 1.0 - pow(o->beta2, t);
+        for (int64_t v = 0; v < N; ++v) {
+            if (mask && !mask[v]) continue;
+            for (int p = 0; p < P; ++p) {
+                size_t i = (size_t)v * P + p;
+                mom1[i] = o->beta1 * mom1[i] + (1.0 - o->beta1) * grad[i];
+                mom2[i] = o->beta2 * mom2[i] + (1.0 - o->beta2) * grad[i] * grad[i];
+                double step_u = o->lr * (mom1[i] / c1) / (sqrt(mom2[i] / c2) + o->eps);
+                u[i] = fmin(fmax(u[i] - step_u, 0.0), 1.0);
+            }
+        }
+        hist[t - 1] = loss;
+        if (loss_hist) loss_hist[t - 1] = loss;
+        done = t;
+        if (o->tol > 0.0 && loss < o->tol) break;
+        if (o->conv_value > 0.0 && o->conv_window > 1 && t >= o->conv_window &&
+            fabs(orc_window_slope(hist + t - o->conv_window, o->conv_window)) < o->conv_value)
+            break;
+    }
+    for (int64_t v = 0; v < N; ++v) /* voxels outside the mask keep their initial parameters */
+        if (!mask || mask[v])
+            for (int p = 0; p < P; ++p) theta[v * P + p] = m->lb[p] + u[v * P + p] * (m->ub[p] - m->lb[p]);
+    if (iters_done) *iters_done = done;
+    free(hist);
+    free(u);
+    free(mom1);
+    free(mom2);
+    free(grad);
+    return 0;
+}

@@ -1,0 +1,459 @@
+// Whole-volume gradient fit (askadam.m, Sec. 2.2.1; Eq. 2, 4, 5): Adam on
+// the L1 or L2 data loss over a masked voxel grid, with an optional total-
+// variation penalty on chosen parameter maps.  One launch per iteration:
+//   fit_step_kernel   every voxel (one thread each, grid-stride): forward
+//                     model and its analytic Jacobian, the data loss and its
+//                     gradient, the total-variation subgradient from the six
+//                     (or four) neighbours' current parameters, and the Adam
+//                     update into the other parameter buffer; each block
+//                     writes its share of the loss;
+//   fit_check_kernel  one block sums the block shares in a fixed order,
+//                     records the iteration's loss and applies the stopping
+//                     rules; once it sets the stop flag, later launches return
+//                     at once.
+// Parameters are optimised in normalised form u = (theta - lb) / (ub - lb),
+// clamped to [0, 1] after each update, stored [P][N] (structure of arrays).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "gac.h"
+#include "gac_internal.h"
+#include "mh_kernel.cuh"
+
+namespace gac {
+
+constexpr int kFitBlock = 256;
+constexpr int kFitMaxWindow = 4096;
+
+template <class R>
+struct FitArgs {
+    const float *data;     // [N][M]
+    const uint8_t *mask;   // [N] or nullptr
+    const float *weight;   // [N] or nullptr
+    int nx, ny, nz;
+    int64_t n;
+    int loss;              // GAC_FIT_L1 / GAC_FIT_L2
+    uint32_t tv_params;
+    int tv_dims;
+    R scale;               // 1 / (n_mask M)
+    R lambda_n;            // lambda / n_mask
+    R lr, beta1, beta2, eps;
+    const int *stop;       // set by fit_check_kernel
+    double *block_loss;    // [gridDim.x]
+};
+
+template <class R>
+__device__ __forceinline__ R sgn(R x) {
+    return static_cast<R>((x > R(0)) - (x < R(0)));
+}
+
+// ------------------------------------------------ models and Jacobians ----
+// visit(k, s_k, J_k[P]) per real measurement (complex data: re then im).
+template <int KIND, class R, class V>
+__device__ __forceinline__ void jacobian(const R *th, const ModelConst &mc, V &&visit) {
+    constexpr int P = model_n_par(KIND);
+    const int n = mc.n_acq;
+    if constexpr (KIND == GAC_MODEL_MONOEXP) {
+        for (int k = 0; k < n; ++k) {
+            const R t = sizeof(R) == 8 ? R(mc.acq_d[k]) : R(mc.acq_f[k]);
+            const R e = exp(-th[1] * t * R(1e-3));
+            R J[P] = {e, -th[0] * t * R(1e-3) * e};
+            visit(k, th[0] * e, J);
+        }
+    } else if constexpr (KIND == GAC_MODEL_MWI3) {
+        for (int k = 0; k < n; ++k) {
+            const R t = sizeof(R) == 8 ? R(mc.acq_d[k]) : R(mc.acq_f[k]);
+            R Jr[P], Ji[P];
+            R re = R(0), im = R(0);
+            const R w2pi = R(6.283185307179586477) * t * R(1e-3);  // d angle / d df
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const R decay = exp(-t / th[3 + j]);
+                const R ang = th[8] - ((j < 2) ? th[6 + j] * w2pi : R(0));
+                R sn, cs;
+                sincos(ang, &sn, &cs);
+                const R amp = th[j] * decay;
+                re += amp * cs;
+                im += amp * sn;
+                Jr[j] = decay * cs;
+                Ji[j] = decay * sn;
+                const R dT = amp * t / (th[3 + j] * th[3 + j]);
+                Jr[3 + j] = dT * cs;
+                Ji[3 + j] = dT * sn;
+                if (j < 2) {
+                    Jr[6 + j] = amp * w2pi * sn;
+                    Ji[6 + j] = -amp * w2pi * cs;
+                }
+            }
+            Jr[8] = -im;
+            Ji[8] = re;
+            visit(2 * k, re, Jr);
+            visit(2 * k + 1, im, Ji);
+        }
+    } else if constexpr (KIND == GAC_MODEL_SMT) {
+        const R f = th[0], da = th[1], dpar = th[2], dperp = th[3];
+        for (int k = 0; k < n; ++k) {
+            const R b = sizeof(R) == 8 ? R(mc.acq_d[k]) : R(mc.acq_f[k]);
+            R gi, dgi, gx, dgx;
+            smt_g_dg(b * da, mc, gi, dgi);
+            smt_g_dg(b * (dpar - dperp), mc, gx, dgx);
+            const R e = exp(-b * dperp);
+            R J[P] = {gi - e * gx, f * b * dgi, (R(1) - f) * e * b * dgx, (R(1) - f) * (-b * e * gx - e * b * dgx)};
+            visit(k, f * gi + (R(1) - f) * e * gx, J);
+        }
+    } else {  // linear test model
+        for (int k = 0; k < n; ++k) {
+            const R t = sizeof(R) == 8 ? R(mc.acq_d[k]) : R(mc.acq_f[k]);
+            R J[P] = {R(1), t};
+            visit(k, th[0] + th[1] * t, J);
+        }
+    }
+}
+
+template <int KIND, int PREC>
+__global__ void __launch_bounds__(kFitBlock) fit_step_kernel(const ModelConst mc, const FitArgs<typename PrecTraits<PREC>::R> fa,
+                                                             const typename PrecTraits<PREC>::R *u_in,
+                                                             typename PrecTraits<PREC>::R *u_out,
+                                                             typename PrecTraits<PREC>::R *m1,
+                                                             typename PrecTraits<PREC>::R *m2,
+                                                             typename PrecTraits<PREC>::R c1,
+                                                             typename PrecTraits<PREC>::R c2) {
+    using R = typename PrecTraits<PREC>::R;
+    constexpr int P = model_n_par(KIND);
+    __shared__ double red[kFitBlock];
+    if (*fa.stop) return;  // the same for every thread
+    model_smem_load<KIND>(mc);
+    __syncthreads();
+    const int M = mc.n_meas;
+    const int64_t n = fa.n;
+    const int64_t sx = 1, sy = fa.nx, sz = static_cast<int64_t>(fa.nx) * fa.ny;
+    double my_loss = 0.0;
+    for (int64_t v = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; v < n;
+         v += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (fa.mask && !fa.mask[v]) {
+#pragma unroll
+            for (int p = 0; p < P; ++p) u_out[p * n + v] = u_in[p * n + v];
+            continue;
+        }
+        R u[P], th[P], g[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            u[p] = u_in[p * n + v];
+            const R lo = sizeof(R) == 8 ? R(mc.lb_d[p]) : R(mc.lb_f[p]);
+            const R hi = sizeof(R) == 8 ? R(mc.ub_d[p]) : R(mc.ub_f[p]);
+            th[p] = lo + u[p] * (hi - lo);
+            g[p] = R(0);
+        }
+        // data term: rho(w (y - s)), drho/ds = -w sign(r) (L1) or -2 w r (L2)
+        const R w = fa.weight ? R(fa.weight[v]) : R(1);
+        const float *y = fa.data + v * M;
+        R loss = R(0);
+        jacobian<KIND, R>(th, mc, [&](int k, R s, const R *J) {
+            const R r = w * (R(__ldg(y + k)) - s);
+            const R d = fa.loss == GAC_FIT_L1 ? -w * sgn(r) : R(-2) * w * r;
+            loss += fa.loss == GAC_FIT_L1 ? fabs(r) : r * r;
+#pragma unroll
+            for (int p = 0; p < P; ++p) g[p] = fma(d, J[p], g[p]);
+        });
+        my_loss += static_cast<double>(loss) * static_cast<double>(fa.scale);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const R range = sizeof(R) == 8 ? R(mc.ub_d[p] - mc.lb_d[p]) : R(mc.ub_f[p] - mc.lb_f[p]);
+            g[p] *= fa.scale * range;
+        }
+        // total variation: pairs (v - e_d, v) and (v, v + e_d) of masked neighbours
+        if (fa.tv_params && fa.lambda_n != R(0)) {
+            const int x = static_cast<int>(v % fa.nx), yy = static_cast<int>((v / fa.nx) % fa.ny);
+            const int z = static_cast<int>(v / sz);
+            const int coord[3] = {x, yy, z}, ext[3] = {fa.nx, fa.ny, fa.nz};
+            const int64_t step[3] = {sx, sy, sz};
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                if (!((fa.tv_params >> p) & 1u)) continue;
+                R tv = R(0), tv_loss = R(0);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    if (d >= fa.tv_dims) break;
+                    if (coord[d] + 1 < ext[d] && (!fa.mask || fa.mask[v + step[d]])) {
+                        const R diff = u_in[p * n + v + step[d]] - u[p];
+                        tv -= sgn(diff);
+                        tv_loss += fabs(diff);
+                    }
+                    if (coord[d] > 0 && (!fa.mask || fa.mask[v - step[d]])) tv += sgn(u[p] - u_in[p * n + v - step[d]]);
+                }
+                g[p] = fma(fa.lambda_n, tv, g[p]);
+                my_loss += static_cast<double>(fa.lambda_n) * static_cast<double>(tv_loss);
+            }
+        }
+        // Adam (bias-corrected moments), then the box
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const R a = fa.beta1 * m1[p * n + v] + (R(1) - fa.beta1) * g[p];
+            const R b = fa.beta2 * m2[p * n + v] + (R(1) - fa.beta2) * g[p] * g[p];
+            m1[p * n + v] = a;
+            m2[p * n + v] = b;
+            const R stepu = fa.lr * (a / c1) / (sqrt(b / c2) + fa.eps);
+            u_out[p * n + v] = fmin(fmax(u[p] - stepu, R(0)), R(1));
+        }
+    }
+    // the block's share of the loss, summed in a fixed order
+    red[threadIdx.x] = my_loss;
+    __syncthreads();
+    for (int s = kFitBlock / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) fa.block_loss[blockIdx.x] = red[0];
+}
+
+// Sums the block shares (fixed order), records loss t, applies the stopping
+// rules: loss < tol, or |least-squares slope of the last `window` losses| <
+// conv_value.
+__global__ void fit_check_kernel(const double *block_loss, int n_blocks, int t, double tol, double conv_value,
+                                 int window, double *hist, int *stop, int *done) {
+    __shared__ double red[kFitBlock];
+    if (*stop) return;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n_blocks; i += blockDim.x) s += block_loss[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = kFitBlock / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double loss = red[0];
+    hist[t - 1] = loss;
+    *done = t;
+    bool halt = tol > 0.0 && loss < tol;
+    if (!halt && conv_value > 0.0 && window > 1 && t >= window) {
+        const double *yv = hist + t - window;
+        const double xm = 0.5 * (window - 1);
+        double ym = 0.0, sxy = 0.0, sxx = 0.0;
+        for (int i = 0; i < window; ++i) ym += yv[i];
+        ym /= window;
+        for (int i = 0; i < window; ++i) {
+            sxy += (i - xm) * (yv[i] - ym);
+            sxx += (i - xm) * (i - xm);
+        }
+        halt = fabs(sxy / sxx) < conv_value;
+    }
+    if (halt) *stop = 1;
+}
+
+// theta [N][P] (double) <-> u [P][N]; outside the mask theta is left alone.
+template <class R>
+__global__ void theta_to_u_kernel(const ModelConst mc, const double *theta, int64_t n, R *u) {
+    const int P = mc.n_par;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n * P;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t v = i / P;
+        const int p = static_cast<int>(i - v * P);
+        const double range = mc.ub_d[p] - mc.lb_d[p];
+        const double x = range > 0 ? (theta[i] - mc.lb_d[p]) / range : 0.0;
+        u[p * n + v] = static_cast<R>(fmin(fmax(x, 0.0), 1.0));
+    }
+}
+template <class R>
+__global__ void u_to_theta_kernel(const ModelConst mc, const R *u, const uint8_t *mask, int64_t n, double *theta) {
+    const int P = mc.n_par;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n * P;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t v = i / P;
+        const int p = static_cast<int>(i - v * P);
+        if (mask && !mask[v]) continue;
+        theta[i] = mc.lb_d[p] + static_cast<double>(u[p * n + v]) * (mc.ub_d[p] - mc.lb_d[p]);
+    }
+}
+
+template <int KIND, int PREC>
+static cudaError_t launch_step(int grid, cudaStream_t s, const ModelConst &mc,
+                               const FitArgs<typename PrecTraits<PREC>::R> &fa, const void *u_in, void *u_out,
+                               void *m1, void *m2, double c1, double c2) {
+    using R = typename PrecTraits<PREC>::R;
+    fit_step_kernel<KIND, PREC><<<grid, kFitBlock, 0, s>>>(mc, fa, static_cast<const R *>(u_in), static_cast<R *>(u_out),
+                                                           static_cast<R *>(m1), static_cast<R *>(m2), R(c1), R(c2));
+    return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t launch_step_kind(int kind, int grid, cudaStream_t s, const ModelConst &mc,
+                                    const FitArgs<typename PrecTraits<PREC>::R> &fa, const void *u_in, void *u_out,
+                                    void *m1, void *m2, double c1, double c2) {
+    switch (kind) {
+    case GAC_MODEL_MONOEXP: return launch_step<GAC_MODEL_MONOEXP, PREC>(grid, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
+    case GAC_MODEL_MWI3: return launch_step<GAC_MODEL_MWI3, PREC>(grid, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
+    case GAC_MODEL_SMT: return launch_step<GAC_MODEL_SMT, PREC>(grid, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
+    default: return launch_step<GAC_MODEL_LINEAR_TEST, PREC>(grid, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
+    }
+}
+
+template <int PREC>
+static gac_status fit_run_prec(const ModelConst &mc, const gac_fit_opts *o, const float *d_data, const uint8_t *d_mask,
+                               const float *d_weight, int64_t n_mask, double *theta, double *loss_history,
+                               int *iterations_done, cudaStream_t s) {
+    using R = typename PrecTraits<PREC>::R;
+    const int P = mc.n_par;
+    const int64_t N = static_cast<int64_t>(o->nx) * o->ny * o->nz;
+    const size_t RB = sizeof(R);
+    DevBuf d_theta;
+    gac_status st = d_theta.make(theta, static_cast<size_t>(N) * P * sizeof(double), true, s, "theta");
+    if (st != GAC_OK) return st;
+    // work arrays: u (two buffers), Adam moments, block losses, history, flags
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((N + kFitBlock - 1) / kFitBlock,
+                                                                           static_cast<int64_t>(sms) * 8)));
+    const int I = o->iterations;
+    const size_t bytes_u = static_cast<size_t>(N) * P * RB;
+    const size_t total = 4 * bytes_u + grid * sizeof(double) + static_cast<size_t>(std::max(I, 1)) * sizeof(double) + 2 * sizeof(int);
+    void *base = nullptr;
+    cudaError_t e = cudaMallocAsync(&base, total, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fit work arrays");
+    struct Free {
+        void *p;
+        cudaStream_t s;
+        ~Free() { cudaFreeAsync(p, s); }
+    } guard{base, s};
+    char *b = static_cast<char *>(base);
+    void *u0 = b, *u1 = b + bytes_u, *m1 = b + 2 * bytes_u, *m2 = b + 3 * bytes_u;
+    double *block_loss = reinterpret_cast<double *>(b + 4 * bytes_u);
+    double *hist = block_loss + grid;
+    int *flags = reinterpret_cast<int *>(hist + std::max(I, 1));  // stop, done
+    if ((e = cudaMemsetAsync(m1, 0, 2 * bytes_u, s)) != cudaSuccess) return cuda_fail(e, "fit memset");
+    if ((e = cudaMemsetAsync(flags, 0, 2 * sizeof(int), s)) != cudaSuccess) return cuda_fail(e, "fit memset");
+    const int conv_grid = static_cast<int>(std::min<int64_t>((N * P + 255) / 256, static_cast<int64_t>(sms) * 8));
+    theta_to_u_kernel<R><<<conv_grid, 256, 0, s>>>(mc, static_cast<const double *>(d_theta.ptr), N, static_cast<R *>(u0));
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "theta to u");
+    FitArgs<R> fa;
+    std::memset(&fa, 0, sizeof fa);
+    fa.data = d_data;
+    fa.mask = d_mask;
+    fa.weight = d_weight;
+    fa.nx = o->nx;
+    fa.ny = o->ny;
+    fa.nz = o->nz;
+    fa.n = N;
+    fa.loss = o->loss;
+    fa.tv_params = o->tv_params;
+    fa.tv_dims = o->tv_dims;
+    fa.scale = static_cast<R>(1.0 / (static_cast<double>(n_mask) * mc.n_meas));
+    fa.lambda_n = static_cast<R>(o->tv_lambda / static_cast<double>(n_mask));
+    fa.lr = static_cast<R>(o->learning_rate);
+    fa.beta1 = static_cast<R>(o->beta1);
+    fa.beta2 = static_cast<R>(o->beta2);
+    fa.eps = static_cast<R>(o->epsilon);
+    fa.stop = flags;
+    fa.block_loss = block_loss;
+    // iterations in chunks; the stop flag is read between chunks
+    constexpr int kChunk = 64;
+    int t = 1;
+    while (t <= I) {
+        const int t_end = std::min(I, t + kChunk - 1);
+        for (; t <= t_end; ++t) {
+            const double c1 = 1.0 - std::pow(o->beta1, t), c2 = 1.0 - std::pow(o->beta2, t);
+            const void *ui = (t & 1) ? u0 : u1;
+            void *uo = (t & 1) ? u1 : u0;
+            if ((e = launch_step_kind<PREC>(mc.kind, grid, s, mc, fa, ui, uo, m1, m2, c1, c2)) != cudaSuccess)
+                return cuda_fail(e, "fit step");
+            fit_check_kernel<<<1, kFitBlock, 0, s>>>(block_loss, grid, t, o->tol, o->convergence_value,
+                                                    o->convergence_window, hist, flags, flags + 1);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "fit check");
+        }
+        int stop = 0;
+        if ((e = cudaMemcpyAsync(&stop, flags, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return cuda_fail(e, "fit flag");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "fit");
+        if (stop) break;
+    }
+    int done = 0;
+    if ((e = cudaMemcpyAsync(&done, flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(e, "fit done");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "fit");
+    if (iterations_done) *iterations_done = done;
+    if (loss_history && done > 0) {
+        if ((e = cudaMemcpyAsync(loss_history, hist, done * sizeof(double), cudaMemcpyDefault, s)) != cudaSuccess)
+            return cuda_fail(e, "loss history");
+    }
+    // u of the last update (iteration `done` wrote buffer (done & 1) ? u1 : u0) -> theta
+    const void *u_fin = done == 0 ? u0 : ((done & 1) ? u1 : u0);
+    u_to_theta_kernel<R><<<conv_grid, 256, 0, s>>>(mc, static_cast<const R *>(u_fin), d_mask, N,
+                                                   static_cast<double *>(d_theta.ptr));
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "u to theta");
+    if ((st = d_theta.copy_out()) != GAC_OK) return st;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "fit");
+    return GAC_OK;
+}
+
+}  // namespace gac
+
+using namespace gac;
+
+extern "C" gac_status gac_fit_run(int model_id, const void *data, const uint8_t *mask, const float *weight,
+                                  const gac_fit_opts *o, double *theta, double *loss_history, int *iterations_done,
+                                  void *stream) {
+    clear_error();
+    ModelConst mc;
+    gac_status st = model_get(model_id, &mc);
+    if (st != GAC_OK) return st;
+    if (!o || !theta || !data) return fail(GAC_ERR_INVALID_ARG, "opts, theta and data must not be NULL");
+    if (mc.kind == GAC_MODEL_AXCAL_SMT) return fail(GAC_ERR_INVALID_ARG, "no analytic gradient for AxCaliberSMT");
+    if (o->nx < 1 || o->ny < 1 || o->nz < 1) return fail(GAC_ERR_INVALID_ARG, "grid extents must be >= 1");
+    if (o->loss != GAC_FIT_L1 && o->loss != GAC_FIT_L2) return fail(GAC_ERR_INVALID_ARG, "unknown loss %d", o->loss);
+    if (o->iterations < 0) return fail(GAC_ERR_INVALID_ARG, "iterations must be >= 0");
+    if (!(o->learning_rate > 0) || !(o->beta1 >= 0 && o->beta1 < 1) || !(o->beta2 >= 0 && o->beta2 < 1) || !(o->epsilon > 0))
+        return fail(GAC_ERR_INVALID_ARG, "Adam needs learning_rate > 0, beta in [0, 1), epsilon > 0");
+    if (o->tv_dims != 2 && o->tv_dims != 3) return fail(GAC_ERR_INVALID_ARG, "tv_dims must be 2 or 3");
+    if (!(o->tv_lambda >= 0) || !(o->tol >= 0) || !(o->convergence_value >= 0))
+        return fail(GAC_ERR_INVALID_ARG, "tv_lambda, tol and convergence_value must be >= 0");
+    if (o->convergence_value > 0 && (o->convergence_window < 2 || o->convergence_window > kFitMaxWindow))
+        return fail(GAC_ERR_INVALID_ARG, "convergence_window must be in [2, %d]", kFitMaxWindow);
+    if (o->precision != GAC_PREC_FP32 && o->precision != GAC_PREC_FP64)
+        return fail(GAC_ERR_INVALID_ARG, "precision must be FP32 or FP64");
+    const int64_t N = static_cast<int64_t>(o->nx) * o->ny * o->nz;
+    const int M = mc.n_meas;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    keep_staging_pool();
+    if (o->iterations == 0) {
+        if (iterations_done) *iterations_done = 0;
+        return GAC_OK;
+    }
+    // the mask count, from the caller's buffer (host or device)
+    std::vector<uint8_t> mk;
+    int64_t n_mask = N;
+    if (mask) {
+        mk.resize(N);
+        if (is_device_ptr(mask)) {
+            cudaError_t e = cudaMemcpy(mk.data(), mask, N, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(e, "mask");
+        } else {
+            std::memcpy(mk.data(), mask, N);
+        }
+        n_mask = 0;
+        for (uint8_t x : mk) n_mask += x != 0;
+    }
+    if (n_mask == 0) {
+        if (iterations_done) *iterations_done = 0;
+        return GAC_OK;
+    }
+    DevBuf d_data, d_mask, d_weight;
+    // every iteration rereads the data, mask and weights: stage them in device memory
+    if ((st = d_data.make(const_cast<void *>(data), static_cast<size_t>(N) * M * sizeof(float), true, s, "data", true)) != GAC_OK)
+        return st;
+    if ((st = d_mask.make(const_cast<uint8_t *>(mask), mask ? static_cast<size_t>(N) : 0, true, s, "mask", true)) != GAC_OK)
+        return st;
+    if ((st = d_weight.make(const_cast<float *>(weight), weight ? static_cast<size_t>(N) * sizeof(float) : 0, true, s, "weight",
+                            true)) != GAC_OK)
+        return st;
+    const auto *dd = static_cast<const float *>(d_data.ptr);
+    const auto *dm = static_cast<const uint8_t *>(d_mask.ptr);
+    const auto *dw = static_cast<const float *>(d_weight.ptr);
+    return o->precision == GAC_PREC_FP64
+               ? fit_run_prec<GAC_PREC_FP64>(mc, o, dd, dm, dw, n_mask, theta, loss_history, iterations_done, s)
+               : fit_run_prec<GAC_PREC_FP32>(mc, o, dd, dm, dw, n_mask, theta, loss_history, iterations_done, s);
+}

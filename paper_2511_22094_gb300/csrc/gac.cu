@@ -79,7 +79,7 @@ DevBuf::~DevBuf() {
 // node: the data crosses once, while the kernel runs, with no staging copy);
 // pageable host memory gets a stream-ordered device allocation (copied in
 // if `in`, out by copy_out).
-gac_status DevBuf::make(void *user, size_t nbytes, bool in, cudaStream_t s, const char *name) {
+gac_status DevBuf::make(void *user, size_t nbytes, bool in, cudaStream_t s, const char *name, bool reread) {
     stream = s;
     bytes = nbytes;
     host = user;
@@ -94,7 +94,7 @@ gac_status DevBuf::make(void *user, size_t nbytes, bool in, cudaStream_t s, cons
             ptr = user;
             return GAC_OK;
         }
-        if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+        if (a.type == cudaMemoryTypeHost && a.devicePointer && !reread) {
             ptr = a.devicePointer;
             return GAC_OK;
         }

@@ -26,7 +26,9 @@ struct DevBuf {
     size_t bytes = 0;
     bool owned = false;
     cudaStream_t stream = nullptr;
-    gac_status make(void *user, size_t nbytes, bool in, cudaStream_t s, const char *name);
+    // reread = true: the kernels read the buffer many times (stage page-locked
+    // host memory too instead of reading it in place)
+    gac_status make(void *user, size_t nbytes, bool in, cudaStream_t s, const char *name, bool reread = false);
     gac_status copy_out();
     ~DevBuf();
 };

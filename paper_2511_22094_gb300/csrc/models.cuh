@@ -161,6 +161,57 @@ __device__ __forceinline__ double smt_g_d(double x) {
     return sum;
 }
 
+// g(x) and g'(x) in FP32 from the same table: the interval polynomial and its
+// derivative (unit intervals, so d/dx = d/dd); g' = -g / (2x) on the tail.
+__device__ __forceinline__ void smt_g_dg(float x, const ModelConst &mc, float &g, float &dg) {
+    constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
+    const float t = x + kRound;
+    const float d = x - (t - kRound);
+    int i = __float_as_int(t) - __float_as_int(kRound) - mc.gtab_lo;
+    i = min(max(i, 0), mc.gtab_n - 1);
+    const float4 lo = smt_gtab_s[i];
+    const float4 hi = smt_gtab_s[kGTabMax + i];
+    float p = fmaf(hi.w, d, hi.z), q = fmaf(7.0f * hi.w, d, 6.0f * hi.z);
+    p = fmaf(p, d, hi.y);
+    q = fmaf(q, d, 5.0f * hi.y);
+    p = fmaf(p, d, hi.x);
+    q = fmaf(q, d, 4.0f * hi.x);
+    p = fmaf(p, d, lo.w);
+    q = fmaf(q, d, 3.0f * lo.w);
+    p = fmaf(p, d, lo.z);
+    q = fmaf(q, d, 2.0f * lo.z);
+    p = fmaf(p, d, lo.y);
+    q = fmaf(q, d, lo.y);
+    p = fmaf(p, d, lo.x);
+    if (x >= kGTail) {
+        const float tail = kSqrtPiHalf * rsqrtf(x);
+        g = tail;
+        dg = -0.5f * tail / x;
+    } else {
+        g = p;
+        dg = q;
+    }
+}
+
+// g(x) and g'(x) in FP64: g' = (e^{-x} - g(x)) / (2x) (integration by parts of
+// -int u^2 e^{-x u^2} du), and near 0, where that form cancels, its Taylor
+// series sum_{n>=1} (-1)^n x^(n-1) / ((n-1)! (2n+1)).
+__device__ __forceinline__ void smt_g_dg(double x, const ModelConst &, double &g, double &dg) {
+    g = smt_g_d(x);
+    if (fabs(x) > 0.5) {
+        dg = (exp(-x) - g) / (2.0 * x);
+        return;
+    }
+    double term = -1.0, sum = 0.0;  // term = (-1)^n x^(n-1) / (n-1)!
+    for (int n = 1; n < 40; ++n) {
+        const double add = term / (2.0 * n + 1.0);  // (-1)^n n x^(n-1) / (n! (2n+1))
+        sum += add;
+        if (fabs(add) <= 1e-17 * fabs(sum)) break;
+        term *= -x / n;
+    }
+    dg = sum;
+}
+
 // sin and cos of x in FP32 for |x| <= kSinCosMaxArg.  Cody & Waite's
 // additive range reduction by pi/2 ("Software Manual for the Elementary
 // Functions", 1980) with a three-part constant whose first two parts have

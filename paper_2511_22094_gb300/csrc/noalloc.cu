@@ -23,7 +23,7 @@ namespace gac {
 static __device__ __align__(256) unsigned char g_noalloc_state[GAC_NOALLOC_STATE_BYTES];
 
 template <int KIND>
-__global__ void __launch_bounds__(kBlock, 2) noalloc_kernel(const ModelConst mc, const RunArgs ra,
+__global__ void __launch_bounds__(kBlock, mh_min_blocks<KIND, GAC_PREC_MIXED>()) noalloc_kernel(const ModelConst mc, const RunArgs ra,
                                                             const SliceState ss, int t_begin, int t_end) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     for (int64_t tile = blockIdx.x; tile < ra.n_tiles; tile += gridDim.x)

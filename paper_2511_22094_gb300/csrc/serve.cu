@@ -37,9 +37,21 @@ struct ServeJob {
     SliceState ss;
 };
 
+// A round's share of one job: iterations t_begin+1 .. t_end of every tile.
+// The tiles of a kind's jobs are numbered consecutively from 0 (first_item
+// of each entry), and blocks claim tile numbers through an atomic counter.
+struct RoundJob {
+    int32_t job;  // index into the round's job table
+    int32_t t_begin;
+    int32_t t_end;
+    int32_t pad;
+    int64_t first_item;
+};
+
+// The tile a block has claimed.
 struct WorkItem {
-    int32_t job;      // index into the round's job table
-    int32_t t_begin;  // iterations t_begin+1 .. t_end
+    int32_t job;
+    int32_t t_begin;
     int32_t t_end;
     int32_t pad;
     int64_t tile;
@@ -56,7 +68,7 @@ __device__ __forceinline__ void block_copy(void *dst, const void *src, int n) {
 // footprint; a round launches the kinds present concurrently on their own
 // streams, and their blocks share the SMs.
 template <int KIND>
-__global__ void __launch_bounds__(kBlock, 2) serve_kernel(const ServeJob *jobs, const WorkItem *items,
+__global__ void __launch_bounds__(kBlock, mh_min_blocks<KIND, GAC_PREC_MIXED>()) serve_kernel(const ServeJob *jobs, const RoundJob *rj, int n_rj,
                                                           int n_items, int *next_item) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(16) ServeJob s_job;
@@ -67,7 +79,19 @@ __global__ void __launch_bounds__(kBlock, 2) serve_kernel(const ServeJob *jobs, 
         __syncthreads();
         if (threadIdx.x == 0) {
             s_idx = atomicAdd(next_item, 1);
-            if (s_idx < n_items) s_item = items[s_idx];
+            if (s_idx < n_items) {  // the last entry whose first tile is <= s_idx
+                int lo = 0, hi = n_rj - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) / 2;
+                    if (rj[mid].first_item <= s_idx) lo = mid;
+                    else hi = mid - 1;
+                }
+                const RoundJob r = rj[lo];
+                s_item.job = r.job;
+                s_item.t_begin = r.t_begin;
+                s_item.t_end = r.t_end;
+                s_item.tile = s_idx - r.first_item;
+            }
         }
         __syncthreads();
         if (s_idx >= n_items) break;
@@ -101,13 +125,13 @@ static const void *serve_fn(int slot) {
     }
 }
 static void launch_serve(int slot, int grid, size_t smem, cudaStream_t s, const ServeJob *jobs,
-                         const WorkItem *items, int n, int *counter) {
+                         const RoundJob *rj, int n_rj, int n, int *counter) {
     switch (slot) {
-    case 0: serve_kernel<GAC_MODEL_MONOEXP><<<grid, kBlock, smem, s>>>(jobs, items, n, counter); break;
-    case 1: serve_kernel<GAC_MODEL_MWI3><<<grid, kBlock, smem, s>>>(jobs, items, n, counter); break;
-    case 2: serve_kernel<GAC_MODEL_SMT><<<grid, kBlock, smem, s>>>(jobs, items, n, counter); break;
-    case 3: serve_kernel<GAC_MODEL_AXCAL_SMT><<<grid, kBlock, smem, s>>>(jobs, items, n, counter); break;
-    default: serve_kernel<GAC_MODEL_LINEAR_TEST><<<grid, kBlock, smem, s>>>(jobs, items, n, counter); break;
+    case 0: serve_kernel<GAC_MODEL_MONOEXP><<<grid, kBlock, smem, s>>>(jobs, rj, n_rj, n, counter); break;
+    case 1: serve_kernel<GAC_MODEL_MWI3><<<grid, kBlock, smem, s>>>(jobs, rj, n_rj, n, counter); break;
+    case 2: serve_kernel<GAC_MODEL_SMT><<<grid, kBlock, smem, s>>>(jobs, rj, n_rj, n, counter); break;
+    case 3: serve_kernel<GAC_MODEL_AXCAL_SMT><<<grid, kBlock, smem, s>>>(jobs, rj, n_rj, n, counter); break;
+    default: serve_kernel<GAC_MODEL_LINEAR_TEST><<<grid, kBlock, smem, s>>>(jobs, rj, n_rj, n, counter); break;
     }
 }
 
@@ -203,7 +227,7 @@ struct gac_server {
     cudaStream_t s_kind[kKinds] = {};
     cudaEvent_t ev_setup = nullptr, ev_kind[kKinds] = {};
     ServeJob *d_jobs = nullptr, *h_jobs = nullptr;
-    WorkItem *d_items = nullptr, *h_items = nullptr;
+    RoundJob *d_items = nullptr, *h_items = nullptr;
     int *d_counter = nullptr;
     size_t cap_jobs = 0, cap_items = 0;
     size_t smem = 0;
@@ -405,10 +429,12 @@ gac_status gac_server::run_round() {
     if (run.empty()) return GAC_OK;
     // Slice lengths.  A round is about round_target_s of work at the current
     // throughput estimate.  Jobs are taken in order of remaining work: one
-    // whose remainder fits in half of what is left of the round's budget runs
-    // to completion in this round (small jobs leave quickly instead of
-    // advancing in lock-step with large ones); the others share the rest of
-    // the budget equally per chain (at least 16 iterations each).
+    // whose remainder fits in half of what is left of the first half of the
+    // round's budget runs to completion in this round (small jobs leave
+    // quickly instead of advancing in lock-step with large ones); the others
+    // share the rest of the budget -- at least half of it, so that a stream
+    // of small arrivals cannot starve a large job -- equally per chain (at
+    // least 16 iterations each).
     std::vector<size_t> order(run.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = i;
     auto remaining = [&](size_t i) {
@@ -417,12 +443,14 @@ gac_status gac_server::run_round() {
     };
     std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return remaining(a) < remaining(b); });
     double budget_ci = round_target_s * ci_per_s;
+    double small_ci = 0.5 * budget_ci;
     std::vector<int> t_end(run.size(), -1);
     int64_t big_chains = 0;
     for (size_t i : order) {
         const double rem = remaining(i);
-        if (rem <= 0.5 * budget_ci) {
+        if (rem <= 0.5 * small_ci) {
             t_end[i] = run[i]->opts.iterations;
+            small_ci -= rem;
             budget_ci -= rem;
         } else {
             big_chains += run[i]->n_vox * run[i]->opts.n_chains;
@@ -433,8 +461,7 @@ gac_status gac_server::run_round() {
         if (t_end[i] < 0)
             t_end[i] = static_cast<int>(std::min<int64_t>(run[i]->opts.iterations, run[i]->t_done + k_big));
     (void)chains;
-    size_t n_items = 0;
-    for (auto &jp : run) n_items += jp->desc.ra.n_tiles;
+    const size_t n_items = run.size();  // one round entry per job
     if (run.size() > cap_jobs) {
         if (d_jobs) cudaFree(d_jobs);
         if (h_jobs) cudaFreeHost(h_jobs);
@@ -448,7 +475,7 @@ gac_status gac_server::run_round() {
         if (h_items) cudaFreeHost(h_items);
         cap_items = std::max(n_items, 2 * cap_items);
         gac_status st = round_alloc(reinterpret_cast<void **>(&d_items), reinterpret_cast<void **>(&h_items),
-                                    cap_items * sizeof(WorkItem));
+                                    cap_items * sizeof(RoundJob));
         if (st != GAC_OK) return st;
     }
     // items grouped by model kind (one contiguous range per kind's kernel),
@@ -461,31 +488,30 @@ gac_status gac_server::run_round() {
     });
     size_t k = 0;
     int64_t work = 0;
-    size_t first_item[kKinds] = {}, count_item[kKinds] = {}, smem_kind[kKinds] = {};
+    size_t first_rj[kKinds] = {}, n_rj[kKinds] = {}, count_item[kKinds] = {}, smem_kind[kKinds] = {};
     for (size_t ji = 0; ji < run.size(); ++ji) h_jobs[ji] = run[ji]->desc;
     for (int slot = 0; slot < kKinds; ++slot) {
-        first_item[slot] = k;
+        first_rj[slot] = k;
+        int64_t tiles = 0;
         for (size_t ji : by_len) {
             Job &j = *run[ji];
             if (kind_slot(j.mc.kind) != slot) continue;
             const RunArgs &ra = j.desc.ra;
             smem_kind[slot] = std::max(smem_kind[slot], tile_smem_bytes(j.mc.n_par, 8, ra.vox_per_block, ra.row_stride, false));
-            const int t0 = j.t_done;
-            const int t1 = t_end[ji];
-            work += static_cast<int64_t>(t1 - t0) * j.n_vox * j.opts.n_chains;
-            for (int64_t tile = 0; tile < ra.n_tiles; ++tile) {
-                WorkItem &wi = h_items[k++];
-                wi.job = static_cast<int32_t>(ji);
-                wi.t_begin = t0;
-                wi.t_end = t1;
-                wi.pad = 0;
-                wi.tile = tile;
-            }
+            work += static_cast<int64_t>(t_end[ji] - j.t_done) * j.n_vox * j.opts.n_chains;
+            RoundJob &r = h_items[k++];
+            r.job = static_cast<int32_t>(ji);
+            r.t_begin = j.t_done;
+            r.t_end = t_end[ji];
+            r.pad = 0;
+            r.first_item = tiles;
+            tiles += ra.n_tiles;
         }
-        count_item[slot] = k - first_item[slot];
+        n_rj[slot] = k - first_rj[slot];
+        count_item[slot] = static_cast<size_t>(tiles);
     }
     cudaError_t e = cudaMemcpyAsync(d_jobs, h_jobs, run.size() * sizeof(ServeJob), cudaMemcpyHostToDevice, s_compute);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_items, h_items, n_items * sizeof(WorkItem), cudaMemcpyHostToDevice, s_compute);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_items, h_items, n_items * sizeof(RoundJob), cudaMemcpyHostToDevice, s_compute);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, kKinds * sizeof(int), s_compute);
     if (e == cudaSuccess) e = cudaEventRecord(ev_setup, s_compute);
     if (e != cudaSuccess) return cuda_fail(e, "round setup");
@@ -497,8 +523,8 @@ gac_status gac_server::run_round() {
         if (e != cudaSuccess) return cuda_fail(e, "occupancy");
         const size_t grid = std::min<size_t>(static_cast<size_t>(std::max(1, per_sm)) * sms, count_item[slot]);
         if ((e = cudaStreamWaitEvent(s_kind[slot], ev_setup, 0)) != cudaSuccess) return cuda_fail(e, "wait");
-        launch_serve(slot, static_cast<int>(grid), smem_kind[slot], s_kind[slot], d_jobs, d_items + first_item[slot],
-                     static_cast<int>(count_item[slot]), d_counter + slot);
+        launch_serve(slot, static_cast<int>(grid), smem_kind[slot], s_kind[slot], d_jobs, d_items + first_rj[slot],
+                     static_cast<int>(n_rj[slot]), static_cast<int>(count_item[slot]), d_counter + slot);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "serve kernel launch");
         if ((e = cudaEventRecord(ev_kind[slot], s_kind[slot])) != cudaSuccess) return cuda_fail(e, "event");
     }

@@ -56,6 +56,18 @@ TRACE_DTYPE = np.dtype([("theta", np.float64, MAX_PAR), ("prop", np.float64, MAX
 assert TRACE_DTYPE.itemsize == ct.sizeof(TraceRec)
 
 
+FIT_L1, FIT_L2 = 1, 2
+
+
+class FitOpts(ct.Structure):
+    _fields_ = [("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int), ("loss", ct.c_int),
+                ("iterations", ct.c_int), ("learning_rate", ct.c_double), ("beta1", ct.c_double),
+                ("beta2", ct.c_double), ("epsilon", ct.c_double), ("tol", ct.c_double),
+                ("convergence_value", ct.c_double), ("convergence_window", ct.c_int),
+                ("tv_lambda", ct.c_double), ("tv_params", ct.c_uint32), ("tv_dims", ct.c_int),
+                ("precision", ct.c_int)]
+
+
 RESULT_KEYS = ("mean", "std", "samples", "accept_rate", "nonfinite", "trace", "rhat", "step_scale")
 
 
@@ -72,7 +84,7 @@ EXPORTS = ["gac_model_register", "gac_model_info", "gac_result_sizes", "gac_mcmc
            "gac_forward", "gac_loglik", "gac_philox_words", "gac_normals", "gac_last_error",
            "gac_version", "gac_server_create", "gac_server_job_bytes", "gac_server_submit",
            "gac_server_poll", "gac_server_wait", "gac_server_cancel", "gac_server_get_stats",
-           "gac_server_destroy", "gac_mcmc_run_noalloc", "gac_ensemble_run"]
+           "gac_server_destroy", "gac_mcmc_run_noalloc", "gac_ensemble_run", "gac_fit_run"]
 NOALLOC_STATE_BYTES = 64 << 20
 
 
@@ -97,6 +109,7 @@ def _load():
                              ct.POINTER(Result), vp],
         "gac_mcmc_run_noalloc": [ct.c_int, vp, i64, vp, ct.c_float, vp, ct.POINTER(McmcOpts), ct.c_int,
                                  ct.POINTER(Result), vp],
+        "gac_fit_run": [ct.c_int, vp, vp, vp, ct.POINTER(FitOpts), vp, vp, ct.POINTER(ct.c_int), vp],
         "gac_server_create": [ct.c_size_t, ct.c_int, ct.POINTER(vp)],
         "gac_server_job_bytes": [ct.c_int, i64, ct.POINTER(McmcOpts), ct.c_int, ct.c_int,
                                  ct.POINTER(ct.c_size_t)],
@@ -213,6 +226,35 @@ def gac_mcmc_run_noalloc(model_id: int, data, n_vox: int, sigma, sigma_scalar: f
     _check(_lib.gac_mcmc_run_noalloc(model_id, _ptr(data), n_vox, _ptr(sigma), sigma_scalar,
                                      _ptr(x0), ct.byref(opts), slice_iterations, ct.byref(r),
                                      _stream(stream)), "gac_mcmc_run_noalloc")
+
+
+def make_fit_opts(shape, *, loss=FIT_L1, iterations=100, learning_rate=0.01, beta1=0.9, beta2=0.999,
+                  epsilon=1e-8, tol=0.0, convergence_value=0.0, convergence_window=20, tv_lambda=0.0,
+                  tv_params=0, tv_dims=3, precision=PREC_FP32) -> FitOpts:
+    return FitOpts(shape[0], shape[1], shape[2], loss, iterations, learning_rate, beta1, beta2, epsilon, tol,
+                   convergence_value, convergence_window, tv_lambda, tv_params, tv_dims, precision)
+
+
+def gac_fit_run(model_id: int, data, mask, weight, opts: FitOpts, theta, loss_history=None, stream=None) -> int:
+    """Whole-volume Adam fit; theta [N][P] float64 is updated in place.
+    Returns the number of updates taken."""
+    done = ct.c_int(0)
+    _check(_lib.gac_fit_run(model_id, _ptr(data), _ptr(mask), _ptr(weight), ct.byref(opts), _ptr(theta),
+                            _ptr(loss_history), ct.byref(done), _stream(stream)), "gac_fit_run")
+    return done.value
+
+
+def fit_host(model_id: int, data, theta0, *, shape, mask=None, weight=None, **kw):
+    """gac_fit_run on host numpy arrays: returns (theta, loss history, updates)."""
+    th = np.array(theta0, np.float64, copy=True, order="C")
+    it = kw.get("iterations", 100)
+    hist = np.full(max(it, 1), np.nan)
+    opts = make_fit_opts(shape, **kw)
+    d = np.ascontiguousarray(data, np.float32)
+    mk = None if mask is None else np.ascontiguousarray(mask, np.uint8)
+    wt = None if weight is None else np.ascontiguousarray(weight, np.float32)
+    done = gac_fit_run(model_id, d, mk, wt, opts, th, hist)
+    return th, hist[:done], done
 
 
 def gac_forward(model_id: int, theta, n: int, precision: int, s, stream=None):

@@ -176,3 +176,21 @@ def test_register_same_description_returns_same_id(gac):
     d["step"] = [0.02, 1.0]
     c = gac.gac_model_register(**d)
     assert a == b and c != a
+
+
+def test_fit_argument_validation(gac):
+    mid = gac.gac_model_register(**MONO)
+    y, th = np.zeros((8, 12), np.float32), np.ones((8, 2))
+    for bad in (dict(loss=3), dict(iterations=-1), dict(learning_rate=0.0), dict(beta1=1.0), dict(tv_dims=1),
+                dict(convergence_value=1e-3, convergence_window=1), dict(precision=0), dict(tv_lambda=-1.0)):
+        with pytest.raises(gac.GacError) as e:
+            gac.fit_host(mid, y, th, shape=(2, 2, 2), **bad)
+        assert e.value.status == 1, bad
+    with pytest.raises(gac.GacError):  # no analytic gradient for AxCaliberSMT
+        ax = gac.gac_model_register(4, [1.0, 13.0, 6.0], [0.2, 0, 0, 0.05], [16, 1, 1, 1.7], [0.1] * 4)
+        gac.fit_host(ax, np.zeros((8, 1), np.float32), np.ones((8, 4)), shape=(2, 2, 2))
+    # zero iterations, or an empty mask: nothing to do, no GPU needed
+    th2, hist, done = gac.fit_host(mid, y, th, shape=(2, 2, 2), iterations=0)
+    assert done == 0 and (th2 == th).all()
+    th3, hist, done = gac.fit_host(mid, y, th, shape=(2, 2, 2), mask=np.zeros(8, np.uint8))
+    assert done == 0 and (th3 == th).all()

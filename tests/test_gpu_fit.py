@@ -1,0 +1,100 @@
+"""Whole-volume gradient fit (askadam.m, Sec. 2.2.1; Eq. 2, 4, 5) on the
+device against the FP64 oracle.
+
+FP64 kernel: the oracle's trajectory, parameters and loss history to
+rounding, for every model with L1 and L2 losses, a mask with holes, per-
+voxel weights and 3D total variation; both stopping rules stop at the
+oracle's iteration.  FP32 kernel: the first update equals the oracle's to the
+FP32 error of the gradient (Adam's first step is lr against the gradient's
+sign, so only near-zero gradient components may differ), and after 200
+updates the loss (to 1%) and the parameter maps (95% within 2% of the prior
+range) agree: the L1 subgradient and the TV signs flip where FP32 and FP64
+residuals straddle zero, after which the trajectories part by Adam steps.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+MONOEXP, MWI3, SMT, LINEAR = 1, 2, 3, 100
+TE12 = np.array([2.0 + 3 * k for k in range(12)])
+TE24 = np.array([2.0 + 44.0 * k / 23 for k in range(24)])
+BVALS = np.array([0.0, 1.0, 2.5, 5.0, 7.5, 10.0])
+MODELS = {
+    MONOEXP: (TE12, [0.5, 10.0], [1.5, 80.0]),
+    MWI3: (TE24, [0.0, 0.0, 0.0, 3.0, 40.0, 30.0, -10.0, -10.0, -np.pi], [1.0, 1.0, 1.0, 20.0, 80.0, 60.0, 20.0, 20.0, np.pi]),
+    SMT: (BVALS, [0.0, 1.0, 0.5, 0.0], [1.0, 3.0, 3.0, 1.5]),
+    LINEAR: (np.linspace(0, 1, 12), [-2.0, -3.0], [2.0, 3.0]),
+}
+SHAPE = (6, 5, 4)
+
+
+def _problem(orc, kind, seed=21, noise=0.02):
+    acq, lb, ub = MODELS[kind]
+    lb, ub = np.array(lb), np.array(ub)
+    rng = np.random.default_rng(seed + kind)
+    N = int(np.prod(SHAPE))
+    truth = rng.uniform(lb + 0.2 * (ub - lb), ub - 0.2 * (ub - lb), (N, len(lb)))
+    y = orc.forward(kind, acq, truth)
+    y = (y + noise * rng.standard_normal(y.shape)).astype(np.float32)
+    theta0 = rng.uniform(lb + 0.3 * (ub - lb), ub - 0.3 * (ub - lb), (N, len(lb)))
+    mask = (rng.uniform(size=N) > 0.15).astype(np.uint8)
+    weight = rng.uniform(0.5, 2.0, N).astype(np.float32)
+    return acq, lb, ub, y, theta0, mask, weight
+
+
+CASES = [(k, loss) for k in (MONOEXP, MWI3, SMT, LINEAR) for loss in (1, 2)]
+
+
+@pytest.mark.parametrize("kind,loss", CASES, ids=[f"{k}-L{l}" for k, l in CASES])
+def test_fp64_follows_the_oracle(gac, orc, kind, loss):
+    acq, lb, ub, y, theta0, mask, weight = _problem(orc, kind)
+    mid = gac.gac_model_register(kind, acq, lb, ub, np.zeros(len(lb)))
+    kw = dict(loss=loss, iterations=60, lr=0.01, lam=0.02, tv_params=0b11, tv_dims=3)
+    r_th, r_hist, r_done = orc.fit_run(kind, acq, lb, ub, y, theta0, shape=SHAPE, mask=mask, weight=weight, **kw)
+    g_th, g_hist, g_done = gac.fit_host(mid, y, theta0, shape=SHAPE, mask=mask, weight=weight, loss=loss,
+                                        iterations=60, learning_rate=0.01, tv_lambda=0.02, tv_params=0b11,
+                                        tv_dims=3, precision=gac.PREC_FP64)
+    assert g_done == r_done == 60
+    np.testing.assert_allclose(g_hist, r_hist, rtol=1e-9)
+    d = np.abs(g_th - r_th) / (ub - lb)
+    print(f"kind {kind} L{loss}: max |dtheta|/range {d.max():.2e}, loss {r_hist[0]:.4e} -> {r_hist[-1]:.4e}")
+    assert (d <= 1e-9).mean() >= 0.999 and d.max() <= 1e-3
+    np.testing.assert_array_equal(g_th[mask == 0], theta0[mask == 0])
+    assert r_hist[-1] < r_hist[0]
+
+
+def test_stopping_rules_match_the_oracle(gac, orc):
+    acq, lb, ub, y, theta0, mask, weight = _problem(orc, MONOEXP)
+    mid = gac.gac_model_register(MONOEXP, acq, lb, ub, [0.0, 0.0])
+    _, full, _ = orc.fit_run(MONOEXP, acq, lb, ub, y, theta0, shape=SHAPE, mask=mask, iterations=300, lr=0.02)
+    tol = float(np.quantile(full, 0.3))
+    W = 20
+    slopes = np.array([abs(np.polyfit(np.arange(W), full[t - W:t], 1)[0]) for t in range(W, 301)])
+    cv = float(np.quantile(slopes, 0.2))
+    for kw_o, kw_g in ((dict(tol=tol), dict(tol=tol)),
+                       (dict(conv_value=cv, conv_window=W), dict(convergence_value=cv, convergence_window=W))):
+        _, r_hist, r_done = orc.fit_run(MONOEXP, acq, lb, ub, y, theta0, shape=SHAPE, mask=mask, iterations=300,
+                                        lr=0.02, **kw_o)
+        _, g_hist, g_done = gac.fit_host(mid, y, theta0, shape=SHAPE, mask=mask, iterations=300, learning_rate=0.02,
+                                         precision=gac.PREC_FP64, **kw_g)
+        assert g_done == r_done < 300
+        np.testing.assert_allclose(g_hist, r_hist, rtol=1e-9)
+
+
+@pytest.mark.parametrize("kind", [MONOEXP, MWI3, SMT])
+def test_fp32_first_step_and_trajectory(gac, orc, kind):
+    acq, lb, ub, y, theta0, mask, weight = _problem(orc, kind)
+    mid = gac.gac_model_register(kind, acq, lb, ub, np.zeros(len(lb)))
+    r1, _, _ = orc.fit_run(kind, acq, lb, ub, y, theta0, shape=SHAPE, mask=mask, iterations=1, lr=0.01, loss=2)
+    g1, _, _ = gac.fit_host(mid, y, theta0, shape=SHAPE, mask=mask, iterations=1, learning_rate=0.01, loss=2)
+    d1 = np.abs(g1 - r1) / (ub - lb)
+    assert (d1 <= 1e-5).mean() >= 0.995, np.quantile(d1, 0.99)
+    kw = dict(iterations=200, lr=0.01, loss=1, lam=0.01, tv_params=0b1, tv_dims=3)
+    r, r_hist, _ = orc.fit_run(kind, acq, lb, ub, y, theta0, shape=SHAPE, mask=mask, **kw)
+    g, g_hist, _ = gac.fit_host(mid, y, theta0, shape=SHAPE, mask=mask, iterations=200, learning_rate=0.01, loss=1,
+                                tv_lambda=0.01, tv_params=0b1, tv_dims=3)
+    d = np.abs(g - r) / (ub - lb)
+    print(f"FP32 kind {kind}: loss {r_hist[-1]:.5e} vs {g_hist[-1]:.5e}; |dtheta|/range p95 {np.quantile(d, 0.95):.2e}")
+    assert abs(g_hist[-1] - r_hist[-1]) <= 1e-2 * r_hist[-1]
+    assert np.quantile(d, 0.95) <= 2e-2

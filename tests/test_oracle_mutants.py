@@ -10,6 +10,7 @@ import pytest
 import test_oracle_adapt as A
 import test_oracle_axcal as X
 import test_oracle_ensemble as E
+import test_oracle_fit as F
 import test_oracle_models as M
 import test_oracle_rng as R
 import test_oracle_sampler as S
@@ -97,6 +98,22 @@ CASES = [
      X.test_restricted_spherical_mean_against_orientation_quadrature),
     ("free-water diffusivity", "fcsf * exp(-b * ORC_AX_DCSF);", "fcsf * exp(-b * ORC_AX_DA);",
      X.test_compartment_reductions),
+    ("Adam second-moment bias correction", "(sqrt(mom2[i] / c2) + o->eps)", "(sqrt(mom2[i]) + o->eps)",
+     F.test_adam_first_step_is_lr_against_the_gradient),
+    ("TV subgradient sign", "grad[w2 * P + p] += o->lambda / (double)n_mask * sgn(diff);",
+     "grad[w2 * P + p] -= o->lambda / (double)n_mask * sgn(diff);",
+     lambda orc: F.test_loss_gradient_against_finite_differences(orc, 3, 2, 0.3)),
+    ("L1 subgradient", "double drho_ds = (o->loss == 1) ? -w * sgn(r) : -2.0 * w * r;",
+     "double drho_ds = (o->loss == 1) ? -w * r : -2.0 * w * r;",
+     lambda orc: F.test_loss_gradient_against_finite_differences(orc, 3, 1, 0.0)),
+    ("gradient in theta, not u", "grad[v * P + p] *= scale * (m->ub[p] - m->lb[p]); /* d/du */",
+     "grad[v * P + p] *= scale; /* d/du */",
+     lambda orc: F.test_loss_gradient_against_finite_differences(orc, 1, 2, 0.0)),
+    ("SMT Jacobian De_perp", "J[k * P + 3] = -(1.0 - f) * bk * ex * (g_ex + dg_ex);",
+     "J[k * P + 3] = -(1.0 - f) * bk * ex * (g_ex - dg_ex);",
+     lambda orc: F.test_jacobian_against_finite_differences(orc, 3)),
+    ("convergence window start", "o->conv_window > 1 && t >= o->conv_window &&", "o->conv_window > 1 && t > o->conv_window &&",
+     F.test_window_slope_and_stopping_rules),
     ("adaptation floor", "if (a < target && e > ORC_ADAPT_EMIN) --e;", "if (a < target) --e;",
      lambda orc: A.test_adaptation_when_every_proposal_is_rejected(orc, 700, -48)),
 ]
