@@ -570,6 +570,7 @@ def run_serving(args):
         gac.gac_server_destroy(srv)
         r = summarize(lat, max(done_t))
         r["rounds"] = st["rounds"]
+        r["scheduler_s"] = {"gpu_wait": st["gpu_s"], "round_prep": st["round_host_s"], "admit_retire": st["admit_s"]}
         return r
 
     def sequential_pass(compress):

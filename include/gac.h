@@ -360,10 +360,15 @@ gac_status gac_server_wait(gac_server *srv, uint64_t job_id, double timeout_s, g
  * boundary.  Polling it afterwards returns GAC_ERR_CANCELLED. */
 gac_status gac_server_cancel(gac_server *srv, uint64_t job_id);
 
-/* Counters: jobs queued, resident, finished; bytes in use; rounds run. */
+/* Counters: jobs queued, resident, finished; bytes in use; rounds run; and
+ * where the scheduler thread's time went: waiting for the rounds' kernels
+ * after its own work for the round was done (gpu_s), preparing rounds
+ * (round_host_s), admitting and retiring jobs (allocations, uploads queued;
+ * admit_s, mostly overlapped with running rounds). */
 typedef struct {
     int64_t queued, resident, finished, rounds;
     size_t bytes_in_use, budget;
+    double gpu_s, round_host_s, admit_s;
 } gac_server_stats;
 gac_status gac_server_get_stats(gac_server *srv, gac_server_stats *st);
 

@@ -141,6 +141,45 @@ static double now_s() {
     return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
 
+// Page-locked host buffers are slow to allocate and free (every page is
+// pinned), so the server keeps the ones its jobs release and hands them out
+// again: sizes are rounded up to powers of two from 64 KiB, and the cache is
+// emptied when the server is destroyed.
+class PinnedCache {
+  public:
+    static size_t size_class(size_t bytes) {
+        size_t c = 64 << 10;
+        while (c < bytes) c <<= 1;
+        return c;
+    }
+    cudaError_t get(void **p, size_t bytes) {
+        const size_t c = size_class(bytes);
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            auto &v = free_[c];
+            if (!v.empty()) {
+                *p = v.back();
+                v.pop_back();
+                return cudaSuccess;
+            }
+        }
+        return cudaMallocHost(p, c);
+    }
+    void put(void *p, size_t bytes) {
+        if (!p) return;
+        std::lock_guard<std::mutex> lk(mu_);
+        free_[size_class(bytes)].push_back(p);
+    }
+    ~PinnedCache() {
+        for (auto &kv : free_)
+            for (void *p : kv.second) cudaFreeHost(p);
+    }
+
+  private:
+    std::mutex mu_;
+    std::map<size_t, std::vector<void *>> free_;
+};
+
 enum class JobState { Queued, Uploading, Running, Finishing, Done, Failed, Cancelled };
 
 struct Job {
@@ -226,6 +265,7 @@ struct gac_server {
     cudaStream_t s_compute = nullptr, s_copy = nullptr;
     cudaStream_t s_kind[kKinds] = {};
     cudaEvent_t ev_setup = nullptr, ev_kind[kKinds] = {};
+    PinnedCache pinned;  // destroyed after every job's buffers are back
     ServeJob *d_jobs = nullptr, *h_jobs = nullptr;
     RoundJob *d_items = nullptr, *h_items = nullptr;
     int *d_counter = nullptr;
@@ -234,13 +274,15 @@ struct gac_server {
     int sms = 1;
     double ci_per_s = 2e10;   // throughput estimate, refined each round
     double round_target_s = 0.025;
+    double t_gpu = 0, t_round_host = 0, t_admit = 0;  // scheduler time split
 
     void loop();
     gac_status init_gpu();
-    gac_status admit_locked();
+    gac_status admit_locked(int max_jobs = 1 << 30);
     gac_status run_round();
     void retire_locked();
     void free_job(Job &j);
+    void free_results(Job &j);
 };
 
 static gac_status round_alloc(void **d, void **h, size_t bytes) {
@@ -273,32 +315,41 @@ gac_status gac_server::init_gpu() {
     }
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (sms < 1) sms = 1;
+    keep_staging_pool();  // job blocks come from the stream-ordered pool
     return GAC_OK;
 }
 
 void gac_server::free_job(Job &j) {
-    if (j.d_block) cudaFree(j.d_block);
+    // stream-ordered: after everything queued on the copy stream (downloads)
+    if (j.d_block) cudaFreeAsync(j.d_block, s_copy ? s_copy : cudaStream_t{});
     j.d_block = nullptr;
     if (j.ev) cudaEventDestroy(j.ev);
     j.ev = nullptr;
-    if (j.h_data) cudaFreeHost(j.h_data);
-    if (j.h_sigma) cudaFreeHost(j.h_sigma);
+    const size_t N = j.n_vox;
+    pinned.put(j.h_data, N * j.mc.n_meas * 4);
+    pinned.put(j.h_sigma, N * 4);
     j.h_data = j.h_sigma = nullptr;
 }
 
-static void free_results(Job &j) {
-    for (void *p : {static_cast<void *>(j.h_mean), static_cast<void *>(j.h_std), static_cast<void *>(j.h_samples),
-                    static_cast<void *>(j.h_acc), static_cast<void *>(j.h_bad), static_cast<void *>(j.h_rhat),
-                    static_cast<void *>(j.h_scale)})
-        if (p) cudaFreeHost(p);
+void gac_server::free_results(Job &j) {
+    const size_t N = j.n_vox, P = j.mc.n_par, C = j.opts.n_chains;
+    pinned.put(j.h_mean, P * N * 8);
+    pinned.put(j.h_std, P * N * 8);
+    pinned.put(j.h_rhat, P * N * 8);
+    pinned.put(j.h_acc, C * N * 4);
+    pinned.put(j.h_bad, C * N * 4);
+    pinned.put(j.h_scale, C * N * 4);
+    pinned.put(j.h_samples, static_cast<size_t>(j.S) * C * P * N * 4);
     j.h_mean = j.h_std = j.h_rhat = nullptr;
     j.h_samples = j.h_acc = j.h_scale = nullptr;
     j.h_bad = nullptr;
 }
 
-// Admits queued jobs in arrival order while they fit (caller holds mu).
-gac_status gac_server::admit_locked() {
-    while (!queue.empty()) {
+// Admits queued jobs in arrival order while they fit, at most max_jobs of
+// them (caller holds mu).
+gac_status gac_server::admit_locked(int max_jobs) {
+    int admitted = 0;
+    while (!queue.empty() && admitted < max_jobs) {
         auto jp = queue.front();
         Job &j = *jp;
         if (j.cancel) {
@@ -312,7 +363,7 @@ gac_status gac_server::admit_locked() {
         queue.pop_front();
         const bool has_sigma = j.h_sigma != nullptr;
         JobLayout l = job_layout(j.mc, j.n_vox, j.opts, j.keep_samples, has_sigma);
-        cudaError_t e = cudaMalloc(&j.d_block, l.total);
+        cudaError_t e = cudaMallocAsync(&j.d_block, l.total, s_copy);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j.ev, cudaEventDisableTiming);
         const size_t N = j.n_vox, P = j.mc.n_par, C = j.opts.n_chains;
         if (e == cudaSuccess) e = cudaMemcpyAsync(static_cast<char *>(j.d_block) + l.data, j.h_data,
@@ -321,14 +372,14 @@ gac_status gac_server::admit_locked() {
             e = cudaMemcpyAsync(static_cast<char *>(j.d_block) + l.sigma, j.h_sigma, N * 4, cudaMemcpyHostToDevice,
                                 s_copy);
         // results on the host (pinned)
-        if (e == cudaSuccess) e = cudaMallocHost(&j.h_mean, P * N * 8);
-        if (e == cudaSuccess) e = cudaMallocHost(&j.h_std, P * N * 8);
-        if (e == cudaSuccess) e = cudaMallocHost(&j.h_acc, C * N * 4);
-        if (e == cudaSuccess) e = cudaMallocHost(&j.h_bad, C * N * 4);
-        if (e == cudaSuccess) e = cudaMallocHost(&j.h_rhat, P * N * 8);
-        if (e == cudaSuccess) e = cudaMallocHost(&j.h_scale, C * N * 4);
-        if (e == cudaSuccess && j.keep_samples && j.S > 0)
-            e = cudaMallocHost(&j.h_samples, static_cast<size_t>(j.S) * C * P * N * 4);
+        auto pin = [&](auto **p, size_t bytes) { return pinned.get(reinterpret_cast<void **>(p), bytes); };
+        if (e == cudaSuccess) e = pin(&j.h_mean, P * N * 8);
+        if (e == cudaSuccess) e = pin(&j.h_std, P * N * 8);
+        if (e == cudaSuccess) e = pin(&j.h_acc, C * N * 4);
+        if (e == cudaSuccess) e = pin(&j.h_bad, C * N * 4);
+        if (e == cudaSuccess) e = pin(&j.h_rhat, P * N * 8);
+        if (e == cudaSuccess) e = pin(&j.h_scale, C * N * 4);
+        if (e == cudaSuccess && j.keep_samples && j.S > 0) e = pin(&j.h_samples, static_cast<size_t>(j.S) * C * P * N * 4);
         if (e == cudaSuccess) e = cudaEventRecord(j.ev, s_copy);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -379,6 +430,7 @@ gac_status gac_server::admit_locked() {
         in_use += j.bytes;
         j.state = JobState::Uploading;
         resident.push_back(jp);
+        ++admitted;
     }
     return GAC_OK;
 }
@@ -427,6 +479,7 @@ gac_status gac_server::run_round() {
         }
     }
     if (run.empty()) return GAC_OK;
+    const double t_prep = now_s();
     // Slice lengths.  A round is about round_target_s of work at the current
     // throughput estimate.  Jobs are taken in order of remaining work: one
     // whose remainder fits in half of what is left of the first half of the
@@ -516,6 +569,7 @@ gac_status gac_server::run_round() {
     if (e == cudaSuccess) e = cudaEventRecord(ev_setup, s_compute);
     if (e != cudaSuccess) return cuda_fail(e, "round setup");
     const double t_start = now_s();
+    t_round_host += t_start - t_prep;
     for (int slot = 0; slot < kKinds; ++slot) {
         if (count_item[slot] == 0) continue;
         int per_sm = 0;
@@ -528,10 +582,22 @@ gac_status gac_server::run_round() {
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "serve kernel launch");
         if ((e = cudaEventRecord(ev_kind[slot], s_kind[slot])) != cudaSuccess) return cuda_fail(e, "event");
     }
+    // while the round runs: retire finished downloads and admit queued jobs
+    // (allocations and uploads), so that the host work overlaps the kernels
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        const double t0 = now_s();
+        retire_locked();
+        gac_status st = admit_locked();
+        t_admit += now_s() - t0;
+        if (st != GAC_OK) return st;
+    }
+    const double t_wait = now_s();
     for (int slot = 0; slot < kKinds; ++slot) {
         if (count_item[slot] == 0) continue;
         if ((e = cudaEventSynchronize(ev_kind[slot])) != cudaSuccess) return cuda_fail(e, "serve kernel");
     }
+    t_gpu += now_s() - t_wait;
     const double dt = now_s() - t_start;
     if (dt > 1e-4 && work > 0) ci_per_s = 0.5 * ci_per_s + 0.5 * (work / dt);
     // advance; start downloads of finished jobs on the copy stream
@@ -565,8 +631,15 @@ void gac_server::loop() {
         {
             std::unique_lock<std::mutex> lk(mu);
             if (st == GAC_OK) {
+                // with nothing on the GPU, admit one job to start a round at
+                // once; the others are admitted while rounds run
+                bool busy = false;
+                for (auto &jp : resident)
+                    busy = busy || jp->state == JobState::Running || jp->state == JobState::Uploading;
+                const double t0 = now_s();
                 retire_locked();
-                admit_locked();
+                admit_locked(busy ? (1 << 30) : 1);
+                t_admit += now_s() - t0;
             }
             if (st != GAC_OK) {
                 // the GPU side failed: fail every job so no caller waits forever
@@ -609,11 +682,12 @@ void gac_server::loop() {
             for (auto &jp : resident)
                 if (jp->state == JobState::Uploading && cudaEventQuery(jp->ev) == cudaSuccess)
                     jp->state = JobState::Running;
-            continue;
         }
-        st = run_round();
+        st = run_round();  // admits the queued jobs while it runs
     }
     // shutdown: wait for the GPU, release everything
+    for (int i = 0; i < kKinds; ++i)
+        if (s_kind[i]) cudaStreamSynchronize(s_kind[i]);
     if (s_compute) cudaStreamSynchronize(s_compute);
     if (s_copy) cudaStreamSynchronize(s_copy);
     std::lock_guard<std::mutex> lk(mu);
@@ -621,6 +695,7 @@ void gac_server::loop() {
         free_job(*kv.second);
         free_results(*kv.second);
     }
+    if (s_copy) cudaStreamSynchronize(s_copy);  // the stream-ordered frees
     if (d_jobs) cudaFree(d_jobs);
     if (h_jobs) cudaFreeHost(h_jobs);
     if (d_items) cudaFree(d_items);
@@ -697,15 +772,15 @@ gac_status gac_server_submit(gac_server *srv, int model_id, const void *data, in
     j.bytes = bytes;
     j.sigma_scalar = sigma_scalar;
     const size_t dbytes = static_cast<size_t>(n_vox) * mc.n_meas * 4;
-    cudaError_t e = cudaMallocHost(&j.h_data, dbytes);
+    cudaError_t e = srv->pinned.get(reinterpret_cast<void **>(&j.h_data), dbytes);
     if (e == cudaSuccess) e = cudaMemcpy(j.h_data, data, dbytes, cudaMemcpyDefault);
     if (e == cudaSuccess && sigma) {
-        e = cudaMallocHost(&j.h_sigma, static_cast<size_t>(n_vox) * 4);
+        e = srv->pinned.get(reinterpret_cast<void **>(&j.h_sigma), static_cast<size_t>(n_vox) * 4);
         if (e == cudaSuccess) e = cudaMemcpy(j.h_sigma, sigma, static_cast<size_t>(n_vox) * 4, cudaMemcpyDefault);
     }
     if (e != cudaSuccess) {
-        if (j.h_data) cudaFreeHost(j.h_data);
-        if (j.h_sigma) cudaFreeHost(j.h_sigma);
+        srv->pinned.put(j.h_data, dbytes);
+        srv->pinned.put(j.h_sigma, static_cast<size_t>(n_vox) * 4);
         return cuda_fail(e, "staging job inputs");
     }
     std::lock_guard<std::mutex> lk(srv->mu);
@@ -748,7 +823,7 @@ static gac_status deliver(gac_server *srv, std::map<uint64_t, std::shared_ptr<Jo
         if (e != cudaSuccess) st = cuda_fail(e, "copy results");
         if (latency_s) *latency_s = j.t_finish - j.t_submit;
     }
-    free_results(j);
+    srv->free_results(j);
     srv->jobs.erase(it);
     return st;
 }
@@ -805,6 +880,9 @@ gac_status gac_server_get_stats(gac_server *srv, gac_server_stats *st) {
     st->rounds = srv->rounds;
     st->bytes_in_use = srv->in_use;
     st->budget = srv->budget;
+    st->gpu_s = srv->t_gpu;
+    st->round_host_s = srv->t_round_host;
+    st->admit_s = srv->t_admit;
     return GAC_OK;
 }
 
@@ -820,7 +898,7 @@ gac_status gac_server_destroy(gac_server *srv) {
     if (!srv->started) {
         for (auto &kv : srv->jobs) {
             srv->free_job(*kv.second);
-            free_results(*kv.second);
+            srv->free_results(*kv.second);
         }
     }
     delete srv;

@@ -77,7 +77,8 @@ class Result(ct.Structure):
 
 class ServerStats(ct.Structure):
     _fields_ = [("queued", ct.c_int64), ("resident", ct.c_int64), ("finished", ct.c_int64),
-                ("rounds", ct.c_int64), ("bytes_in_use", ct.c_size_t), ("budget", ct.c_size_t)]
+                ("rounds", ct.c_int64), ("bytes_in_use", ct.c_size_t), ("budget", ct.c_size_t),
+                ("gpu_s", ct.c_double), ("round_host_s", ct.c_double), ("admit_s", ct.c_double)]
 
 
 EXPORTS = ["gac_model_register", "gac_model_info", "gac_result_sizes", "gac_mcmc_run",
