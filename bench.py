@@ -278,6 +278,8 @@ def run_fit(args):
     hh = torch.empty(it, dtype=torch.float64).pin_memory()
     h0 = torch.from_numpy(theta0)
     reps = max(1, min(args.steps, 3))
+    hth.copy_(h0)
+    gac.gac_fit_run(mid, hy, hmk, hwt, opts, hth, hh, stream)  # warm-up
     t0 = time.perf_counter()
     for _ in range(reps):
         hth.copy_(h0)
@@ -302,18 +304,18 @@ def run_fit(args):
             "clocks": clocks, "gpu_launches": args.steps * (2 * it + 2), "wall_s": t_wall}
     if not args.no_cpu_baseline:
         import oracle
-        sub = (16, 16, 16)
+        sub = (20, 20, 20)
         ns = int(np.prod(sub))
         th_s, _, theta0_s, mask_s = _fit_problem(w, sub)
         ys = W.noisy_data(oracle.forward(w.kind, w.acq, th_s), W.noise(w, 0, ns), W.sigma(w, th_s))
-        its = 10
+        its = 1000
         t0 = time.perf_counter()
         oracle.fit_run(w.kind, w.acq, w.lb, w.ub, ys, theta0_s, shape=sub, mask=mask_s,
                        weight=1.0 / W.sigma(w, th_s), loss=1, iterations=its, lr=0.01, lam=1e-3, tv_params=1,
                        tv_dims=3)
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": ns * its / dt, "unit": FIT_UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"16^3 voxels x {its} updates ({dt:.1f} s)"}
+                                "sample": f"20^3 voxels x {its} updates ({dt:.1f} s)"}
     print(json.dumps(line), flush=True)
 
 

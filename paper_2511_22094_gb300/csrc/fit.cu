@@ -42,6 +42,8 @@ struct FitArgs {
     R scale;               // 1 / (n_mask M)
     R lambda_n;            // lambda / n_mask
     R lr, beta1, beta2, eps;
+    int row_stride;        // shared-memory floats per staged measurement row (odd)
+    int double_buffer;     // two staged tiles (the next one copied during the current one) or one
     const int *stop;       // set by fit_check_kernel
     double *block_loss;    // [gridDim.x]
 };
@@ -114,92 +116,263 @@ __device__ __forceinline__ void jacobian(const R *th, const ModelConst &mc, V &&
     }
 }
 
+// The 3-pool model and its Jacobian in FP32 for evenly spaced echoes, from
+// the anchored recurrence of the unit-amplitude pool terms
+// u_j(t) = e^{-t/T2*_j} e^{i(phi0 - w_j t)} (the MH kernel's recurrence with
+// A_j = 1): with them every entry of the Jacobian is a product,
+//   dS/dA_j = u_j,  dS/dT2*_j = A_j t / T2*_j^2 u_j,
+//   dS/d df_j = -i 2 pi 1e-3 t A_j u_j,  dS/d phi0 = i S.
+template <class V>
+__device__ __forceinline__ void jacobian_mwi3_rec_f(const float *th, const ModelConst &mc, V &&visit) {
+    const float phi0 = th[8];
+    const int n = mc.n_acq;
+    const float r0 = 1.0f / th[3], r1 = 1.0f / th[4], r2 = 1.0f / th[5];
+    const float2 w = make_float2(kTwoPiMilli * th[6], kTwoPiMilli * th[7]);
+    const float2 m0 = make_float2(expf(-mc.t0_f * r0), expf(-mc.t0_f * r1));
+    const float2 m1 = make_float2(expf(-mc.dt_f * r0), expf(-mc.dt_f * r1));
+    const float2 mk = make_float2(expf(-mc.dtk_f * r0), expf(-mc.dtk_f * r1));
+    float2 sn, cs;
+    sincos_cw2(__ffma2_rn(make_float2(-w.x, -w.y), f2(mc.t0_f), f2(phi0)), sn, cs);
+    float2 X = __fmul2_rn(m0, cs), Y = __fmul2_rn(m0, sn);
+    sincos_cw2(__fmul2_rn(make_float2(-w.x, -w.y), f2(mc.dt_f)), sn, cs);
+    const float2 RR = __fmul2_rn(m1, cs), RI = __fmul2_rn(m1, sn), NRI = make_float2(-RI.x, -RI.y);
+    sincos_cw2(__fmul2_rn(make_float2(-w.x, -w.y), f2(mc.dtk_f)), sn, cs);
+    const float2 KR = __fmul2_rn(mk, cs), KI = __fmul2_rn(mk, sn), NKI = make_float2(-KI.x, -KI.y);
+    float se, ce;
+    sincos_cw(phi0, se, ce);
+    const float e2 = expf(-mc.t0_f * r2);
+    float2 Z = make_float2(e2 * ce, e2 * se);
+    const float2 R2 = f2(expf(-mc.dt_f * r2)), K2 = f2(expf(-mc.dtk_f * r2));
+    const float a0 = th[0], a1 = th[1], a2 = th[2];
+    const float q0 = a0 * r0 * r0, q1 = a1 * r1 * r1, q2 = a2 * r2 * r2;  // dT factors / t
+    auto echo = [&](int k, float2 x, float2 y, float2 z) {
+        const float t = fmaf(static_cast<float>(k), mc.dt_f, mc.t0_f);
+        const float re = fmaf(a0, x.x, fmaf(a1, x.y, a2 * z.x));
+        const float im = fmaf(a0, y.x, fmaf(a1, y.y, a2 * z.y));
+        const float wt = kTwoPiMilli * t;
+        float Jr[9] = {x.x, x.y, z.x, q0 * t * x.x, q1 * t * x.y, q2 * t * z.x, a0 * wt * y.x, a1 * wt * y.y, -im};
+        float Ji[9] = {y.x, y.y, z.y, q0 * t * y.x, q1 * t * y.y, q2 * t * z.y, -a0 * wt * x.x, -a1 * wt * x.y, re};
+        visit(2 * k, re, Jr);
+        visit(2 * k + 1, im, Ji);
+    };
+    int a = 0;
+    for (; a < n; a += kAnchor) {
+        float2 x = X, y = Y, z = Z;
+        const int cnt = min(kAnchor, n - a);
+        for (int i = 0; i < cnt; ++i) {
+            echo(a + i, x, y, z);
+            const float2 xn = __ffma2_rn(x, RR, __fmul2_rn(y, NRI));
+            y = __ffma2_rn(x, RI, __fmul2_rn(y, RR));
+            x = xn;
+            z = __fmul2_rn(z, R2);
+        }
+        const float2 xn = __ffma2_rn(X, KR, __fmul2_rn(Y, NKI));
+        Y = __ffma2_rn(X, KI, __fmul2_rn(Y, KR));
+        X = xn;
+        Z = __fmul2_rn(Z, K2);
+    }
+}
+
+// One voxel's update: forward model and Jacobian against its staged data row
+// y, the loss gradient, the total-variation subgradient, Adam and the box.
+// Returns the voxel's share of the loss (0 outside the mask).
 template <int KIND, int PREC>
-__global__ void __launch_bounds__(kFitBlock) fit_step_kernel(const ModelConst mc, const FitArgs<typename PrecTraits<PREC>::R> fa,
+__device__ __forceinline__ double fit_voxel(const ModelConst &mc, const FitArgs<typename PrecTraits<PREC>::R> &fa,
+                                            int64_t v, const float *y, const typename PrecTraits<PREC>::R *u_in,
+                                            typename PrecTraits<PREC>::R *u_out, typename PrecTraits<PREC>::R *m1,
+                                            typename PrecTraits<PREC>::R *m2, typename PrecTraits<PREC>::R c1,
+                                            typename PrecTraits<PREC>::R c2) {
+    using R = typename PrecTraits<PREC>::R;
+    constexpr int P = model_n_par(KIND);
+    const int64_t n = fa.n;
+    const int64_t sx = 1, sy = fa.nx, sz = static_cast<int64_t>(fa.nx) * fa.ny;
+    double vl = 0.0;
+    // Every load the update needs is issued here, before the model's long
+    // arithmetic hides its latency: own parameters, mask and weight, the
+    // usable neighbours (bit 2d: v + e_d, bit 2d + 1: v - e_d; inside the grid
+    // and the mask) and the neighbours' values of the first penalised map.
+    R u[P], th[P], g[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) u[p] = u_in[p * n + v];
+    const bool inside = !fa.mask || fa.mask[v];
+    const R w = fa.weight ? R(fa.weight[v]) : R(1);
+    const bool tv_on = fa.tv_params && fa.lambda_n != R(0);
+    const int64_t step[3] = {sx, sy, sz};
+    unsigned grid_bit = 0, nbit = 0;  // neighbours inside the grid; inside the grid and the mask
+    int p0 = P;                       // first penalised map (P: none)
+    R nb0[6];
+    if (tv_on) {
+        const int coord[3] = {static_cast<int>(v % fa.nx), static_cast<int>((v / fa.nx) % fa.ny),
+                              static_cast<int>(v / sz)};
+        const int ext[3] = {fa.nx, fa.ny, fa.nz};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const bool use = d < fa.tv_dims;
+            grid_bit |= static_cast<unsigned>(use && coord[d] + 1 < ext[d]) << (2 * d) |
+                        static_cast<unsigned>(use && coord[d] > 0) << (2 * d + 1);
+        }
+        // the mask loads and the neighbour values do not wait on each other
+        nbit = grid_bit;
+        if (fa.mask) {
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+                const int64_t o = ((grid_bit >> j) & 1u) ? ((j & 1) ? -step[j >> 1] : step[j >> 1]) : 0;
+                nbit &= ~(static_cast<unsigned>(fa.mask[v + o] == 0) << j);
+            }
+        }
+        p0 = __ffs(fa.tv_params) - 1;
+        if (p0 < P) {
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+                const int64_t o = ((grid_bit >> j) & 1u) ? ((j & 1) ? -step[j >> 1] : step[j >> 1]) : 0;
+                nb0[j] = u_in[p0 * n + v + o];
+            }
+        }
+    }
+    if (!inside) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) u_out[p * n + v] = u[p];
+        return 0.0;
+    }
+    // Adam's moments are read at the end: start bringing them into L2 now
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(m1 + p * n + v));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(m2 + p * n + v));
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const R lo = sizeof(R) == 8 ? R(mc.lb_d[p]) : R(mc.lb_f[p]);
+        const R hi = sizeof(R) == 8 ? R(mc.ub_d[p]) : R(mc.ub_f[p]);
+        th[p] = lo + u[p] * (hi - lo);
+        g[p] = R(0);
+    }
+    // data term: rho(w (y - s)), drho/ds = -w sign(r) (L1) or -2 w r (L2)
+    R loss = R(0);
+    auto visit = [&](int k, R s, const R *J) {
+        const R r = w * (R(y[k]) - s);
+        const R d = fa.loss == GAC_FIT_L1 ? -w * sgn(r) : R(-2) * w * r;
+        loss += fa.loss == GAC_FIT_L1 ? fabs(r) : r * r;
+#pragma unroll
+        for (int p = 0; p < P; ++p) g[p] = fma(d, J[p], g[p]);
+    };
+    if constexpr (KIND == GAC_MODEL_MWI3 && PREC == GAC_PREC_FP32) {
+        if (mc.even) jacobian_mwi3_rec_f(th, mc, visit);  // the same branch for every thread
+        else jacobian<KIND, R>(th, mc, visit);
+    } else {
+        jacobian<KIND, R>(th, mc, visit);
+    }
+    vl += static_cast<double>(loss) * static_cast<double>(fa.scale);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const R range = sizeof(R) == 8 ? R(mc.ub_d[p] - mc.lb_d[p]) : R(mc.ub_f[p] - mc.lb_f[p]);
+        g[p] *= fa.scale * range;
+    }
+    // total variation: pairs (v - e_d, v) and (v, v + e_d) of masked neighbours
+    if (tv_on) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            if (!((fa.tv_params >> p) & 1u)) continue;
+            R nb[6];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+                const int64_t o = ((grid_bit >> j) & 1u) ? ((j & 1) ? -step[j >> 1] : step[j >> 1]) : 0;
+                nb[j] = p == p0 ? nb0[j] : u_in[p * n + v + o];
+            }
+            R tv = R(0), tv_loss = R(0);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if ((nbit >> (2 * d)) & 1u) {
+                    const R diff = nb[2 * d] - u[p];
+                    tv -= sgn(diff);
+                    tv_loss += fabs(diff);
+                }
+                if ((nbit >> (2 * d + 1)) & 1u) tv += sgn(u[p] - nb[2 * d + 1]);
+            }
+            g[p] = fma(fa.lambda_n, tv, g[p]);
+            vl += static_cast<double>(fa.lambda_n) * static_cast<double>(tv_loss);
+        }
+    }
+    // Adam (bias-corrected moments), then the box
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const R a = fa.beta1 * m1[p * n + v] + (R(1) - fa.beta1) * g[p];
+        const R b = fa.beta2 * m2[p * n + v] + (R(1) - fa.beta2) * g[p] * g[p];
+        m1[p * n + v] = a;
+        m2[p * n + v] = b;
+        const R stepu = fa.lr * (a / c1) / (sqrt(b / c2) + fa.eps);
+        u_out[p * n + v] = fmin(fmax(u[p] - stepu, R(0)), R(1));
+    }
+    return vl;
+}
+
+// 4-byte asynchronous global -> shared copies (no register round trip), in
+// commit groups; wait<N> returns when at most N groups are still in flight.
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Persistent blocks over tiles of kFitBlock voxels (tile b, b + grid, ...).
+// The measurement rows of the next tile are copied into the second of two
+// shared-memory buffers while the current tile computes; rows sit at an odd
+// float stride so that a warp's reads of one column hit distinct banks.
+// FP32 kernels keep two blocks (16 warps) on an SM.
+constexpr int fit_min_blocks(int prec) { return prec == GAC_PREC_FP32 ? 2 : 1; }
+
+template <int KIND, int PREC>
+__global__ void __launch_bounds__(kFitBlock, fit_min_blocks(PREC)) fit_step_kernel(const ModelConst mc, const FitArgs<typename PrecTraits<PREC>::R> fa,
                                                              const typename PrecTraits<PREC>::R *u_in,
                                                              typename PrecTraits<PREC>::R *u_out,
                                                              typename PrecTraits<PREC>::R *m1,
                                                              typename PrecTraits<PREC>::R *m2,
                                                              typename PrecTraits<PREC>::R c1,
                                                              typename PrecTraits<PREC>::R c2) {
-    using R = typename PrecTraits<PREC>::R;
-    constexpr int P = model_n_par(KIND);
     __shared__ double red[kFitBlock];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *ytile = reinterpret_cast<float *>(smem_raw);  // [1 or 2][kFitBlock][row_stride]
     if (*fa.stop) return;  // the same for every thread
     model_smem_load<KIND>(mc);
-    __syncthreads();
     const int M = mc.n_meas;
     const int64_t n = fa.n;
-    const int64_t sx = 1, sy = fa.nx, sz = static_cast<int64_t>(fa.nx) * fa.ny;
+    const int64_t n_tiles = (n + kFitBlock - 1) / kFitBlock;
+    const int tile_floats = kFitBlock * fa.row_stride;
+    auto stage = [&](int64_t tile, float *dst) {
+        const int64_t base = tile * kFitBlock;
+        const int total = static_cast<int>(min(static_cast<int64_t>(kFitBlock), n - base)) * M;
+        const float *src = fa.data + base * M;
+        for (int e = threadIdx.x; e < total; e += kFitBlock) {
+            const int row = e / M;
+            cp_async4(dst + row * fa.row_stride + (e - row * M), src + e);
+        }
+    };
     double my_loss = 0.0;
-    for (int64_t v = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; v < n;
-         v += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        if (fa.mask && !fa.mask[v]) {
-#pragma unroll
-            for (int p = 0; p < P; ++p) u_out[p * n + v] = u_in[p * n + v];
-            continue;
+    int64_t tile = blockIdx.x;
+    if (fa.double_buffer && tile < n_tiles) stage(tile, ytile);
+    cp_async_commit();
+    for (int buf = 0; tile < n_tiles; tile += gridDim.x, buf ^= 1) {
+        const float *cur = ytile;
+        if (fa.double_buffer) {
+            // the other buffer was last read before the barrier that ended the previous tile
+            if (tile + gridDim.x < n_tiles) stage(tile + gridDim.x, ytile + (buf ^ 1) * tile_floats);
+            cp_async_commit();
+            cp_async_wait<1>();
+            cur += buf * tile_floats;
+        } else {
+            stage(tile, ytile);
+            cp_async_commit();
+            cp_async_wait<0>();
         }
-        R u[P], th[P], g[P];
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            u[p] = u_in[p * n + v];
-            const R lo = sizeof(R) == 8 ? R(mc.lb_d[p]) : R(mc.lb_f[p]);
-            const R hi = sizeof(R) == 8 ? R(mc.ub_d[p]) : R(mc.ub_f[p]);
-            th[p] = lo + u[p] * (hi - lo);
-            g[p] = R(0);
-        }
-        // data term: rho(w (y - s)), drho/ds = -w sign(r) (L1) or -2 w r (L2)
-        const R w = fa.weight ? R(fa.weight[v]) : R(1);
-        const float *y = fa.data + v * M;
-        R loss = R(0);
-        jacobian<KIND, R>(th, mc, [&](int k, R s, const R *J) {
-            const R r = w * (R(__ldg(y + k)) - s);
-            const R d = fa.loss == GAC_FIT_L1 ? -w * sgn(r) : R(-2) * w * r;
-            loss += fa.loss == GAC_FIT_L1 ? fabs(r) : r * r;
-#pragma unroll
-            for (int p = 0; p < P; ++p) g[p] = fma(d, J[p], g[p]);
-        });
-        my_loss += static_cast<double>(loss) * static_cast<double>(fa.scale);
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const R range = sizeof(R) == 8 ? R(mc.ub_d[p] - mc.lb_d[p]) : R(mc.ub_f[p] - mc.lb_f[p]);
-            g[p] *= fa.scale * range;
-        }
-        // total variation: pairs (v - e_d, v) and (v, v + e_d) of masked neighbours
-        if (fa.tv_params && fa.lambda_n != R(0)) {
-            const int x = static_cast<int>(v % fa.nx), yy = static_cast<int>((v / fa.nx) % fa.ny);
-            const int z = static_cast<int>(v / sz);
-            const int coord[3] = {x, yy, z}, ext[3] = {fa.nx, fa.ny, fa.nz};
-            const int64_t step[3] = {sx, sy, sz};
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                if (!((fa.tv_params >> p) & 1u)) continue;
-                R tv = R(0), tv_loss = R(0);
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    if (d >= fa.tv_dims) break;
-                    if (coord[d] + 1 < ext[d] && (!fa.mask || fa.mask[v + step[d]])) {
-                        const R diff = u_in[p * n + v + step[d]] - u[p];
-                        tv -= sgn(diff);
-                        tv_loss += fabs(diff);
-                    }
-                    if (coord[d] > 0 && (!fa.mask || fa.mask[v - step[d]])) tv += sgn(u[p] - u_in[p * n + v - step[d]]);
-                }
-                g[p] = fma(fa.lambda_n, tv, g[p]);
-                my_loss += static_cast<double>(fa.lambda_n) * static_cast<double>(tv_loss);
-            }
-        }
-        // Adam (bias-corrected moments), then the box
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const R a = fa.beta1 * m1[p * n + v] + (R(1) - fa.beta1) * g[p];
-            const R b = fa.beta2 * m2[p * n + v] + (R(1) - fa.beta2) * g[p] * g[p];
-            m1[p * n + v] = a;
-            m2[p * n + v] = b;
-            const R stepu = fa.lr * (a / c1) / (sqrt(b / c2) + fa.eps);
-            u_out[p * n + v] = fmin(fmax(u[p] - stepu, R(0)), R(1));
-        }
+        __syncthreads();
+        const int64_t v = tile * kFitBlock + threadIdx.x;
+        if (v < n)
+            my_loss += fit_voxel<KIND, PREC>(mc, fa, v, cur + threadIdx.x * fa.row_stride, u_in, u_out, m1, m2, c1, c2);
+        __syncthreads();
     }
+    cp_async_wait<0>();
     // the block's share of the loss, summed in a fixed order
     red[threadIdx.x] = my_loss;
     __syncthreads();
@@ -270,25 +443,35 @@ __global__ void u_to_theta_kernel(const ModelConst mc, const R *u, const uint8_t
     }
 }
 
+template <int PREC>
+static const void *step_ptr(int kind) {
+    switch (kind) {
+    case GAC_MODEL_MONOEXP: return reinterpret_cast<const void *>(&fit_step_kernel<GAC_MODEL_MONOEXP, PREC>);
+    case GAC_MODEL_MWI3: return reinterpret_cast<const void *>(&fit_step_kernel<GAC_MODEL_MWI3, PREC>);
+    case GAC_MODEL_SMT: return reinterpret_cast<const void *>(&fit_step_kernel<GAC_MODEL_SMT, PREC>);
+    default: return reinterpret_cast<const void *>(&fit_step_kernel<GAC_MODEL_LINEAR_TEST, PREC>);
+    }
+}
+
 template <int KIND, int PREC>
-static cudaError_t launch_step(int grid, cudaStream_t s, const ModelConst &mc,
+static cudaError_t launch_step(int grid, size_t smem, cudaStream_t s, const ModelConst &mc,
                                const FitArgs<typename PrecTraits<PREC>::R> &fa, const void *u_in, void *u_out,
                                void *m1, void *m2, double c1, double c2) {
     using R = typename PrecTraits<PREC>::R;
-    fit_step_kernel<KIND, PREC><<<grid, kFitBlock, 0, s>>>(mc, fa, static_cast<const R *>(u_in), static_cast<R *>(u_out),
+    fit_step_kernel<KIND, PREC><<<grid, kFitBlock, smem, s>>>(mc, fa, static_cast<const R *>(u_in), static_cast<R *>(u_out),
                                                            static_cast<R *>(m1), static_cast<R *>(m2), R(c1), R(c2));
     return cudaGetLastError();
 }
 
 template <int PREC>
-static cudaError_t launch_step_kind(int kind, int grid, cudaStream_t s, const ModelConst &mc,
+static cudaError_t launch_step_kind(int kind, int grid, size_t smem, cudaStream_t s, const ModelConst &mc,
                                     const FitArgs<typename PrecTraits<PREC>::R> &fa, const void *u_in, void *u_out,
                                     void *m1, void *m2, double c1, double c2) {
     switch (kind) {
-    case GAC_MODEL_MONOEXP: return launch_step<GAC_MODEL_MONOEXP, PREC>(grid, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
-    case GAC_MODEL_MWI3: return launch_step<GAC_MODEL_MWI3, PREC>(grid, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
-    case GAC_MODEL_SMT: return launch_step<GAC_MODEL_SMT, PREC>(grid, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
-    default: return launch_step<GAC_MODEL_LINEAR_TEST, PREC>(grid, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
+    case GAC_MODEL_MONOEXP: return launch_step<GAC_MODEL_MONOEXP, PREC>(grid, smem, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
+    case GAC_MODEL_MWI3: return launch_step<GAC_MODEL_MWI3, PREC>(grid, smem, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
+    case GAC_MODEL_SMT: return launch_step<GAC_MODEL_SMT, PREC>(grid, smem, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
+    default: return launch_step<GAC_MODEL_LINEAR_TEST, PREC>(grid, smem, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
     }
 }
 
@@ -303,17 +486,32 @@ static gac_status fit_run_prec(const ModelConst &mc, const gac_fit_opts *o, cons
     DevBuf d_theta;
     gac_status st = d_theta.make(theta, static_cast<size_t>(N) * P * sizeof(double), true, s, "theta");
     if (st != GAC_OK) return st;
-    // work arrays: u (two buffers), Adam moments, block losses, history, flags
-    int sms = 0, dev = 0;
+    // staged data tiles: two when they fit beside a second block on the SM
+    int sms = 0, dev = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((N + kFitBlock - 1) / kFitBlock,
-                                                                           static_cast<int64_t>(sms) * 8)));
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int row_stride = mc.n_meas | 1;  // odd: the rows of a warp's voxels fall into distinct banks
+    const size_t tile_bytes = static_cast<size_t>(kFitBlock) * row_stride * sizeof(float);
+    const bool dbl = 4 * tile_bytes + 8 * 1024 <= static_cast<size_t>(smem_max);
+    const size_t smem = (dbl ? 2 : 1) * tile_bytes;
+    const void *fn = step_ptr<PREC>(mc.kind);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFitBlock, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "fit kernel attributes");
+    // persistent blocks, each given the same number of tiles (+-1)
+    const int64_t tiles = (N + kFitBlock - 1) / kFitBlock;
+    const int64_t slots = static_cast<int64_t>(sms) * std::max(per_sm, 1);
+    const int64_t per_block = (tiles + slots - 1) / slots;
+    const int grid = static_cast<int>((tiles + per_block - 1) / per_block);
+    // work arrays: u (two buffers), Adam moments, block losses, history, flags
     const int I = o->iterations;
     const size_t bytes_u = static_cast<size_t>(N) * P * RB;
     const size_t total = 4 * bytes_u + grid * sizeof(double) + static_cast<size_t>(std::max(I, 1)) * sizeof(double) + 2 * sizeof(int);
     void *base = nullptr;
-    cudaError_t e = cudaMallocAsync(&base, total, s);
+    e = cudaMallocAsync(&base, total, s);
     if (e != cudaSuccess) return cuda_fail(e, "fit work arrays");
     struct Free {
         void *p;
@@ -350,6 +548,8 @@ static gac_status fit_run_prec(const ModelConst &mc, const gac_fit_opts *o, cons
     fa.eps = static_cast<R>(o->epsilon);
     fa.stop = flags;
     fa.block_loss = block_loss;
+    fa.row_stride = row_stride;
+    fa.double_buffer = dbl;
     // iterations in chunks; the stop flag is read between chunks
     constexpr int kChunk = 64;
     int t = 1;
@@ -359,7 +559,7 @@ static gac_status fit_run_prec(const ModelConst &mc, const gac_fit_opts *o, cons
             const double c1 = 1.0 - std::pow(o->beta1, t), c2 = 1.0 - std::pow(o->beta2, t);
             const void *ui = (t & 1) ? u0 : u1;
             void *uo = (t & 1) ? u1 : u0;
-            if ((e = launch_step_kind<PREC>(mc.kind, grid, s, mc, fa, ui, uo, m1, m2, c1, c2)) != cudaSuccess)
+            if ((e = launch_step_kind<PREC>(mc.kind, grid, smem, s, mc, fa, ui, uo, m1, m2, c1, c2)) != cudaSuccess)
                 return cuda_fail(e, "fit step");
             fit_check_kernel<<<1, kFitBlock, 0, s>>>(block_loss, grid, t, o->tol, o->convergence_value,
                                                     o->convergence_window, hist, flags, flags + 1);

@@ -10,6 +10,9 @@ sign, so only near-zero gradient components may differ), and after 200
 updates the loss (to 1%) and the parameter maps (95% within 2% of the prior
 range) agree: the L1 subgradient and the TV signs flip where FP32 and FP64
 residuals straddle zero, after which the trajectories part by Adam steps.
+Volumes of 40k-120k voxels give every persistent block two or more tiles of
+256 voxels and end in a ragged tile; 64 echoes of the 3-pool model (128
+values a voxel) take the one-buffer staging path.
 """
 import numpy as np
 import pytest
@@ -29,11 +32,12 @@ MODELS = {
 SHAPE = (6, 5, 4)
 
 
-def _problem(orc, kind, seed=21, noise=0.02):
-    acq, lb, ub = MODELS[kind]
+def _problem(orc, kind, seed=21, noise=0.02, shape=SHAPE, acq=None):
+    acq0, lb, ub = MODELS[kind]
+    acq = acq0 if acq is None else acq
     lb, ub = np.array(lb), np.array(ub)
     rng = np.random.default_rng(seed + kind)
-    N = int(np.prod(SHAPE))
+    N = int(np.prod(shape))
     truth = rng.uniform(lb + 0.2 * (ub - lb), ub - 0.2 * (ub - lb), (N, len(lb)))
     y = orc.forward(kind, acq, truth)
     y = (y + noise * rng.standard_normal(y.shape)).astype(np.float32)
@@ -98,3 +102,31 @@ def test_fp32_first_step_and_trajectory(gac, orc, kind):
     print(f"FP32 kind {kind}: loss {r_hist[-1]:.5e} vs {g_hist[-1]:.5e}; |dtheta|/range p95 {np.quantile(d, 0.95):.2e}")
     assert abs(g_hist[-1] - r_hist[-1]) <= 1e-2 * r_hist[-1]
     assert np.quantile(d, 0.95) <= 2e-2
+
+
+TE64 = np.array([2.0 + 1.0 * k for k in range(64)])
+BIG = [(MONOEXP, None, (60, 50, 40), 64), (MWI3, None, (50, 40, 21), 64), (MWI3, TE64, (50, 40, 21), 64),
+       (SMT, None, (50, 40, 40), 64), (MWI3, None, (50, 40, 41), 32), (MWI3, TE64, (50, 40, 21), 32)]
+
+
+@pytest.mark.parametrize("kind,acq,shape,prec", BIG,
+                         ids=[f"{k}-{'te64' if a is not None else 'std'}-{'x'.join(map(str, sh))}-fp{p}"
+                              for k, a, sh, p in BIG])
+def test_large_volume_many_tiles_per_block(gac, orc, kind, acq, shape, prec):
+    acq, lb, ub, y, theta0, mask, weight = _problem(orc, kind, shape=shape, acq=acq)
+    mid = gac.gac_model_register(kind, acq, lb, ub, np.zeros(len(lb)))
+    it = 3 if prec == 64 else 1
+    kw = dict(iterations=it, lr=0.01, loss=2, lam=0.02, tv_params=0b1, tv_dims=3)
+    r, r_hist, _ = orc.fit_run(kind, acq, lb, ub, y, theta0, shape=shape, mask=mask, weight=weight, **kw)
+    g, g_hist, g_done = gac.fit_host(mid, y, theta0, shape=shape, mask=mask, weight=weight, iterations=it,
+                                     learning_rate=0.01, loss=2, tv_lambda=0.02, tv_params=0b1, tv_dims=3,
+                                     precision=gac.PREC_FP64 if prec == 64 else gac.PREC_FP32)
+    assert g_done == it
+    np.testing.assert_array_equal(g[mask == 0], theta0[mask == 0])
+    d = np.abs(g - r) / (ub - lb)
+    if prec == 64:
+        np.testing.assert_allclose(g_hist, r_hist, rtol=1e-9)
+        assert (d <= 1e-9).mean() >= 0.999 and d.max() <= 1e-3
+    else:
+        np.testing.assert_allclose(g_hist, r_hist, rtol=1e-5)
+        assert (d <= 1e-5).mean() >= 0.995, np.quantile(d, 0.99)
