@@ -36,28 +36,53 @@ UNIT = "chain-iter/s"
 
 # Algorithmic operation counts per chain-iteration of the direct form of each
 # model (every echo evaluated with its own exp / sin / cos), counted from the
-# oracle's expression tree: MUFU = exp, log, sin, cos, sqrt, reciprocal;
-# FP32 = add/mul/fma/min/max; INT = Philox (10 rounds x (2 wide multiplies,
-# 2 three-input xors, 2 key adds) per call).
+# oracle's expression tree.  MUFU operations by the special-function op that
+# serves them: ex2 (exp; erf counted as one exp-class op), sin (sin and cos),
+# lg2 (log), sqrt, rcp.  FP32 = add/mul/fma/min/max; INT = Philox (10 rounds x
+# (2 wide multiplies, 2 three-input xors, 2 key adds) per call).
+#   3-pool: 24 echoes x 3 pools x (exp, sin, cos) + 3 rcp (1/T2*) + Box-Muller
+#     5 pairs x (log, sqrt, sin, cos) + the acceptance log = 240
+#   SMT: 6 b-values x (exp + 2 g, g = sqrt, erf, rcp) + 2 pairs + log = 51
+#   mono-exp: 12 exp + 1 pair + log = 17
+#   AxCaliberSMT: 2 timings x 18 cylinder-series terms x 3 exp + 16
+#     measurements x (2 exp + 2 g) + 2 pairs + log = 245
 OPS = {
-    "mwi3_1m": dict(mufu=240, fp32=520, int=180),
-    "smt_1p5m": dict(mufu=51, fp32=103, int=120),
-    "monoexp_4k": dict(mufu=17, fp32=65, int=60),
-    # 2 timings x 18 cylinder-series terms x (3 exp + 12 FP32) + 16 b-values x
-    # (2 exp + 2 g at 4 MUFU + 8 FP32 each + 10 FP32)
-    "axcal_250k": dict(mufu=275, fp32=888, int=120),
+    "mwi3_1m": dict(mufu=dict(ex2=72, sin=154, lg2=6, sqrt=5, rcp=3), fp32=520, int=180),
+    "smt_1p5m": dict(mufu=dict(ex2=18, sin=4, lg2=3, sqrt=14, rcp=12), fp32=103, int=120),
+    "monoexp_4k": dict(mufu=dict(ex2=12, sin=2, lg2=2, sqrt=1), fp32=65, int=60),
+    "axcal_250k": dict(mufu=dict(ex2=172, sin=4, lg2=3, sqrt=34, rcp=32), fp32=888, int=120),
 }
 # Ensemble walker-move counts: the same model evaluation, one Philox call, no
-# Box-Muller; the stretch z costs a log (MUFU) and a few FP32 ops.
+# Box-Muller; the acceptance log and the stretch z's log, a few FP32 ops.
 OPS_ENSEMBLE = {
-    "mwi3_1m": dict(mufu=221, fp32=490, int=60),
-    "smt_1p5m": dict(mufu=44, fp32=92, int=60),
-    "monoexp_4k": dict(mufu=14, fp32=64, int=60),
-    "axcal_250k": dict(mufu=269, fp32=874, int=60),
+    "mwi3_1m": dict(mufu=dict(ex2=72, sin=144, lg2=2, rcp=3), fp32=490, int=60),
+    "smt_1p5m": dict(mufu=dict(ex2=18, lg2=2, sqrt=12, rcp=12), fp32=92, int=60),
+    "monoexp_4k": dict(mufu=dict(ex2=12, lg2=2), fp32=64, int=60),
+    "axcal_250k": dict(mufu=dict(ex2=172, lg2=2, sqrt=32, rcp=32), fp32=874, int=60),
 }
+# Data-sheet rates per SM clock, used only when the pipe-rate probe cannot run.
 MUFU_PER_CLK_SM = 16
 FP32_PER_CLK_SM = 128
 ISSUE_PER_CLK_SM = 4  # warp-instructions
+
+
+def _pipe_rates(gac, stream):
+    """Results per SM clock of each arithmetic pipe operation, measured by the
+    library's probe kernels (None if the probe fails)."""
+    try:
+        return {op: gac.gac_pipe_rate(op, stream) for op in gac.PIPE_OPS}
+    except Exception:  # noqa: BLE001 - the roofline then falls back to the data sheet
+        return None
+
+
+def _alu_peaks(mix: dict, rates):
+    """(MUFU results per SM clock for this operation mix, FP32 per SM clock,
+    basis): the mix's time is sum_op n_op / rate_op."""
+    if not rates:
+        return MUFU_PER_CLK_SM, FP32_PER_CLK_SM, "data sheet"
+    n = sum(mix.values())
+    mufu = n / sum(k / rates[op] for op, k in mix.items())
+    return mufu, rates["ffma"], "measured by the pipe-rate probe"
 
 # From the ncu captures summarised under profiles/: DRAM bytes of one full
 # launch of the sampler kernel (read + write) and executed warp instructions
@@ -289,7 +314,9 @@ def run_fit(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     f_max = (_peaks().get("sm_max_mhz") or 2070.0) * 1e6
     vi_s = vi / (t_total / args.steps)
-    peak = sms * FP32_PER_CLK_SM * f_max / 1e9
+    rates = _pipe_rates(gac, stream)
+    fp32_clk = rates["ffma"] if rates else FP32_PER_CLK_SM
+    peak = sms * fp32_clk * f_max / 1e9
     achieved = FIT_OPS["fp32"] * vi_s / 1e9
     line = {"metric": FIT_METRIC, "value": value, "unit": FIT_UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3, "higher_is_better": True,
@@ -298,7 +325,11 @@ def run_fit(args):
                        "tv": "3D, A_MW, lambda 1e-3", "mask": "inner 98^3", "iterations_per_step": it,
                        "updates_done": done},
             "roofline": {"bound": "alu", "pipe": "fp32", "count": "direct-form", "achieved": achieved,
-                         "peak": peak, "unit": "Gop/s", "frac": achieved / peak, "traffic": None},
+                         "peak": peak, "unit": "Gop/s", "frac": achieved / peak, "traffic": None,
+                         "peak_basis": f"{sms} SMs x {fp32_clk:.2f}/clk ("
+                                       f"{'measured by the pipe-rate probe' if rates else 'data sheet'}) x "
+                                       f"{f_max / 1e6:.0f} MHz (max SM clock)"},
+            "pipe_rates_per_sm_clk": rates,
             "e2e": {"value": vi / e2e_s, "unit": FIT_UNIT, "h2d_bytes_per_step": y.numel() * 4 + N * (1 + 4 + 8 * P),
                     "d2h_bytes_per_step": N * 8 * P + it * 8},
             "clocks": clocks, "gpu_launches": args.steps * (2 * it + 2), "wall_s": t_wall}
@@ -393,6 +424,7 @@ def run_ours(args, w):
             pg.barrier()
         torch.cuda.synchronize()
 
+    rates = _pipe_rates(gac, stream)  # the roofline's denominators, before any timing
     for _ in range(args.warmup):
         step()
     barrier()
@@ -450,18 +482,22 @@ def run_ours(args, w):
     base_name = w.name.replace("_ensemble", "")
     ops = (OPS_ENSEMBLE if args.sampler == "ensemble" else OPS)[base_name]
     ci_s = ci_per_step / kernel_s
-    t_mufu = ops["mufu"] / (sms * MUFU_PER_CLK_SM * f_max)
-    t_alu = (ops["fp32"] + ops["int"]) / (sms * FP32_PER_CLK_SM * f_max)
+    n_mufu = sum(ops["mufu"].values())
+    mufu_clk, fp32_clk, rate_basis = _alu_peaks(ops["mufu"], rates)
+    t_mufu = n_mufu / (sms * mufu_clk * f_max)
+    t_alu = (ops["fp32"] + ops["int"]) / (sms * fp32_clk * f_max)
     if t_mufu >= t_alu:
-        pipe, achieved, peak = "mufu", ops["mufu"] * ci_s / 1e9, sms * MUFU_PER_CLK_SM * f_max / 1e9
+        pipe, achieved, peak = "mufu", n_mufu * ci_s / 1e9, sms * mufu_clk * f_max / 1e9
+        per_clk = mufu_clk
     else:
         pipe, achieved = "fp32+int", (ops["fp32"] + ops["int"]) * ci_s / 1e9
-        peak = sms * FP32_PER_CLK_SM * f_max / 1e9
+        peak = sms * fp32_clk * f_max / 1e9
+        per_clk = fp32_clk
     f_med = (clocks.get("sm_mhz") or 0) * 1e6
     meas = _measured(base_name, args.sampler) if (world == 1 and args.precision == "mixed") else {}
     roof = {"bound": "alu", "pipe": pipe, "count": "direct-form", "achieved": achieved,
             "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
-            "peak_basis": f"{sms} SMs x {MUFU_PER_CLK_SM if pipe == 'mufu' else FP32_PER_CLK_SM}/clk x {f_max / 1e6:.0f} MHz (max SM clock)",
+            "peak_basis": f"{sms} SMs x {per_clk:.2f}/clk ({rate_basis}) x {f_max / 1e6:.0f} MHz (max SM clock)",
             "frac_at_sampled_clock": (achieved / peak * f_max / f_med) if f_med else None,
             "traffic": meas.get("traffic_bytes") if N == W.WORKLOADS[base_name].n_vox else None,
             "kernel_ms": kernel_s * 1e3}
@@ -480,7 +516,7 @@ def run_ours(args, w):
                        "burnin": w.burnin, "thin": w.thin, "samples_stored": True,
                        "precision": args.precision, "parallelism": f"voxel-shard x{world}",
                        "l2": f"inputs {y.numel() * 4 / 1e6:.0f} MB + samples {S * C * P * N * 4 / 1e9:.1f} GB written per step > 129 MB L2"},
-            "roofline": roof, "clocks": clocks, "gpu_launches": args.steps,
+            "roofline": roof, "pipe_rates_per_sm_clk": rates, "clocks": clocks, "gpu_launches": args.steps,
             "wall_s": t_wall}
     if e2e:
         line["e2e"] = e2e

@@ -212,6 +212,29 @@ gac_status gac_normals(uint64_t seed, const uint32_t *t, const uint32_t *v, cons
                        int64_t n, int n_par, int precision, double *z, uint32_t *w_acc,
                        void *stream);
 
+/* Pipe-rate probe (not part of the method: the denominators of the
+ * sampler's arithmetic roofline, measured on the device).  Runs one kernel of
+ * 4 blocks of 256 threads per SM, each thread 8 independent chains of 4096
+ * dependent steps of operation `op`, after one warm-up launch, and writes the
+ * median over SMs of results per SM clock (clock64 around each block's loop;
+ * an SM's span runs from its first block's start to its last block's end).
+ * FFMA2 counts two results per step.  Synchronises `stream`.  Errors:
+ * GAC_ERR_INVALID_ARG for an unknown op or a NULL output, GAC_ERR_CUDA. */
+typedef enum {
+    GAC_PIPE_FFMA = 0,    /* fma.rn.f32 */
+    GAC_PIPE_FFMA2 = 1,   /* paired FP32 fma (two results) */
+    GAC_PIPE_EX2 = 2,     /* ex2.approx.ftz.f32 */
+    GAC_PIPE_SIN = 3,     /* sin.approx.ftz.f32 (cos runs on the same unit) */
+    GAC_PIPE_LG2 = 4,     /* lg2.approx.ftz.f32 */
+    GAC_PIPE_RSQRT = 5,   /* rsqrt.approx.ftz.f32 */
+    GAC_PIPE_RCP = 6,     /* rcp.approx.ftz.f32 */
+    GAC_PIPE_SQRT = 7,    /* sqrt.approx.ftz.f32 */
+    GAC_PIPE_DFMA = 8,    /* fma.rn.f64 */
+    GAC_PIPE_IMAD_HI = 9, /* mad.hi.u32 (Philox's high products) */
+    GAC_PIPE_LOP3 = 10    /* lop3.b32 (three-input xor) */
+} gac_pipe_op;
+gac_status gac_pipe_rate(int op, double *per_clk_sm, void *stream);
+
 /* Affine-invariant ensemble sampler (the paper's second mcmc.m algorithm,
  * Sec. 2.2.2: Nwalkers walkers and one stepSize for all parameters; Table 1:
  * 50 walkers x 2000 iterations).  Goodman & Weare's stretch move with the

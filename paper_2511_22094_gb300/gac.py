@@ -85,7 +85,8 @@ EXPORTS = ["gac_model_register", "gac_model_info", "gac_result_sizes", "gac_mcmc
            "gac_forward", "gac_loglik", "gac_philox_words", "gac_normals", "gac_last_error",
            "gac_version", "gac_server_create", "gac_server_job_bytes", "gac_server_submit",
            "gac_server_poll", "gac_server_wait", "gac_server_cancel", "gac_server_get_stats",
-           "gac_server_destroy", "gac_mcmc_run_noalloc", "gac_ensemble_run", "gac_fit_run"]
+           "gac_server_destroy", "gac_mcmc_run_noalloc", "gac_ensemble_run", "gac_fit_run",
+           "gac_pipe_rate"]
 NOALLOC_STATE_BYTES = 64 << 20
 
 
@@ -111,6 +112,7 @@ def _load():
         "gac_mcmc_run_noalloc": [ct.c_int, vp, i64, vp, ct.c_float, vp, ct.POINTER(McmcOpts), ct.c_int,
                                  ct.POINTER(Result), vp],
         "gac_fit_run": [ct.c_int, vp, vp, vp, ct.POINTER(FitOpts), vp, vp, ct.POINTER(ct.c_int), vp],
+        "gac_pipe_rate": [ct.c_int, ct.POINTER(ct.c_double), vp],
         "gac_server_create": [ct.c_size_t, ct.c_int, ct.POINTER(vp)],
         "gac_server_job_bytes": [ct.c_int, i64, ct.POINTER(McmcOpts), ct.c_int, ct.c_int,
                                  ct.POINTER(ct.c_size_t)],
@@ -276,6 +278,18 @@ def gac_philox_words(seed: int, t, v, c, n: int, n_words: int, out, stream=None)
 def gac_normals(seed: int, t, v, c, n: int, n_par: int, precision: int, z, w_acc, stream=None):
     _check(_lib.gac_normals(seed, _ptr(t), _ptr(v), _ptr(c), n, n_par, precision, _ptr(z),
                             _ptr(w_acc), _stream(stream)), "gac_normals")
+
+
+PIPE_OPS = {"ffma": 0, "ffma2": 1, "ex2": 2, "sin": 3, "lg2": 4, "rsqrt": 5, "rcp": 6, "sqrt": 7,
+            "dfma": 8, "imad_hi": 9, "lop3": 10}
+
+
+def gac_pipe_rate(op, stream=None) -> float:
+    """Results per SM clock of one arithmetic pipe operation (name or code)."""
+    code = PIPE_OPS[op] if isinstance(op, str) else int(op)
+    r = ct.c_double()
+    _check(_lib.gac_pipe_rate(code, ct.byref(r), _stream(stream)), "gac_pipe_rate")
+    return r.value
 
 
 # ------------------------------------------------------------- serving -----

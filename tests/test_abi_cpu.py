@@ -194,3 +194,12 @@ def test_fit_argument_validation(gac):
     assert done == 0 and (th2 == th).all()
     th3, hist, done = gac.fit_host(mid, y, th, shape=(2, 2, 2), mask=np.zeros(8, np.uint8))
     assert done == 0 and (th3 == th).all()
+
+
+def test_pipe_probe_rejects_bad_arguments(gac):
+    for op in (-1, 11, 99):
+        with pytest.raises(gac.GacError) as e:
+            gac.gac_pipe_rate(op)
+        assert e.value.status == 1
+    assert gac._lib.gac_pipe_rate(0, None, None) == 1
+    assert set(gac.PIPE_OPS.values()) == set(range(11))

@@ -1,0 +1,43 @@
+"""Host logic of the benchmark's arithmetic roofline: the direct-form MUFU
+counts per chain-iteration add up to the totals derived from the models'
+expression trees, and the mix's MUFU rate is the harmonic combination of the
+per-operation rates the pipe-rate probe measures."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    return m
+
+
+def test_direct_form_totals(bench):
+    # 3-pool: 24 echoes x 3 pools x (exp, sin, cos) + 3 rcp + 5 Box-Muller pairs x 4 + 1
+    assert sum(bench.OPS["mwi3_1m"]["mufu"].values()) == 24 * 3 * 3 + 3 + 5 * 4 + 1 == 240
+    # SMT: 6 b x (exp + 2 g x (sqrt, erf, rcp)) + 2 pairs x 4 + 1
+    assert sum(bench.OPS["smt_1p5m"]["mufu"].values()) == 6 * 7 + 2 * 4 + 1 == 51
+    assert sum(bench.OPS["monoexp_4k"]["mufu"].values()) == 12 + 4 + 1 == 17
+    # AxCaliberSMT: 2 timings x 18 terms x 3 exp + 16 x (2 exp + 2 g) + 2 pairs + 1
+    assert sum(bench.OPS["axcal_250k"]["mufu"].values()) == 2 * 18 * 3 + 16 * (2 + 6) + 2 * 4 + 1 == 245
+    # ensemble: no Box-Muller, one acceptance log and one stretch log
+    for k, w in (("mwi3_1m", 240 - 20 - 1), ("smt_1p5m", 51 - 8 - 1), ("monoexp_4k", 17 - 4 - 1),
+                 ("axcal_250k", 245 - 8 - 1)):
+        assert sum(bench.OPS_ENSEMBLE[k]["mufu"].values()) == w + 2
+
+
+def test_mix_rate_is_harmonic(bench):
+    flat = dict.fromkeys(("ex2", "sin", "lg2", "sqrt", "rcp", "rsqrt"), 16.0)
+    flat["ffma"] = 128.0
+    mufu, fp32, basis = bench._alu_peaks({"ex2": 10, "sin": 30}, flat)
+    assert mufu == pytest.approx(16.0) and fp32 == 128.0 and "measured" in basis
+    fast = dict(flat, ex2=32.0)
+    mufu, _, _ = bench._alu_peaks({"ex2": 10, "sin": 30}, fast)
+    assert mufu == pytest.approx(40.0 / (10 / 32.0 + 30 / 16.0))
+    assert bench._alu_peaks({"ex2": 1}, None)[:2] == (bench.MUFU_PER_CLK_SM, bench.FP32_PER_CLK_SM)
