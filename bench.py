@@ -222,6 +222,56 @@ def cpu_oracle_rate(w, target_s=15.0, sampler="mh", stretch=2.0):
     return ci / dt, r["threads"], f"first {n} of {w.n_vox} voxels, all {w.n_chains} chains x {w.iterations} iterations ({dt:.1f} s)"
 
 
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def run_oracle_study(args):
+    """The oracle's timing protocol: for every workload, chain-iterations/s of
+    the FP64 oracle on all host cores and on one core (the paper's CPU
+    baseline is one core), each the median of `repeats` runs on a bounded
+    voxel sample (about `target` seconds a run), with the host described."""
+    import platform
+
+    import oracle
+    oracle.build()
+    repeats, target = 5, 2.0
+    host = {"nproc": os.cpu_count(), "omp_threads": oracle.max_threads(), "cpu": _cpu_model(),
+            "machine": platform.machine()}
+    res = {}
+    for name in ("monoexp_4k", "mwi3_1m", "smt_1p5m", "axcal_250k"):
+        w = W.WORKLOADS[name]
+        for label, nt in (("all_cores", 0), ("one_core", 1)):
+            def run(n):
+                y, sig = _host_inputs_for_oracle(w, n)
+                t0 = time.perf_counter()
+                r = oracle.mcmc_run(w.kind, w.acq, w.lb, w.ub, w.step, y, sig, n_chains=w.n_chains,
+                                    iterations=w.iterations, burnin=w.burnin, thin=w.thin, seed=w.mcmc_seed,
+                                    n_threads=nt)
+                return time.perf_counter() - t0, r["threads"]
+            dt, threads = run(threads_pilot := max(1, oracle.max_threads() if nt == 0 else 1))
+            per_vox = dt / threads_pilot
+            n = int(min(w.n_vox, max(threads, target / max(per_vox, 1e-9))))
+            n = max(threads, (n // threads) * threads)
+            rates = []
+            for _ in range(repeats):
+                dt, _ = run(n)
+                rates.append(n * w.n_chains * w.iterations / dt)
+            res.setdefault(name, {})[label] = {"value": float(np.median(rates)), "unit": UNIT, "threads": threads,
+                                               "sample": f"first {n} voxels, all {w.n_chains} chains x "
+                                                         f"{w.iterations} iterations; median of {repeats}",
+                                               "min": float(min(rates)), "max": float(max(rates))}
+    print(json.dumps({"metric": "oracle " + METRIC, "unit": UNIT, "host": host, "workloads": res}), flush=True)
+
+
 FIT_METRIC = "whole-volume fit voxel-iterations/s"
 FIT_UNIT = "voxel-iter/s"
 # Direct-form counts per voxel-iteration of the 3-pool fit (24 echoes x 3
@@ -659,7 +709,12 @@ def main():
     ap.add_argument("--serving-saturated", action="store_true")
     ap.add_argument("--fit", action="store_true", help="whole-volume Adam fit instead of MCMC")
     ap.add_argument("--fit-iterations", type=int, default=100)
+    ap.add_argument("--oracle-study", action="store_true",
+                    help="time the CPU oracle on all cores and on one core for every workload")
     args = ap.parse_args()
+    if args.oracle_study:
+        run_oracle_study(args)
+        return
     if args.serving:
         run_serving(args)
         return
