@@ -23,7 +23,7 @@ static cudaError_t ens_go(int grid, size_t smem, cudaStream_t s, const ModelCons
         *fn = ens_ptr<KIND, PREC, TRACE>();
         return cudaSuccess;
     }
-    ens_kernel<KIND, PREC, TRACE><<<grid, kBlock, smem, s>>>(mc, ra, ea);
+    ens_kernel<KIND, PREC, TRACE><<<grid, kEnsBlock, smem, s>>>(mc, ra, ea);
     return cudaGetLastError();
 }
 
@@ -118,7 +118,7 @@ extern "C" gac_status gac_ensemble_run(int model_id, const void *data, int64_t n
     ra.voxel_base = o->voxel_base;
     ra.moments_mode = o->moments_mode;
     ra.trace_n = o->trace_n_vox;
-    ra.vox_per_block = kBlock / H;
+    ra.vox_per_block = kEnsBlock / H;
     ra.row_stride = row_stride_for(mc.kind, M);
     ra.n_tiles = (n_vox + ra.vox_per_block - 1) / ra.vox_per_block;
     EnsArgs ea;
@@ -139,7 +139,7 @@ extern "C" gac_status gac_ensemble_run(int model_id, const void *data, int64_t n
     e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return cuda_fail(e, "ensemble kernel carveout");
     int per_sm = 0, sms = 0, dev = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, smem)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kEnsBlock, smem)) != cudaSuccess)
         return cuda_fail(e, "occupancy");
     if (per_sm < 1) return fail(GAC_ERR_INVALID_ARG, "ensemble tile does not fit on an SM (%zu bytes)", smem);
     cudaGetDevice(&dev);
