@@ -219,18 +219,24 @@ static double cheb8_fit(F &&f, float af[8]) {
     return worst;
 }
 
-// Fills mc->gtab with, for each centre c = c_lo .. 16, the monomial
+// Fills mc->gtab with, for each centre c = c_lo .. c_hi, the monomial
 // coefficients in d of the degree-7 polynomial that interpolates g(c + d) at
 // the eight Chebyshev points of [-1/2, 1/2], and checks every interval on 65
 // points against the quadrature (relative error of the float coefficients
 // evaluated in double at most 2e-7; the interpolation error itself is below
-// 1e-9 for unit intervals).
-static gac_status build_g_table(int c_lo, ModelConst *mc) {
+// 1e-9 for unit intervals).  c_hi = the centre nearest xmax (the largest
+// argument the model's bounds allow) when that fits in kGTabMax intervals:
+// then the kernels need no asymptote.  Otherwise the table ends at c_hi >= 16
+// and x >= c_hi + 1/2 takes sqrt(pi)/2 x^-1/2.
+static gac_status build_g_table(int c_lo, double xmax, ModelConst *mc) {
     static const GaussLegendre01 gl;
-    const int n_int = static_cast<int>(kGTail) - c_lo + 1;
-    if (c_lo < static_cast<int>(kSmtArgMin) - 1 || n_int > kGTabMax)
+    if (c_lo < static_cast<int>(kSmtArgMin) - 1)
         return fail(GAC_ERR_INVALID_ARG, "SMT argument range starts at %d, below %d", c_lo,
                     static_cast<int>(kSmtArgMin));
+    const double c_need = std::max(std::ceil(xmax - 0.5), static_cast<double>(kGTail));
+    const int n_int = static_cast<int>(std::min<double>(kGTabMax, c_need - c_lo + 1));
+    const int c_hi = c_lo + n_int - 1;
+    if (c_hi < static_cast<int>(kGTail)) return fail(GAC_ERR_INVALID_ARG, "g(x) table too short");
     for (int i = 0; i < n_int; ++i) {
         const double c = c_lo + i;
         float af[8];
@@ -240,6 +246,8 @@ static gac_status build_g_table(int c_lo, ModelConst *mc) {
     }
     mc->gtab_lo = c_lo;
     mc->gtab_n = n_int;
+    mc->gtab_tail = c_hi + 0.5 >= xmax ? 0 : 1;
+    mc->gtab_tail_x = static_cast<float>(c_hi + 0.5);
     return GAC_OK;
 }
 
@@ -298,6 +306,25 @@ static gac_status build_axcal(const gac_model_desc *d, ModelConst *mc) {
         ax.g2_f[k] = static_cast<float>(g2);
         ax.csf_f[k] = static_cast<float>(ax.csf_d[k]);
     }
+    // the FP32 path's measurements in timing order (stable), with their constants
+    constexpr double kLog2e = 1.44269504088896340736;
+    int pos = 0;
+    for (int t = 0; t < ax.n_timing; ++t) {
+        ax.first[t] = pos;
+        for (int k = 0; k < K; ++k) {
+            if (ax.t[k] != t) continue;
+            float *m = ax.meas + 8 * pos++;
+            m[0] = static_cast<float>(ax.b_d[k] * kAxDaD);
+            m[1] = static_cast<float>(ax.g2_d[k]);
+            m[2] = static_cast<float>(ax.g2_d[k] * kLog2e);
+            m[3] = static_cast<float>(ax.b_d[k] * kLog2e);
+            m[4] = static_cast<float>(ax.b_d[k]);
+            m[5] = ax.csf_f[k];
+            std::memcpy(&m[6], &k, sizeof k);
+            m[7] = 0.0f;
+        }
+    }
+    for (int t = ax.n_timing; t <= kAxMaxTiming; ++t) ax.first[t] = pos;
     double x2d[kAxMaxTerms], c[kAxMaxTerms];
     for (int m = 0; m < kAxMaxTerms; ++m) {
         const double x = j1p_zero(m + 1), x2 = x * x;
@@ -544,19 +571,26 @@ gac_status gac_model_register(const gac_model_desc *d, int *model_id) {
         }
     }
     if (d->kind == GAC_MODEL_SMT) {
-        double xmin = 0.0;  // the smallest argument b Da or b (De_par - De_perp) the bounds allow
-        for (int k = 0; k < d->n_acq; ++k)
+        // the smallest and largest arguments b Da, b (De_par - De_perp) the bounds allow
+        double xmin = 0.0, xmax = 0.0;
+        for (int k = 0; k < d->n_acq; ++k) {
             xmin = std::min({xmin, d->acq[k] * d->lb[1], d->acq[k] * (d->lb[2] - d->ub[3])});
-        const gac_status st = build_g_table(static_cast<int>(std::floor(xmin)), &mc);
+            xmax = std::max({xmax, d->acq[k] * d->ub[1], d->acq[k] * (d->ub[2] - d->lb[3])});
+        }
+        const gac_status st = build_g_table(static_cast<int>(std::floor(xmin)), xmax, &mc);
         if (st != GAC_OK) return st;
     }
     if (d->kind == GAC_MODEL_AXCAL_SMT) {
         gac_status st = build_axcal(d, &mc);
         if (st != GAC_OK) return st;
-        // g arguments: b Da - kappa >= 0 (up to rounding) and b (1.7 - De_R)
-        double xmin = -1.0;
-        for (int k = 0; k < mc.n_meas; ++k) xmin = std::min(xmin, d->acq[3 * k] * (kAxDeParD - d->ub[3]));
-        if ((st = build_g_table(static_cast<int>(std::floor(xmin)), &mc)) != GAC_OK) return st;
+        // g arguments: 0 <= b Da - kappa <= b Da (up to rounding) and b (1.7 - De_R)
+        double xmin = -1.0, xmax = 0.0;
+        for (int k = 0; k < mc.n_meas; ++k) {
+            const double b = d->acq[3 * k];
+            xmin = std::min(xmin, b * (kAxDeParD - d->ub[3]));
+            xmax = std::max({xmax, b * kAxDaD, b * (kAxDeParD - d->lb[3])});
+        }
+        if ((st = build_g_table(static_cast<int>(std::floor(xmin)), xmax, &mc)) != GAC_OK) return st;
     }
     std::lock_guard<std::mutex> lk(g_reg_mu);
     for (size_t i = 0; i < g_models.size(); ++i)  // ModelConst is zero-filled before it is set

@@ -29,8 +29,8 @@ namespace gac {
 constexpr int kAnchor = 6;
 constexpr float kSinCosMaxArg = 6000.0f;  // |x| bound of sincos_cw (registration checks it)
 constexpr float kSmtArgMin = -12.0f;  // registration keeps b (De_par - De_perp), b Da >= -12
-constexpr int kGTabMax = 32;          // unit intervals of the g(x) table, centres c_lo .. 16
-constexpr float kGTail = 16.0f;       // x >= 16: g(x) = sqrt(pi)/2 x^-1/2 (erfc(4) = 1.5e-8)
+constexpr int kGTabMax = 64;          // unit intervals of the g(x) table, centres c_lo .. c_hi
+constexpr float kGTail = 16.0f;       // x >= 16: g(x) = sqrt(pi)/2 x^-1/2 within erfc(4) = 1.5e-8
 
 // AxCaliberSMT (Sec. 2.5, after Fan et al. 2020): measurements are
 // (b, Delta, delta) triplets; the cylinder series runs over the zeros of J1'.
@@ -62,6 +62,11 @@ struct AxConst {
     int tab_n;
     float tab_off, tab_inv_w;  // t = log2 R * tab_inv_w + tab_off; interval rint(t), d = t - rint(t)
     alignas(16) float tab[kAxMaxTiming * 2 * kAxTabMax * 4];
+    // FP32 path, measurements in timing order: timing j owns positions
+    // first[j] .. first[j+1]-1; position i holds (b Da, g2, g2 log2 e,
+    // b log2 e) and (b, e^{-b D_csf}, the measurement's index as int bits, 0).
+    int first[kAxMaxTiming + 1];
+    alignas(16) float meas[kAxMaxMeas * 2 * 4];
 };
 
 struct ModelConst {
@@ -76,12 +81,17 @@ struct ModelConst {
     float lb_f[GAC_MAX_PAR], ub_f[GAC_MAX_PAR], step_f[GAC_MAX_PAR];
     double lb_d[GAC_MAX_PAR], ub_d[GAC_MAX_PAR], step_d[GAC_MAX_PAR];
     // g(x) = int_0^1 exp(-x u^2) du on unit intervals centred at the integers
-    // c = gtab_lo .. 16: g(c + d) = sum_{n<=7} a_n d^n for |d| <= 1/2 (the
-    // Chebyshev interpolant of degree 7).  Layout [2][kGTabMax][4]: a_0..a_3
-    // of every interval, then a_4..a_7, so one interval is two 16-byte loads.
+    // c = gtab_lo .. gtab_lo + gtab_n - 1: g(c + d) = sum_{n<=7} a_n d^n for
+    // |d| <= 1/2 (the Chebyshev interpolant of degree 7).  Layout
+    // [2][kGTabMax][4]: a_0..a_3 of every interval, then a_4..a_7, so one
+    // interval is two 16-byte loads.  When the table covers every argument
+    // the model's bounds allow, gtab_tail = 0; otherwise x >= gtab_tail_x
+    // (>= 16.5) takes the asymptote sqrt(pi)/2 x^-1/2.
     alignas(16) float gtab[2 * kGTabMax * 4];
     int gtab_lo;
     int gtab_n;
+    int gtab_tail;
+    float gtab_tail_x;
     AxConst ax;  // GAC_MODEL_AXCAL_SMT only
 };
 
@@ -105,8 +115,10 @@ constexpr double kSqrtPiHalfD = 0.886226925452758014;
 // different intervals, which the constant bank would serialise).
 static __shared__ float4 smt_gtab_s[2 * kGTabMax];
 
-// The AxCaliberSMT series table of the block's model (FP32 path).
+// The AxCaliberSMT series table and per-measurement constants of the
+// block's model (FP32 path).
 static __shared__ float4 ax_tab_s[kAxMaxTiming * 2 * kAxTabMax];
+static __shared__ float4 ax_meas_s[kAxMaxMeas * 2];
 
 template <int KIND>
 __device__ __forceinline__ void model_smem_load(const ModelConst &mc) {
@@ -117,14 +129,18 @@ __device__ __forceinline__ void model_smem_load(const ModelConst &mc) {
     if constexpr (KIND == GAC_MODEL_AXCAL_SMT) {
         float *dst = reinterpret_cast<float *>(ax_tab_s);
         for (int e = threadIdx.x; e < kAxMaxTiming * 2 * kAxTabMax * 4; e += blockDim.x) dst[e] = mc.ax.tab[e];
+        float *dm = reinterpret_cast<float *>(ax_meas_s);
+        for (int e = threadIdx.x; e < kAxMaxMeas * 2 * 4; e += blockDim.x) dm[e] = mc.ax.meas[e];
     }
 }
 
 // g(x) in FP32 without branches: the interval is c = rint(x), taken from the
 // bits of x + 1.5 * 2^23 (exact for |x| < 2^22), and d = x - c is exact;
-// Horner in d over the interval's eight coefficients.  For x >= 16 the
-// asymptote sqrt(pi)/2 x^-1/2 replaces the table (relative error erfc(4)).
-// The clamped index keeps every load inside the table for any x.
+// Horner in d over the interval's eight coefficients.  With TAIL, x >=
+// gtab_tail_x takes the asymptote sqrt(pi)/2 x^-1/2 instead (relative error
+// below erfc(4)); without it the table covers every argument the bounds
+// allow.  The clamped index keeps every load inside the table for any x.
+template <bool TAIL>
 __device__ __forceinline__ float smt_g_f(float x, const ModelConst &mc) {
     constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
     const float t = x + kRound;
@@ -140,8 +156,12 @@ __device__ __forceinline__ float smt_g_f(float x, const ModelConst &mc) {
     p = fmaf(p, d, lo.z);
     p = fmaf(p, d, lo.y);
     p = fmaf(p, d, lo.x);
-    const float tail = kSqrtPiHalf * rsqrtf(x);
-    return x >= kGTail ? tail : p;
+    if constexpr (TAIL) {
+        const float tail = kSqrtPiHalf * rsqrtf(x);
+        return x >= mc.gtab_tail_x ? tail : p;
+    } else {
+        return p;
+    }
 }
 
 __device__ __forceinline__ double smt_g_d(double x) {
@@ -183,7 +203,7 @@ __device__ __forceinline__ void smt_g_dg(float x, const ModelConst &mc, float &g
     p = fmaf(p, d, lo.y);
     q = fmaf(q, d, lo.y);
     p = fmaf(p, d, lo.x);
-    if (x >= kGTail) {
+    if (mc.gtab_tail && x >= mc.gtab_tail_x) {
         const float tail = kSqrtPiHalf * rsqrtf(x);
         g = tail;
         dg = -0.5f * tail / x;
@@ -391,7 +411,7 @@ __device__ __forceinline__ void eval_mwi3_f(const float *th, const ModelConst &m
     }
 }
 
-template <class V>
+template <bool TAIL, class V>
 __device__ __forceinline__ void eval_smt_f(const float *th, const ModelConst &mc, V &&visit) {
     const float f = th[0], da = th[1], dpar = th[2], dperp = th[3];
     const float ddiff = dpar - dperp;
@@ -404,8 +424,8 @@ __device__ __forceinline__ void eval_smt_f(const float *th, const ModelConst &mc
                 visit(k, 1.0f);
                 continue;
             }
-            const float intra = smt_g_f(b * da, mc);
-            const float extra = expf(-b * dperp) * smt_g_f(b * ddiff, mc);
+            const float intra = smt_g_f<TAIL>(b * da, mc);
+            const float extra = expf(-b * dperp) * smt_g_f<TAIL>(b * ddiff, mc);
             visit(k, fmaf(f, intra, (1.0f - f) * extra));
         }
         end_block(visit, 0);
@@ -492,7 +512,18 @@ __device__ __forceinline__ void ax_phi_table_f(float R, const AxConst &ax, float
     }
 }
 
-template <class V>
+// 2^x on the special-function unit (ex2.approx; the callers fold log2 e into
+// their constants).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Measurements in timing order, so that the timing's attenuation phi_j is a
+// loop constant; per measurement two 16-byte shared-memory loads bring
+// b Da, g2, g2 log2 e, b log2 e, b, e^{-b D_csf} and the measurement's index.
+template <bool TAIL, class V>
 __device__ __forceinline__ void eval_axcal_f(const float *th, const ModelConst &mc, V &&visit) {
     const AxConst &ax = mc.ax;
     const float R = 0.5f * th[0], fn = th[1], fcsf = th[2], der = th[3];
@@ -500,19 +531,21 @@ __device__ __forceinline__ void eval_axcal_f(const float *th, const ModelConst &
     if (ax.tab_n > 0) ax_phi_table_f(R, ax, phi);  // the same branch for every thread
     else ax_phi_series_f(R, ax, phi);
     const float w_r = (1.0f - fcsf) * fn, w_h = (1.0f - fcsf) * (1.0f - fn), dh = kAxDePar - der;
-    const int n = mc.n_meas;
-    for (int k0 = 0; k0 < n; k0 += kAnchor) {
-        const int k1 = min(k0 + kAnchor, n);
-        for (int k = k0; k < k1; ++k) {
-            const float b = ax.b_f[k];
-            const int t = ax.t[k];
-            const float ph = t == 0 ? phi[0] : (t == 1 ? phi[1] : (t == 2 ? phi[2] : phi[3]));
-            const float kap = ax.g2_f[k] * ph;
-            const float sr = __expf(-kap) * smt_g_f(fmaf(b, kAxDa, -kap), mc);
-            const float sh = __expf(-b * der) * smt_g_f(b * dh, mc);
-            visit(k, fmaf(w_r, sr, fmaf(w_h, sh, fcsf * ax.csf_f[k])));
+    for (int j = 0; j < ax.n_timing; ++j) {
+        const float nph = -(j == 0 ? phi[0] : (j == 1 ? phi[1] : (j == 2 ? phi[2] : phi[3])));
+        const int end = ax.first[j + 1];
+        for (int i0 = ax.first[j]; i0 < end; i0 += kAnchor) {
+            const int i1 = min(i0 + kAnchor, end);
+            for (int i = i0; i < i1; ++i) {
+                const float4 A = ax_meas_s[2 * i], B = ax_meas_s[2 * i + 1];
+                // restricted: e^{-kappa} g(b Da - kappa), kappa = g2 phi_j
+                const float sr = ex2_approx(A.z * nph) * smt_g_f<TAIL>(fmaf(A.y, nph, A.x), mc);
+                // hindered: e^{-b De_R} g(b (De_par - De_R))
+                const float sh = ex2_approx(-A.w * der) * smt_g_f<TAIL>(B.x * dh, mc);
+                visit(__float_as_int(B.z), fmaf(w_r, sr, fmaf(w_h, sh, fcsf * B.y)));
+            }
+            end_block(visit, 0);
         }
-        end_block(visit, 0);
     }
 }
 
@@ -603,8 +636,13 @@ template <int KIND, class V>
 __device__ __forceinline__ void eval_f(const float *th, const ModelConst &mc, V &&visit) {
     if constexpr (KIND == GAC_MODEL_MONOEXP) eval_monoexp_f(th, mc, visit);
     else if constexpr (KIND == GAC_MODEL_MWI3) eval_mwi3_f(th, mc, visit);
-    else if constexpr (KIND == GAC_MODEL_SMT) eval_smt_f(th, mc, visit);
-    else if constexpr (KIND == GAC_MODEL_AXCAL_SMT) eval_axcal_f(th, mc, visit);
+    else if constexpr (KIND == GAC_MODEL_SMT) {
+        if (mc.gtab_tail) eval_smt_f<true>(th, mc, visit);  // the same branch for every thread
+        else eval_smt_f<false>(th, mc, visit);
+    } else if constexpr (KIND == GAC_MODEL_AXCAL_SMT) {
+        if (mc.gtab_tail) eval_axcal_f<true>(th, mc, visit);
+        else eval_axcal_f<false>(th, mc, visit);
+    }
     else eval_linear_f(th, mc, visit);
 }
 

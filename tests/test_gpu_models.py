@@ -85,6 +85,30 @@ def test_smt_g_both_branches(gac, orc):
         assert np.abs(s[:, 0] - 1.0).max() <= (1e-6 if prec != gac.PREC_FP64 else 1e-15)
 
 
+def test_g_table_beyond_its_range(gac, orc):
+    """b-values large enough that g's argument passes the end of the table:
+    those arguments take the asymptote sqrt(pi)/2 x^-1/2 (both models), the
+    rest the table."""
+    rng = np.random.default_rng(11)
+    n = 40_000
+    w = W.SMT_1P5M
+    b = np.array([0.0, 2.0, 10.0, 20.0, 40.0])
+    lb, ub = [0.0, 1.0, 1.25, 0.0], [1.0, 3.0, 3.0, 1.5]  # b (De_par - De_perp) >= -12 at b = 40
+    mid = gac.gac_model_register(w.kind, b, lb, ub, w.step)
+    th = rng.uniform(lb, ub, (n, w.n_par))
+    ref = orc.forward(w.kind, b, th)
+    a = W.AXCAL_250K
+    acq = np.array([[0.8, 13.0, 6.0], [6.0, 13.0, 6.0], [30.0, 30.0, 6.0], [60.0, 30.0, 6.0]]).ravel()
+    mid_a = gac.gac_model_register(a.kind, acq, a.lb, a.ub, a.step)
+    th_a = rng.uniform(a.lb, a.ub, (n, a.n_par))
+    ref_a = orc.forward(a.kind, acq, th_a)
+    for prec in (gac.PREC_MIXED, gac.PREC_FP32):
+        for m, t, r in ((mid, th, ref), (mid_a, th_a, ref_a)):
+            s = gac.forward_host(m, t, prec)
+            rel = np.linalg.norm(s - r, axis=1) / np.linalg.norm(r, axis=1)
+            assert rel.max() <= 1e-5, (m, prec, rel.max())
+
+
 LOGLIK = [(W.MONOEXP_4K, 1e-3), (W.MWI3_1M, 1e-3), (W.SMT_1P5M, 1e-3), (W.AXCAL_250K, 1e-3),
           (W.MWI3_1M.with_(name="mwi3_snr50", snr=50.0), 1e-3),
           (W.MWI3_1M.with_(name="mwi3_snr300", snr=300.0), 2e-3)]
