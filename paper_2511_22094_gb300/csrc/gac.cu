@@ -544,6 +544,7 @@ gac_status gac_model_register(const gac_model_desc *d, int *model_id) {
     for (int k = 0; k < d->n_acq; ++k) {
         mc.acq_d[k] = d->acq[k];
         mc.acq_f[k] = static_cast<float>(d->acq[k]);
+        mc.acq_l2e_f[k] = static_cast<float>(d->acq[k] * 1.44269504088896340736);
     }
     for (int p = 0; p < P; ++p) {
         mc.lb_d[p] = d->lb[p];

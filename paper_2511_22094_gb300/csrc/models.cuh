@@ -77,6 +77,7 @@ struct ModelConst {
     int even;       // acquisitions evenly spaced (recurrence allowed)
     float t0_f, dt_f, dtk_f;  // first acquisition, spacing, kAnchor * spacing
     float acq_f[GAC_MAX_ACQ];
+    float acq_l2e_f[GAC_MAX_ACQ];  // acquisition x log2 e (exponentials as 2^x)
     double acq_d[GAC_MAX_ACQ];
     float lb_f[GAC_MAX_PAR], ub_f[GAC_MAX_PAR], step_f[GAC_MAX_PAR];
     double lb_d[GAC_MAX_PAR], ub_d[GAC_MAX_PAR], step_d[GAC_MAX_PAR];
@@ -132,6 +133,14 @@ __device__ __forceinline__ void model_smem_load(const ModelConst &mc) {
         float *dm = reinterpret_cast<float *>(ax_meas_s);
         for (int e = threadIdx.x; e < kAxMaxMeas * 2 * 4; e += blockDim.x) dm[e] = mc.ax.meas[e];
     }
+}
+
+// 2^x on the special-function unit (ex2.approx; the callers fold log2 e into
+// their constants).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
 // g(x) in FP32 without branches: the interval is c = rint(x), taken from the
@@ -425,7 +434,7 @@ __device__ __forceinline__ void eval_smt_f(const float *th, const ModelConst &mc
                 continue;
             }
             const float intra = smt_g_f<TAIL>(b * da, mc);
-            const float extra = expf(-b * dperp) * smt_g_f<TAIL>(b * ddiff, mc);
+            const float extra = ex2_approx(-mc.acq_l2e_f[k] * dperp) * smt_g_f<TAIL>(b * ddiff, mc);
             visit(k, fmaf(f, intra, (1.0f - f) * extra));
         }
         end_block(visit, 0);
@@ -510,14 +519,6 @@ __device__ __forceinline__ void ax_phi_table_f(float R, const AxConst &ax, float
             phi[j] = fmaf(p, d, lo.x);
         }
     }
-}
-
-// 2^x on the special-function unit (ex2.approx; the callers fold log2 e into
-// their constants).
-__device__ __forceinline__ float ex2_approx(float x) {
-    float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
 }
 
 // Measurements in timing order, so that the timing's attenuation phi_j is a
