@@ -8,9 +8,13 @@
 // of voxels, iteration slice) from every resident job through an atomic
 // counter; the block copies its job's descriptor into shared memory and runs
 // the same tile routine as gac_mcmc_run, with chain state in HBM between
-// slices.  Finished jobs are copied back on the copy stream while the next
-// round runs; their memory then returns to the budget.  No device code waits
-// on the host: every wait is a host-side stream/event synchronisation.
+// slices.  Two rounds are in flight: while round r runs, round r+1 is planned
+// from the iterations the earlier rounds will have reached, launched behind
+// it on the same streams, and only then does the host wait for round r-1, so
+// the GPU does not idle between rounds.  A job's last round enqueues its
+// result download on the copy stream behind that round's kernels; its memory
+// returns to the budget when the download is done.  No device code waits on
+// the host: every wait is a host-side stream/event synchronisation.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -262,14 +266,26 @@ struct gac_server {
     bool started = false;
     int device = 0;
     // GPU resources, created by the scheduler thread
-    cudaStream_t s_compute = nullptr, s_copy = nullptr;
+    // s_copy: allocations and uploads; s_down: result downloads and frees,
+    // which wait for rounds in flight (kept off s_copy so uploads never queue
+    // behind those waits)
+    cudaStream_t s_compute = nullptr, s_copy = nullptr, s_down = nullptr;
     cudaStream_t s_kind[kKinds] = {};
-    cudaEvent_t ev_setup = nullptr, ev_kind[kKinds] = {};
+    // per round buffer set b = round & 1 (two rounds in flight)
+    cudaEvent_t ev_setup[2] = {}, ev_kind[2][kKinds] = {};
     PinnedCache pinned;  // destroyed after every job's buffers are back
-    ServeJob *d_jobs = nullptr, *h_jobs = nullptr;
-    RoundJob *d_items = nullptr, *h_items = nullptr;
-    int *d_counter = nullptr;
-    size_t cap_jobs = 0, cap_items = 0;
+    ServeJob *d_jobs[2] = {}, *h_jobs[2] = {};
+    RoundJob *d_items[2] = {}, *h_items[2] = {};
+    int *d_counter = nullptr;  // [2][kKinds]
+    size_t cap_jobs[2] = {}, cap_items[2] = {};
+    struct Inflight {
+        int b;
+        bool kind_ran[kKinds];
+        int64_t work;
+    };
+    std::deque<Inflight> inflight;
+    int64_t round_seq = 0;
+    double t_last_done = 0;
     size_t smem = 0;
     int sms = 1;
     double ci_per_s = 2e10;   // throughput estimate, refined each round
@@ -279,7 +295,8 @@ struct gac_server {
     void loop();
     gac_status init_gpu();
     gac_status admit_locked(int max_jobs = 1 << 30);
-    gac_status run_round();
+    gac_status run_round(bool *launched);
+    gac_status wait_oldest_round();
     void retire_locked();
     void free_job(Job &j);
     void free_results(Job &j);
@@ -298,12 +315,16 @@ gac_status gac_server::init_gpu() {
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     if ((e = cudaStreamCreateWithFlags(&s_compute, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "stream");
     if ((e = cudaStreamCreateWithFlags(&s_copy, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "stream");
-    if ((e = cudaMalloc(&d_counter, kKinds * sizeof(int))) != cudaSuccess) return cuda_fail(e, "counter");
-    if ((e = cudaEventCreateWithFlags(&ev_setup, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "event");
-    for (int i = 0; i < kKinds; ++i) {
-        if ((e = cudaStreamCreateWithFlags(&s_kind[i], cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "stream");
-        if ((e = cudaEventCreateWithFlags(&ev_kind[i], cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "event");
+    if ((e = cudaStreamCreateWithFlags(&s_down, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "stream");
+    if ((e = cudaMalloc(&d_counter, 2 * kKinds * sizeof(int))) != cudaSuccess) return cuda_fail(e, "counter");
+    for (int b = 0; b < 2; ++b) {
+        if ((e = cudaEventCreateWithFlags(&ev_setup[b], cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "event");
+        for (int i = 0; i < kKinds; ++i)
+            if ((e = cudaEventCreateWithFlags(&ev_kind[b][i], cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(e, "event");
     }
+    for (int i = 0; i < kKinds; ++i)
+        if ((e = cudaStreamCreateWithFlags(&s_kind[i], cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "stream");
     // the largest measurement tile any job can need (C = 1, 256 voxels, 64
     // complex echoes); each round launches with its own jobs' largest tile
     smem = static_cast<size_t>(kBlock) * row_stride_for(GAC_MODEL_MWI3, 2 * GAC_MAX_ACQ) * sizeof(float);
@@ -320,8 +341,13 @@ gac_status gac_server::init_gpu() {
 }
 
 void gac_server::free_job(Job &j) {
-    // stream-ordered: after everything queued on the copy stream (downloads)
-    if (j.d_block) cudaFreeAsync(j.d_block, s_copy ? s_copy : cudaStream_t{});
+    // stream-ordered: after the job's upload (a job is freed only once its
+    // event has completed), its download and every round launched so far (a
+    // cancelled job may be in one)
+    if (j.d_block && s_down)
+        for (int b = 0; b < 2; ++b)
+            for (int i = 0; i < kKinds; ++i) cudaStreamWaitEvent(s_down, ev_kind[b][i], 0);
+    if (j.d_block) cudaFreeAsync(j.d_block, s_down ? s_down : cudaStream_t{});
     j.d_block = nullptr;
     if (j.ev) cudaEventDestroy(j.ev);
     j.ev = nullptr;
@@ -385,6 +411,7 @@ gac_status gac_server::admit_locked(int max_jobs) {
             cudaGetLastError();
             j.err = e == cudaErrorMemoryAllocation ? GAC_ERR_OOM : GAC_ERR_CUDA;
             j.state = JobState::Failed;
+            cudaStreamSynchronize(s_copy);  // an upload may be in flight into the block
             free_job(j);
             free_results(j);
             cv_done.notify_all();
@@ -462,20 +489,21 @@ void gac_server::retire_locked() {
     }
 }
 
-gac_status gac_server::run_round() {
+// Plans round r from the iterations the launched rounds will have reached,
+// launches it behind them, queues the downloads of the jobs it completes,
+// then admits and retires jobs while the GPU works.  *launched = false when
+// no job can run.
+gac_status gac_server::run_round(bool *launched) {
+    *launched = false;
     // choose the jobs and the slice length under the lock
     std::vector<std::shared_ptr<Job>> run;
-    int64_t chains = 0;
     {
         std::lock_guard<std::mutex> lk(mu);
         for (auto &jp : resident) {
             Job &j = *jp;
             if (j.cancel) continue;
             if (j.state == JobState::Uploading && cudaEventQuery(j.ev) == cudaSuccess) j.state = JobState::Running;
-            if (j.state == JobState::Running) {
-                run.push_back(jp);
-                chains += j.n_vox * j.opts.n_chains;
-            }
+            if (j.state == JobState::Running && j.t_done < j.opts.iterations) run.push_back(jp);
         }
     }
     if (run.empty()) return GAC_OK;
@@ -513,22 +541,25 @@ gac_status gac_server::run_round() {
     for (size_t i = 0; i < run.size(); ++i)
         if (t_end[i] < 0)
             t_end[i] = static_cast<int>(std::min<int64_t>(run[i]->opts.iterations, run[i]->t_done + k_big));
-    (void)chains;
+    // this round's buffer set: its previous user, round r-2, has completed
+    const int b = static_cast<int>(round_seq & 1);
     const size_t n_items = run.size();  // one round entry per job
-    if (run.size() > cap_jobs) {
-        if (d_jobs) cudaFree(d_jobs);
-        if (h_jobs) cudaFreeHost(h_jobs);
-        cap_jobs = std::max<size_t>(run.size(), 2 * cap_jobs);
-        gac_status st = round_alloc(reinterpret_cast<void **>(&d_jobs), reinterpret_cast<void **>(&h_jobs),
-                                    cap_jobs * sizeof(ServeJob));
+    if (run.size() > cap_jobs[b]) {
+        if (d_jobs[b]) cudaFree(d_jobs[b]);
+        if (h_jobs[b]) cudaFreeHost(h_jobs[b]);
+        d_jobs[b] = h_jobs[b] = nullptr;
+        cap_jobs[b] = std::max<size_t>(run.size(), 2 * cap_jobs[b]);
+        gac_status st = round_alloc(reinterpret_cast<void **>(&d_jobs[b]), reinterpret_cast<void **>(&h_jobs[b]),
+                                    cap_jobs[b] * sizeof(ServeJob));
         if (st != GAC_OK) return st;
     }
-    if (n_items > cap_items) {
-        if (d_items) cudaFree(d_items);
-        if (h_items) cudaFreeHost(h_items);
-        cap_items = std::max(n_items, 2 * cap_items);
-        gac_status st = round_alloc(reinterpret_cast<void **>(&d_items), reinterpret_cast<void **>(&h_items),
-                                    cap_items * sizeof(RoundJob));
+    if (n_items > cap_items[b]) {
+        if (d_items[b]) cudaFree(d_items[b]);
+        if (h_items[b]) cudaFreeHost(h_items[b]);
+        d_items[b] = h_items[b] = nullptr;
+        cap_items[b] = std::max(n_items, 2 * cap_items[b]);
+        gac_status st = round_alloc(reinterpret_cast<void **>(&d_items[b]), reinterpret_cast<void **>(&h_items[b]),
+                                    cap_items[b] * sizeof(RoundJob));
         if (st != GAC_OK) return st;
     }
     // items grouped by model kind (one contiguous range per kind's kernel),
@@ -536,13 +567,13 @@ gac_status gac_server::run_round() {
     // order, so the jobs that run to completion start at the beginning
     std::vector<size_t> by_len(run.size());
     for (size_t i = 0; i < by_len.size(); ++i) by_len[i] = i;
-    std::stable_sort(by_len.begin(), by_len.end(), [&](size_t a, size_t b) {
-        return t_end[a] - run[a]->t_done > t_end[b] - run[b]->t_done;
+    std::stable_sort(by_len.begin(), by_len.end(), [&](size_t a, size_t c) {
+        return t_end[a] - run[a]->t_done > t_end[c] - run[c]->t_done;
     });
     size_t k = 0;
     int64_t work = 0;
     size_t first_rj[kKinds] = {}, n_rj[kKinds] = {}, count_item[kKinds] = {}, smem_kind[kKinds] = {};
-    for (size_t ji = 0; ji < run.size(); ++ji) h_jobs[ji] = run[ji]->desc;
+    for (size_t ji = 0; ji < run.size(); ++ji) h_jobs[b][ji] = run[ji]->desc;
     for (int slot = 0; slot < kKinds; ++slot) {
         first_rj[slot] = k;
         int64_t tiles = 0;
@@ -552,7 +583,7 @@ gac_status gac_server::run_round() {
             const RunArgs &ra = j.desc.ra;
             smem_kind[slot] = std::max(smem_kind[slot], tile_smem_bytes(j.mc.n_par, 8, ra.vox_per_block, ra.row_stride, false));
             work += static_cast<int64_t>(t_end[ji] - j.t_done) * j.n_vox * j.opts.n_chains;
-            RoundJob &r = h_items[k++];
+            RoundJob &r = h_items[b][k++];
             r.job = static_cast<int32_t>(ji);
             r.t_begin = j.t_done;
             r.t_end = t_end[ji];
@@ -563,65 +594,97 @@ gac_status gac_server::run_round() {
         n_rj[slot] = k - first_rj[slot];
         count_item[slot] = static_cast<size_t>(tiles);
     }
-    cudaError_t e = cudaMemcpyAsync(d_jobs, h_jobs, run.size() * sizeof(ServeJob), cudaMemcpyHostToDevice, s_compute);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_items, h_items, n_items * sizeof(RoundJob), cudaMemcpyHostToDevice, s_compute);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, kKinds * sizeof(int), s_compute);
-    if (e == cudaSuccess) e = cudaEventRecord(ev_setup, s_compute);
+    int *counter = d_counter + b * kKinds;
+    cudaError_t e = cudaMemcpyAsync(d_jobs[b], h_jobs[b], run.size() * sizeof(ServeJob), cudaMemcpyHostToDevice, s_compute);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_items[b], h_items[b], n_items * sizeof(RoundJob), cudaMemcpyHostToDevice, s_compute);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, kKinds * sizeof(int), s_compute);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_setup[b], s_compute);
     if (e != cudaSuccess) return cuda_fail(e, "round setup");
-    const double t_start = now_s();
-    t_round_host += t_start - t_prep;
+    Inflight rec{};
+    rec.b = b;
+    rec.work = work;
     for (int slot = 0; slot < kKinds; ++slot) {
         if (count_item[slot] == 0) continue;
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_fn(slot), kBlock, smem_kind[slot]);
         if (e != cudaSuccess) return cuda_fail(e, "occupancy");
         const size_t grid = std::min<size_t>(static_cast<size_t>(std::max(1, per_sm)) * sms, count_item[slot]);
-        if ((e = cudaStreamWaitEvent(s_kind[slot], ev_setup, 0)) != cudaSuccess) return cuda_fail(e, "wait");
-        launch_serve(slot, static_cast<int>(grid), smem_kind[slot], s_kind[slot], d_jobs, d_items + first_rj[slot],
-                     static_cast<int>(n_rj[slot]), static_cast<int>(count_item[slot]), d_counter + slot);
+        if ((e = cudaStreamWaitEvent(s_kind[slot], ev_setup[b], 0)) != cudaSuccess) return cuda_fail(e, "wait");
+        launch_serve(slot, static_cast<int>(grid), smem_kind[slot], s_kind[slot], d_jobs[b], d_items[b] + first_rj[slot],
+                     static_cast<int>(n_rj[slot]), static_cast<int>(count_item[slot]), counter + slot);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "serve kernel launch");
-        if ((e = cudaEventRecord(ev_kind[slot], s_kind[slot])) != cudaSuccess) return cuda_fail(e, "event");
+        if ((e = cudaEventRecord(ev_kind[b][slot], s_kind[slot])) != cudaSuccess) return cuda_fail(e, "event");
+        rec.kind_ran[slot] = true;
     }
-    // while the round runs: retire finished downloads and admit queued jobs
-    // (allocations and uploads), so that the host work overlaps the kernels
+    inflight.push_back(rec);
+    ++round_seq;
+    *launched = true;
+    t_round_host += now_s() - t_prep;
     {
+        // advance to the iterations this round reaches; a job it completes
+        // downloads its results on the copy stream behind the round's kernel
         std::lock_guard<std::mutex> lk(mu);
         const double t0 = now_s();
+        for (size_t ji = 0; ji < run.size(); ++ji) {
+            Job &j = *run[ji];
+            j.t_done = t_end[ji];
+            if (j.t_done < j.opts.iterations) continue;
+            const size_t N = j.n_vox, P = j.mc.n_par, C = j.opts.n_chains;
+            const RunArgs &ra = j.desc.ra;
+            e = cudaStreamWaitEvent(s_down, ev_kind[b][kind_slot(j.mc.kind)], 0);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_mean, ra.mean, P * N * 8, cudaMemcpyDeviceToHost, s_down);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_std, ra.std, P * N * 8, cudaMemcpyDeviceToHost, s_down);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_acc, ra.accept, C * N * 4, cudaMemcpyDeviceToHost, s_down);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_bad, ra.nonfinite, C * N * 4, cudaMemcpyDeviceToHost, s_down);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_rhat, ra.rhat, P * N * 8, cudaMemcpyDeviceToHost, s_down);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_scale, ra.step_scale, C * N * 4, cudaMemcpyDeviceToHost, s_down);
+            if (e == cudaSuccess && ra.samples)
+                e = cudaMemcpyAsync(j.h_samples, ra.samples, static_cast<size_t>(j.S) * C * P * N * 4,
+                                    cudaMemcpyDeviceToHost, s_down);
+            if (e == cudaSuccess) e = cudaEventRecord(j.ev, s_down);
+            if (e != cudaSuccess) return cuda_fail(e, "result download");
+            j.state = JobState::Finishing;
+        }
+        // while the rounds run: retire finished downloads and admit queued
+        // jobs (allocations and uploads), so that the host work overlaps the
+        // kernels
         retire_locked();
         gac_status st = admit_locked();
         t_admit += now_s() - t0;
         if (st != GAC_OK) return st;
     }
+    // keep one round queued behind the running one
+    while (inflight.size() > 1) {
+        gac_status st = wait_oldest_round();
+        if (st != GAC_OK) return st;
+    }
+    return GAC_OK;
+}
+
+// Waits for the oldest round in flight; refines the throughput estimate from
+// the interval between round completions (back-to-back rounds).
+gac_status gac_server::wait_oldest_round() {
+    if (inflight.empty()) return GAC_OK;
+    const Inflight r = inflight.front();
+    inflight.pop_front();
     const double t_wait = now_s();
     for (int slot = 0; slot < kKinds; ++slot) {
-        if (count_item[slot] == 0) continue;
-        if ((e = cudaEventSynchronize(ev_kind[slot])) != cudaSuccess) return cuda_fail(e, "serve kernel");
+        if (!r.kind_ran[slot]) continue;
+        cudaError_t e = cudaEventSynchronize(ev_kind[r.b][slot]);
+        if (e != cudaSuccess) return cuda_fail(e, "serve kernel");
     }
-    t_gpu += now_s() - t_wait;
-    const double dt = now_s() - t_start;
-    if (dt > 1e-4 && work > 0) ci_per_s = 0.5 * ci_per_s + 0.5 * (work / dt);
-    // advance; start downloads of finished jobs on the copy stream
+    const double t = now_s();
+    t_gpu += t - t_wait;
+    // a round that had ended before the host looked gives no timing, nor
+    // does one that did not start right at its predecessor's end
+    const bool waited = t - t_wait > 1e-4;
+    if (waited && t_last_done > 0 && r.work > 0) {
+        const double dt = t - t_last_done;
+        if (dt > 1e-4) ci_per_s = 0.5 * ci_per_s + 0.5 * (r.work / dt);
+    }
+    t_last_done = (waited && !inflight.empty()) ? t : 0.0;
     std::lock_guard<std::mutex> lk(mu);
     ++rounds;
-    for (size_t ji = 0; ji < run.size(); ++ji) {
-        Job &j = *run[ji];
-        j.t_done = t_end[ji];
-        if (j.t_done < j.opts.iterations || j.cancel) continue;
-        const size_t N = j.n_vox, P = j.mc.n_par, C = j.opts.n_chains;
-        const RunArgs &ra = j.desc.ra;
-        e = cudaMemcpyAsync(j.h_mean, ra.mean, P * N * 8, cudaMemcpyDeviceToHost, s_copy);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_std, ra.std, P * N * 8, cudaMemcpyDeviceToHost, s_copy);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_acc, ra.accept, C * N * 4, cudaMemcpyDeviceToHost, s_copy);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_bad, ra.nonfinite, C * N * 4, cudaMemcpyDeviceToHost, s_copy);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_rhat, ra.rhat, P * N * 8, cudaMemcpyDeviceToHost, s_copy);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_scale, ra.step_scale, C * N * 4, cudaMemcpyDeviceToHost, s_copy);
-        if (e == cudaSuccess && ra.samples)
-            e = cudaMemcpyAsync(j.h_samples, ra.samples, static_cast<size_t>(j.S) * C * P * N * 4,
-                                cudaMemcpyDeviceToHost, s_copy);
-        if (e == cudaSuccess) e = cudaEventRecord(j.ev, s_copy);
-        if (e != cudaSuccess) return cuda_fail(e, "result download");
-        j.state = JobState::Finishing;
-    }
     return GAC_OK;
 }
 
@@ -632,13 +695,15 @@ void gac_server::loop() {
             std::unique_lock<std::mutex> lk(mu);
             if (st == GAC_OK) {
                 // with nothing on the GPU, admit one job to start a round at
-                // once; the others are admitted while rounds run
-                bool busy = false;
+                // once; otherwise admission waits for the next round's launch
+                // (run_round admits while its kernels run), so that the GPU
+                // does not idle between rounds while jobs are admitted
+                bool busy = !inflight.empty();
                 for (auto &jp : resident)
                     busy = busy || jp->state == JobState::Running || jp->state == JobState::Uploading;
                 const double t0 = now_s();
                 retire_locked();
-                admit_locked(busy ? (1 << 30) : 1);
+                if (!busy) admit_locked(1);
                 t_admit += now_s() - t0;
             }
             if (st != GAC_OK) {
@@ -647,6 +712,7 @@ void gac_server::loop() {
                 for (auto &jp : resident) { jp->state = JobState::Failed; jp->err = st; }
                 queue.clear();
                 resident.clear();
+                inflight.clear();
                 cv_done.notify_all();
                 cv_work.wait(lk, [&] { return stop || !queue.empty(); });
                 if (stop) break;
@@ -655,13 +721,17 @@ void gac_server::loop() {
             if (stop) break;
             bool runnable = false, waiting = false;
             for (auto &jp : resident) {
-                if (jp->state == JobState::Running || jp->state == JobState::Uploading) runnable = true;
+                if ((jp->state == JobState::Running && jp->t_done < jp->opts.iterations) ||
+                    jp->state == JobState::Uploading)
+                    runnable = true;
                 if (jp->state == JobState::Finishing) waiting = true;
             }
             if (!runnable) {
-                if (waiting) {
+                if (!inflight.empty() || waiting) {
+                    // the last rounds and downloads: wait for them, then retire
                     lk.unlock();
-                    cudaStreamSynchronize(s_copy);
+                    while (st == GAC_OK && !inflight.empty()) st = wait_oldest_round();
+                    if (st == GAC_OK) cudaStreamSynchronize(s_down);
                     continue;
                 }
                 cv_work.wait(lk, [&] { return stop || !queue.empty(); });
@@ -669,46 +739,46 @@ void gac_server::loop() {
                 continue;
             }
         }
-        bool any_running = false;
-        {
-            std::lock_guard<std::mutex> lk(mu);
-            for (auto &jp : resident)
-                if (jp->state == JobState::Running) any_running = true;
+        bool launched = false;
+        st = run_round(&launched);  // admits the queued jobs while the rounds run
+        if (st == GAC_OK && !launched) {
+            // only uploads in flight (or every runnable job already has its
+            // rounds queued): finish the rounds, wait for the uploads
+            while (st == GAC_OK && !inflight.empty()) st = wait_oldest_round();
+            if (st == GAC_OK) cudaStreamSynchronize(s_copy);
         }
-        if (!any_running) {
-            // only uploads in flight: wait for them
-            cudaStreamSynchronize(s_copy);
-            std::lock_guard<std::mutex> lk(mu);
-            for (auto &jp : resident)
-                if (jp->state == JobState::Uploading && cudaEventQuery(jp->ev) == cudaSuccess)
-                    jp->state = JobState::Running;
-        }
-        st = run_round();  // admits the queued jobs while it runs
     }
     // shutdown: wait for the GPU, release everything
     for (int i = 0; i < kKinds; ++i)
         if (s_kind[i]) cudaStreamSynchronize(s_kind[i]);
     if (s_compute) cudaStreamSynchronize(s_compute);
     if (s_copy) cudaStreamSynchronize(s_copy);
+    if (s_down) cudaStreamSynchronize(s_down);
     std::lock_guard<std::mutex> lk(mu);
     for (auto &kv : jobs) {
         free_job(*kv.second);
         free_results(*kv.second);
     }
-    if (s_copy) cudaStreamSynchronize(s_copy);  // the stream-ordered frees
-    if (d_jobs) cudaFree(d_jobs);
-    if (h_jobs) cudaFreeHost(h_jobs);
-    if (d_items) cudaFree(d_items);
-    if (h_items) cudaFreeHost(h_items);
+    if (s_down) cudaStreamSynchronize(s_down);  // the stream-ordered frees
+    for (int b = 0; b < 2; ++b) {
+        if (d_jobs[b]) cudaFree(d_jobs[b]);
+        if (h_jobs[b]) cudaFreeHost(h_jobs[b]);
+        if (d_items[b]) cudaFree(d_items[b]);
+        if (h_items[b]) cudaFreeHost(h_items[b]);
+    }
     if (d_counter) cudaFree(d_counter);
     for (int i = 0; i < kKinds; ++i) {
         if (s_kind[i]) cudaStreamSynchronize(s_kind[i]);
         if (s_kind[i]) cudaStreamDestroy(s_kind[i]);
-        if (ev_kind[i]) cudaEventDestroy(ev_kind[i]);
     }
-    if (ev_setup) cudaEventDestroy(ev_setup);
+    for (int b = 0; b < 2; ++b) {
+        for (int i = 0; i < kKinds; ++i)
+            if (ev_kind[b][i]) cudaEventDestroy(ev_kind[b][i]);
+        if (ev_setup[b]) cudaEventDestroy(ev_setup[b]);
+    }
     if (s_compute) cudaStreamDestroy(s_compute);
     if (s_copy) cudaStreamDestroy(s_copy);
+    if (s_down) cudaStreamDestroy(s_down);
 }
 
 static gac_status job_bytes(const ModelConst &mc, int64_t n_vox, const gac_mcmc_opts &o, int keep, bool has_sigma,

@@ -117,3 +117,43 @@ def test_destroy_with_jobs_in_flight(gac, orc):
     for i in range(3):
         gac.gac_server_submit(srv, mid, y, y.shape[0], sig, 0.0, gac.make_opts(2000, 200, 100, 4, i))
     gac.gac_server_destroy(srv)  # must return without waiting for the jobs to finish
+
+
+def test_cancel_while_rounds_are_in_flight(gac, orc):
+    """Cancelling running jobs while later rounds are already queued: their
+    memory returns only after those rounds, so jobs admitted into it and the
+    job that keeps running all equal their runs alone."""
+    import time
+    w = W.MWI3_1M
+    mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
+    th, sig, y = make_voxels(orc, w, 0, 40_000)
+    srv = gac.gac_server_create(8 << 30, 16)
+    try:
+        # three jobs of ~0.1 s each alone, so the cancels land mid-run
+        big = [gac.gac_server_submit(srv, mid, y, y.shape[0], sig, 0.0, gac.make_opts(20000, 2000, 1000, 4, 10 + i))
+               for i in range(3)]
+        time.sleep(0.05)
+        gac.gac_server_cancel(srv, big[0])
+        gac.gac_server_cancel(srv, big[1])
+        small = []
+        for i in range(3):
+            opts = gac.make_opts(800, 80, 20, 2, 20 + i)
+            ys, ss = y[2000 * i:2000 * (i + 1)], sig[2000 * i:2000 * (i + 1)]
+            small.append((gac.gac_server_submit(srv, mid, ys, 2000, ss, 0.0, opts, keep_samples=True), ys, ss, opts))
+        for jid, ys, ss, opts in small:
+            ref = _alone(gac, mid, ys, ss, opts)
+            out = _out_like(ref)
+            gac.gac_server_wait(srv, jid, 300.0, out)
+            np.testing.assert_array_equal(out["samples"], ref["samples"])
+            np.testing.assert_allclose(out["mean"], ref["mean"], rtol=1e-12, atol=0)
+        opts = gac.make_opts(20000, 2000, 1000, 4, 12)
+        ref = _alone(gac, mid, y, sig, opts)
+        out = {"mean": np.empty_like(ref["mean"]), "accept_rate": np.empty_like(ref["accept_rate"])}
+        gac.gac_server_wait(srv, big[2], 300.0, out)
+        np.testing.assert_array_equal(out["accept_rate"], ref["accept_rate"])
+        np.testing.assert_allclose(out["mean"], ref["mean"], rtol=1e-12, atol=0)
+        for jid in big[:2]:
+            with pytest.raises(gac.GacError):
+                gac.gac_server_wait(srv, jid, 60.0, {})
+    finally:
+        gac.gac_server_destroy(srv)
