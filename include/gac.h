@@ -336,12 +336,14 @@ gac_status gac_mcmc_run_noalloc(int model_id, const void *data, int64_t n_vox, c
  * A server owns a scheduler thread.  Submitted jobs wait in arrival order
  * until their device memory fits under the HBM budget (and a resident slot is
  * free); admitted jobs are uploaded on a copy stream while others compute.
- * The scheduler then runs rounds: each round is one launch of a persistent
- * kernel whose blocks claim work items -- (job, tile of voxels, slice of
- * iterations) -- from every resident job, whatever its model, so small and
- * large jobs share the GPU.  Chain state (theta, L, counters, Welford
- * accumulators) stays in HBM between slices.  A job that finishes is copied
- * back while the next round runs, and its memory is returned to the budget.
+ * The scheduler then runs rounds: each round is one launch per model kind of
+ * a persistent kernel whose blocks claim work items -- (job, tile of voxels,
+ * slice of iterations) -- from every resident job, so small and large jobs
+ * share the GPU.  Chain state (theta, L, counters, Welford accumulators)
+ * stays in HBM between slices.  Two rounds are in flight: the next one is
+ * planned and queued behind the running one.  A job's results are copied
+ * back behind its last round, and its memory returns to the budget once
+ * that copy is done.
  * Results equal those of gac_mcmc_run with the same inputs: the random
  * numbers depend only on (seed, t, voxel, chain) and slices resume exactly.
  * Serving runs the MIXED precision path; trace_n_vox must be 0.
@@ -379,8 +381,9 @@ gac_status gac_server_poll(gac_server *srv, uint64_t job_id, int *done, gac_resu
 gac_status gac_server_wait(gac_server *srv, uint64_t job_id, double timeout_s, gac_result *out,
                            double *latency_s);
 
-/* Cancels a queued or running job; its memory is released at the next round
- * boundary.  Polling it afterwards returns GAC_ERR_CANCELLED. */
+/* Cancels a queued or running job; its memory is released behind the rounds
+ * already in flight.  Polling it afterwards returns GAC_ERR_CANCELLED (a job
+ * whose last round was already queued completes normally). */
 gac_status gac_server_cancel(gac_server *srv, uint64_t job_id);
 
 /* Counters: jobs queued, resident, finished; bytes in use; rounds run; and
