@@ -619,11 +619,12 @@ gac_status gac_server::run_round(bool *launched) {
     inflight.push_back(rec);
     ++round_seq;
     *launched = true;
-    t_round_host += now_s() - t_prep;
+    const double t_launched = now_s();
     {
         // advance to the iterations this round reaches; a job it completes
         // downloads its results on the copy stream behind the round's kernel
         std::lock_guard<std::mutex> lk(mu);
+        t_round_host += t_launched - t_prep;  // the counters are read under the lock
         const double t0 = now_s();
         for (size_t ji = 0; ji < run.size(); ++ji) {
             Job &j = *run[ji];
@@ -674,7 +675,6 @@ gac_status gac_server::wait_oldest_round() {
         if (e != cudaSuccess) return cuda_fail(e, "serve kernel");
     }
     const double t = now_s();
-    t_gpu += t - t_wait;
     // a round that had ended before the host looked gives no timing, nor
     // does one that did not start right at its predecessor's end
     const bool waited = t - t_wait > 1e-4;
@@ -684,6 +684,7 @@ gac_status gac_server::wait_oldest_round() {
     }
     t_last_done = (waited && !inflight.empty()) ? t : 0.0;
     std::lock_guard<std::mutex> lk(mu);
+    t_gpu += t - t_wait;
     ++rounds;
     return GAC_OK;
 }
