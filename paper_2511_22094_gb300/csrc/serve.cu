@@ -512,10 +512,13 @@ gac_status gac_server::run_round(bool *launched) {
     // throughput estimate.  Jobs are taken in order of remaining work: one
     // whose remainder fits in half of what is left of the first half of the
     // round's budget runs to completion in this round (small jobs leave
-    // quickly instead of advancing in lock-step with large ones); the others
-    // share the rest of the budget -- at least half of it, so that a stream
-    // of small arrivals cannot starve a large job -- equally per chain (at
-    // least 16 iterations each).
+    // quickly instead of advancing in lock-step with large ones).  The others
+    // get the rest of the budget -- at least half of it, so that a stream of
+    // small arrivals cannot starve a large job -- in order of their slowdown
+    // so far (time since submission over the job's time alone at the current
+    // throughput), each as many iterations as the remaining budget allows and
+    // at least 16: the job that has waited longest relative to its size goes
+    // first instead of every large job advancing at a shared rate.
     std::vector<size_t> order(run.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = i;
     auto remaining = [&](size_t i) {
@@ -526,7 +529,7 @@ gac_status gac_server::run_round(bool *launched) {
     double budget_ci = round_target_s * ci_per_s;
     double small_ci = 0.5 * budget_ci;
     std::vector<int> t_end(run.size(), -1);
-    int64_t big_chains = 0;
+    std::vector<size_t> big;
     for (size_t i : order) {
         const double rem = remaining(i);
         if (rem <= 0.5 * small_ci) {
@@ -534,13 +537,24 @@ gac_status gac_server::run_round(bool *launched) {
             small_ci -= rem;
             budget_ci -= rem;
         } else {
-            big_chains += run[i]->n_vox * run[i]->opts.n_chains;
+            big.push_back(i);
         }
     }
-    const int64_t k_big = std::max<int64_t>(16, static_cast<int64_t>(std::max(budget_ci, 0.0) / std::max<int64_t>(big_chains, 1)));
-    for (size_t i = 0; i < run.size(); ++i)
-        if (t_end[i] < 0)
-            t_end[i] = static_cast<int>(std::min<int64_t>(run[i]->opts.iterations, run[i]->t_done + k_big));
+    const double now = now_s();
+    auto slowdown = [&](size_t i) {
+        const Job &j = *run[i];
+        const double alone = static_cast<double>(j.opts.iterations) * j.n_vox * j.opts.n_chains / ci_per_s;
+        return (now - j.t_submit) / std::max(alone, 1e-9);
+    };
+    std::stable_sort(big.begin(), big.end(), [&](size_t a, size_t c) { return slowdown(a) > slowdown(c); });
+    double left = std::max(budget_ci, 0.0);
+    for (size_t i : big) {
+        const Job &j = *run[i];
+        const int64_t chains = j.n_vox * j.opts.n_chains;
+        const int64_t k = std::max<int64_t>(16, static_cast<int64_t>(left / static_cast<double>(chains)));
+        t_end[i] = static_cast<int>(std::min<int64_t>(j.opts.iterations, j.t_done + k));
+        left = std::max(0.0, left - static_cast<double>(t_end[i] - j.t_done) * chains);
+    }
     // this round's buffer set: its previous user, round r-2, has completed
     const int b = static_cast<int>(round_seq & 1);
     const size_t n_items = run.size();  // one round entry per job
