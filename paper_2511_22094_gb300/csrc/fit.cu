@@ -116,14 +116,21 @@ __device__ __forceinline__ void jacobian(const R *th, const ModelConst &mc, V &&
     }
 }
 
-// The 3-pool model and its Jacobian in FP32 for evenly spaced echoes, from
-// the anchored recurrence of the unit-amplitude pool terms
+// The 3-pool model's data loss and its gradient in FP32 for evenly spaced
+// echoes, from the anchored recurrence of the unit-amplitude pool terms
 // u_j(t) = e^{-t/T2*_j} e^{i(phi0 - w_j t)} (the MH kernel's recurrence with
-// A_j = 1): with them every entry of the Jacobian is a product,
+// A_j = 1).  Every entry of the Jacobian is a product,
 //   dS/dA_j = u_j,  dS/dT2*_j = A_j t / T2*_j^2 u_j,
-//   dS/d df_j = -i 2 pi 1e-3 t A_j u_j,  dS/d phi0 = i S.
-template <class V>
-__device__ __forceinline__ void jacobian_mwi3_rec_f(const float *th, const ModelConst &mc, V &&visit) {
+//   dS/d df_j = -i 2 pi 1e-3 t A_j u_j,  dS/d phi0 = i S,
+// so with d = (d_re, d_im) the loss derivative with respect to (Re S, Im S) at
+// an echo, the gradient sums factor into per-pool sums of Re(conj(d) u_j)
+// (the amplitudes), of t times them (T2*, scaled by A_j / T2*_j^2 at the end)
+// and of t Im(conj(d) u_j) (the frequencies, scaled by A_j 2 pi 1e-3); the
+// two offset pools are carried as lane pairs.  rho and its derivative as in
+// the visitor of fit_voxel: r = w (y - s), L1 |r| with d = -w sign(r), L2
+// r^2 with d = -2 w r.  Adds the gradient to g[9]; returns the data loss.
+__device__ __forceinline__ float mwi3_rec_loss_grad_f(const float *th, const ModelConst &mc, const float *yrow,
+                                                      float wgt, bool l1, float *g) {
     const float phi0 = th[8];
     const int n = mc.n_acq;
     const float r0 = 1.0f / th[3], r1 = 1.0f / th[4], r2 = 1.0f / th[5];
@@ -144,19 +151,30 @@ __device__ __forceinline__ void jacobian_mwi3_rec_f(const float *th, const Model
     float2 Z = make_float2(e2 * ce, e2 * se);
     const float2 R2 = f2(expf(-mc.dt_f * r2)), K2 = f2(expf(-mc.dtk_f * r2));
     const float a0 = th[0], a1 = th[1], a2 = th[2];
-    const float q0 = a0 * r0 * r0, q1 = a1 * r1 * r1, q2 = a2 * r2 * r2;  // dT factors / t
+    // sums over echoes: amplitude terms, t x amplitude terms, t x frequency terms
+    float2 G01 = f2(0.0f), T01 = f2(0.0f), C01 = f2(0.0f);
+    float G2 = 0.0f, T2 = 0.0f, G8 = 0.0f, loss = 0.0f;
     auto echo = [&](int k, float2 x, float2 y, float2 z) {
         const float t = fmaf(static_cast<float>(k), mc.dt_f, mc.t0_f);
         const float re = fmaf(a0, x.x, fmaf(a1, x.y, a2 * z.x));
         const float im = fmaf(a0, y.x, fmaf(a1, y.y, a2 * z.y));
-        const float wt = kTwoPiMilli * t;
-        float Jr[9] = {x.x, x.y, z.x, q0 * t * x.x, q1 * t * x.y, q2 * t * z.x, a0 * wt * y.x, a1 * wt * y.y, -im};
-        float Ji[9] = {y.x, y.y, z.y, q0 * t * y.x, q1 * t * y.y, q2 * t * z.y, -a0 * wt * x.x, -a1 * wt * x.y, re};
-        visit(2 * k, re, Jr);
-        visit(2 * k + 1, im, Ji);
+        const float rr = wgt * (yrow[2 * k] - re), ri = wgt * (yrow[2 * k + 1] - im);
+        const float dr = l1 ? -wgt * sgn(rr) : -2.0f * wgt * rr;
+        const float di = l1 ? -wgt * sgn(ri) : -2.0f * wgt * ri;
+        loss += l1 ? fabsf(rr) + fabsf(ri) : fmaf(rr, rr, ri * ri);
+        const float2 D = f2(dr), E = f2(di);
+        const float2 inc = __ffma2_rn(E, y, __fmul2_rn(D, x));                       // Re(conj(d) u), pools 0, 1
+        const float2 crs = __ffma2_rn(make_float2(-di, -di), x, __fmul2_rn(D, y));  // Im(conj(d) u)
+        const float2 tt = f2(t);
+        G01 = __fadd2_rn(G01, inc);
+        T01 = __ffma2_rn(tt, inc, T01);
+        C01 = __ffma2_rn(tt, crs, C01);
+        const float inc2 = fmaf(di, z.y, dr * z.x);
+        G2 += inc2;
+        T2 = fmaf(t, inc2, T2);
+        G8 = fmaf(di, re, fmaf(-dr, im, G8));
     };
-    int a = 0;
-    for (; a < n; a += kAnchor) {
+    for (int a = 0; a < n; a += kAnchor) {
         float2 x = X, y = Y, z = Z;
         const int cnt = min(kAnchor, n - a);
         for (int i = 0; i < cnt; ++i) {
@@ -171,6 +189,16 @@ __device__ __forceinline__ void jacobian_mwi3_rec_f(const float *th, const Model
         X = xn;
         Z = __fmul2_rn(Z, K2);
     }
+    g[0] += G01.x;
+    g[1] += G01.y;
+    g[2] += G2;
+    g[3] += a0 * r0 * r0 * T01.x;
+    g[4] += a1 * r1 * r1 * T01.y;
+    g[5] += a2 * r2 * r2 * T2;
+    g[6] += a0 * kTwoPiMilli * C01.x;
+    g[7] += a1 * kTwoPiMilli * C01.y;
+    g[8] += G8;
+    return loss;
 }
 
 // One voxel's update: forward model and Jacobian against its staged data row
@@ -257,7 +285,7 @@ __device__ __forceinline__ double fit_voxel(const ModelConst &mc, const FitArgs<
         for (int p = 0; p < P; ++p) g[p] = fma(d, J[p], g[p]);
     };
     if constexpr (KIND == GAC_MODEL_MWI3 && PREC == GAC_PREC_FP32) {
-        if (mc.even) jacobian_mwi3_rec_f(th, mc, visit);  // the same branch for every thread
+        if (mc.even) loss = mwi3_rec_loss_grad_f(th, mc, y, w, fa.loss == GAC_FIT_L1, g);  // same branch for every thread
         else jacobian<KIND, R>(th, mc, visit);
     } else {
         jacobian<KIND, R>(th, mc, visit);
