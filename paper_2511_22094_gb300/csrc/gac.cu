@@ -445,9 +445,22 @@ gac_status plan_launch(const ModelConst &mc, int prec, bool trace, int C, int64_
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, smem);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (per_sm < 1) return fail(GAC_ERR_INVALID_ARG, "kernel does not fit on an SM (smem %zu)", smem);
-    *vb = kBlock / C;
-    *n_tiles = (n_vox + *vb - 1) / *vb;
+    // Voxels per tile: a full block's worth, unless the problem is too small
+    // to give every resident block a full tile; then tiles shrink (in whole
+    // warps of chains) so that the chains spread over all SMs instead of
+    // crowding a few -- a small problem is bound by the latency of one
+    // iteration, which a warp alone on its SM sub-partition runs fastest.
+    // The block's remaining threads stay idle; results do not depend on the
+    // tiling (random numbers are keyed by voxel, chain and iteration).
     const int64_t resident = static_cast<int64_t>(per_sm) * sm_count();
+    const int64_t chains = n_vox * C;
+    int threads = kBlock;
+    if (chains < resident * kBlock) {
+        const int64_t want = (chains + resident - 1) / resident;  // chains per block
+        threads = static_cast<int>(std::min<int64_t>(kBlock, std::max<int64_t>(32, (want + 31) / 32 * 32)));
+    }
+    *vb = std::max(1, threads / C);
+    *n_tiles = (n_vox + *vb - 1) / *vb;
     cfg->grid = static_cast<int>(std::min<int64_t>(*n_tiles, resident));
     cfg->smem = smem;
     return GAC_OK;
