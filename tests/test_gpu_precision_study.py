@@ -104,7 +104,7 @@ def paired_seed_check(runs, pairs, label):
 def test_independent_seed_agreement(gac, orc):
     """The paper's CPU/GPU validation design (Demo 2, Sec. 2.6.2): the
     GPU-minus-CPU disagreement of posterior means under independent random
-    streams is judged against the CPU-minus-CPU disagreement of two
+    streams is measured against the CPU-minus-CPU disagreement of two
     independent CPU runs.  3-pool model at SNR 150, chains started at the
     true parameters (so that the comparison is of posterior samples, not of
     burn-in from different starts)."""

@@ -254,3 +254,21 @@ def test_linear_gaussian_posterior_on_device(gac, orc):
     assert np.all(np.abs(m - mu) < 5 * se), (m, mu, se)
     var = np.array([np.mean((s[:, p] - mu[p]) ** 2) for p in range(2)])
     assert np.allclose(var, np.diag(cov), rtol=0.03)
+
+
+def test_small_and_full_tiles_give_the_same_bits(gac, orc):
+    """A volume too small to fill every resident block runs in tiles of one
+    warp of chains; a large one in full blocks.  The random numbers depend
+    only on (seed, t, voxel, chain), so the first voxels of a large run equal
+    the same voxels run alone, bit for bit."""
+    w = W.MWI3_1M
+    mid = _register(gac, w)
+    n_big, n_small = 60_000, 700  # 240,000 chains fill full blocks; 2,800 do not
+    th, sig, y = make_voxels(orc, w, 0, n_big)
+    kw = dict(iterations=300, burnin=100, thin=20, n_chains=4, seed=5)
+    big = gac.run_host(mid, y, sig, **kw)
+    small = gac.run_host(mid, y[:n_small], sig[:n_small], **kw)
+    tail = gac.run_host(mid, y[-n_small:], sig[-n_small:], voxel_base=n_big - n_small, **kw)
+    for k in ("samples", "accept_rate", "mean", "std"):
+        np.testing.assert_array_equal(small[k], big[k][..., :n_small], err_msg=k)
+        np.testing.assert_array_equal(tail[k], big[k][..., -n_small:], err_msg=k)
