@@ -91,7 +91,9 @@ def test_cancel_and_poll(gac, orc):
     th, sig, y = make_voxels(orc, w, 0, 20_000)
     srv = gac.gac_server_create(8 << 30, 8)
     try:
-        long_job = gac.gac_server_submit(srv, mid, y, y.shape[0], sig, 0.0, gac.make_opts(5000, 500, 100, 4, 1))
+        # long enough (~0.6 s alone) that no single round can take it to the end,
+        # so the cancel always lands before its last round is queued
+        long_job = gac.gac_server_submit(srv, mid, y, y.shape[0], sig, 0.0, gac.make_opts(200_000, 2000, 1000, 4, 1))
         short = gac.gac_server_submit(srv, mid, y[:100], 100, sig[:100], 0.0, gac.make_opts(200, 20, 10, 1, 2))
         gac.gac_server_cancel(srv, long_job)
         gac.gac_server_wait(srv, short, 120.0, {})
@@ -155,5 +157,39 @@ def test_cancel_while_rounds_are_in_flight(gac, orc):
         for jid in big[:2]:
             with pytest.raises(gac.GacError):
                 gac.gac_server_wait(srv, jid, 60.0, {})
+    finally:
+        gac.gac_server_destroy(srv)
+
+
+def test_large_job_is_not_starved_by_small_arrivals(gac, orc):
+    """A stream of small jobs, each finishing within one round, keeps arriving
+    while a large job runs: small jobs take at most half of a round, so the
+    large job still finishes within a few times its time alone."""
+    import time
+    w = W.MWI3_1M
+    mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
+    th, sig, y = make_voxels(orc, w, 0, 60_000)
+    big_opts = gac.make_opts(6000, 600, 100, 4, 1)
+    t0 = time.perf_counter()
+    gac.run_host(mid, y, sig, iterations=6000, burnin=600, thin=100, n_chains=4, seed=1, want_samples=False)
+    alone = time.perf_counter() - t0
+    srv = gac.gac_server_create(8 << 30, 64)
+    try:
+        big = gac.gac_server_submit(srv, mid, y, y.shape[0], sig, 0.0, big_opts)
+        small = []
+        t_start = time.perf_counter()
+        while True:
+            done, lat = gac.gac_server_poll(srv, big)
+            if done:
+                break
+            small.append(gac.gac_server_submit(srv, mid, y[:500], 500, sig[:500], 0.0,
+                                               gac.make_opts(400, 40, 20, 2, 100 + len(small))))
+            time.sleep(0.002)
+            assert time.perf_counter() - t_start < 60.0
+        for jid in small:
+            gac.gac_server_wait(srv, jid, 60.0, {})
+        print(f"large job alone {alone:.3f} s, in the stream {lat:.3f} s, {len(small)} small jobs")
+        assert lat < 5.0 * alone + 1.0
+        assert len(small) > 10
     finally:
         gac.gac_server_destroy(srv)
