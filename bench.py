@@ -461,8 +461,13 @@ def run_ours(args, w):
                samples=torch.empty((S, C, P, N), dtype=torch.float32, device=dev),
                accept_rate=torch.empty((C, N), dtype=torch.float32, device=dev),
                nonfinite=torch.empty((C, N), dtype=torch.int32, device=dev))
+    if args.rhat and args.sampler == "mh":
+        out["rhat"] = torch.empty((P, N), dtype=torch.float64, device=dev)
+        out["step_scale"] = torch.empty((C, N), dtype=torch.float32, device=dev)
     prec = {"mixed": gac.PREC_MIXED, "fp32": gac.PREC_FP32, "fp64": gac.PREC_FP64}[args.precision]
-    opts = gac.make_opts(w.iterations, w.burnin, w.thin, C, w.mcmc_seed, voxel_base=base, precision=prec)
+    opts = gac.make_opts(w.iterations, w.burnin, w.thin, C, w.mcmc_seed, voxel_base=base, precision=prec,
+                         moments_mode=gac.MOMENTS_ALL_POSTBURNIN if args.moments == "all" else gac.MOMENTS_THINNED,
+                         adapt_window=args.adapt_window, adapt_target=args.adapt_target if args.adapt_window else 0.0)
 
     def step():
         if args.sampler == "ensemble":
@@ -550,7 +555,8 @@ def run_ours(args, w):
             "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
             "peak_basis": f"{sms} SMs x {per_clk:.2f}/clk ({rate_basis}) x {f_max / 1e6:.0f} MHz (max SM clock)",
             "frac_at_sampled_clock": (achieved / peak * f_max / f_med) if f_med else None,
-            "traffic": meas.get("traffic_bytes") if N == W.WORKLOADS[base_name].n_vox else None,
+            "traffic": (meas.get("traffic_bytes") if N == W.WORKLOADS[base_name].n_vox and not args.rhat
+                        and not args.adapt_window and args.moments == "thinned" else None),
             "kernel_ms": kernel_s * 1e3}
     if meas.get("warp_instr"):
         issue_peak = sms * ISSUE_PER_CLK_SM * f_max
@@ -566,6 +572,8 @@ def run_ours(args, w):
                        ("n_walkers" if args.sampler == "ensemble" else "n_chains"): C, "iterations": w.iterations,
                        "burnin": w.burnin, "thin": w.thin, "samples_stored": True,
                        "precision": args.precision, "parallelism": f"voxel-shard x{world}",
+                       "adapt_window": args.adapt_window, "moments": args.moments,
+                       "rhat_and_step_scale": bool(args.rhat and args.sampler == "mh"),
                        "l2": f"inputs {y.numel() * 4 / 1e6:.0f} MB + samples {S * C * P * N * 4 / 1e9:.1f} GB written per step > 129 MB L2"},
             "roofline": roof, "pipe_rates_per_sm_clk": rates, "clocks": clocks, "gpu_launches": args.steps,
             "wall_s": t_wall}
@@ -710,6 +718,11 @@ def main():
     ap.add_argument("--serving-saturated", action="store_true")
     ap.add_argument("--fit", action="store_true", help="whole-volume Adam fit instead of MCMC")
     ap.add_argument("--fit-iterations", type=int, default=100)
+    ap.add_argument("--adapt-window", type=int, default=0, help="burn-in step adaptation window (0: off)")
+    ap.add_argument("--adapt-target", type=float, default=0.3, help="adaptation's target acceptance rate")
+    ap.add_argument("--moments", choices=("thinned", "all"), default="thinned",
+                    help="moments over the thinned samples or over every post-burn-in state")
+    ap.add_argument("--rhat", action="store_true", help="also write R-hat and the final step multipliers")
     ap.add_argument("--oracle-study", action="store_true",
                     help="time the CPU oracle on all cores and on one core for every workload")
     args = ap.parse_args()

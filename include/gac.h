@@ -100,7 +100,12 @@ gac_status gac_model_info(int model_id, int *n_par, int *n_meas);
  * FP32, plain sums.  FP64: everything in FP64. */
 enum { GAC_PREC_MIXED = 0, GAC_PREC_FP32 = 1, GAC_PREC_FP64 = 2 };
 /* What the posterior moments average: the thinned samples (default, as the
- * paper's output) or every post-burn-in state. */
+ * paper's output) or every post-burn-in state.  On the MIXED path the latter
+ * sums the states of each block of 64 consecutive post-burn-in iterations in
+ * FP32, as deviations from the block's first state, and merges each block
+ * into the FP64 accumulators (pairwise update of count, mean and M2); the
+ * result agrees with a per-state FP64 update to the FP32 rounding of the
+ * block sums (~1e-7 of the posterior SD). */
 enum { GAC_MOMENTS_THINNED = 0, GAC_MOMENTS_ALL_POSTBURNIN = 1 };
 
 typedef struct {
@@ -310,10 +315,12 @@ gac_status gac_fit_run(int model_id, const void *data, const uint8_t *mask, cons
  * GPU where it is loaded, until the process exits.
  *   - Every array (data, sigma, x0 and the result buffers) must be device
  *     memory; host pointers are rejected with GAC_ERR_INVALID_ARG.
- *   - The chain state needs about (20 P + 20) bytes per chain (P parameters):
- *     n_vox * n_chains must stay within GAC_NOALLOC_STATE_BYTES of it (e.g.
- *     ~335,000 chains of the 9-parameter model); larger runs are rejected
- *     with GAC_ERR_INVALID_ARG and a message giving the limit.
+ *   - The chain state needs about (20 P + 20) bytes per chain (P parameters),
+ *     32 P + 20 with moments over every post-burn-in state (the FP32 block
+ *     partials of that mode are carried between slices): n_vox * n_chains
+ *     must stay within GAC_NOALLOC_STATE_BYTES of it (e.g. ~335,000 chains
+ *     of the 9-parameter model); larger runs are rejected with
+ *     GAC_ERR_INVALID_ARG and a message giving the limit.
  *   - precision must be GAC_PREC_MIXED and trace_n_vox 0; results equal
  *     gac_mcmc_run's for the same inputs.
  *   - The first call on a device looks up the array's device address (a

@@ -399,9 +399,10 @@ int row_stride_for(int kind, int M) {
     return M | 1;
 }
 
-size_t smem_bytes_for(int kind, int prec, int C, int M) {
+size_t smem_bytes_for(int kind, int prec, int C, int M, int moments_mode) {
     const size_t w = (prec == GAC_PREC_FP32) ? sizeof(float) : sizeof(double);
-    return tile_smem_bytes(model_n_par(kind), w, kBlock / C, row_stride_for(kind, M), true);
+    const bool blocked = prec == GAC_PREC_MIXED && moments_mode == GAC_MOMENTS_ALL_POSTBURNIN;
+    return tile_smem_bytes(model_n_par(kind), w, kBlock / C, row_stride_for(kind, M), true, blocked);
 }
 
 const void *mh_kernel_ptr(int kind, int prec, bool trace) {
@@ -429,11 +430,11 @@ cudaError_t launch_mh(int kind, int prec, bool trace, const ModelConst &mc, cons
 
 // Grid: one block per tile of voxels, capped at the number of blocks that
 // are resident at once (the kernel strides over the remaining tiles).
-gac_status plan_launch(const ModelConst &mc, int prec, bool trace, int C, int64_t n_vox,
+gac_status plan_launch(const ModelConst &mc, int prec, bool trace, int C, int64_t n_vox, int moments_mode,
                        LaunchCfg *cfg, int64_t *n_tiles, int *vb) {
     const void *fn = mh_kernel_ptr(mc.kind, prec, trace);
     if (!fn) return fail(GAC_ERR_INVALID_ARG, "no kernel for kind %d precision %d", mc.kind, prec);
-    const size_t smem = smem_bytes_for(mc.kind, prec, C, mc.n_meas);
+    const size_t smem = smem_bytes_for(mc.kind, prec, C, mc.n_meas, moments_mode);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
@@ -690,7 +691,8 @@ gac_status gac_mcmc_run(int model_id, const void *data, int64_t n_vox, const flo
     LaunchCfg cfg;
     int64_t n_tiles = 0;
     int vb = 0;
-    if ((st = plan_launch(mc, o->precision, trace, C, n_vox, &cfg, &n_tiles, &vb)) != GAC_OK) return st;
+    if ((st = plan_launch(mc, o->precision, trace, C, n_vox, o->moments_mode, &cfg, &n_tiles, &vb)) != GAC_OK)
+        return st;
     cfg.stream = s;
 
     RunArgs ra;

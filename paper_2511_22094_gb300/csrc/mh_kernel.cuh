@@ -97,7 +97,17 @@ struct SliceState {
     void *wf_mean;   // [P][N*C] of W
     void *wf_m2;     // [P][N*C] of W
     int32_t *adapt;  // [2][N*C]: adaptation exponent e, accepted count at the window start
+    float *blk;      // [3P][N*C]: MIXED all-post-burn-in block partials (sum d, sum d^2, reference)
 };
+
+// MIXED path, moments over every post-burn-in state: the states of blocks of
+// kMomBlock consecutive post-burn-in iterations (aligned to t - B = 0, so the
+// blocks do not depend on slicing) are summed in FP32 as deviations d = x -
+// x_ref from the block's first state; each full block, and the last partial
+// one, is merged into the FP64 Welford state with Chan et al.'s pairwise
+// formula.  One FP64 merge per block instead of an FP64 update per iteration:
+// FP64 issues at 1/73 of the FP32 rate on this part.
+constexpr int kMomBlock = 64;
 
 // Host: the adaptation fields of RunArgs.  a > target W <=> a > floor(target W)
 // and a < target W <=> a < ceil(target W) for integer a.
@@ -173,11 +183,13 @@ __device__ __forceinline__ bool accept_step(typename PrecTraits<PREC>::R Lp,
 }
 
 // Shared-memory bytes of one block: Welford accumulators (one-launch driver
-// only) + the measurement tile.
+// only) + the measurement tile + the MIXED all-post-burn-in block partials
+// ([3P][kBlock] floats, when blocked_moments).
 __host__ __device__ inline size_t tile_smem_bytes(int P, size_t w_bytes, int VB, int row_stride,
-                                                  bool welford_in_smem) {
+                                                  bool welford_in_smem, bool blocked_moments = false) {
     return (welford_in_smem ? 2 * static_cast<size_t>(P) * kBlock * w_bytes : 0) +
-           static_cast<size_t>(VB) * row_stride * sizeof(float);
+           static_cast<size_t>(VB) * row_stride * sizeof(float) +
+           (blocked_moments ? 3 * static_cast<size_t>(P) * kBlock * sizeof(float) : 0);
 }
 
 // Pools one parameter of C chains that each hold n values, from their
@@ -259,6 +271,8 @@ __device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra
 
     const int64_t left = ra.n_vox - v0;
     const int nv = left < VB ? static_cast<int>(left) : VB;
+    // MIXED all-post-burn-in block partials: s1 [P][kBlock], s2, reference
+    float *const bs = ytile + VB * ra.row_stride;
 
     // a1: stage measurements of voxels [v0, v0 + nv) (and the model's
     // table) in shared memory
@@ -342,6 +356,20 @@ __device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra
         // moments taken so far, and the next iteration on the thinning grid
         const bool all_mode = ra.moments_mode == GAC_MOMENTS_ALL_POSTBURNIN;
         int n_mom = all_mode ? max(t_begin - ra.B, 0) : (t_begin > ra.B ? (t_begin - ra.B) / ra.T : 0);
+        // blocked accumulation (MIXED, all states): states in the open block,
+        // n_mom = states already merged into the FP64 Welford state
+        constexpr bool kBlocked = PREC == GAC_PREC_MIXED;
+        int blk_n = 0;
+        if constexpr (kBlocked) {
+            if (all_mode) {
+                blk_n = n_mom % kMomBlock;
+                n_mom -= blk_n;
+                if constexpr (SLICED) {
+                    if (blk_n > 0)
+                        for (int k = 0; k < 3 * P; ++k) bs[k * kBlock + tid] = ss.blk[k * nchains + ch];
+                }
+            }
+        }
         int to_thin = t_begin < ra.B ? ra.B + ra.T : ra.B + ((t_begin - ra.B) / ra.T + 1) * ra.T;
         // next window end of the burn-in adaptation (INT_MAX: none left)
         const int W_ad = ra.adapt_window;
@@ -415,7 +443,44 @@ __device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra
                         for (int p = 0; p < P; ++p) dst[p * ra.n_vox] = static_cast<float>(th[p]);
                     }
                 }
-                if (all_mode ? (t > ra.B) : on_grid) {
+                if (kBlocked && all_mode) {
+                    if (t > ra.B) {
+                        float *s1 = bs + tid, *s2 = bs + P * kBlock + tid, *ref = bs + 2 * P * kBlock + tid;
+                        if (blk_n == 0) {  // a block's first state is its reference (the same t for every thread)
+#pragma unroll
+                            for (int p = 0; p < P; ++p) {
+                                ref[p * kBlock] = static_cast<float>(th[p]);
+                                s1[p * kBlock] = 0.0f;
+                                s2[p * kBlock] = 0.0f;
+                            }
+                        } else {
+#pragma unroll
+                            for (int p = 0; p < P; ++p) {
+                                const float d = static_cast<float>(th[p]) - ref[p * kBlock];
+                                s1[p * kBlock] += d;
+                                s2[p * kBlock] = fmaf(d, d, s2[p * kBlock]);
+                            }
+                        }
+                        if (++blk_n == kMomBlock || t == ra.I) {
+                            // merge the block (n_b states, mean ref + s1/n_b, M2 = s2 - s1^2/n_b)
+                            // into the n_mom states of the FP64 Welford state
+                            const double nb = blk_n, nn = static_cast<double>(n_mom) + nb;
+                            const double inv_nb = 1.0 / nb, w_b = nb / nn, cross = static_cast<double>(n_mom) * w_b;
+#pragma unroll
+                            for (int p = 0; p < P; ++p) {
+                                const double a = s1[p * kBlock];
+                                const double mb = static_cast<double>(ref[p * kBlock]) + a * inv_nb;
+                                const double m2b = fma(-a, a * inv_nb, static_cast<double>(s2[p * kBlock]));
+                                const double m = static_cast<double>(wf_mean[p * wf_stride + wf_idx]);
+                                const double delta = mb - m;
+                                wf_mean[p * wf_stride + wf_idx] = static_cast<W>(fma(delta, w_b, m));
+                                wf_m2[p * wf_stride + wf_idx] += static_cast<W>(fma(delta * delta, cross, m2b));
+                            }
+                            n_mom += blk_n;
+                            blk_n = 0;
+                        }
+                    }
+                } else if (all_mode ? (t > ra.B) : on_grid) {
                     ++n_mom;
                     const W inv_n = W(1) / W(n_mom);
 #pragma unroll
@@ -450,6 +515,10 @@ __device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra
             ss.n_bad[ch] = n_bad;
             ss.adapt[ch] = ad_e;
             ss.adapt[nchains + ch] = ad_acc0;
+            if constexpr (kBlocked) {
+                if (all_mode && blk_n > 0)
+                    for (int k = 0; k < 3 * P; ++k) ss.blk[k * nchains + ch] = bs[k * kBlock + tid];
+            }
         }
     }
 

@@ -99,7 +99,10 @@ extern "C" gac_status gac_mcmc_run_noalloc(int model_id, const void *data, int64
     const size_t off_L = up256(P * NC * 4), off_acc = off_L + up256(NC * 4), off_bad = off_acc + up256(NC * 4);
     const size_t off_ad = off_bad + up256(NC * 4);
     const size_t off_wm = off_ad + up256(2 * NC * 4), off_w2 = off_wm + up256(P * NC * 8);
-    const size_t need = off_w2 + up256(P * NC * 8);
+    // all-post-burn-in moments: the block partials of the FP32 accumulation (3P floats per chain)
+    const bool blocked = o->moments_mode == GAC_MOMENTS_ALL_POSTBURNIN;
+    const size_t off_blk = off_w2 + up256(P * NC * 8);
+    const size_t need = off_blk + (blocked ? up256(3 * P * NC * 4) : 0);
     if (need > GAC_NOALLOC_STATE_BYTES)
         return fail(GAC_ERR_INVALID_ARG,
                     "%lld voxels x %d chains need %zu bytes of chain state; this entry point holds at most %zu",
@@ -124,6 +127,7 @@ extern "C" gac_status gac_mcmc_run_noalloc(int model_id, const void *data, int64
     ss.adapt = reinterpret_cast<int32_t *>(b + off_ad);
     ss.wf_mean = b + off_wm;
     ss.wf_m2 = b + off_w2;
+    ss.blk = blocked ? reinterpret_cast<float *>(b + off_blk) : nullptr;
 
     RunArgs ra;
     std::memset(&ra, 0, sizeof ra);
@@ -155,7 +159,7 @@ extern "C" gac_status gac_mcmc_run_noalloc(int model_id, const void *data, int64
     ra.step_scale = out->step_scale;
 
     const void *fn = noalloc_fn(mc.kind);
-    const size_t smem = tile_smem_bytes(mc.n_par, 8, ra.vox_per_block, ra.row_stride, false);
+    const size_t smem = tile_smem_bytes(mc.n_par, 8, ra.vox_per_block, ra.row_stride, false, blocked);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);

@@ -213,8 +213,8 @@ struct Job {
 
 // Layout of one job's device block.
 struct JobLayout {
-    size_t data, sigma, theta, L, n_acc, n_bad, adapt, wf_mean, wf_m2, mean, std, acc, bad, rhat, scale, samples,
-        total;
+    size_t data, sigma, theta, L, n_acc, n_bad, adapt, wf_mean, wf_m2, blk, mean, std, acc, bad, rhat, scale,
+        samples, total;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
@@ -235,6 +235,7 @@ static JobLayout job_layout(const ModelConst &mc, int64_t n_vox, const gac_mcmc_
     l.adapt = take(2 * N * C * 4);
     l.wf_mean = take(P * N * C * 8);
     l.wf_m2 = take(P * N * C * 8);
+    l.blk = take(o.moments_mode == GAC_MOMENTS_ALL_POSTBURNIN ? 3 * P * N * C * 4 : 0);
     l.mean = take(P * N * 8);
     l.std = take(P * N * 8);
     l.acc = take(C * N * 4);
@@ -327,7 +328,8 @@ gac_status gac_server::init_gpu() {
         if ((e = cudaStreamCreateWithFlags(&s_kind[i], cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "stream");
     // the largest measurement tile any job can need (C = 1, 256 voxels, 64
     // complex echoes); each round launches with its own jobs' largest tile
-    smem = static_cast<size_t>(kBlock) * row_stride_for(GAC_MODEL_MWI3, 2 * GAC_MAX_ACQ) * sizeof(float);
+    smem = static_cast<size_t>(kBlock) * row_stride_for(GAC_MODEL_MWI3, 2 * GAC_MAX_ACQ) * sizeof(float) +
+           3 * static_cast<size_t>(GAC_MAX_PAR) * kBlock * sizeof(float);  // + all-post-burn-in block partials
     for (int i = 0; i < kKinds; ++i) {
         e = cudaFuncSetAttribute(serve_fn(i), cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return cuda_fail(e, "serve kernel smem");
@@ -453,6 +455,7 @@ gac_status gac_server::admit_locked(int max_jobs) {
         ss.adapt = reinterpret_cast<int32_t *>(b + l.adapt);
         ss.wf_mean = b + l.wf_mean;
         ss.wf_m2 = b + l.wf_m2;
+        ss.blk = j.opts.moments_mode == GAC_MOMENTS_ALL_POSTBURNIN ? reinterpret_cast<float *>(b + l.blk) : nullptr;
         j.desc.mc = j.mc;
         in_use += j.bytes;
         j.state = JobState::Uploading;
@@ -595,7 +598,9 @@ gac_status gac_server::run_round(bool *launched) {
             Job &j = *run[ji];
             if (kind_slot(j.mc.kind) != slot) continue;
             const RunArgs &ra = j.desc.ra;
-            smem_kind[slot] = std::max(smem_kind[slot], tile_smem_bytes(j.mc.n_par, 8, ra.vox_per_block, ra.row_stride, false));
+            smem_kind[slot] = std::max(smem_kind[slot],
+                                       tile_smem_bytes(j.mc.n_par, 8, ra.vox_per_block, ra.row_stride, false,
+                                                       ra.moments_mode == GAC_MOMENTS_ALL_POSTBURNIN));
             work += static_cast<int64_t>(t_end[ji] - j.t_done) * j.n_vox * j.opts.n_chains;
             RoundJob &r = h_items[b][k++];
             r.job = static_cast<int32_t>(ji);

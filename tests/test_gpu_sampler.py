@@ -272,3 +272,24 @@ def test_small_and_full_tiles_give_the_same_bits(gac, orc):
     for k in ("samples", "accept_rate", "mean", "std"):
         np.testing.assert_array_equal(small[k], big[k][..., :n_small], err_msg=k)
         np.testing.assert_array_equal(tail[k], big[k][..., -n_small:], err_msg=k)
+
+
+def test_mixed_all_postburnin_moments_blocked(gac, orc):
+    """MIXED moments over every post-burn-in state come from FP32 sums over
+    blocks of 64 states merged into the FP64 Welford state; with thinning 1 the
+    thinned mode's per-state FP64 Welford sees the same states of the same
+    chains, so the two must agree to the FP32 rounding of the block sums."""
+    w = W.MWI3_1M
+    mid = _register(gac, w)
+    th, sig, y = make_voxels(orc, w, 0, 500)
+    kw = dict(iterations=1300, burnin=300, thin=1, n_chains=4, seed=17)  # 15 full blocks + 40 states
+    per_state = gac.run_host(mid, y, sig, moments_mode=0, **kw)
+    blocked = gac.run_host(mid, y, sig, moments_mode=1, want_samples=False, **kw)
+    np.testing.assert_array_equal(blocked["accept_rate"], per_state["accept_rate"])
+    sd = per_state["std"]
+    ok = sd > 0
+    dm = np.abs(blocked["mean"] - per_state["mean"])[ok] / sd[ok]
+    ds = np.abs(blocked["std"] - sd)[ok] / sd[ok]
+    print(f"blocked vs per-state moments: |dmean|/SD max {dm.max():.2e}, |dSD|/SD max {ds.max():.2e}")
+    assert dm.max() <= 1e-5 and ds.max() <= 1e-4
+    assert np.all(blocked["std"][~ok] <= 1e-6)

@@ -193,3 +193,27 @@ def test_large_job_is_not_starved_by_small_arrivals(gac, orc):
         assert len(small) > 10
     finally:
         gac.gac_server_destroy(srv)
+
+
+def test_all_postburnin_moments_jobs_equal_alone(gac, orc):
+    """Moments over every post-burn-in state: the FP32 block partials carried
+    between the server's slices give the same moments as one launch."""
+    jobs = []
+    for i, (w, n, C, I, B) in enumerate([(W.MWI3_1M, 3000, 4, 900, 100), (W.SMT_1P5M, 4000, 2, 1100, 150),
+                                         (W.MONOEXP_4K, 2000, 1, 800, 80)]):
+        mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
+        th, sig, y = make_voxels(orc, w, 700 * i, n)
+        jobs.append((mid, y, sig, gac.make_opts(I, B, 10, C, 300 + i, moments_mode=1)))
+    srv = gac.gac_server_create(8 << 30, 64)
+    try:
+        ids = [gac.gac_server_submit(srv, mid, y, y.shape[0], sig, 0.0, opts) for (mid, y, sig, opts) in jobs]
+        for jid, (mid, y, sig, opts) in zip(ids, jobs):
+            ref = gac.run_host(mid, y, sig, iterations=opts.iterations, burnin=opts.burnin, thin=opts.thin,
+                               n_chains=opts.n_chains, seed=opts.seed, moments_mode=1, want_samples=False)
+            out = {k: np.empty_like(ref[k]) for k in ("mean", "std", "accept_rate")}
+            gac.gac_server_wait(srv, jid, 300.0, out)
+            np.testing.assert_array_equal(out["accept_rate"], ref["accept_rate"])
+            np.testing.assert_allclose(out["mean"], ref["mean"], rtol=1e-12, atol=0)
+            np.testing.assert_allclose(out["std"], ref["std"], rtol=1e-9, atol=0)
+    finally:
+        gac.gac_server_destroy(srv)

@@ -8,7 +8,9 @@ those of the ordinary entry point, gac_mcmc_run, within the tolerances of the
 serving tests (samples, acceptance rates and counters identical; means to
 1e-12 and SDs to 1e-9 relative), on calls in a row -- each call finds the
 previous call's contents in the shared array -- including one whose burn-in
-step adaptation is carried across slices.  This file is collected
+step adaptation is carried across slices, and ones whose moments over every
+post-burn-in state carry their FP32 block partials across slices.  This file
+is collected
 last so that a failing run stopped at the first failure has already run
 every other test.
 """
@@ -44,18 +46,23 @@ def _device_run(gac, fn, mid, y, sig, opts, P, slice_iters=None):
     return {k: v.cpu().numpy() for k, v in out.items()}
 
 
-CALLS = [  # two different jobs in a row through the same array
-    (W.MWI3_1M, 1500, 4, 700, 70, 10, 128, 0),
-    (W.MONOEXP_4K, 3000, 1, 900, 100, 5, 64, 0),
-    (W.SMT_1P5M, 2000, 4, 500, 200, 10, 37, 20),  # burn-in adaptation resumed across slices
+CALLS = [  # different jobs in a row through the same array (..., adaptation window, moments mode)
+    (W.MWI3_1M, 1500, 4, 700, 70, 10, 128, 0, 0),
+    (W.MONOEXP_4K, 3000, 1, 900, 100, 5, 64, 0, 0),
+    (W.SMT_1P5M, 2000, 4, 500, 200, 10, 37, 20, 0),  # burn-in adaptation resumed across slices
+    # moments over every post-burn-in state: blocks of 64 states whose FP32
+    # partial sums are carried across slices of 45 iterations
+    (W.MWI3_1M, 1200, 4, 620, 60, 10, 45, 0, 1),
+    (W.SMT_1P5M, 1000, 2, 700, 100, 10, 53, 25, 1),
 ]
 
 
 def test_noalloc_matches_gac_mcmc_run_on_two_calls(gac, orc):
-    for i, (w, n, C, I, B, T, slice_iters, Wa) in enumerate(CALLS):
+    for i, (w, n, C, I, B, T, slice_iters, Wa, mm) in enumerate(CALLS):
         mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
         th, sig, y = make_voxels(orc, w, 500 * i, n)
-        opts = gac.make_opts(I, B, T, C, 4242 + i, adapt_window=Wa, adapt_target=0.3 if Wa else 0.0)
+        opts = gac.make_opts(I, B, T, C, 4242 + i, adapt_window=Wa, adapt_target=0.3 if Wa else 0.0,
+                             moments_mode=mm)
         ref = _device_run(gac, gac.gac_mcmc_run, mid, y, sig, opts, w.n_par)
         got = _device_run(gac, gac.gac_mcmc_run_noalloc, mid, y, sig, opts, w.n_par, slice_iters)
         for k in ("samples", "accept_rate", "nonfinite", "step_scale"):
