@@ -129,7 +129,8 @@ extern "C" gac_status gac_ensemble_run(int model_id, const void *data, int64_t n
 
     const bool trace = o->trace_n_vox > 0;
     const size_t rb = o->precision == GAC_PREC_FP64 ? 8 : 4, wb = o->precision == GAC_PREC_FP32 ? 4 : 8;
-    const size_t smem = ens_smem_bytes(P, rb, wb, ra.vox_per_block, L, ra.row_stride);
+    const size_t smem = ens_smem_bytes(P, rb, wb, ra.vox_per_block, L, ra.row_stride,
+                                       o->precision == GAC_PREC_MIXED && o->moments_mode == GAC_MOMENTS_ALL_POSTBURNIN);
     const void *fn = nullptr;
     ens_dispatch(mc.kind, o->precision, trace, 0, 0, s, mc, ra, ea, &fn);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));

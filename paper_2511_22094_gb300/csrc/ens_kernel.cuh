@@ -29,11 +29,12 @@ struct EnsArgs {
 };
 
 __host__ __device__ inline size_t ens_smem_bytes(int P, size_t r_bytes, size_t w_bytes, int VB, int L,
-                                                 int row_stride) {
+                                                 int row_stride, bool blocked_moments = false) {
     return 2 * static_cast<size_t>(P) * VB * L * w_bytes  // Welford per walker
            + static_cast<size_t>(VB) * L * P * r_bytes     // positions
            + static_cast<size_t>(VB) * L * r_bytes         // log-likelihoods
-           + static_cast<size_t>(VB) * row_stride * sizeof(float);
+           + static_cast<size_t>(VB) * row_stride * sizeof(float)
+           + (blocked_moments ? 3 * static_cast<size_t>(P) * VB * L * sizeof(float) : 0);  // block partials
 }
 
 // Blocks of 128 threads (5 voxels of 25 threads at 50 walkers), 4 per SM:
@@ -55,6 +56,9 @@ __global__ void __launch_bounds__(kEnsBlock, 4) ens_kernel(const ModelConst mc, 
     R *X = reinterpret_cast<R *>(wf_m2 + P * nw);    // [VB][L][P]
     R *LL = X + nw * P;                              // [VB][L]
     float *ytile = reinterpret_cast<float *>(LL + nw);
+    // MIXED, moments over every post-burn-in state: FP32 block partials per
+    // walker, s1 [P][nw], s2, reference (the MH kernel's blocked accumulation)
+    float *const bs = ytile + VB * ra.row_stride;
 
     const int tid = threadIdx.x;
     const int lv = tid / H;
@@ -124,7 +128,9 @@ __global__ void __launch_bounds__(kEnsBlock, 4) ens_kernel(const ModelConst mc, 
             }
         }
         const bool all_mode = ra.moments_mode == GAC_MOMENTS_ALL_POSTBURNIN;
-        int n_mom = 0;
+        constexpr bool kBlocked = PREC == GAC_PREC_MIXED;
+        const bool blocked = kBlocked && all_mode;
+        int n_mom = 0, blk_n = 0;
         int to_thin = ra.B + ra.T;
         for (int t = 1; t <= ra.I; ++t) {
 #pragma unroll
@@ -206,7 +212,7 @@ __global__ void __launch_bounds__(kEnsBlock, 4) ens_kernel(const ModelConst mc, 
             if (on_grid) to_thin += ra.T;
             const bool take = all_mode ? (t > ra.B) : on_grid;
             if (active && (on_grid || take)) {
-                if (take) ++n_mom;
+                if (take && !blocked) ++n_mom;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int k = h * H + i;
@@ -217,7 +223,24 @@ __global__ void __launch_bounds__(kEnsBlock, 4) ens_kernel(const ModelConst mc, 
 #pragma unroll
                         for (int p = 0; p < P; ++p) dst[p * ra.n_vox] = static_cast<float>(xk[p]);
                     }
-                    if (take) {
+                    if (take && blocked) {
+                        float *s1 = bs + lv * L + k, *s2 = s1 + P * nw, *ref = s2 + P * nw;
+                        if (blk_n == 0) {  // the block's first state is its reference
+#pragma unroll
+                            for (int p = 0; p < P; ++p) {
+                                ref[p * nw] = static_cast<float>(xk[p]);
+                                s1[p * nw] = 0.0f;
+                                s2[p * nw] = 0.0f;
+                            }
+                        } else {
+#pragma unroll
+                            for (int p = 0; p < P; ++p) {
+                                const float d = static_cast<float>(xk[p]) - ref[p * nw];
+                                s1[p * nw] += d;
+                                s2[p * nw] = fmaf(d, d, s2[p * nw]);
+                            }
+                        }
+                    } else if (take) {
                         const W inv_n = W(1) / W(n_mom);
 #pragma unroll
                         for (int p = 0; p < P; ++p) {
@@ -231,6 +254,31 @@ __global__ void __launch_bounds__(kEnsBlock, 4) ens_kernel(const ModelConst mc, 
                         }
                     }
                 }
+            }
+            // a full block (or the run's last states) merges into the FP64 Welford state
+            if (blocked && t > ra.B && (++blk_n == kMomBlock || t == ra.I)) {
+                if (active) {
+                    const double nb = blk_n, nn = static_cast<double>(n_mom) + nb;
+                    const double inv_nb = 1.0 / nb, w_b = nb / nn, cross = static_cast<double>(n_mom) * w_b;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int k = h * H + i;
+                        const float *s1 = bs + lv * L + k, *s2 = s1 + P * nw, *ref = s2 + P * nw;
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            const int q = p * nw + lv * L + k;
+                            const double a = s1[p * nw];
+                            const double mb = static_cast<double>(ref[p * nw]) + a * inv_nb;
+                            const double m2b = fma(-a, a * inv_nb, static_cast<double>(s2[p * nw]));
+                            const double m = static_cast<double>(wf_mean[q]);
+                            const double delta = mb - m;
+                            wf_mean[q] = static_cast<W>(fma(delta, w_b, m));
+                            wf_m2[q] += static_cast<W>(fma(delta * delta, cross, m2b));
+                        }
+                    }
+                }
+                n_mom += blk_n;
+                blk_n = 0;
             }
         }
         if (active) {

@@ -157,3 +157,22 @@ def test_ensemble_linear_gaussian_posterior_on_device(gac, orc):
     assert np.all(np.abs(m - mu) < 5 * se), (m, mu, se)
     var = np.array([np.mean((s[:, :, p] - mu[p]) ** 2) for p in range(2)])
     assert np.allclose(var, np.diag(cov), rtol=0.04)
+
+
+def test_ensemble_mixed_all_postburnin_moments_blocked(gac, orc):
+    """MIXED ensemble moments over every post-burn-in state use the blocked
+    FP32 accumulation; with thinning 1 the thinned mode's per-state FP64
+    Welford sees the same walkers, so the two agree to FP32 rounding."""
+    w = W.SMT_1P5M
+    mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
+    th, sig, y = make_voxels(orc, w, 0, 200)
+    kw = dict(iterations=900, burnin=100, thin=1, n_walkers=20, seed=8)  # 12 full blocks + 32 states
+    per_state = gac.run_ensemble_host(mid, y, sig, moments_mode=0, **kw)
+    blocked = gac.run_ensemble_host(mid, y, sig, moments_mode=1, want_samples=False, **kw)
+    np.testing.assert_array_equal(blocked["accept_rate"], per_state["accept_rate"])
+    sd = per_state["std"]
+    ok = sd > 0
+    dm = np.abs(blocked["mean"] - per_state["mean"])[ok] / sd[ok]
+    ds = np.abs(blocked["std"] - sd)[ok] / sd[ok]
+    print(f"ensemble blocked vs per-state moments: |dmean|/SD max {dm.max():.2e}, |dSD|/SD max {ds.max():.2e}")
+    assert dm.max() <= 1e-5 and ds.max() <= 1e-4
