@@ -506,7 +506,10 @@ gac_status gac_server::run_round(bool *launched) {
             Job &j = *jp;
             if (j.cancel) continue;
             if (j.state == JobState::Uploading && cudaEventQuery(j.ev) == cudaSuccess) j.state = JobState::Running;
-            if (j.state == JobState::Running && j.t_done < j.opts.iterations) run.push_back(jp);
+            // a Running job has rounds left to plan (the round that reaches its last
+            // iteration turns it into Finishing); a zero-iteration job takes one
+            // empty round, which initialises its chains and writes its outputs
+            if (j.state == JobState::Running) run.push_back(jp);
         }
     }
     if (run.empty()) return GAC_OK;
@@ -741,7 +744,7 @@ void gac_server::loop() {
             if (stop) break;
             bool runnable = false, waiting = false;
             for (auto &jp : resident) {
-                if ((jp->state == JobState::Running && jp->t_done < jp->opts.iterations) ||
+                if (jp->state == JobState::Running ||
                     jp->state == JobState::Uploading)
                     runnable = true;
                 if (jp->state == JobState::Finishing) waiting = true;

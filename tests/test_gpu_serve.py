@@ -217,3 +217,22 @@ def test_all_postburnin_moments_jobs_equal_alone(gac, orc):
             np.testing.assert_allclose(out["std"], ref["std"], rtol=1e-9, atol=0)
     finally:
         gac.gac_server_destroy(srv)
+
+
+def test_zero_iteration_job_completes(gac, orc):
+    """A job with no iterations takes one empty round: its chains are
+    initialised and its outputs written as gac_mcmc_run writes them."""
+    w = W.SMT_1P5M
+    mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
+    th, sig, y = make_voxels(orc, w, 0, 300)
+    srv = gac.gac_server_create(1 << 30, 8)
+    try:
+        opts = gac.make_opts(0, 0, 1, 2, 9)
+        jid = gac.gac_server_submit(srv, mid, y, y.shape[0], sig, 0.0, opts)
+        ref = gac.run_host(mid, y, sig, iterations=0, burnin=0, thin=1, n_chains=2, seed=9, want_samples=False)
+        out = {k: np.empty_like(ref[k]) for k in ("mean", "std", "accept_rate", "nonfinite")}
+        gac.gac_server_wait(srv, jid, 60.0, out)
+        for k in out:
+            np.testing.assert_array_equal(out[k], ref[k], err_msg=k)
+    finally:
+        gac.gac_server_destroy(srv)
