@@ -185,31 +185,30 @@ struct GaussLegendre01 {
 };
 }  // namespace
 
-// Monomial coefficients af[0..7] (float) in d of the degree-7 polynomial that
-// interpolates f(d) at the eight Chebyshev points of [-1/2, 1/2], and the
-// largest relative error of that float polynomial, evaluated in double, on 65
-// points of the interval.
-template <class F>
-static double cheb8_fit(F &&f, float af[8]) {
-    constexpr int K = 8;
+// Monomial coefficients af[0..K-1] (float) in d of the degree-(K-1)
+// polynomial that interpolates f(d) at the K Chebyshev points of [-h, h], and
+// the largest relative error of that float polynomial, evaluated in double,
+// on 65 points of the interval.
+template <int K, class F>
+static double cheb_fit(F &&f, float af[K], double h) {
     double T[K][K] = {};  // T[n][m]: coefficient of s^m in the Chebyshev polynomial T_n(s)
     T[0][0] = 1.0;
     T[1][1] = 1.0;
     for (int n = 2; n < K; ++n)
         for (int m = 0; m < K; ++m) T[n][m] = (m > 0 ? 2.0 * T[n - 1][m - 1] : 0.0) - T[n - 2][m];
     double fv[K];
-    for (int j = 0; j < K; ++j) fv[j] = f(0.5 * std::cos(M_PI * (j + 0.5) / K));
-    double a[K] = {};  // monomial coefficients in s = 2 d
+    for (int j = 0; j < K; ++j) fv[j] = f(h * std::cos(M_PI * (j + 0.5) / K));
+    double a[K] = {};  // monomial coefficients in s = d / h
     for (int n = 0; n < K; ++n) {
         double b = 0.0;  // Chebyshev coefficient b_n
         for (int j = 0; j < K; ++j) b += fv[j] * std::cos(M_PI * n * (j + 0.5) / K);
         b *= (n == 0 ? 1.0 : 2.0) / K;
         for (int m = 0; m < K; ++m) a[m] += b * T[n][m];
     }
-    for (int m = 0; m < K; ++m) af[m] = static_cast<float>(std::ldexp(a[m], m));  // coefficient of d^m
+    for (int m = 0; m < K; ++m) af[m] = static_cast<float>(a[m] / std::pow(h, m));  // coefficient of d^m
     double worst = 0.0;
     for (int q = 0; q <= 64; ++q) {
-        const double dd = -0.5 + q / 64.0;
+        const double dd = -h + 2.0 * h * q / 64.0;
         double p = af[K - 1];
         for (int m = K - 2; m >= 0; --m) p = p * dd + af[m];
         const double ref = f(dd);
@@ -218,36 +217,47 @@ static double cheb8_fit(F &&f, float af[8]) {
     }
     return worst;
 }
+template <class F>
+static double cheb8_fit(F &&f, float af[8]) {
+    return cheb_fit<8>(f, af, 0.5);
+}
 
-// Fills mc->gtab with, for each centre c = c_lo .. c_hi, the monomial
-// coefficients in d of the degree-7 polynomial that interpolates g(c + d) at
-// the eight Chebyshev points of [-1/2, 1/2], and checks every interval on 65
-// points against the quadrature (relative error of the float coefficients
-// evaluated in double at most 2e-7; the interpolation error itself is below
-// 1e-9 for unit intervals).  c_hi = the centre nearest xmax (the largest
-// argument the model's bounds allow) when that fits in kGTabMax intervals:
-// then the kernels need no asymptote.  Otherwise the table ends at c_hi >= 16
-// and x >= c_hi + 1/2 takes sqrt(pi)/2 x^-1/2.
-static gac_status build_g_table(int c_lo, double xmax, ModelConst *mc) {
+// Fills mc->gtab with, for each centre c = k/2, k = k_lo .. k_hi, the
+// monomial coefficients in d of the degree-5 polynomial that interpolates
+// g(c + d) at the six Chebyshev points of [-1/4, 1/4], and checks every
+// interval on 65 points against the quadrature (relative error of the float
+// coefficients evaluated in double at most 2e-7; the interpolation error
+// itself is about 1e-8 on quarter-width half-intervals).  k_hi = the centre
+// nearest xmax (the largest argument the model's bounds allow) when that fits
+// in kGTabMax intervals: then the kernels need no asymptote.  Otherwise the
+// table ends at a centre >= 16 and x >= c_hi + 1/4 takes sqrt(pi)/2 x^-1/2.
+static gac_status build_g_table(double xmin, double xmax, ModelConst *mc) {
     static const GaussLegendre01 gl;
-    if (c_lo < static_cast<int>(kSmtArgMin) - 1)
-        return fail(GAC_ERR_INVALID_ARG, "SMT argument range starts at %d, below %d", c_lo,
+    const int k_lo = static_cast<int>(std::floor(2.0 * xmin - 0.5));
+    if (k_lo < 2 * static_cast<int>(kSmtArgMin) - 2)
+        return fail(GAC_ERR_INVALID_ARG, "SMT argument range starts at %g, below %d", xmin,
                     static_cast<int>(kSmtArgMin));
-    const double c_need = std::max(std::ceil(xmax - 0.5), static_cast<double>(kGTail));
-    const int n_int = static_cast<int>(std::min<double>(kGTabMax, c_need - c_lo + 1));
-    const int c_hi = c_lo + n_int - 1;
-    if (c_hi < static_cast<int>(kGTail)) return fail(GAC_ERR_INVALID_ARG, "g(x) table too short");
+    const double k_need = std::max(std::ceil(2.0 * xmax - 0.5), 2.0 * kGTail);
+    const int n_int = static_cast<int>(std::min<double>(kGTabMax, k_need - k_lo + 1));
+    const int k_hi = k_lo + n_int - 1;
+    if (k_hi < 2 * static_cast<int>(kGTail)) return fail(GAC_ERR_INVALID_ARG, "g(x) table too short");
     for (int i = 0; i < n_int; ++i) {
-        const double c = c_lo + i;
-        float af[8];
-        const double err = cheb8_fit([&](double d) { return gl.g(c + d); }, af);
-        for (int m = 0; m < 8; ++m) mc->gtab[((m < 4 ? 0 : kGTabMax) + i) * 4 + (m & 3)] = af[m];
+        const double c = 0.5 * (k_lo + i);
+        float af[6];
+        const double err = cheb_fit<6>([&](double d) { return gl.g(c + d); }, af, 0.25);
+        for (int m = 0; m < 4; ++m) mc->gtab[i * 4 + m] = af[m];
+        mc->gtab[(kGTabMax + i) * 4 + 0] = af[4];
+        mc->gtab[(kGTabMax + i) * 4 + 1] = af[5];
+        mc->gtab[(kGTabMax + i) * 4 + 2] = 0.0f;
+        mc->gtab[(kGTabMax + i) * 4 + 3] = 0.0f;
         if (!(err <= 2e-7)) return fail(GAC_ERR_INVALID_ARG, "g(x) table check failed near x = %g", c);
     }
+    const int c_lo = k_lo;
+    const double c_hi = 0.5 * k_hi;
     mc->gtab_lo = c_lo;
     mc->gtab_n = n_int;
-    mc->gtab_tail = c_hi + 0.5 >= xmax ? 0 : 1;
-    mc->gtab_tail_x = static_cast<float>(c_hi + 0.5);
+    mc->gtab_tail = c_hi + 0.25 >= xmax ? 0 : 1;
+    mc->gtab_tail_x = static_cast<float>(c_hi + 0.25);
     return GAC_OK;
 }
 
@@ -592,7 +602,7 @@ gac_status gac_model_register(const gac_model_desc *d, int *model_id) {
             xmin = std::min({xmin, d->acq[k] * d->lb[1], d->acq[k] * (d->lb[2] - d->ub[3])});
             xmax = std::max({xmax, d->acq[k] * d->ub[1], d->acq[k] * (d->ub[2] - d->lb[3])});
         }
-        const gac_status st = build_g_table(static_cast<int>(std::floor(xmin)), xmax, &mc);
+        const gac_status st = build_g_table(xmin, xmax, &mc);
         if (st != GAC_OK) return st;
     }
     if (d->kind == GAC_MODEL_AXCAL_SMT) {
@@ -605,7 +615,7 @@ gac_status gac_model_register(const gac_model_desc *d, int *model_id) {
             xmin = std::min(xmin, b * (kAxDeParD - d->ub[3]));
             xmax = std::max({xmax, b * kAxDaD, b * (kAxDeParD - d->lb[3])});
         }
-        if ((st = build_g_table(static_cast<int>(std::floor(xmin)), xmax, &mc)) != GAC_OK) return st;
+        if ((st = build_g_table(xmin, xmax, &mc)) != GAC_OK) return st;
     }
     std::lock_guard<std::mutex> lk(g_reg_mu);
     for (size_t i = 0; i < g_models.size(); ++i)  // ModelConst is zero-filled before it is set

@@ -29,7 +29,7 @@ namespace gac {
 constexpr int kAnchor = 6;
 constexpr float kSinCosMaxArg = 6000.0f;  // |x| bound of sincos_cw (registration checks it)
 constexpr float kSmtArgMin = -12.0f;  // registration keeps b (De_par - De_perp), b Da >= -12
-constexpr int kGTabMax = 64;          // unit intervals of the g(x) table, centres c_lo .. c_hi
+constexpr int kGTabMax = 96;          // half-unit intervals of the g(x) table, centres c_lo/2 .. c_hi/2
 constexpr float kGTail = 16.0f;       // x >= 16: g(x) = sqrt(pi)/2 x^-1/2 within erfc(4) = 1.5e-8
 
 // AxCaliberSMT (Sec. 2.5, after Fan et al. 2020): measurements are
@@ -81,13 +81,14 @@ struct ModelConst {
     double acq_d[GAC_MAX_ACQ];
     float lb_f[GAC_MAX_PAR], ub_f[GAC_MAX_PAR], step_f[GAC_MAX_PAR];
     double lb_d[GAC_MAX_PAR], ub_d[GAC_MAX_PAR], step_d[GAC_MAX_PAR];
-    // g(x) = int_0^1 exp(-x u^2) du on unit intervals centred at the integers
-    // c = gtab_lo .. gtab_lo + gtab_n - 1: g(c + d) = sum_{n<=7} a_n d^n for
-    // |d| <= 1/2 (the Chebyshev interpolant of degree 7).  Layout
-    // [2][kGTabMax][4]: a_0..a_3 of every interval, then a_4..a_7, so one
-    // interval is two 16-byte loads.  When the table covers every argument
-    // the model's bounds allow, gtab_tail = 0; otherwise x >= gtab_tail_x
-    // (>= 16.5) takes the asymptote sqrt(pi)/2 x^-1/2.
+    // g(x) = int_0^1 exp(-x u^2) du on half-unit intervals centred at the
+    // half-integers c = k/2, k = gtab_lo .. gtab_lo + gtab_n - 1:
+    // g(c + d) = sum_{n<=5} a_n d^n for |d| <= 1/4 (the Chebyshev interpolant
+    // of degree 5).  Layout [2][kGTabMax][4]: a_0..a_3 of every interval, then
+    // a_4, a_5 (and two zeros), so one interval is two 16-byte loads.  When
+    // the table covers every argument the model's bounds allow, gtab_tail =
+    // 0; otherwise x >= gtab_tail_x (>= 16.25) takes the asymptote
+    // sqrt(pi)/2 x^-1/2.
     alignas(16) float gtab[2 * kGTabMax * 4];
     int gtab_lo;
     int gtab_n;
@@ -143,24 +144,22 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return r;
 }
 
-// g(x) in FP32 without branches: the interval is c = rint(x), taken from the
-// bits of x + 1.5 * 2^23 (exact for |x| < 2^22), and d = x - c is exact;
-// Horner in d over the interval's eight coefficients.  With TAIL, x >=
+// g(x) in FP32 without branches: the interval is k = rint(2x), taken from
+// the bits of 2x + 1.5 * 2^23 (exact for |x| < 2^21), and d = x - k/2 is
+// exact; Horner in d over the interval's six coefficients.  With TAIL, x >=
 // gtab_tail_x takes the asymptote sqrt(pi)/2 x^-1/2 instead (relative error
 // below erfc(4)); without it the table covers every argument the bounds
 // allow.  The clamped index keeps every load inside the table for any x.
 template <bool TAIL>
 __device__ __forceinline__ float smt_g_f(float x, const ModelConst &mc) {
     constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
-    const float t = x + kRound;
-    const float d = x - (t - kRound);
+    const float t = fmaf(x, 2.0f, kRound);
+    const float d = fmaf(t - kRound, -0.5f, x);
     int i = __float_as_int(t) - __float_as_int(kRound) - mc.gtab_lo;
     i = min(max(i, 0), mc.gtab_n - 1);
     const float4 lo = smt_gtab_s[i];
     const float4 hi = smt_gtab_s[kGTabMax + i];
-    float p = fmaf(hi.w, d, hi.z);
-    p = fmaf(p, d, hi.y);
-    p = fmaf(p, d, hi.x);
+    float p = fmaf(hi.y, d, hi.x);
     p = fmaf(p, d, lo.w);
     p = fmaf(p, d, lo.z);
     p = fmaf(p, d, lo.y);
@@ -191,20 +190,16 @@ __device__ __forceinline__ double smt_g_d(double x) {
 }
 
 // g(x) and g'(x) in FP32 from the same table: the interval polynomial and its
-// derivative (unit intervals, so d/dx = d/dd); g' = -g / (2x) on the tail.
+// derivative (d/dx = d/dd); g' = -g / (2x) on the tail.
 __device__ __forceinline__ void smt_g_dg(float x, const ModelConst &mc, float &g, float &dg) {
     constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
-    const float t = x + kRound;
-    const float d = x - (t - kRound);
+    const float t = fmaf(x, 2.0f, kRound);
+    const float d = fmaf(t - kRound, -0.5f, x);
     int i = __float_as_int(t) - __float_as_int(kRound) - mc.gtab_lo;
     i = min(max(i, 0), mc.gtab_n - 1);
     const float4 lo = smt_gtab_s[i];
     const float4 hi = smt_gtab_s[kGTabMax + i];
-    float p = fmaf(hi.w, d, hi.z), q = fmaf(7.0f * hi.w, d, 6.0f * hi.z);
-    p = fmaf(p, d, hi.y);
-    q = fmaf(q, d, 5.0f * hi.y);
-    p = fmaf(p, d, hi.x);
-    q = fmaf(q, d, 4.0f * hi.x);
+    float p = fmaf(hi.y, d, hi.x), q = fmaf(5.0f * hi.y, d, 4.0f * hi.x);
     p = fmaf(p, d, lo.w);
     q = fmaf(q, d, 3.0f * lo.w);
     p = fmaf(p, d, lo.z);
