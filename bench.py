@@ -93,9 +93,9 @@ KERNEL_SOURCES = ("include/gac.h", "paper_2511_22094_gb300/csrc/mh_kernel.cuh",
 KIND_SOURCE = {"mwi3_1m": "mh_mwi3.cu", "smt_1p5m": "mh_smt.cu", "monoexp_4k": "mh_monoexp.cu",
                "axcal_250k": "mh_axcal.cu"}
 MEASURED = {
-    "mwi3_1m": dict(sources="a4fd0f4a0890114d", traffic_bytes=287.6e6 + 6621.9e6, warp_instr=966.2),
-    "smt_1p5m": dict(sources="8147ba10f90f808b", traffic_bytes=118.2e6 + 4427.8e6, warp_instr=516.0),
-    "axcal_250k": dict(sources="259e84fa9f00e741", traffic_bytes=111.8e6 + 3602.5e6, warp_instr=1285.8),
+    "mwi3_1m": dict(sources="d5b7ae3e7872a7b8", traffic_bytes=282.5e6 + 6620.6e6, warp_instr=966.2),
+    "smt_1p5m": dict(sources="079ca28eeebba727", traffic_bytes=111.9e6 + 4425.4e6, warp_instr=511.0),
+    "axcal_250k": dict(sources="c577ca3415b96872", traffic_bytes=106.3e6 + 3599.1e6, warp_instr=1244.8),
 }
 
 

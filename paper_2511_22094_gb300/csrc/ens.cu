@@ -11,19 +11,19 @@
 
 namespace gac {
 
-template <int KIND, int PREC, bool TRACE>
+template <int KIND, int PREC, bool TRACE, bool BLOCKED = false>
 static const void *ens_ptr() {
-    return reinterpret_cast<const void *>(&ens_kernel<KIND, PREC, TRACE>);
+    return reinterpret_cast<const void *>(&ens_kernel<KIND, PREC, TRACE, BLOCKED>);
 }
 
-template <int KIND, int PREC, bool TRACE>
+template <int KIND, int PREC, bool TRACE, bool BLOCKED = false>
 static cudaError_t ens_go(int grid, size_t smem, cudaStream_t s, const ModelConst &mc, const RunArgs &ra,
                           const EnsArgs &ea, const void **fn) {
     if (fn) {
-        *fn = ens_ptr<KIND, PREC, TRACE>();
+        *fn = ens_ptr<KIND, PREC, TRACE, BLOCKED>();
         return cudaSuccess;
     }
-    ens_kernel<KIND, PREC, TRACE><<<grid, kEnsBlock, smem, s>>>(mc, ra, ea);
+    ens_kernel<KIND, PREC, TRACE, BLOCKED><<<grid, kEnsBlock, smem, s>>>(mc, ra, ea);
     return cudaGetLastError();
 }
 
@@ -32,6 +32,9 @@ static cudaError_t ens_by_prec(int prec, bool trace, int grid, size_t smem, cuda
                                const RunArgs &ra, const EnsArgs &ea, const void **fn) {
     switch (prec) {
     case GAC_PREC_MIXED:
+        if (ra.moments_mode == GAC_MOMENTS_ALL_POSTBURNIN)
+            return trace ? ens_go<KIND, GAC_PREC_MIXED, true, true>(grid, smem, s, mc, ra, ea, fn)
+                         : ens_go<KIND, GAC_PREC_MIXED, false, true>(grid, smem, s, mc, ra, ea, fn);
         return trace ? ens_go<KIND, GAC_PREC_MIXED, true>(grid, smem, s, mc, ra, ea, fn)
                      : ens_go<KIND, GAC_PREC_MIXED, false>(grid, smem, s, mc, ra, ea, fn);
     case GAC_PREC_FP32:

@@ -42,7 +42,10 @@ __host__ __device__ inline size_t ens_smem_bytes(int P, size_t r_bytes, size_t w
 // warps (measured 4.6% faster on the 3-pool benchmark than 2 blocks of 256).
 constexpr int kEnsBlock = 128;
 
-template <int KIND, int PREC, bool TRACE>
+// BLOCKED (MIXED, moments over every post-burn-in state): the blocked FP32
+// accumulation; a separate instantiation so that the other modes keep their
+// code unchanged.
+template <int KIND, int PREC, bool TRACE, bool BLOCKED = false>
 __global__ void __launch_bounds__(kEnsBlock, 4) ens_kernel(const ModelConst mc, const RunArgs ra, const EnsArgs ea) {
     using R = typename PrecTraits<PREC>::R;
     using W = typename PrecTraits<PREC>::W;
@@ -128,8 +131,7 @@ __global__ void __launch_bounds__(kEnsBlock, 4) ens_kernel(const ModelConst mc, 
             }
         }
         const bool all_mode = ra.moments_mode == GAC_MOMENTS_ALL_POSTBURNIN;
-        constexpr bool kBlocked = PREC == GAC_PREC_MIXED;
-        const bool blocked = kBlocked && all_mode;
+        constexpr bool blocked = BLOCKED && PREC == GAC_PREC_MIXED;
         int n_mom = 0, blk_n = 0;
         int to_thin = ra.B + ra.T;
         for (int t = 1; t <= ra.I; ++t) {
