@@ -384,7 +384,9 @@ gac_status gac_server_poll(gac_server *srv, uint64_t job_id, int *done, gac_resu
                            double *latency_s);
 
 /* Blocks until the job is done or timeout_s passes (GAC_ERR_TIMEOUT); then
- * behaves as gac_server_poll. */
+ * behaves as gac_server_poll.  timeout_s >= 0 (INFINITY waits without end);
+ * otherwise INVALID_ARG.  If another thread collects the job first (poll or
+ * wait), this call returns UNKNOWN_JOB. */
 gac_status gac_server_wait(gac_server *srv, uint64_t job_id, double timeout_s, gac_result *out,
                            double *latency_s);
 

@@ -939,15 +939,30 @@ gac_status gac_server_poll(gac_server *srv, uint64_t job_id, int *done, gac_resu
 gac_status gac_server_wait(gac_server *srv, uint64_t job_id, double timeout_s, gac_result *out, double *latency_s) {
     clear_error();
     if (!srv) return fail(GAC_ERR_INVALID_ARG, "srv must not be NULL");
+    if (!(timeout_s >= 0.0)) return fail(GAC_ERR_INVALID_ARG, "timeout_s must be >= 0");
     std::unique_lock<std::mutex> lk(srv->mu);
     auto it = srv->jobs.find(job_id);
     if (it == srv->jobs.end()) return fail(GAC_ERR_UNKNOWN_JOB, "no job %llu", static_cast<unsigned long long>(job_id));
     auto jp = it->second;
-    const bool ok = srv->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), [&] {
+    // timeouts beyond a year wait a year at a time (the clock's duration type
+    // would overflow); the job's state is re-checked after every wake-up
+    const double kMaxWait = 3.15e7;
+    auto done = [&] {
         return jp->state == JobState::Done || jp->state == JobState::Failed || jp->state == JobState::Cancelled;
-    });
+    };
+    bool ok = false;
+    for (double left = timeout_s; !ok;) {
+        const double chunk = std::min(left, kMaxWait);
+        ok = srv->cv_done.wait_for(lk, std::chrono::duration<double>(chunk), done);
+        left -= chunk;
+        if (left <= 0.0) break;
+    }
     if (!ok) return fail(GAC_ERR_TIMEOUT, "job %llu not done after %.3f s", static_cast<unsigned long long>(job_id), timeout_s);
-    return deliver(srv, srv->jobs.find(job_id), out, latency_s);
+    // another thread may have collected the job (poll or wait) meanwhile
+    it = srv->jobs.find(job_id);
+    if (it == srv->jobs.end() || it->second != jp)
+        return fail(GAC_ERR_UNKNOWN_JOB, "job %llu was collected by another call", static_cast<unsigned long long>(job_id));
+    return deliver(srv, it, out, latency_s);
 }
 
 gac_status gac_server_cancel(gac_server *srv, uint64_t job_id) {

@@ -152,6 +152,14 @@ def test_server_host_side_checks(gac):
         assert e.value.status == 9  # UNKNOWN_JOB
         with pytest.raises(gac.GacError):
             gac.gac_server_cancel(srv, 12345)
+        for bad in (-1.0, float("nan")):  # the timeout is checked before the job
+            with pytest.raises(gac.GacError) as e:
+                gac.gac_server_wait(srv, 12345, bad)
+            assert e.value.status == 1
+        for ok in (0.0, float("inf")):
+            with pytest.raises(gac.GacError) as e:
+                gac.gac_server_wait(srv, 12345, ok)
+            assert e.value.status == 9
         st = gac.gac_server_get_stats(srv)
         assert st["queued"] == 0 and st["budget"] == 1 << 20
     finally:

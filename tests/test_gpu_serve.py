@@ -236,3 +236,34 @@ def test_zero_iteration_job_completes(gac, orc):
             np.testing.assert_array_equal(out[k], ref[k], err_msg=k)
     finally:
         gac.gac_server_destroy(srv)
+
+
+def test_two_waiters_on_one_job(gac, orc):
+    """Two host threads wait for the same job: one receives the results, the
+    other UNKNOWN_JOB (the job was collected while it slept); neither hangs."""
+    import threading
+
+    w = W.MWI3_1M
+    mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
+    th, sig, y = make_voxels(orc, w, 0, 4000)
+    srv = gac.gac_server_create(8 << 30, 8)
+    try:
+        jid = gac.gac_server_submit(srv, mid, y, y.shape[0], sig, 0.0, gac.make_opts(3000, 300, 100, 4, 5))
+        statuses = []
+
+        def waiter():
+            try:
+                gac.gac_server_wait(srv, jid, 120.0, {})
+                statuses.append(0)
+            except gac.GacError as e:
+                statuses.append(e.status)
+
+        ts = [threading.Thread(target=waiter) for _ in range(2)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join(180.0)
+        assert not any(t.is_alive() for t in ts)
+        assert sorted(statuses) == [0, 9], statuses
+    finally:
+        gac.gac_server_destroy(srv)
