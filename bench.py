@@ -19,6 +19,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -86,24 +87,35 @@ def _alu_peaks(mix: dict, rates):
 
 # From the ncu captures summarised under profiles/: DRAM bytes of one full
 # launch of the sampler kernel (read + write) and executed warp instructions
-# per 32 chain-iterations.  Reported only while the kernel's sources hash to
-# the value they were measured with (otherwise null).
+# per 32 chain-iterations.  Reported only while the kernel's sources (their
+# code: comments and layout aside) hash to the value they were measured with
+# (otherwise null).
 KERNEL_SOURCES = ("include/gac.h", "paper_2511_22094_gb300/csrc/mh_kernel.cuh",
                   "paper_2511_22094_gb300/csrc/models.cuh", "paper_2511_22094_gb300/csrc/philox.cuh")
 KIND_SOURCE = {"mwi3_1m": "mh_mwi3.cu", "smt_1p5m": "mh_smt.cu", "monoexp_4k": "mh_monoexp.cu",
                "axcal_250k": "mh_axcal.cu"}
 MEASURED = {
-    "mwi3_1m": dict(sources="d5b7ae3e7872a7b8", traffic_bytes=282.5e6 + 6620.6e6, warp_instr=966.2),
-    "smt_1p5m": dict(sources="079ca28eeebba727", traffic_bytes=111.9e6 + 4425.4e6, warp_instr=511.0),
-    "axcal_250k": dict(sources="c577ca3415b96872", traffic_bytes=106.3e6 + 3599.1e6, warp_instr=1244.8),
+    "mwi3_1m": dict(sources="989bafbcb8bbf4ac", traffic_bytes=282.5e6 + 6620.6e6, warp_instr=966.2),
+    "smt_1p5m": dict(sources="2022dc6fdbec6948", traffic_bytes=111.9e6 + 4425.4e6, warp_instr=511.0),
+    "axcal_250k": dict(sources="89b09c945f92ef7f", traffic_bytes=106.3e6 + 3599.1e6, warp_instr=1244.8),
 }
+
+
+_C_TOKENS = re.compile(r'//[^\n]*|/\*.*?\*/|"(?:\\.|[^"\\])*"|\'(?:\\.|[^\'\\])*\'', re.S)
+
+
+def _code_only(text: str) -> str:
+    """C/C++ source without comments and with whitespace runs collapsed:
+    edits to comments and layout leave the hash (and the kernel) unchanged."""
+    text = _C_TOKENS.sub(lambda m: " " if m.group(0)[0] == "/" else m.group(0), text)
+    return " ".join(text.split())
 
 
 def _sources_hash(workload: str) -> str:
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES + ("paper_2511_22094_gb300/csrc/" + KIND_SOURCE[workload],):
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

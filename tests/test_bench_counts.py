@@ -41,3 +41,13 @@ def test_mix_rate_is_harmonic(bench):
     mufu, _, _ = bench._alu_peaks({"ex2": 10, "sin": 30}, fast)
     assert mufu == pytest.approx(40.0 / (10 / 32.0 + 30 / 16.0))
     assert bench._alu_peaks({"ex2": 1}, None)[:2] == (bench.MUFU_PER_CLK_SM, bench.FP32_PER_CLK_SM)
+
+
+def test_source_hash_ignores_comments_and_layout(bench):
+    a = 'int f(int x) { // doubles x\n  return 2 * x; /* no\n overflow check */ }\nconst char *s = "a//b";\n'
+    b = 'int f(int x) {\n    return 2 * x;\n}\nconst char *s = "a//b";'
+    assert bench._code_only(a) == bench._code_only(b)
+    assert bench._code_only(a) != bench._code_only(b.replace("2 * x", "3 * x"))
+    assert '"a//b"' in bench._code_only(a)  # string literals are kept whole
+    for w in bench.MEASURED:  # every measured workload has a hashable source set
+        assert len(bench._sources_hash(w)) == 16
