@@ -22,6 +22,7 @@ def test_monoexp_closed_form_limits(orc):
     s0 = orc.forward(MONOEXP, [0.0], th)[:, 0]
     np.testing.assert_allclose(s0, th[:, 0], rtol=0, atol=0)  # S(TE = 0) = S0
     s = orc.forward(MONOEXP, TE12, th)
+    assert (s > 0).all()  # a mono-exponential never reaches 0 at these TE
     for i in range(50):  # log S is linear in TE with slope -R2* (TE in ms, R2* in 1/s)
         slope, icpt = np.polyfit(TE12, np.log(s[i]), 1)
         assert slope == pytest.approx(-th[i, 1] * 1e-3, rel=1e-12)
