@@ -13,7 +13,10 @@ reported mean and SD equal those of the stored thinned samples.  Over the
 whole volume (properties that hold at any size): no non-finite
 log-likelihood, every stored sample and every mean inside the prior box,
 SD >= 0, R-hat >= sqrt((n - 1) / n) wherever the within-chain variance is
-positive (and not finite only where every chain is constant).
+positive (and not finite only where every chain is constant).  The ensemble
+sampler runs at Table 1's settings over 250,000 voxels (the ensemble
+benchmark) and is checked on sampled voxels by the paper's independent-seed
+design.
 """
 import numpy as np
 import pytest
@@ -102,3 +105,71 @@ def test_full_size_against_oracle_on_sampled_voxels(gac, orc, w):
           f"within 0.05 SD {(gap <= 0.05).mean():.4f}; accept-rate gap {dacc:.4f}")
     assert (gap <= 0.05).mean() >= 0.99
     assert dacc < 0.01
+
+
+ENS_CASES = [W.MWI3_1M, W.SMT_1P5M]
+ENS_BLOCK = 64
+
+
+@pytest.mark.parametrize("w0", ENS_CASES, ids=[w.name for w in ENS_CASES])
+def test_ensemble_full_size_on_sampled_voxels(gac, orc, w0):
+    """The ensemble sampler in the benchmark's launch configuration: Table 1's
+    50 walkers x 2,000 iterations (burn-in 200, thinning 100) over 250,000
+    voxels in one gac_ensemble_run, MIXED, device buffers (the stored samples
+    span more than 2^31 floats for the 3-pool model).  Whole volume: no
+    non-finite log-likelihood, stored samples and means inside the prior box,
+    SD >= 0.  On 512 sampled voxels (the first and last blocks and six seeded
+    ones): the reported moments are those of the stored samples, and the
+    posterior means agree with the FP64 oracle under independent random
+    streams as closely as two oracle runs agree with each other (Demo 2's
+    design, Sec. 2.6.2), with the same acceptance rate within 0.01."""
+    from test_gpu_precision_study import paired_seed_check
+
+    w = w0.with_(n_vox=250_000, n_chains=50, iterations=2000, burnin=200, thin=100)
+    N, L, P = w.n_vox, w.n_chains, w.n_par
+    I, B, T = w.iterations, w.burnin, w.thin
+    S = gac.n_samples(I, B, T)
+    mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
+    th, sig, y = make_voxels(orc, w, 0, N)
+    dev = torch.device("cuda:0")
+    out = dict(mean=torch.empty((P, N), dtype=torch.float64, device=dev),
+               std=torch.empty((P, N), dtype=torch.float64, device=dev),
+               samples=torch.empty((S, L, P, N), dtype=torch.float32, device=dev),
+               accept_rate=torch.empty((L, N), dtype=torch.float32, device=dev),
+               nonfinite=torch.empty((L, N), dtype=torch.int32, device=dev))
+    opts = gac.make_opts(I, B, T, L, w.mcmc_seed)
+    gac.gac_ensemble_run(mid, torch.from_numpy(y).to(dev), N, torch.from_numpy(sig).to(dev), 0.0, None, opts,
+                         2.0, out, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+
+    lb = torch.tensor(np.float32(w.lb).astype(np.float64), device=dev)[:, None]
+    ub = torch.tensor(np.float32(w.ub).astype(np.float64), device=dev)[:, None]
+    assert int(out["nonfinite"].sum()) == 0
+    for s in range(S):  # every stored sample inside the box (walkers reject outside proposals)
+        smp = out["samples"][s].double()  # [L][P][N]
+        assert bool(((smp >= lb[None]) & (smp <= ub[None])).all()), s
+    slack = 1e-12 * torch.maximum(lb.abs(), ub.abs())
+    assert bool(((out["mean"] >= lb - slack) & (out["mean"] <= ub + slack)).all())
+    assert bool((out["std"] >= 0).all())
+    assert 0.0 < float(out["accept_rate"].mean()) < 1.0
+
+    rng = np.random.default_rng(w.data_seed)
+    blocks = rng.choice(np.arange(1, N // ENS_BLOCK - 1), 6, replace=False)
+    starts = [0, N - ENS_BLOCK] + sorted(int(b) * ENS_BLOCK for b in blocks)
+    idx = np.concatenate([np.arange(v0, v0 + ENS_BLOCK) for v0 in starts])
+    assert np.unique(idx).size == idx.size == 8 * ENS_BLOCK
+    it = torch.from_numpy(idx).to(dev)
+    g = {k: out[k].index_select(out[k].dim() - 1, it).cpu().numpy() for k in ("mean", "std", "accept_rate")}
+    smp = out["samples"].index_select(3, it).double().cpu().numpy()  # [S][L][P][512]
+    del out
+    # the reported moments are those of the stored samples, pooled over walkers
+    pooled = smp.transpose(2, 3, 0, 1).reshape(P, idx.size, S * L)
+    scale = np.abs(pooled).max(-1)
+    assert (np.abs(g["mean"] - pooled.mean(-1)) <= 1e-10 * scale + 1e-300).all()
+    assert (np.abs(g["std"] - pooled.std(-1, ddof=1)) <= 1e-9 * scale + 1e-300).all()
+
+    kw = dict(iterations=I, burnin=B, thin=T, n_walkers=L, stretch=2.0, want_samples=False)
+    runs = {s: orc.ensemble_run(w.kind, w.acq, w.lb, w.ub, y[idx], sig[idx], seed=s, **kw) for s in (11, 22, 44)}
+    runs[33] = g
+    paired_seed_check(runs, ((11, 22), (33, 44)), f"ensemble {w.name} full size")
+    assert abs(g["accept_rate"].mean() - runs[44]["accept_rate"].mean()) < 0.01
