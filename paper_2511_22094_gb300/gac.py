@@ -157,10 +157,12 @@ def _ptr(x):
     if x is None:
         return None
     if isinstance(x, np.ndarray):
-        assert x.flags.c_contiguous, "arrays must be C-contiguous"
+        if not x.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
         return x.ctypes.data
     if hasattr(x, "data_ptr"):
-        assert x.is_contiguous(), "tensors must be contiguous"
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
         return x.data_ptr()
     if isinstance(x, int):
         return x

@@ -8,6 +8,7 @@ import subprocess
 
 import numpy as np
 import pytest
+import torch
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -211,3 +212,12 @@ def test_pipe_probe_rejects_bad_arguments(gac):
         assert e.value.status == 1
     assert gac._lib.gac_pipe_rate(0, None, None) == 1
     assert set(gac.PIPE_OPS.values()) == set(range(11))
+
+
+def test_binding_rejects_non_contiguous_buffers(gac):
+    a = np.zeros((4, 12), np.float32)
+    with pytest.raises(ValueError):
+        gac._ptr(a[:, ::2])
+    with pytest.raises(ValueError):
+        gac._ptr(torch.zeros(4, 12).t())
+    assert gac._ptr(a) == a.ctypes.data and gac._ptr(None) is None
