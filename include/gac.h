@@ -354,6 +354,9 @@ gac_status gac_mcmc_run_noalloc(int model_id, const void *data, int64_t n_vox, c
  * Results equal those of gac_mcmc_run with the same inputs: the random
  * numbers depend only on (seed, t, voxel, chain) and slices resume exactly.
  * Serving runs the MIXED precision path; trace_n_vox must be 0.
+ * Threads: submit, poll, wait, cancel and get_stats may be called from any
+ * host threads at once; destroy must not overlap any other call on the same
+ * server.
  * ---------------------------------------------------------------------- */
 typedef struct gac_server gac_server;
 
@@ -407,7 +410,9 @@ typedef struct {
 } gac_server_stats;
 gac_status gac_server_get_stats(gac_server *srv, gac_server_stats *st);
 
-/* Stops the scheduler (after the current round), frees every job. */
+/* Stops the scheduler (after the current round), frees every job (results
+ * not yet collected are lost).  No other call on `srv` may run meanwhile or
+ * follow it. */
 gac_status gac_server_destroy(gac_server *srv);
 
 /* Message for the last non-OK status on the calling thread ("" if none). */
