@@ -51,3 +51,39 @@ def test_source_hash_ignores_comments_and_layout(bench):
     assert '"a//b"' in bench._code_only(a)  # string literals are kept whole
     for w in bench.MEASURED:  # every measured workload has a hashable source set
         assert len(bench._sources_hash(w)) == 16
+
+
+def _json_lines(text):
+    import json
+    return [json.loads(l) for l in text.splitlines() if l.startswith("{")]
+
+
+def test_reference_arm_line(bench):
+    """`bench.py --impl reference` (the oracle on the host cores) prints one
+    JSON line with the benchmark contract's keys; under torchrun only rank 0
+    prints and every rank exits 0."""
+    import subprocess
+    import sys
+    args = ["--impl", "reference", "--steps", "1", "--warmup", "0", "--workload", "monoexp_4k",
+            "--n-vox", "256", "--iterations", "200"]
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], capture_output=True, text=True,
+                       timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = _json_lines(r.stdout)
+    assert len(lines) == 1
+    d = lines[0]
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["config"]["workload"] == "monoexp_4k"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["e2e"]["d2h_bytes_per_step"] == 0
+
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", "29541", os.path.join(ROOT, "bench.py"),
+                        "--gpus", "2", *args], capture_output=True, text=True, timeout=300, cwd=ROOT, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert len(_json_lines(r.stdout)) == 1
