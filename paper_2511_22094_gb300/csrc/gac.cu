@@ -593,6 +593,23 @@ gac_status gac_model_register(const gac_model_desc *d, int *model_id) {
             mc.t0_f = static_cast<float>(t0);
             mc.dt_f = static_cast<float>(dt);
             mc.dtk_f = static_cast<float>(kAnchor * dt);
+            auto dd = [](double x) {
+                const float hi = static_cast<float>(x);
+                return make_float2(hi, static_cast<float>(x - static_cast<double>(hi)));
+            };
+            mc.dd_t0 = dd(t0);
+            mc.dd_dt = dd(dt);
+            mc.dd_w0 = dd(kTwoPiMilliD * t0);
+            mc.dd_w1 = dd(kTwoPiMilliD * dt);
+            mc.dd_wk = dd(kTwoPiMilliD * kAnchor * dt);
+            if (d->kind == GAC_MODEL_MWI3) {
+                // the 3-pool set-up evaluates e^{-t/T2*} - 1 for t = t0, dt >= 0 only
+                if (t0 < 0) mc.even = 0;
+                double dfmax = 0;
+                for (int j = 6; j < 8; ++j) dfmax = std::max({dfmax, std::fabs(d->lb[j]), std::fabs(d->ub[j])});
+                const double bmax = kTwoPiMilliD * dfmax * std::max(std::fabs(t0), dt);
+                mc.mwi3_small_b = bmax <= 0.78 ? 1 : 0;  // below pi/4
+            }
         }
     }
     if (d->kind == GAC_MODEL_SMT) {

@@ -12,12 +12,15 @@
 //
 // FP32 evaluation of evenly spaced echoes (MONOEXP, MWI3) uses an anchored
 // geometric recurrence: with t_k = t_0 + k dt, each pool's term is
-// E_k = E_0 R^k with R = exp(-dt (rate + i w)).  E_0, R and R^K (K = 6) come
-// from expf and sincos_cw (below); inside a block of K echoes the term advances by
-// one complex multiply, and each block starts from the previous anchor times
-// R^K.  This replaces 3 transcendental calls per echo and pool by one
-// multiply while keeping the error near that of direct evaluation (every term
-// is at most ~K + n/K roundings away from an accurately computed value).
+// E_k = E_0 R^k with R = exp(-dt (rate + i w)).  Inside a block of K = 6
+// echoes the term advances by one complex multiply, and each block starts
+// from the previous anchor times R^K.  This replaces 3 transcendental calls
+// per echo and pool by one multiply.  MONOEXP takes E_0, R and R^K from expf.
+// MWI3, whose log-likelihood at high SNR needs the forward model to a few
+// 1e-7, carries R and R^K as d = R - 1 (small for the slowly decaying pools,
+// so their rounding is far below an ulp of R and does not compound along a
+// block) and computes E_0, d and d_K from double-float arguments with an own
+// expm1 and sincos (details at eval_mwi3_f).
 // Unevenly spaced echoes, and the FP64 path, evaluate every echo directly.
 #pragma once
 #include <cstdint>
@@ -76,6 +79,10 @@ struct ModelConst {
     int n_meas;
     int even;       // acquisitions evenly spaced (recurrence allowed)
     float t0_f, dt_f, dtk_f;  // first acquisition, spacing, kAnchor * spacing
+    // the same as double-float pairs (x = hi + lo), and 2 pi 1e-3 t for t =
+    // t0, dt, kAnchor dt (the phase per Hz, in rad), for the 3-pool recurrence
+    float2 dd_t0, dd_dt, dd_w0, dd_w1, dd_wk;
+    int mwi3_small_b;  // |2 pi 1e-3 df t| <= pi/4 for t = t0, dt and every df the bounds allow
     float acq_f[GAC_MAX_ACQ];
     float acq_l2e_f[GAC_MAX_ACQ];  // acquisition x log2 e (exponentials as 2^x)
     double acq_d[GAC_MAX_ACQ];
@@ -268,6 +275,7 @@ __device__ __forceinline__ void sincos_cw(float x, float &sn, float &cs) {
 // performs exactly the operation of the scalar code, so results are
 // bit-identical while two values take one instruction.
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
 // sincos_cw on both lanes of x.
 __device__ __forceinline__ void sincos_cw2(float2 x, float2 &sn, float2 &cs) {
@@ -291,6 +299,86 @@ __device__ __forceinline__ void sincos_cw2(float2 x, float2 &sn, float2 &cs) {
     const float a1 = (n1 & 1) ? cr.y : sr.y, b1 = (n1 & 1) ? sr.y : cr.y;
     sn = make_float2((n0 & 2) ? -a0 : a0, (n1 & 2) ? -a1 : a1);
     cs = make_float2(((n0 + 1) & 2) ? -b0 : b0, ((n1 + 1) & 2) ? -b1 : b1);
+}
+
+// sincos_cw on both lanes, also returning cm = cos x - 1.  For |x| <= pi/4
+// (no quadrant shift) cm is the polynomial's own cos r - 1 = r^2 pc, so it
+// keeps its relative accuracy however small x is; otherwise cos x is far from
+// 1 and cm = cos x - 1 loses nothing.
+__device__ __forceinline__ void sincos_cm2(float2 x, float2 &sn, float2 &cs, float2 &cm) {
+    const float2 qx = __fmul2_rn(x, f2(0.636619772367581343f));
+    const float2 q = make_float2(rintf(qx.x), rintf(qx.y));
+    float2 r = __ffma2_rn(q, f2(-1.5703125f), x);
+    r = __ffma2_rn(q, f2(-4.837512969970703125e-4f), r);
+    r = __ffma2_rn(q, f2(-7.549790126404332e-8f), r);
+    const float2 r2 = __fmul2_rn(r, r);
+    float2 ps = __ffma2_rn(r2, f2(2.75573192e-6f), f2(-1.98412698e-4f));
+    ps = __ffma2_rn(ps, r2, f2(8.33333333e-3f));
+    ps = __ffma2_rn(ps, r2, f2(-1.66666667e-1f));
+    const float2 sr = __ffma2_rn(__fmul2_rn(ps, r2), r, r);
+    float2 pc = __ffma2_rn(r2, f2(-2.75573192e-7f), f2(2.48015873e-5f));
+    pc = __ffma2_rn(pc, r2, f2(-1.38888889e-3f));
+    pc = __ffma2_rn(pc, r2, f2(4.16666667e-2f));
+    pc = __ffma2_rn(pc, r2, f2(-0.5f));
+    const float2 cm0 = __fmul2_rn(pc, r2);  // cos r - 1
+    const float2 cr = __fadd2_rn(cm0, f2(1.0f));
+    const int n0 = static_cast<int>(q.x), n1 = static_cast<int>(q.y);
+    const float a0 = (n0 & 1) ? cr.x : sr.x, b0 = (n0 & 1) ? sr.x : cr.x;
+    const float a1 = (n1 & 1) ? cr.y : sr.y, b1 = (n1 & 1) ? sr.y : cr.y;
+    sn = make_float2((n0 & 2) ? -a0 : a0, (n1 & 2) ? -a1 : a1);
+    cs = make_float2(((n0 + 1) & 2) ? -b0 : b0, ((n1 + 1) & 2) ? -b1 : b1);
+    cm = make_float2(n0 == 0 ? cm0.x : cs.x - 1.0f, n1 == 0 ? cm0.y : cs.y - 1.0f);
+}
+
+// e^x - 1 on both lanes, FP32, relative accuracy kept for small |x|.  With
+// k = rint(x log2 e) and r = x - k ln 2 (ln 2 split Cody-Waite style, the
+// high part with 9 trailing zero bits so that k * hi is exact for |k| < 2^9),
+// e^r - 1 is its Taylor series to r^8/8! (|r| <= ln2/2: the rest is below
+// 6e-10 of the value) and e^x - 1 = 2^k (e^r - 1) + (2^k - 1).  For |x| <
+// ln2/2 (k = 0) the result is the polynomial itself.  x >= -80 after a clamp
+// (e^-80 - 1 = -1 in FP32); callers keep x <= 80, so 2^k stays a normal float.
+__device__ __forceinline__ float2 expm1_f2(float2 x) {
+    constexpr float kRound = 12582912.0f;  // 1.5 * 2^23: adding it rounds to an integer
+    x = make_float2(fmaxf(x.x, -80.0f), fmaxf(x.y, -80.0f));
+    const float2 t = __ffma2_rn(x, f2(1.44269504088896341f), f2(kRound));
+    const float2 k = __fadd2_rn(t, f2(-kRound));
+    float2 r = __ffma2_rn(k, f2(-0.693145751953125f), x);
+    r = __ffma2_rn(k, f2(-1.42860682030941723e-6f), r);
+    float2 p = __ffma2_rn(r, f2(2.48015873015873016e-5f), f2(1.98412698412698413e-4f));  // 1/8!, 1/7!
+    p = __ffma2_rn(p, r, f2(1.38888888888888889e-3f));                                   // 1/6!
+    p = __ffma2_rn(p, r, f2(8.33333333333333333e-3f));                                   // 1/5!
+    p = __ffma2_rn(p, r, f2(4.16666666666666667e-2f));                                   // 1/4!
+    p = __ffma2_rn(p, r, f2(1.66666666666666667e-1f));                                   // 1/3!
+    p = __ffma2_rn(p, r, f2(0.5f));                                                      // 1/2!
+    const float2 em = __ffma2_rn(__fmul2_rn(r, r), p, r);
+    // 2^k from the low bits of t (k + 127 is the biased exponent)
+    const float2 p2k = make_float2(__int_as_float((__float_as_int(t.x) << 23) + 0x3f800000),
+                                   __int_as_float((__float_as_int(t.y) << 23) + 0x3f800000));
+    return __ffma2_rn(p2k, em, __fadd2_rn(p2k, f2(-1.0f)));
+}
+
+// sin x and cos x - 1 on both lanes for |x| <= pi/4: the Taylor polynomials of
+// sincos_cw without its range reduction (cos x - 1 = x^2 pc keeps its
+// relative accuracy for small x).
+__device__ __forceinline__ void sincos_small2(float2 x, float2 &sn, float2 &cm) {
+    const float2 r2 = __fmul2_rn(x, x);
+    float2 ps = __ffma2_rn(r2, f2(2.75573192e-6f), f2(-1.98412698e-4f));
+    ps = __ffma2_rn(ps, r2, f2(8.33333333e-3f));
+    ps = __ffma2_rn(ps, r2, f2(-1.66666667e-1f));
+    sn = __ffma2_rn(__fmul2_rn(ps, r2), x, x);
+    float2 pc = __ffma2_rn(r2, f2(-2.75573192e-7f), f2(2.48015873e-5f));
+    pc = __ffma2_rn(pc, r2, f2(-1.38888889e-3f));
+    pc = __ffma2_rn(pc, r2, f2(4.16666667e-2f));
+    pc = __ffma2_rn(pc, r2, f2(-0.5f));
+    cm = __fmul2_rn(pc, r2);
+}
+
+// 1/x on the special-function unit (rcp.approx, ~1 ulp); callers that need
+// the exact reciprocal add the Newton residual r (1 - r x) as a low part.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
 // ----------------------------------------------------------- FP32 models --
@@ -341,51 +429,114 @@ __device__ __forceinline__ void eval_mwi3_f(const float *th, const ModelConst &m
     const float phi0 = th[8];
     const int n = mc.n_acq;
     if (mc.even) {
-        // Per pool: E_0 = A exp(-t0/T2*) e^{i(phi0 - w t0)}, R = exp(-dt (1/T2* + i w))
-        // and R^K.  The myelin- and intra-axonal pools (which have frequency
-        // offsets) are carried as lane pairs: X = (Re E_MW, Re E_IW),
-        // Y = (Im E_MW, Im E_IW); the extra-cellular pool, whose ratio R is
-        // real, as Z = (Re E_EW, Im E_EW).
-        const float rate0 = 1.0f / th[3], rate1 = 1.0f / th[4], rate2 = 1.0f / th[5];
-        const float2 w = make_float2(kTwoPiMilli * th[6], kTwoPiMilli * th[7]);  // rad / ms
-        const float2 m0 = make_float2(th[0] * expf(-mc.t0_f * rate0), th[1] * expf(-mc.t0_f * rate1));
-        const float2 m1 = make_float2(expf(-mc.dt_f * rate0), expf(-mc.dt_f * rate1));
-        const float2 mk = make_float2(expf(-mc.dtk_f * rate0), expf(-mc.dtk_f * rate1));
-        float2 s, c;
-        sincos_cw2(__ffma2_rn(make_float2(-w.x, -w.y), f2(mc.t0_f), f2(phi0)), s, c);
-        float2 X = __fmul2_rn(m0, c), Y = __fmul2_rn(m0, s);
-        sincos_cw2(__fmul2_rn(make_float2(-w.x, -w.y), f2(mc.dt_f)), s, c);
-        const float2 RR = __fmul2_rn(m1, c), RI = __fmul2_rn(m1, s);
-        const float2 NRI = make_float2(-RI.x, -RI.y);
-        sincos_cw2(__fmul2_rn(make_float2(-w.x, -w.y), f2(mc.dtk_f)), s, c);
-        const float2 KR = __fmul2_rn(mk, c), KI = __fmul2_rn(mk, s);
-        const float2 NKI = make_float2(-KI.x, -KI.y);
+        // Per pool j: E_0 = A_j e^{-t0/T2*_j} e^{i(phi0 - w_j t0)} and the ratios
+        // R = e^{-dt (1/T2*_j + i w_j)} and R^K, the ratios in delta form
+        // d = R - 1.  The slow pools have |d| << 1, so rounding d costs far
+        // less than an ulp of R, and E <- E + E d advances a term without
+        // compounding R's own rounding over the block.  The set-up, in FP32:
+        //  - a = t / T2* for t = t0, dt as a double-float (t and 1/T2* as
+        //    hi + lo pairs), e^{-a} - 1 = expm1_f2(-a_hi) - a_lo e^{-a};
+        //  - (1 + em_dt)^K - 1 by squaring in delta form;
+        //  - the phases b = w t = df (2 pi 1e-3 t) as double-floats, the
+        //    phasor e^{-ib} - 1 = (cos b - 1, -sin b) of the high part,
+        //    corrected to first order by the low part;
+        //  - d = (1 + em)(1 + cm + i sn) - 1 = em + cm + em cm + i (sn + em sn);
+        //  - E_0 = A (1 + em_0) e^{i phi0} e^{-i b0}, the last factor applied
+        //    in delta form to e^{i phi0} (which the extra-cellular pool uses
+        //    as it is), and A (1 + em_0) c = A c + (A em_0 c + err(A c)).
+        // The myelin- and intra-axonal pools (frequency offsets) are carried as
+        // lane pairs: X = (Re E_MW, Re E_IW), Y = (Im E_MW, Im E_IW); the
+        // extra-cellular pool, whose ratio is real, as Z = (Re E_EW, Im E_EW).
+        static_assert(kAnchor == 6, "R^K is formed as ((1 + d)^2 (1 + d))^2");
+        const float2 T2 = make_float2(th[3], th[4]);
+        const float2 rh = make_float2(rcp_approx(th[3]), rcp_approx(th[4]));
+        const float2 rl = __fmul2_rn(rh, __ffma2_rn(neg2(rh), T2, f2(1.0f)));
+        const float rh2 = rcp_approx(th[5]);
+        const float rl2 = rh2 * fmaf(-rh2, th[5], 1.0f);
+        // e^{-t r} - 1 per lane, t = th + tl, r = rh + rl
+        auto em_of = [](float2 rh_, float2 rl_, float2 th_, float2 tl_) {
+            const float2 ah = __fmul2_rn(rh_, th_);
+            float2 al = __ffma2_rn(rh_, th_, neg2(ah));
+            al = __ffma2_rn(rl_, th_, al);
+            al = __ffma2_rn(rh_, tl_, al);
+            const float2 em = expm1_f2(neg2(ah));
+            return __ffma2_rn(neg2(al), em, __fadd2_rn(em, neg2(al)));
+        };
+        const float2 em0 = em_of(rh, rl, f2(mc.dd_t0.x), f2(mc.dd_t0.y));  // MW, IW over t0
+        const float2 em1 = em_of(rh, rl, f2(mc.dd_dt.x), f2(mc.dd_dt.y));  // MW, IW over dt
+        const float2 emE = em_of(f2(rh2), f2(rl2), make_float2(mc.dd_t0.x, mc.dd_dt.x),
+                                 make_float2(mc.dd_t0.y, mc.dd_dt.y));  // EW over t0, dt
+        // (1 + e)^6 - 1: e2 = e (2 + e), e3 = e2 + e + e2 e, e6 = e3 (2 + e3)
+        const float2 e2 = __ffma2_rn(em1, em1, __fadd2_rn(em1, em1));
+        const float2 e3 = __ffma2_rn(e2, em1, __fadd2_rn(e2, em1));
+        const float2 emK = __ffma2_rn(e3, e3, __fadd2_rn(e3, e3));
+        const float dE = emE.y;
+        const float dE2 = fmaf(dE, dE, dE + dE), dE3 = fmaf(dE2, dE, dE2 + dE);
+        const float dKE = fmaf(dE3, dE3, dE3 + dE3);
+        // phases b = df (2 pi 1e-3 t) as hi + lo
+        const float2 df = make_float2(th[6], th[7]);
+        auto phase = [&df](float2 c, float2 &lo) {
+            const float2 bh = __fmul2_rn(df, f2(c.x));
+            lo = __ffma2_rn(df, f2(c.y), __ffma2_rn(df, f2(c.x), neg2(bh)));
+            return bh;
+        };
+        // e^{-i(bh + bl)} - 1 as (cos - 1, sin); SMALL: |bh| <= pi/4
+        auto phasor = [](float2 bh, float2 bl, bool small, float2 &cm1, float2 &sn1) {
+            float2 sn, cs, cm;
+            if (small) {
+                sincos_small2(neg2(bh), sn, cm);
+                cs = __fadd2_rn(cm, f2(1.0f));
+            } else {
+                sincos_cm2(neg2(bh), sn, cs, cm);
+            }
+            sn1 = __ffma2_rn(cs, neg2(bl), sn);
+            cm1 = __ffma2_rn(sn, bl, cm);
+        };
+        const bool small = mc.mwi3_small_b != 0;  // the same for every thread
+        float2 b0l, b1l, bkl;
+        const float2 b0h = phase(mc.dd_w0, b0l), b1h = phase(mc.dd_w1, b1l), bkh = phase(mc.dd_wk, bkl);
+        float2 DR, DI, KR, KI, cmb, snb;
+        phasor(b1h, b1l, small, cmb, snb);
+        DR = __ffma2_rn(em1, cmb, __fadd2_rn(em1, cmb));
+        DI = __ffma2_rn(em1, snb, snb);
+        phasor(bkh, bkl, false, cmb, snb);
+        KR = __ffma2_rn(emK, cmb, __fadd2_rn(emK, cmb));
+        KI = __ffma2_rn(emK, snb, snb);
+        // E_0: e^{i phi0} (1 + cm + i sn) = e^{i phi0} + (ce cm - se sn, se cm + ce sn)
         float se, ce;
         sincos_cw(phi0, se, ce);
-        const float m2 = th[2] * expf(-mc.t0_f * rate2);
-        float2 Z = make_float2(m2 * ce, m2 * se);
-        const float2 R2 = f2(expf(-mc.dt_f * rate2));
-        const float2 K2 = f2(expf(-mc.dtk_f * rate2));
+        phasor(b0h, b0l, small, cmb, snb);
+        const float2 c0 = __fadd2_rn(f2(ce), __ffma2_rn(f2(ce), cmb, __fmul2_rn(f2(-se), snb)));
+        const float2 s0 = __fadd2_rn(f2(se), __ffma2_rn(f2(se), cmb, __fmul2_rn(f2(ce), snb)));
+        auto amp = [](float2 a, float2 aem, float2 c) {
+            const float2 p = __fmul2_rn(a, c);
+            return __fadd2_rn(p, __ffma2_rn(aem, c, __ffma2_rn(a, c, neg2(p))));
+        };
+        const float2 A = make_float2(th[0], th[1]);
+        const float2 Aem = __fmul2_rn(A, em0);
+        float2 X = amp(A, Aem, c0), Y = amp(A, Aem, s0);
+        float2 Z = amp(f2(th[2]), f2(th[2] * emE.x), make_float2(ce, se));
+        const float2 NDI = neg2(DI), NKI = neg2(KI);
         // one block of echoes a .. a+cnt-1 from the current anchors
         auto block = [&](int a, int cnt, bool full) {
             float2 x = X, y = Y, z = Z;
 #pragma unroll
             for (int i = 0; i < kAnchor; ++i) {
                 if (full || i < cnt) visit(a + i, x.x + x.y + z.x, y.x + y.y + z.y);
-                const float2 xn = __ffma2_rn(x, RR, __fmul2_rn(y, NRI));
-                y = __ffma2_rn(x, RI, __fmul2_rn(y, RR));
+                const float2 xn = __ffma2_rn(x, DR, __ffma2_rn(y, NDI, x));
+                y = __ffma2_rn(y, DR, __ffma2_rn(x, DI, y));
                 x = xn;
-                z = __fmul2_rn(z, R2);
+                z = __ffma2_rn(z, f2(dE), z);
             }
         };
         int a = 0;
         for (; a + kAnchor <= n; a += kAnchor) {
             block(a, kAnchor, true);
             end_block(visit, 0);
-            const float2 xn = __ffma2_rn(X, KR, __fmul2_rn(Y, NKI));
-            Y = __ffma2_rn(X, KI, __fmul2_rn(Y, KR));
+            const float2 xn = __ffma2_rn(X, KR, __ffma2_rn(Y, NKI, X));
+            Y = __ffma2_rn(Y, KR, __ffma2_rn(X, KI, Y));
             X = xn;
-            Z = __fmul2_rn(Z, K2);
+            Z = __ffma2_rn(Z, f2(dKE), Z);
         }
         if (a < n) block(a, n - a, false);
     } else {

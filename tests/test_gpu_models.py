@@ -111,16 +111,17 @@ def test_g_table_beyond_its_range(gac, orc):
 
 LOGLIK = [(W.MONOEXP_4K, 1e-3), (W.MWI3_1M, 1e-3), (W.SMT_1P5M, 1e-3), (W.AXCAL_250K, 1e-3),
           (W.MWI3_1M.with_(name="mwi3_snr50", snr=50.0), 1e-3),
-          (W.MWI3_1M.with_(name="mwi3_snr300", snr=300.0), 2e-3)]
+          (W.MWI3_1M.with_(name="mwi3_snr300", snr=300.0), 1e-3)]
 
 
 @pytest.mark.parametrize("w,tol", LOGLIK, ids=[c[0].name for c in LOGLIK])
 def test_loglik_parity_at_posterior_typical_theta(gac, orc, w, tol):
     """|L_gpu - L_ref| at the true parameters, a typical posterior draw
-    (|L| ~ M/2).  The FP32 forward model carries a relative error of a few
-    1e-7 of |S|, i.e. ~SNR x 1e-7 in units of sigma per measurement, so the
-    bound grows with SNR: 1e-3 holds up to SNR 150; at SNR 300 the FP32
-    paths reach ~1.2e-3 (the FP64 path is exact to 1e-8)."""
+    (|L| ~ M/2).  The FP32 forward model's error enters L as ~sqrt(M) x
+    (relative error) x SNR, so the SNR-300 case is the tight one: the 3-pool
+    recurrence in delta form with its double-float set-up keeps the relative
+    error near 2.6e-7, i.e. |dL| ~ 5e-4 there (the FP64 path is exact to
+    1e-8)."""
     mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
     n = 100_000
     th, sig, y = make_voxels(orc, w, 0, n)
