@@ -409,10 +409,31 @@ int row_stride_for(int kind, int M) {
     return M | 1;
 }
 
+template <int KIND>
+static int block_of(int prec) {
+    switch (prec) {
+    case GAC_PREC_MIXED: return mh_block<KIND, GAC_PREC_MIXED>();
+    case GAC_PREC_FP32: return mh_block<KIND, GAC_PREC_FP32>();
+    default: return mh_block<KIND, GAC_PREC_FP64>();
+    }
+}
+
+// Threads per block of the one-launch kernel for (kind, precision).
+int mh_block_size(int kind, int prec) {
+    switch (kind) {
+    case GAC_MODEL_MONOEXP: return block_of<GAC_MODEL_MONOEXP>(prec);
+    case GAC_MODEL_MWI3: return block_of<GAC_MODEL_MWI3>(prec);
+    case GAC_MODEL_SMT: return block_of<GAC_MODEL_SMT>(prec);
+    case GAC_MODEL_AXCAL_SMT: return block_of<GAC_MODEL_AXCAL_SMT>(prec);
+    default: return block_of<GAC_MODEL_LINEAR_TEST>(prec);
+    }
+}
+
 size_t smem_bytes_for(int kind, int prec, int C, int M, int moments_mode) {
     const size_t w = (prec == GAC_PREC_FP32) ? sizeof(float) : sizeof(double);
     const bool blocked = prec == GAC_PREC_MIXED && moments_mode == GAC_MOMENTS_ALL_POSTBURNIN;
-    return tile_smem_bytes(model_n_par(kind), w, kBlock / C, row_stride_for(kind, M), true, blocked);
+    const int block = mh_block_size(kind, prec);
+    return tile_smem_bytes(model_n_par(kind), w, block / C, row_stride_for(kind, M), true, blocked, block);
 }
 
 const void *mh_kernel_ptr(int kind, int prec, bool trace) {
@@ -453,7 +474,8 @@ gac_status plan_launch(const ModelConst &mc, int prec, bool trace, int C, int64_
     e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(carveout)");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, smem);
+    const int block = mh_block_size(mc.kind, prec);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (per_sm < 1) return fail(GAC_ERR_INVALID_ARG, "kernel does not fit on an SM (smem %zu)", smem);
     // Voxels per tile: a full block's worth, unless the problem is too small
@@ -465,10 +487,10 @@ gac_status plan_launch(const ModelConst &mc, int prec, bool trace, int C, int64_
     // tiling (random numbers are keyed by voxel, chain and iteration).
     const int64_t resident = static_cast<int64_t>(per_sm) * sm_count();
     const int64_t chains = n_vox * C;
-    int threads = kBlock;
-    if (chains < resident * kBlock) {
+    int threads = block;
+    if (chains < resident * block) {
         const int64_t want = (chains + resident - 1) / resident;  // chains per block
-        threads = static_cast<int>(std::min<int64_t>(kBlock, std::max<int64_t>(32, (want + 31) / 32 * 32)));
+        threads = static_cast<int>(std::min<int64_t>(block, std::max<int64_t>(32, (want + 31) / 32 * 32)));
     }
     *vb = std::max(1, threads / C);
     *n_tiles = (n_vox + *vb - 1) / *vb;
@@ -608,7 +630,10 @@ gac_status gac_model_register(const gac_model_desc *d, int *model_id) {
                 double dfmax = 0;
                 for (int j = 6; j < 8; ++j) dfmax = std::max({dfmax, std::fabs(d->lb[j]), std::fabs(d->ub[j])});
                 const double bmax = kTwoPiMilliD * dfmax * std::max(std::fabs(t0), dt);
-                mc.mwi3_small_b = bmax <= 0.78 ? 1 : 0;  // below pi/4
+                const double bkh = kTwoPiMilliD * dfmax * 0.5 * kAnchor * dt;
+                mc.dd_wkh = dd(kTwoPiMilliD * 0.5 * kAnchor * dt);
+                mc.mwi3_flags = (bmax <= 0.78 ? kMwi3SmallB : 0) | (bkh <= 0.78 ? kMwi3SmallBK : 0) |
+                                (std::max(t0, dt) / d->lb[5] <= 0.34 ? kMwi3SmallEW : 0);  // pi/4, ln2/2
             }
         }
     }

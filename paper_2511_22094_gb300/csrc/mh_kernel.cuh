@@ -58,6 +58,19 @@ constexpr int mh_min_blocks() {
     return PREC == GAC_PREC_FP64 ? 1 : ((KIND == GAC_MODEL_MWI3 || KIND == GAC_MODEL_AXCAL_SMT) ? 2 : 3);
 }
 
+// The one-launch kernel's own block size and blocks per SM (the serving and
+// allocation-free kernels always run blocks of kBlock).  Measured on the
+// 3-pool MIXED kernel: blocks of 128 threads, 5 or 6 per SM (20 or 24 warps),
+// ran 3% slower than 2 blocks of 256, so every kind keeps kBlock.
+template <int KIND, int PREC>
+__host__ __device__ constexpr int mh_block() {
+    return kBlock;
+}
+template <int KIND, int PREC>
+constexpr int mh_launch_min_blocks() {
+    return mh_block<KIND, PREC>() == kBlock ? mh_min_blocks<KIND, PREC>() : 5;
+}
+
 struct RunArgs {
     const float *data;   // [N][M]
     const float *sigma;  // [N] or nullptr
@@ -184,12 +197,13 @@ __device__ __forceinline__ bool accept_step(typename PrecTraits<PREC>::R Lp,
 
 // Shared-memory bytes of one block: Welford accumulators (one-launch driver
 // only) + the measurement tile + the MIXED all-post-burn-in block partials
-// ([3P][kBlock] floats, when blocked_moments).
+// ([3P][block] floats, when blocked_moments), for blocks of `block` threads.
 __host__ __device__ inline size_t tile_smem_bytes(int P, size_t w_bytes, int VB, int row_stride,
-                                                  bool welford_in_smem, bool blocked_moments = false) {
-    return (welford_in_smem ? 2 * static_cast<size_t>(P) * kBlock * w_bytes : 0) +
+                                                  bool welford_in_smem, bool blocked_moments = false,
+                                                  int block = kBlock) {
+    return (welford_in_smem ? 2 * static_cast<size_t>(P) * block * w_bytes : 0) +
            static_cast<size_t>(VB) * row_stride * sizeof(float) +
-           (blocked_moments ? 3 * static_cast<size_t>(P) * kBlock * sizeof(float) : 0);
+           (blocked_moments ? 3 * static_cast<size_t>(P) * block * sizeof(float) : 0);
 }
 
 // Pools one parameter of C chains that each hold n values, from their
@@ -231,7 +245,7 @@ __device__ __forceinline__ void pool_chains(const W *mean_k, const W *m2_k, int 
 // SLICED = false: t_begin = 0, t_end = I, Welford accumulators in shared
 // memory at the start of `smem`; SLICED = true: chain state and accumulators
 // in `ss` (HBM).
-template <int KIND, int PREC, bool TRACE, bool SLICED>
+template <int KIND, int PREC, bool TRACE, bool SLICED, int BLK = kBlock>
 __device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra,
                                          const SliceState &ss, int64_t tile, int t_begin,
                                          int t_end, unsigned char *smem) {
@@ -263,15 +277,15 @@ __device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra
         ytile = reinterpret_cast<float *>(smem);
     } else {
         wf_mean = reinterpret_cast<W *>(smem);
-        wf_m2 = wf_mean + P * kBlock;
-        wf_stride = kBlock;
+        wf_m2 = wf_mean + P * BLK;
+        wf_stride = BLK;
         wf_idx = tid;
-        ytile = reinterpret_cast<float *>(wf_m2 + P * kBlock);
+        ytile = reinterpret_cast<float *>(wf_m2 + P * BLK);
     }
 
     const int64_t left = ra.n_vox - v0;
     const int nv = left < VB ? static_cast<int>(left) : VB;
-    // MIXED all-post-burn-in block partials: s1 [P][kBlock], s2, reference
+    // MIXED all-post-burn-in block partials: s1 [P][BLK], s2, reference
     float *const bs = ytile + VB * ra.row_stride;
 
     // a1: stage measurements of voxels [v0, v0 + nv) (and the model's
@@ -283,7 +297,7 @@ __device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra
         const int total = nv * M;
         if (ra.data_vec4) {
             const float4 *src4 = reinterpret_cast<const float4 *>(src);
-            for (int i = tid; i < total / 4; i += kBlock) {
+            for (int i = tid; i < total / 4; i += BLK) {
                 const float4 q = __ldg(src4 + i);
                 const int e = 4 * i, row = e / M, col = e - row * M;
                 float *dst = ytile + row * ra.row_stride + col;
@@ -293,7 +307,7 @@ __device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra
                 dst[3] = q.w;
             }
         } else {
-            for (int i = tid; i < total; i += kBlock) {
+            for (int i = tid; i < total; i += BLK) {
                 const int row = i / M, col = i - row * M;
                 ytile[row * ra.row_stride + col] = __ldg(src + i);
             }
@@ -366,7 +380,7 @@ __device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra
                 n_mom -= blk_n;
                 if constexpr (SLICED) {
                     if (blk_n > 0)
-                        for (int k = 0; k < 3 * P; ++k) bs[k * kBlock + tid] = ss.blk[k * nchains + ch];
+                        for (int k = 0; k < 3 * P; ++k) bs[k * BLK + tid] = ss.blk[k * nchains + ch];
                 }
             }
         }
@@ -445,20 +459,20 @@ __device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra
                 }
                 if (kBlocked && all_mode) {
                     if (t > ra.B) {
-                        float *s1 = bs + tid, *s2 = bs + P * kBlock + tid, *ref = bs + 2 * P * kBlock + tid;
+                        float *s1 = bs + tid, *s2 = bs + P * BLK + tid, *ref = bs + 2 * P * BLK + tid;
                         if (blk_n == 0) {  // a block's first state is its reference (the same t for every thread)
 #pragma unroll
                             for (int p = 0; p < P; ++p) {
-                                ref[p * kBlock] = static_cast<float>(th[p]);
-                                s1[p * kBlock] = 0.0f;
-                                s2[p * kBlock] = 0.0f;
+                                ref[p * BLK] = static_cast<float>(th[p]);
+                                s1[p * BLK] = 0.0f;
+                                s2[p * BLK] = 0.0f;
                             }
                         } else {
 #pragma unroll
                             for (int p = 0; p < P; ++p) {
-                                const float d = static_cast<float>(th[p]) - ref[p * kBlock];
-                                s1[p * kBlock] += d;
-                                s2[p * kBlock] = fmaf(d, d, s2[p * kBlock]);
+                                const float d = static_cast<float>(th[p]) - ref[p * BLK];
+                                s1[p * BLK] += d;
+                                s2[p * BLK] = fmaf(d, d, s2[p * BLK]);
                             }
                         }
                         if (++blk_n == kMomBlock || t == ra.I) {
@@ -468,9 +482,9 @@ __device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra
                             const double inv_nb = 1.0 / nb, w_b = nb / nn, cross = static_cast<double>(n_mom) * w_b;
 #pragma unroll
                             for (int p = 0; p < P; ++p) {
-                                const double a = s1[p * kBlock];
-                                const double mb = static_cast<double>(ref[p * kBlock]) + a * inv_nb;
-                                const double m2b = fma(-a, a * inv_nb, static_cast<double>(s2[p * kBlock]));
+                                const double a = s1[p * BLK];
+                                const double mb = static_cast<double>(ref[p * BLK]) + a * inv_nb;
+                                const double m2b = fma(-a, a * inv_nb, static_cast<double>(s2[p * BLK]));
                                 const double m = static_cast<double>(wf_mean[p * wf_stride + wf_idx]);
                                 const double delta = mb - m;
                                 wf_mean[p * wf_stride + wf_idx] = static_cast<W>(fma(delta, w_b, m));
@@ -517,7 +531,7 @@ __device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra
             ss.adapt[nchains + ch] = ad_acc0;
             if constexpr (kBlocked) {
                 if (all_mode && blk_n > 0)
-                    for (int k = 0; k < 3 * P; ++k) ss.blk[k * nchains + ch] = bs[k * kBlock + tid];
+                    for (int k = 0; k < 3 * P; ++k) ss.blk[k * nchains + ch] = bs[k * BLK + tid];
             }
         }
     }
@@ -537,12 +551,12 @@ __device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra
 
 // One job, one launch: every tile runs all I iterations.
 template <int KIND, int PREC, bool TRACE>
-__global__ void __launch_bounds__(kBlock, mh_min_blocks<KIND, PREC>())
+__global__ void __launch_bounds__(mh_block<KIND, PREC>(), mh_launch_min_blocks<KIND, PREC>())
     mh_kernel(const ModelConst mc, const RunArgs ra) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SliceState none{};
     for (int64_t tile = blockIdx.x; tile < ra.n_tiles; tile += gridDim.x)
-        run_tile<KIND, PREC, TRACE, false>(mc, ra, none, tile, 0, ra.I, smem_raw);
+        run_tile<KIND, PREC, TRACE, false, mh_block<KIND, PREC>()>(mc, ra, none, tile, 0, ra.I, smem_raw);
 }
 
 }  // namespace gac

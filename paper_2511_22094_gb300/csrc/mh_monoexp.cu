@@ -20,7 +20,7 @@ const void *mh_ptr_monoexp(int prec, bool trace) {
 
 template <int PREC, bool TRACE>
 static cudaError_t go(const ModelConst &mc, const RunArgs &ra, const LaunchCfg &cfg) {
-    mh_kernel<GAC_MODEL_MONOEXP, PREC, TRACE><<<cfg.grid, kBlock, cfg.smem, cfg.stream>>>(mc, ra);
+    mh_kernel<GAC_MODEL_MONOEXP, PREC, TRACE><<<cfg.grid, (mh_block<GAC_MODEL_MONOEXP, PREC>()), cfg.smem, cfg.stream>>>(mc, ra);
     return cudaGetLastError();
 }
 

@@ -20,7 +20,7 @@ const void *mh_ptr_mwi3(int prec, bool trace) {
 
 template <int PREC, bool TRACE>
 static cudaError_t go(const ModelConst &mc, const RunArgs &ra, const LaunchCfg &cfg) {
-    mh_kernel<GAC_MODEL_MWI3, PREC, TRACE><<<cfg.grid, kBlock, cfg.smem, cfg.stream>>>(mc, ra);
+    mh_kernel<GAC_MODEL_MWI3, PREC, TRACE><<<cfg.grid, (mh_block<GAC_MODEL_MWI3, PREC>()), cfg.smem, cfg.stream>>>(mc, ra);
     return cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@
 // Unevenly spaced echoes, and the FP64 path, evaluate every echo directly.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 
 #include "gac.h"
 
@@ -82,7 +83,12 @@ struct ModelConst {
     // the same as double-float pairs (x = hi + lo), and 2 pi 1e-3 t for t =
     // t0, dt, kAnchor dt (the phase per Hz, in rad), for the 3-pool recurrence
     float2 dd_t0, dd_dt, dd_w0, dd_w1, dd_wk;
-    int mwi3_small_b;  // |2 pi 1e-3 df t| <= pi/4 for t = t0, dt and every df the bounds allow
+    // 3-pool set-up shortcuts that registration proved safe for every
+    // parameter the bounds allow: kMwi3SmallB |2 pi 1e-3 df t| <= pi/4 for
+    // t = t0, dt; kMwi3SmallBK the same for t = kAnchor dt / 2;
+    // kMwi3SmallEW t / T2*_EW <= ln2/2 for t = t0, dt
+    int mwi3_flags;
+    float2 dd_wkh;  // dd_wk / 2
     float acq_f[GAC_MAX_ACQ];
     float acq_l2e_f[GAC_MAX_ACQ];  // acquisition x log2 e (exponentials as 2^x)
     double acq_d[GAC_MAX_ACQ];
@@ -113,6 +119,7 @@ __host__ __device__ constexpr int model_n_par(int kind) {
 }
 __host__ __device__ constexpr bool model_complex(int kind) { return kind == GAC_MODEL_MWI3; }
 
+constexpr int kMwi3SmallB = 1, kMwi3SmallBK = 2, kMwi3SmallEW = 4;
 constexpr float kTwoPiMilli = 6.28318530717958648e-3f;  // 2 pi * 1e-3: Hz * ms -> rad
 constexpr double kTwoPiMilliD = 6.28318530717958648e-3;
 constexpr float kSqrtPiHalf = 0.886226925452758014f;
@@ -337,13 +344,20 @@ __device__ __forceinline__ void sincos_cm2(float2 x, float2 &sn, float2 &cs, flo
 // 6e-10 of the value) and e^x - 1 = 2^k (e^r - 1) + (2^k - 1).  For |x| <
 // ln2/2 (k = 0) the result is the polynomial itself.  x >= -80 after a clamp
 // (e^-80 - 1 = -1 in FP32); callers keep x <= 80, so 2^k stays a normal float.
+// SMALL: the caller guarantees |x| <= ln2/2, so k = 0 and r = x.
+template <bool SMALL = false>
 __device__ __forceinline__ float2 expm1_f2(float2 x) {
     constexpr float kRound = 12582912.0f;  // 1.5 * 2^23: adding it rounds to an integer
-    x = make_float2(fmaxf(x.x, -80.0f), fmaxf(x.y, -80.0f));
-    const float2 t = __ffma2_rn(x, f2(1.44269504088896341f), f2(kRound));
-    const float2 k = __fadd2_rn(t, f2(-kRound));
-    float2 r = __ffma2_rn(k, f2(-0.693145751953125f), x);
-    r = __ffma2_rn(k, f2(-1.42860682030941723e-6f), r);
+    float2 t, r;
+    if constexpr (SMALL) {
+        r = x;
+    } else {
+        x = make_float2(fmaxf(x.x, -80.0f), fmaxf(x.y, -80.0f));
+        t = __ffma2_rn(x, f2(1.44269504088896341f), f2(kRound));
+        const float2 k = __fadd2_rn(t, f2(-kRound));
+        r = __ffma2_rn(k, f2(-0.693145751953125f), x);
+        r = __ffma2_rn(k, f2(-1.42860682030941723e-6f), r);
+    }
     float2 p = __ffma2_rn(r, f2(2.48015873015873016e-5f), f2(1.98412698412698413e-4f));  // 1/8!, 1/7!
     p = __ffma2_rn(p, r, f2(1.38888888888888889e-3f));                                   // 1/6!
     p = __ffma2_rn(p, r, f2(8.33333333333333333e-3f));                                   // 1/5!
@@ -351,6 +365,7 @@ __device__ __forceinline__ float2 expm1_f2(float2 x) {
     p = __ffma2_rn(p, r, f2(1.66666666666666667e-1f));                                   // 1/3!
     p = __ffma2_rn(p, r, f2(0.5f));                                                      // 1/2!
     const float2 em = __ffma2_rn(__fmul2_rn(r, r), p, r);
+    if constexpr (SMALL) return em;
     // 2^k from the low bits of t (k + 127 is the biased exponent)
     const float2 p2k = make_float2(__int_as_float((__float_as_int(t.x) << 23) + 0x3f800000),
                                    __int_as_float((__float_as_int(t.y) << 23) + 0x3f800000));
@@ -454,18 +469,20 @@ __device__ __forceinline__ void eval_mwi3_f(const float *th, const ModelConst &m
         const float rh2 = rcp_approx(th[5]);
         const float rl2 = rh2 * fmaf(-rh2, th[5], 1.0f);
         // e^{-t r} - 1 per lane, t = th + tl, r = rh + rl
-        auto em_of = [](float2 rh_, float2 rl_, float2 th_, float2 tl_) {
+        auto em_of = [](float2 rh_, float2 rl_, float2 th_, float2 tl_, auto small) {
             const float2 ah = __fmul2_rn(rh_, th_);
             float2 al = __ffma2_rn(rh_, th_, neg2(ah));
             al = __ffma2_rn(rl_, th_, al);
             al = __ffma2_rn(rh_, tl_, al);
-            const float2 em = expm1_f2(neg2(ah));
+            const float2 em = expm1_f2<decltype(small)::value>(neg2(ah));
             return __ffma2_rn(neg2(al), em, __fadd2_rn(em, neg2(al)));
         };
-        const float2 em0 = em_of(rh, rl, f2(mc.dd_t0.x), f2(mc.dd_t0.y));  // MW, IW over t0
-        const float2 em1 = em_of(rh, rl, f2(mc.dd_dt.x), f2(mc.dd_dt.y));  // MW, IW over dt
-        const float2 emE = em_of(f2(rh2), f2(rl2), make_float2(mc.dd_t0.x, mc.dd_dt.x),
-                                 make_float2(mc.dd_t0.y, mc.dd_dt.y));  // EW over t0, dt
+        using Full = std::false_type;
+        const float2 em0 = em_of(rh, rl, f2(mc.dd_t0.x), f2(mc.dd_t0.y), Full{});  // MW, IW over t0
+        const float2 em1 = em_of(rh, rl, f2(mc.dd_dt.x), f2(mc.dd_dt.y), Full{});  // MW, IW over dt
+        const float2 tE = make_float2(mc.dd_t0.x, mc.dd_dt.x), tlE = make_float2(mc.dd_t0.y, mc.dd_dt.y);
+        const float2 emE = (mc.mwi3_flags & kMwi3SmallEW) ? em_of(f2(rh2), f2(rl2), tE, tlE, std::true_type{})
+                                                          : em_of(f2(rh2), f2(rl2), tE, tlE, Full{});  // EW over t0, dt
         // (1 + e)^6 - 1: e2 = e (2 + e), e3 = e2 + e + e2 e, e6 = e3 (2 + e3)
         const float2 e2 = __ffma2_rn(em1, em1, __fadd2_rn(em1, em1));
         const float2 e3 = __ffma2_rn(e2, em1, __fadd2_rn(e2, em1));
@@ -492,14 +509,27 @@ __device__ __forceinline__ void eval_mwi3_f(const float *th, const ModelConst &m
             sn1 = __ffma2_rn(cs, neg2(bl), sn);
             cm1 = __ffma2_rn(sn, bl, cm);
         };
-        const bool small = mc.mwi3_small_b != 0;  // the same for every thread
-        float2 b0l, b1l, bkl;
-        const float2 b0h = phase(mc.dd_w0, b0l), b1h = phase(mc.dd_w1, b1l), bkh = phase(mc.dd_wk, bkl);
+        const bool small = (mc.mwi3_flags & kMwi3SmallB) != 0;  // the same for every thread
+        float2 b0l, b1l;
+        const float2 b0h = phase(mc.dd_w0, b0l), b1h = phase(mc.dd_w1, b1l);
         float2 DR, DI, KR, KI, cmb, snb;
         phasor(b1h, b1l, small, cmb, snb);
         DR = __ffma2_rn(em1, cmb, __fadd2_rn(em1, cmb));
         DI = __ffma2_rn(em1, snb, snb);
-        phasor(bkh, bkl, false, cmb, snb);
+        if (mc.mwi3_flags & kMwi3SmallBK) {
+            // e^{-i bK} - 1 = u (2 + u) from u = e^{-i bK/2} - 1
+            float2 bkl;
+            const float2 bkh = phase(mc.dd_wkh, bkl);
+            float2 ur, ui;
+            phasor(bkh, bkl, true, ur, ui);
+            const float2 ur2 = __fadd2_rn(ur, ur);
+            cmb = __ffma2_rn(ur, ur, __ffma2_rn(neg2(ui), ui, ur2));
+            snb = __ffma2_rn(ur2, ui, __fadd2_rn(ui, ui));
+        } else {
+            float2 bkl;
+            const float2 bkh = phase(mc.dd_wk, bkl);
+            phasor(bkh, bkl, false, cmb, snb);
+        }
         KR = __ffma2_rn(emK, cmb, __fadd2_rn(emK, cmb));
         KI = __ffma2_rn(emK, snb, snb);
         // E_0: e^{i phi0} (1 + cm + i sn) = e^{i phi0} + (ce cm - se sn, se cm + ce sn)
