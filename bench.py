@@ -7,9 +7,13 @@ moments).  Default workload: the 3-pool complex myelin-water model at
 samples stored), synthetic seeded data, inputs resident in HBM.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload mwi3_1m|smt_1p5m|monoexp_4k]
+                    [--workload mwi3_1m|smt_1p5m|monoexp_4k] [--no-extras]
 
-Prints one JSON line (rank 0).  Under torchrun each rank samples its own
+Prints one JSON line (rank 0).  At one GPU on the default workload the line
+also carries `workloads` (the mono-exponential 4k and the Standard Model 1.5M
+workloads, each timed like the headline) and `serving` (the 200-job serving
+trace, continuous batching against one launch per job, Poisson arrivals and
+all at t = 0), each with the clocks sampled while it ran.  Under torchrun each rank samples its own
 volume of the same size (voxel_base = rank * N: weak scaling, no collective on
 the data path; the barrier and max-over-ranks timing use the process group).
 """
@@ -437,6 +441,106 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def _roofline(base_name, sampler, ci_s, rates, sms, clocks, meas):
+    """The direct-form ALU roofline of a sampler workload at ci_s
+    chain-iterations (or walker moves) per second: the model's algorithmic
+    MUFU and FP32+INT counts against the measured pipe rates at the maximum
+    SM clock, whichever bounds; with the executed-instruction (issue) fraction
+    when an ncu count for the current sources exists."""
+    f_max = (_peaks().get("sm_max_mhz") or 2070.0) * 1e6
+    ops = (OPS_ENSEMBLE if sampler == "ensemble" else OPS)[base_name]
+    n_mufu = sum(ops["mufu"].values())
+    mufu_clk, fp32_clk, rate_basis = _alu_peaks(ops["mufu"], rates)
+    t_mufu = n_mufu / (sms * mufu_clk * f_max)
+    t_alu = (ops["fp32"] + ops["int"]) / (sms * fp32_clk * f_max)
+    if t_mufu >= t_alu:
+        pipe, achieved, peak = "mufu", n_mufu * ci_s / 1e9, sms * mufu_clk * f_max / 1e9
+        per_clk = mufu_clk
+    else:
+        pipe, achieved = "fp32+int", (ops["fp32"] + ops["int"]) * ci_s / 1e9
+        peak = sms * fp32_clk * f_max / 1e9
+        per_clk = fp32_clk
+    f_med = (clocks.get("sm_mhz") or 0) * 1e6
+    roof = {"bound": "alu", "pipe": pipe, "count": "direct-form", "achieved": achieved,
+            "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
+            "peak_basis": f"{sms} SMs x {per_clk:.2f}/clk ({rate_basis}) x {f_max / 1e6:.0f} MHz (max SM clock)",
+            "frac_at_sampled_clock": (achieved / peak * f_max / f_med) if f_med else None}
+    if meas.get("warp_instr"):
+        issue_peak = sms * ISSUE_PER_CLK_SM * f_max
+        roof["executed"] = {"warp_instr_per_32_units": meas["warp_instr"],
+                            "issue_frac": meas["warp_instr"] * ci_s / 32 / issue_peak,
+                            "basis": f"{sms} SMs x {ISSUE_PER_CLK_SM} warp-instr/clk x {f_max / 1e6:.0f} MHz"}
+    return roof
+
+
+def _device_inputs(gac, w, mid, dev, stream, base=0):
+    """Seeded truths and noise of voxels [base, base + N); the signal from the
+    library's own forward model on the device (FP64)."""
+    import torch
+    N, M = w.n_vox, w.n_meas
+    th = torch.from_numpy(W.truths(w, base, N)).to(dev)
+    sig = torch.from_numpy(W.sigma(w, th.cpu().numpy())).to(dev)
+    s = torch.empty((N, M), dtype=torch.float64, device=dev)
+    gac.gac_forward(mid, th, N, gac.PREC_FP64, s, stream)
+    z = torch.from_numpy(W.noise(w, base, N)).to(dev)
+    y = (s + sig.double()[:, None] * z).float().contiguous()
+    return y, sig
+
+
+def time_workload(gac, name, dev, stream, rates, steps=5, warmup=3):
+    """One more single-GPU workload of the sampler, timed like the headline
+    (inputs resident in HBM, samples stored, CUDA events on the launching
+    stream, clocks sampled during the timed region); its own line's figures."""
+    import torch
+    w = W.WORKLOADS[name]
+    N, C, P, S = w.n_vox, w.n_chains, w.n_par, w.n_samples
+    mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
+    y, sig = _device_inputs(gac, w, mid, dev, stream)
+    out = dict(mean=torch.empty((P, N), dtype=torch.float64, device=dev),
+               std=torch.empty((P, N), dtype=torch.float64, device=dev),
+               samples=torch.empty((S, C, P, N), dtype=torch.float32, device=dev),
+               accept_rate=torch.empty((C, N), dtype=torch.float32, device=dev),
+               nonfinite=torch.empty((C, N), dtype=torch.int32, device=dev))
+    opts = gac.make_opts(w.iterations, w.burnin, w.thin, C, w.mcmc_seed)
+    for _ in range(warmup):
+        gac.gac_mcmc_run(mid, y, N, sig, 0.0, None, opts, out, stream)
+    torch.cuda.synchronize()
+    # a short workload runs more steps, so that the clocks are sampled (every
+    # 200 ms) while it runs: at least ~1.5 s of timed kernel time
+    t0 = time.perf_counter()
+    gac.gac_mcmc_run(mid, y, N, sig, 0.0, None, opts, out, stream)
+    torch.cuda.synchronize()
+    steps = int(min(4000, max(steps, np.ceil(1.5 / max(time.perf_counter() - t0, 1e-6)))))
+    # buffers that fit in L2 (129 MB) are evicted before every step by writing
+    # a larger buffer outside the timed events
+    touched = sum(t.numel() * t.element_size() for t in (y, sig, *out.values()))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if touched < (256 << 20) else None
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with ClockSampler(dev.index or 0) as clk:
+        torch.cuda.synchronize()
+        for e0, e1 in ev:
+            if flush is not None:
+                flush.fill_(1)
+            e0.record(stream)
+            gac.gac_mcmc_run(mid, y, N, sig, 0.0, None, opts, out, stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+    kernel_s = sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3 / steps
+    ci = w.chain_iterations
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clocks = clk.summary()
+    roof = _roofline(name, "mh", ci / kernel_s, rates, sms, clocks, _measured(name, "mh"))
+    del out, y, sig, flush
+    torch.cuda.empty_cache()
+    return {"value": ci / kernel_s, "unit": UNIT, "ms_per_step": kernel_s * 1e3, "steps": steps,
+            "warmup": warmup, "config": {"n_vox": N, "n_chains": C, "iterations": w.iterations,
+                                         "burnin": w.burnin, "thin": w.thin, "samples_stored": True,
+                                         "l2": ("flushed before every step (256 MB write outside the timed events)"
+                                                if flush is not None else
+                                                f"inputs + outputs {touched / 1e9:.1f} GB per step > 129 MB L2")},
+            "roofline": roof, "clocks": clocks, "gpu_launches": steps}
+
+
 def run_ours(args, w):
     import torch
     from paper_2511_22094_gb300 import build
@@ -461,13 +565,7 @@ def run_ours(args, w):
 
     # synthetic inputs: seeded truths and noise; the signal from the library's
     # own forward model on the device
-    th = torch.from_numpy(W.truths(w, base, N)).to(dev)
-    sig = torch.from_numpy(W.sigma(w, th.cpu().numpy())).to(dev)
-    s = torch.empty((N, M), dtype=torch.float64, device=dev)
-    gac.gac_forward(mid, th, N, gac.PREC_FP64, s, stream)
-    z = torch.from_numpy(W.noise(w, base, N)).to(dev)
-    y = (s + sig.double()[:, None] * z).float().contiguous()
-    del s, z, th
+    y, sig = _device_inputs(gac, w, mid, dev, stream, base)
     out = dict(mean=torch.empty((P, N), dtype=torch.float64, device=dev),
                std=torch.empty((P, N), dtype=torch.float64, device=dev),
                samples=torch.empty((S, C, P, N), dtype=torch.float32, device=dev),
@@ -544,37 +642,13 @@ def run_ours(args, w):
             pg.destroy_process_group()
         return
     clocks = clk.summary()
-    peaks = _peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    f_max = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
     base_name = w.name.replace("_ensemble", "")
-    ops = (OPS_ENSEMBLE if args.sampler == "ensemble" else OPS)[base_name]
-    ci_s = ci_per_step / kernel_s
-    n_mufu = sum(ops["mufu"].values())
-    mufu_clk, fp32_clk, rate_basis = _alu_peaks(ops["mufu"], rates)
-    t_mufu = n_mufu / (sms * mufu_clk * f_max)
-    t_alu = (ops["fp32"] + ops["int"]) / (sms * fp32_clk * f_max)
-    if t_mufu >= t_alu:
-        pipe, achieved, peak = "mufu", n_mufu * ci_s / 1e9, sms * mufu_clk * f_max / 1e9
-        per_clk = mufu_clk
-    else:
-        pipe, achieved = "fp32+int", (ops["fp32"] + ops["int"]) * ci_s / 1e9
-        peak = sms * fp32_clk * f_max / 1e9
-        per_clk = fp32_clk
-    f_med = (clocks.get("sm_mhz") or 0) * 1e6
     meas = _measured(base_name, args.sampler) if (world == 1 and args.precision == "mixed") else {}
-    roof = {"bound": "alu", "pipe": pipe, "count": "direct-form", "achieved": achieved,
-            "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
-            "peak_basis": f"{sms} SMs x {per_clk:.2f}/clk ({rate_basis}) x {f_max / 1e6:.0f} MHz (max SM clock)",
-            "frac_at_sampled_clock": (achieved / peak * f_max / f_med) if f_med else None,
-            "traffic": (meas.get("traffic_bytes") if N == W.WORKLOADS[base_name].n_vox and not args.rhat
-                        and not args.adapt_window and args.moments == "thinned" else None),
-            "kernel_ms": kernel_s * 1e3}
-    if meas.get("warp_instr"):
-        issue_peak = sms * ISSUE_PER_CLK_SM * f_max
-        roof["executed"] = {"warp_instr_per_32_units": meas["warp_instr"],
-                            "issue_frac": meas["warp_instr"] * ci_s / 32 / issue_peak,
-                            "basis": f"{sms} SMs x {ISSUE_PER_CLK_SM} warp-instr/clk x {f_max / 1e6:.0f} MHz"}
+    roof = _roofline(base_name, args.sampler, ci_per_step / kernel_s, rates, sms, clocks, meas)
+    roof["traffic"] = (meas.get("traffic_bytes") if N == W.WORKLOADS[base_name].n_vox and not args.rhat
+                       and not args.adapt_window and args.moments == "thinned" else None)
+    roof["kernel_ms"] = kernel_s * 1e3
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -595,17 +669,22 @@ def run_ours(args, w):
         rate, threads, sample = cpu_oracle_rate(w, sampler=args.sampler, stretch=args.stretch)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": sample}
+    if world == 1 and not args.no_extras and args.sampler == "mh" and w.name == "mwi3_1m" \
+            and args.n_vox is None and args.iterations is None:
+        # the other single-GPU workloads and the serving trace, measured in the
+        # same run (after the headline's timed region, which they do not touch)
+        del out, y, sig
+        torch.cuda.empty_cache()
+        line["workloads"] = {name: time_workload(gac, name, dev, stream, rates)
+                             for name in ("monoexp_4k", "smt_1p5m")}
+        line["serving"] = serving_study(gac, dev, 200, saturated=True)
     print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()
 
 
 def run_serving(args):
-    """Serving trace: 200 jobs with Poisson arrivals (mean gap 0.2 s), mixed
-    models, 10k-2M voxels, 1-4 chains, 1k-5k iterations, under a 120 GB HBM
-    budget.  Continuous batching (gac_server_*) against the plain form: the
-    same jobs run one gac_mcmc_run after another in arrival order.  Inputs
-    start in pinned host memory and results end there in both forms."""
+    """The serving study alone (see serving_study), as its own JSON line."""
     import torch
     from paper_2511_22094_gb300 import build
     build.build()
@@ -613,7 +692,19 @@ def run_serving(args):
 
     torch.cuda.set_device(0)
     dev = torch.device("cuda:0")
-    trace = W.serving_trace(n_jobs=args.serving_jobs)
+    print(json.dumps(serving_study(gac, dev, args.serving_jobs, args.serving_saturated)), flush=True)
+
+
+def serving_study(gac, dev, n_jobs=200, saturated=True):
+    """Serving trace: 200 jobs with Poisson arrivals (mean gap 0.2 s), mixed
+    models, 10k-2M voxels, 1-4 chains, 1k-5k iterations, under a 120 GB HBM
+    budget.  Continuous batching (gac_server_*) against the plain form: the
+    same jobs run one gac_mcmc_run after another in arrival order.  Inputs
+    start in pinned host memory and results end there in both forms.  With
+    `saturated`, the same jobs also all arrive at t = 0.  Each pass carries
+    the clocks sampled while it ran."""
+    import torch
+    trace = W.serving_trace(n_jobs=n_jobs)
     mids = {}
     jobs = []
     t_prep = time.perf_counter()
@@ -695,20 +786,31 @@ def run_serving(args):
             lat.append(end - at)
         return summarize(lat, end)
 
+    def clocked(fn, compress):
+        with ClockSampler(dev.index or 0) as clk:
+            r = fn(compress)
+        r["clocks"] = clk.summary()
+        return r
+
     # warm up both paths on the first few jobs
     for j in jobs[:3]:
         gac.gac_mcmc_run(j["mid"], j["y"], j["N"], j["sig"], 0.0, None, j["opts"], outs(j))
-    res = {"continuous_batching": serve_pass(1.0), "sequential": sequential_pass(1.0)}
-    if args.serving_saturated:
-        res["continuous_batching_all_at_t0"] = serve_pass(0.0)
-        res["sequential_all_at_t0"] = sequential_pass(0.0)
-    line = {"metric": "serving trace: throughput and job latency", "unit": UNIT,
+    res = {"continuous_batching": clocked(serve_pass, 1.0), "sequential": clocked(sequential_pass, 1.0)}
+    if saturated:
+        res["continuous_batching_all_at_t0"] = clocked(serve_pass, 0.0)
+        res["sequential_all_at_t0"] = clocked(sequential_pass, 0.0)
+    for a, b in (("continuous_batching", "sequential"), ("continuous_batching_all_at_t0", "sequential_all_at_t0")):
+        if a in res:
+            res[a]["vs_sequential"] = {"throughput": res[a]["throughput"] / res[b]["throughput"],
+                                       "p50_speedup": res[b]["p50_s"] / res[a]["p50_s"],
+                                       "p99_speedup": res[b]["p99_s"] / res[a]["p99_s"],
+                                       "mean_speedup": res[b]["mean_s"] / res[a]["mean_s"]}
+    return {"metric": "serving trace: throughput and job latency", "unit": UNIT,
             "trace": {"jobs": len(jobs), "arrivals": "Poisson, mean gap 0.2 s",
                       "span_s": trace[-1].arrival_s,
                       "chain_iterations": sum(j["ci"] for j in jobs),
                       "budget_bytes": 120 << 30, "max_resident": 64, "prep_s": t_prep},
             **res}
-    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -725,6 +827,8 @@ def main():
     ap.add_argument("--n-vox", type=int, default=None, help="smaller case (profiling only)")
     ap.add_argument("--iterations", type=int, default=None, help="smaller case (profiling only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline workload only (skip the other workloads and the serving trace)")
     ap.add_argument("--serving", action="store_true", help="run the serving trace instead")
     ap.add_argument("--serving-jobs", type=int, default=200)
     ap.add_argument("--serving-saturated", action="store_true")

@@ -67,8 +67,9 @@ def test_precision_study(gac, orc, snr):
     # 0.05-SD criterion compares chains that follow the oracle's until an
     # acceptance decision falls inside the FP32 error band; after it the two
     # differ by Monte Carlo error.  At SNR 50 that happens to ~1% of voxels
-    # (98.95% within 0.05 SD measured); test_independent_seed_agreement shows
-    # those differences are distributed like oracle-vs-oracle ones.
+    # (98.95% within 0.05 SD measured); test_independent_seed_agreement, run
+    # at the same SNRs, shows those differences are distributed like
+    # oracle-vs-oracle ones.
     min_frac = 0.99 if snr >= 150 else 0.985
     for name, r in report["variants"].items():
         assert r["forward_rel_err_max"] <= (1e-12 if name == "fp64" else 1e-5), name
@@ -99,16 +100,23 @@ def paired_seed_check(runs, pairs, label):
           f"ratio {ratio:.3f}, paired t {t:.2f} over {d.size} voxels")
     assert abs(t) < 4.0
     assert 0.9 < ratio < 1.1
+    return {"gpu_cpu_median": float(np.median(s_gpu)), "cpu_cpu_median": float(np.median(s_cpu)),
+            "ratio": float(ratio), "paired_t": float(t), "voxels": int(d.size)}
 
 
-def test_independent_seed_agreement(gac, orc):
+@pytest.mark.parametrize("snr", [50.0, 150.0, 300.0])
+def test_independent_seed_agreement(gac, orc, snr):
     """The paper's CPU/GPU validation design (Demo 2, Sec. 2.6.2): the
     GPU-minus-CPU disagreement of posterior means under independent random
     streams is measured against the CPU-minus-CPU disagreement of two
-    independent CPU runs.  3-pool model at SNR 150, chains started at the
-    true parameters (so that the comparison is of posterior samples, not of
-    burn-in from different starts)."""
-    w = W.MWI3_1M
+    independent CPU runs.  3-pool model at the precision study's SNRs (50 and
+    300, the same seeded volumes) and the workload's 150, chains started at
+    the true parameters (so that the comparison is of posterior samples, not
+    of burn-in from different starts).  At SNR 50 this is the check that
+    covers the shared-stream chains that part from the oracle's after an
+    acceptance inside the FP32 error band."""
+    w = W.MWI3_1M if snr == 150.0 else W.MWI3_1M.with_(name=f"mwi3_snr{snr:.0f}", snr=snr,
+                                                        data_seed=4 if snr == 50.0 else 5)
     mid = gac.gac_model_register(w.kind, w.acq, w.lb, w.ub, w.step)
     n = 2048
     th, sig, y = make_voxels(orc, w, 100_000, n)
@@ -117,4 +125,5 @@ def test_independent_seed_agreement(gac, orc):
               want_samples=False)
     runs = {s: orc.mcmc_run(w.kind, w.acq, w.lb, w.ub, w.step, y, sig, seed=s, **kw) for s in (11, 22, 44)}
     runs[33] = gac.run_host(mid, y, sig, seed=33, **kw)
-    paired_seed_check(runs, ((11, 22), (33, 44)), "MH 3-pool")
+    r = paired_seed_check(runs, ((11, 22), (33, 44)), f"MH 3-pool SNR {snr:.0f}")
+    print("INDEPENDENT_SEEDS " + json.dumps({"snr": snr, **r}))
