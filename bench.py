@@ -577,7 +577,8 @@ def run_ours(args, w):
     prec = {"mixed": gac.PREC_MIXED, "fp32": gac.PREC_FP32, "fp64": gac.PREC_FP64}[args.precision]
     opts = gac.make_opts(w.iterations, w.burnin, w.thin, C, w.mcmc_seed, voxel_base=base, precision=prec,
                          moments_mode=gac.MOMENTS_ALL_POSTBURNIN if args.moments == "all" else gac.MOMENTS_THINNED,
-                         adapt_window=args.adapt_window, adapt_target=args.adapt_target if args.adapt_window else 0.0)
+                         adapt_window=args.adapt_window, adapt_target=args.adapt_target if args.adapt_window else 0.0,
+                         lanes_per_chain=args.lanes)
 
     def step():
         if args.sampler == "ensemble":
@@ -660,6 +661,7 @@ def run_ours(args, w):
                        "precision": args.precision, "parallelism": f"voxel-shard x{world}",
                        "adapt_window": args.adapt_window, "moments": args.moments,
                        "rhat_and_step_scale": bool(args.rhat and args.sampler == "mh"),
+                       "lanes_per_chain": args.lanes or "library's choice",
                        "l2": f"inputs {y.numel() * 4 / 1e6:.0f} MB + samples {S * C * P * N * 4 / 1e9:.1f} GB written per step > 129 MB L2"},
             "roofline": roof, "pipe_rates_per_sm_clk": rates, "clocks": clocks, "gpu_launches": args.steps,
             "wall_s": t_wall}
@@ -827,6 +829,8 @@ def main():
     ap.add_argument("--n-vox", type=int, default=None, help="smaller case (profiling only)")
     ap.add_argument("--iterations", type=int, default=None, help="smaller case (profiling only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lanes", type=int, default=0, choices=(0, 1, 2, 4),
+                    help="lanes per chain (0: the library chooses; results do not depend on it)")
     ap.add_argument("--no-extras", action="store_true",
                     help="headline workload only (skip the other workloads and the serving trace)")
     ap.add_argument("--serving", action="store_true", help="run the serving trace instead")

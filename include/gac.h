@@ -123,6 +123,17 @@ typedef struct {
     int adapt_window;    /* 0 (default): fixed steps, as in the paper.  W > 0:
                             adapt each chain's steps during burn-in (below) */
     double adapt_target; /* target acceptance rate of the adaptation, in (0, 1) */
+    int lanes_per_chain; /* gac_mcmc_run only (other entry points ignore it).
+                            0 (default): the library chooses; 1: one thread per
+                            chain; 2 or 4: that many lanes of a warp per chain,
+                            each evaluating one block of six echoes, the block
+                            sums combined by warp shuffles (MIXED precision,
+                            mono-exponential or 3-pool model with evenly spaced
+                            echoes in at most that many blocks, trace_n_vox 0;
+                            GAC_ERR_INVALID_ARG otherwise).  Results do not
+                            depend on it, bit for bit; the library uses lanes
+                            when the chains are too few to give every SM
+                            sub-partition a warp. */
 } gac_mcmc_opts;
 
 /* Step adaptation during burn-in (an extension; the paper has no

@@ -14,6 +14,7 @@
 #include "gac.h"
 #include "gac_internal.h"
 #include "launch.h"
+#include "mh_split.cuh"
 
 namespace gac {
 
@@ -517,6 +518,60 @@ gac_status validate_opts(const gac_mcmc_opts *o, int64_t n_vox) {
         return fail(GAC_ERR_INVALID_ARG, "adapt_target must be in (0, 1)");
     if (o->voxel_base > (1ull << 32) || static_cast<uint64_t>(n_vox) > (1ull << 32) - o->voxel_base)
         return fail(GAC_ERR_INVALID_ARG, "voxel_base + n_vox must be <= 2^32 (32-bit counter word)");
+    if (o->lanes_per_chain != 0 && o->lanes_per_chain != 1 && o->lanes_per_chain != 2 && o->lanes_per_chain != 4)
+        return fail(GAC_ERR_INVALID_ARG, "lanes_per_chain must be 0, 1, 2 or 4");
+    return GAC_OK;
+}
+
+// Lanes per chain of a gac_mcmc_run (1: the one-thread kernel).  The
+// lane-split kernel handles MIXED runs without trace of the mono-exponential
+// and 3-pool models with evenly spaced echoes in 2..4 blocks of kAnchor; the
+// library uses it when the chains would give fewer than one warp per SM
+// sub-partition (there it shortens the latency of an iteration; on larger
+// problems one thread per chain keeps more chains in flight).
+static gac_status choose_lanes(const ModelConst &mc, const gac_mcmc_opts *o, int64_t n_vox, int *lanes) {
+    const int nb = (mc.n_acq + kAnchor - 1) / kAnchor;
+    const bool eligible = o->precision == GAC_PREC_MIXED && o->trace_n_vox == 0 && mc.even &&
+                          (mc.kind == GAC_MODEL_MONOEXP || mc.kind == GAC_MODEL_MWI3) && nb >= 2 && nb <= 4;
+    *lanes = 1;
+    if (o->lanes_per_chain == 1) return GAC_OK;
+    if (o->lanes_per_chain > 1) {
+        if (!eligible || nb > o->lanes_per_chain)
+            return fail(GAC_ERR_INVALID_ARG,
+                        "lanes_per_chain %d needs MIXED precision, no trace and a mono-exponential or 3-pool "
+                        "model with evenly spaced echoes in at most %d blocks of %d",
+                        o->lanes_per_chain, o->lanes_per_chain, kAnchor);
+        *lanes = o->lanes_per_chain;
+        return GAC_OK;
+    }
+    const int64_t one_warp_each = static_cast<int64_t>(sm_count()) * 4 * 32;
+    if (eligible && n_vox * o->n_chains < one_warp_each) *lanes = nb <= 2 ? 2 : 4;
+    return GAC_OK;
+}
+
+// Lane-split launch: blocks just large enough to give every SM the same
+// number of warps (whole voxels per block), as many as fit at once.
+static gac_status plan_split(const ModelConst &mc, int G, int C, int64_t n_vox, int moments_mode, LaunchCfg *cfg,
+                             int64_t *n_tiles, int *vb) {
+    const bool all = moments_mode == GAC_MOMENTS_ALL_POSTBURNIN;
+    const void *fn = mc.kind == GAC_MODEL_MONOEXP ? mh_split_ptr_monoexp(G, all) : mh_split_ptr_mwi3(G, all);
+    if (!fn) return fail(GAC_ERR_INVALID_ARG, "no lane-split kernel for kind %d with %d lanes", mc.kind, G);
+    const int sms = sm_count();
+    const int64_t warps = (n_vox * C * G + 31) / 32;
+    int threads = static_cast<int>(std::min<int64_t>(kBlock, 32 * ((warps + sms - 1) / sms)));
+    threads = std::max(threads, 32 * ((C * G + 31) / 32));  // at least one voxel
+    *vb = std::max(1, threads / (C * G));
+    const size_t smem = split_smem_bytes(mc.n_par, G, threads, *vb, row_stride_for(mc.kind, mc.n_meas), all);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem)) != cudaSuccess)
+        return cuda_fail(e, "occupancy query");
+    if (per_sm < 1) return fail(GAC_ERR_INVALID_ARG, "lane-split kernel does not fit on an SM (smem %zu)", smem);
+    *n_tiles = (n_vox + *vb - 1) / *vb;
+    cfg->grid = static_cast<int>(std::min<int64_t>(*n_tiles, static_cast<int64_t>(per_sm) * sms));
+    cfg->smem = smem;
+    cfg->block = threads;
     return GAC_OK;
 }
 
@@ -718,7 +773,10 @@ gac_status gac_mcmc_run(int model_id, const void *data, int64_t n_vox, const flo
         return fail(GAC_ERR_INVALID_ARG, "sigma is NULL and sigma_scalar is not a positive number");
     if (o->trace_n_vox > 0 && !out->trace)
         return fail(GAC_ERR_INVALID_ARG, "trace_n_vox > 0 needs out->trace");
+    int lanes = 1;  // lanes per chain: a requested count is checked before anything runs
+    if (o->lanes_per_chain > 1 && (st = choose_lanes(mc, o, n_vox, &lanes)) != GAC_OK) return st;
     if (n_vox == 0) return GAC_OK;
+    if (o->lanes_per_chain == 0 && (st = choose_lanes(mc, o, n_vox, &lanes)) != GAC_OK) return st;
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     keep_staging_pool();
@@ -743,8 +801,9 @@ gac_status gac_mcmc_run(int model_id, const void *data, int64_t n_vox, const flo
     LaunchCfg cfg;
     int64_t n_tiles = 0;
     int vb = 0;
-    if ((st = plan_launch(mc, o->precision, trace, C, n_vox, o->moments_mode, &cfg, &n_tiles, &vb)) != GAC_OK)
-        return st;
+    st = lanes > 1 ? plan_split(mc, lanes, C, n_vox, o->moments_mode, &cfg, &n_tiles, &vb)
+                   : plan_launch(mc, o->precision, trace, C, n_vox, o->moments_mode, &cfg, &n_tiles, &vb);
+    if (st != GAC_OK) return st;
     cfg.stream = s;
 
     RunArgs ra;
@@ -778,7 +837,10 @@ gac_status gac_mcmc_run(int model_id, const void *data, int64_t n_vox, const flo
     ra.rhat = static_cast<double *>(d_rhat.ptr);
     ra.step_scale = static_cast<float *>(d_scale.ptr);
 
-    cudaError_t e = launch_mh(mc.kind, o->precision, trace, mc, ra, cfg);
+    cudaError_t e = lanes == 1 ? launch_mh(mc.kind, o->precision, trace, mc, ra, cfg)
+                    : mc.kind == GAC_MODEL_MONOEXP
+                        ? launch_mh_split_monoexp(lanes, o->moments_mode == GAC_MOMENTS_ALL_POSTBURNIN, mc, ra, cfg)
+                        : launch_mh_split_mwi3(lanes, o->moments_mode == GAC_MOMENTS_ALL_POSTBURNIN, mc, ra, cfg);
     if (e != cudaSuccess) return cuda_fail(e, "MH kernel launch");
     for (DevBuf *b : {&d_mean, &d_std, &d_samples, &d_acc, &d_bad, &d_trace, &d_rhat, &d_scale})
         if ((st = b->copy_out()) != GAC_OK) return st;

@@ -113,6 +113,33 @@ struct SliceState {
     float *blk;      // [3P][N*C]: MIXED all-post-burn-in block partials (sum d, sum d^2, reference)
 };
 
+// 1/n for the FP64 Welford updates, n < kInvN: a constant-bank load (one
+// address per warp, broadcast) instead of an FP64 division, whose several
+// FP64 instructions each hold a GB300 sub-partition's FP64 pipe for ~76
+// cycles (1.68 FP64 results per SM clock).  The table is computed at compile
+// time with IEEE division, so it holds exactly what the division returns.
+constexpr int kInvN = 4096;
+struct InvTable {
+    double v[kInvN];
+};
+constexpr InvTable make_inv_table() {
+    InvTable t{};
+    for (int i = 1; i < kInvN; ++i) t.v[i] = 1.0 / static_cast<double>(i);
+    return t;
+}
+static __constant__ InvTable c_inv_n = make_inv_table();
+
+// The Welford update's multiply-adds, written as explicit FMAs so that every
+// kernel that accumulates moments rounds them the same way.
+__device__ __forceinline__ double welford_fma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float welford_fma(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <class W>
+__device__ __forceinline__ W inv_count(int n) {
+    if constexpr (sizeof(W) == 8) return n < kInvN ? c_inv_n.v[n] : 1.0 / static_cast<double>(n);
+    else return W(1) / W(n);
+}
+
 // MIXED path, moments over every post-burn-in state: the states of blocks of
 // kMomBlock consecutive post-burn-in iterations (aligned to t - B = 0, so the
 // blocks do not depend on slicing) are summed in FP32 as deviations d = x -
@@ -169,6 +196,27 @@ __device__ __forceinline__ typename PrecTraits<PREC>::R loglik_any(
     else return loglik_f<KIND, typename PrecTraits<PREC>::Acc>(th, y, inv_s2, mc);
 }
 
+// MIXED acceptance, FP64 semantics at FP32 cost, from lu32 = __logf(u01_f(w)).
+// Error of the FP32 quantities against their FP64 counterparts:
+//   d32 = Lp - L:        one rounding of the exact difference of two floats,
+//                        <= 2^-24 |Lp - L|;
+//   lu32 = __logf(u32):  <= 2^-21.41 absolute on [0.5, 2], 3 ulp otherwise
+//                        (|ln u| <= 22.2 -> < 6e-6), plus 2^-24 from
+//                        rounding u to float.
+// A margin of 1e-5 + 2^-22 |d32| covers both (with room for the rounding of
+// the gap itself); inside it the decision is recomputed in FP64 from the same
+// L, Lp and word.  NaN lands in the FP64 branch and rejects.  (The bound does
+// not grow with |L| + |Lp|: far from the posterior, where both are large and
+// their difference is not, the FP64 branch stays rare -- each FP64
+// instruction holds a GB300 sub-partition's FP64 pipe for ~76 cycles.)
+__device__ __forceinline__ bool accept_mixed(float Lp, float L, float lu32, uint32_t w) {
+    const float d32 = Lp - L;
+    const float margin = fmaf(0x1p-22f, fabsf(d32), 1e-5f);
+    const float gap = d32 - lu32;
+    if (fabsf(gap) > margin) return gap > 0.0f;
+    return log(u01_d(w)) < static_cast<double>(Lp) - static_cast<double>(L);
+}
+
 // Acceptance: log u < Lp - L.
 template <int PREC>
 __device__ __forceinline__ bool accept_step(typename PrecTraits<PREC>::R Lp,
@@ -178,20 +226,8 @@ __device__ __forceinline__ bool accept_step(typename PrecTraits<PREC>::R Lp,
     } else if constexpr (PREC == GAC_PREC_FP32) {
         return logf(u01_f(w)) < Lp - L;
     } else {
-        // FP64 semantics at FP32 cost.  Error of the FP32 quantities:
-        //   d32 = Lp - L:        <= 2^-24 |d32|  (Lp, L are exact floats)
-        //   lu32 = __logf(u32):  <= 2^-21.41 absolute on [0.5, 2], 3 ulp
-        //                        otherwise (|ln u| <= 22.2 -> < 6e-6), plus
-        //                        2^-24 from rounding u to float.
-        // A margin of 1e-5 + 2^-20 (|L| + |Lp|) covers both; inside it the
-        // decision is recomputed in FP64.  NaN lands in the FP64 branch and
-        // rejects.
-        const float d32 = Lp - L;
-        const float lu32 = __logf(u01_f(w));
-        const float margin = 1e-5f + 0x1p-20f * (fabsf(L) + fabsf(Lp));
-        const float gap = d32 - lu32;
-        if (fabsf(gap) > margin) return gap > 0.0f;
-        return log(u01_d(w)) < static_cast<double>(Lp) - static_cast<double>(L);
+        // FP64 semantics at FP32 cost (accept_mixed).
+        return accept_mixed(Lp, L, __logf(u01_f(w)), w);
     }
 }
 
@@ -496,15 +532,15 @@ __device__ __forceinline__ void run_tile(const ModelConst &mc, const RunArgs &ra
                     }
                 } else if (all_mode ? (t > ra.B) : on_grid) {
                     ++n_mom;
-                    const W inv_n = W(1) / W(n_mom);
+                    const W inv_n = inv_count<W>(n_mom);
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
                         const W x = static_cast<W>(th[p]);
                         W m = wf_mean[p * wf_stride + wf_idx];
                         const W d = x - m;
-                        m += d * inv_n;
+                        m = welford_fma(d, inv_n, m);
                         wf_mean[p * wf_stride + wf_idx] = m;
-                        wf_m2[p * wf_stride + wf_idx] += d * (x - m);
+                        wf_m2[p * wf_stride + wf_idx] = welford_fma(d, x - m, wf_m2[p * wf_stride + wf_idx]);
                     }
                 }
             }

@@ -1,6 +1,7 @@
 // Instantiations of the MH kernel for GAC_MODEL_MONOEXP (all precisions, with and
-// without step tracing).
+// without step tracing) and of its lane-split form (MIXED, 2 or 4 lanes).
 #include "launch.h"
+#include "mh_split.cuh"
 
 namespace gac {
 
@@ -32,6 +33,24 @@ cudaError_t launch_mh_monoexp(int prec, bool trace, const ModelConst &mc, const 
     case GAC_PREC_FP64: return trace ? go<GAC_PREC_FP64, true>(mc, ra, cfg) : go<GAC_PREC_FP64, false>(mc, ra, cfg);
     default: return cudaErrorInvalidValue;
     }
+}
+
+const void *mh_split_ptr_monoexp(int G, bool all) {
+    if (G == 2) return all ? reinterpret_cast<const void *>(&mh_split_kernel<GAC_MODEL_MONOEXP, 2, true>)
+                           : reinterpret_cast<const void *>(&mh_split_kernel<GAC_MODEL_MONOEXP, 2, false>);
+    if (G == 4) return all ? reinterpret_cast<const void *>(&mh_split_kernel<GAC_MODEL_MONOEXP, 4, true>)
+                           : reinterpret_cast<const void *>(&mh_split_kernel<GAC_MODEL_MONOEXP, 4, false>);
+    return nullptr;
+}
+
+cudaError_t launch_mh_split_monoexp(int G, bool all, const ModelConst &mc, const RunArgs &ra, const LaunchCfg &cfg) {
+    const dim3 grid(cfg.grid), block(cfg.block);
+    if (G == 2 && all) mh_split_kernel<GAC_MODEL_MONOEXP, 2, true><<<grid, block, cfg.smem, cfg.stream>>>(mc, ra);
+    else if (G == 2) mh_split_kernel<GAC_MODEL_MONOEXP, 2, false><<<grid, block, cfg.smem, cfg.stream>>>(mc, ra);
+    else if (G == 4 && all) mh_split_kernel<GAC_MODEL_MONOEXP, 4, true><<<grid, block, cfg.smem, cfg.stream>>>(mc, ra);
+    else if (G == 4) mh_split_kernel<GAC_MODEL_MONOEXP, 4, false><<<grid, block, cfg.smem, cfg.stream>>>(mc, ra);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 }  // namespace gac

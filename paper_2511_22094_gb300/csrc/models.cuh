@@ -406,30 +406,46 @@ __device__ __forceinline__ auto end_block(V &v, int) -> decltype(v.block_end(), 
 template <class V>
 __device__ __forceinline__ void end_block(V &, long) {}
 
+// The mono-exponential recurrence for evenly spaced echoes: the first
+// anchor S0 e^{-t0 R2*} and the per-echo and per-block ratios.
+struct MonoRec {
+    float anchor, r1, rk;
+};
+__device__ __forceinline__ MonoRec monoexp_setup_f(const float *th, const ModelConst &mc) {
+    const float rate = th[1] * 1e-3f;  // 1/s -> 1/ms
+    return {th[0] * expf(-mc.t0_f * rate), expf(-mc.dt_f * rate), expf(-mc.dtk_f * rate)};
+}
+
+// Echoes a .. a+cnt-1 (FULL: cnt = kAnchor) from the block's anchor.
+template <bool FULL, class V>
+__device__ __forceinline__ void monoexp_block_f(float e, float r1, int a, int cnt, V &visit) {
+#pragma unroll
+    for (int i = 0; i < kAnchor; ++i) {
+        if (FULL || i < cnt) visit(a + i, e);
+        e = __fmul_rn(e, r1);
+    }
+}
+
 template <class V>
 __device__ __forceinline__ void eval_monoexp_f(const float *th, const ModelConst &mc, V &&visit) {
     const float s0 = th[0];
     const float rate = th[1] * 1e-3f;  // 1/s -> 1/ms
     const int n = mc.n_acq;
     if (mc.even) {
-        float anchor = s0 * expf(-mc.t0_f * rate);
-        const float r1 = expf(-mc.dt_f * rate);
-        const float rk = expf(-mc.dtk_f * rate);
+        const MonoRec mr = monoexp_setup_f(th, mc);
+        float anchor = mr.anchor;
+        const float r1 = mr.r1;
+        const float rk = mr.rk;
+        // products rounded explicitly (never contracted into the residual's
+        // subtraction), so that every caller of this recurrence -- the
+        // one-thread and the lane-split samplers -- gets the same bits
         int a = 0;
         for (; a + kAnchor <= n; a += kAnchor) {
-            float e = anchor;
-#pragma unroll
-            for (int i = 0; i < kAnchor; ++i) {
-                visit(a + i, e);
-                e *= r1;
-            }
+            monoexp_block_f<true>(anchor, r1, a, kAnchor, visit);
             end_block(visit, 0);
-            anchor *= rk;
+            anchor = __fmul_rn(anchor, rk);
         }
-        for (float e = anchor; a < n; ++a) {  // last, partial block
-            visit(a, e);
-            e *= r1;
-        }
+        if (a < n) monoexp_block_f<false>(anchor, r1, a, n - a, visit);  // last, partial block
     } else {
         for (int k0 = 0; k0 < n; k0 += kAnchor) {
             const int k1 = min(k0 + kAnchor, n);
@@ -439,136 +455,160 @@ __device__ __forceinline__ void eval_monoexp_f(const float *th, const ModelConst
     }
 }
 
+// The 3-pool recurrence for evenly spaced echoes: its set-up (anchors of the
+// first block and the ratios in delta form), one block of echoes, and the
+// step from one block's anchors to the next.  eval_mwi3_f strings them
+// together; the lane-split sampler gives the blocks to different lanes,
+// each lane stepping its anchors the same way, so both give the same bits.
+struct Mwi3Rec {
+    float2 X, Y, Z;              // anchors of block 0: (Re MW, Re IW), (Im MW, Im IW), (Re EW, Im EW)
+    float2 DR, DI, NDI;          // per-echo ratio - 1 of MW, IW (real, imaginary, -imaginary)
+    float2 KR, KI, NKI;          // per-block ratio - 1 of MW, IW
+    float dE, dKE;               // per-echo and per-block ratio - 1 of EW (real)
+};
+
+__device__ __forceinline__ Mwi3Rec mwi3_setup_f(const float *th, const ModelConst &mc) {
+    const float phi0 = th[8];
+    // Per pool j: E_0 = A_j e^{-t0/T2*_j} e^{i(phi0 - w_j t0)} and the ratios
+    // R = e^{-dt (1/T2*_j + i w_j)} and R^K, the ratios in delta form
+    // d = R - 1.  The slow pools have |d| << 1, so rounding d costs far
+    // less than an ulp of R, and E <- E + E d advances a term without
+    // compounding R's own rounding over the block.  The set-up, in FP32:
+    //  - a = t / T2* for t = t0, dt as a double-float (t and 1/T2* as
+    //    hi + lo pairs), e^{-a} - 1 = expm1_f2(-a_hi) - a_lo e^{-a};
+    //  - (1 + em_dt)^K - 1 by squaring in delta form;
+    //  - the phases b = w t = df (2 pi 1e-3 t) as double-floats, the
+    //    phasor e^{-ib} - 1 = (cos b - 1, -sin b) of the high part,
+    //    corrected to first order by the low part;
+    //  - d = (1 + em)(1 + cm + i sn) - 1 = em + cm + em cm + i (sn + em sn);
+    //  - E_0 = A (1 + em_0) e^{i phi0} e^{-i b0}, the last factor applied
+    //    in delta form to e^{i phi0} (which the extra-cellular pool uses
+    //    as it is), and A (1 + em_0) c = A c + (A em_0 c + err(A c)).
+    // The myelin- and intra-axonal pools (frequency offsets) are carried as
+    // lane pairs: X = (Re E_MW, Re E_IW), Y = (Im E_MW, Im E_IW); the
+    // extra-cellular pool, whose ratio is real, as Z = (Re E_EW, Im E_EW).
+    static_assert(kAnchor == 6, "R^K is formed as ((1 + d)^2 (1 + d))^2");
+    const float2 T2 = make_float2(th[3], th[4]);
+    const float2 rh = make_float2(rcp_approx(th[3]), rcp_approx(th[4]));
+    const float2 rl = __fmul2_rn(rh, __ffma2_rn(neg2(rh), T2, f2(1.0f)));
+    const float rh2 = rcp_approx(th[5]);
+    const float rl2 = rh2 * fmaf(-rh2, th[5], 1.0f);
+    // e^{-t r} - 1 per lane, t = th + tl, r = rh + rl
+    auto em_of = [](float2 rh_, float2 rl_, float2 th_, float2 tl_, auto small) {
+        const float2 ah = __fmul2_rn(rh_, th_);
+        float2 al = __ffma2_rn(rh_, th_, neg2(ah));
+        al = __ffma2_rn(rl_, th_, al);
+        al = __ffma2_rn(rh_, tl_, al);
+        const float2 em = expm1_f2<decltype(small)::value>(neg2(ah));
+        return __ffma2_rn(neg2(al), em, __fadd2_rn(em, neg2(al)));
+    };
+    using Full = std::false_type;
+    const float2 em0 = em_of(rh, rl, f2(mc.dd_t0.x), f2(mc.dd_t0.y), Full{});  // MW, IW over t0
+    const float2 em1 = em_of(rh, rl, f2(mc.dd_dt.x), f2(mc.dd_dt.y), Full{});  // MW, IW over dt
+    const float2 tE = make_float2(mc.dd_t0.x, mc.dd_dt.x), tlE = make_float2(mc.dd_t0.y, mc.dd_dt.y);
+    const float2 emE = (mc.mwi3_flags & kMwi3SmallEW) ? em_of(f2(rh2), f2(rl2), tE, tlE, std::true_type{})
+                                                      : em_of(f2(rh2), f2(rl2), tE, tlE, Full{});  // EW over t0, dt
+    // (1 + e)^6 - 1: e2 = e (2 + e), e3 = e2 + e + e2 e, e6 = e3 (2 + e3)
+    const float2 e2 = __ffma2_rn(em1, em1, __fadd2_rn(em1, em1));
+    const float2 e3 = __ffma2_rn(e2, em1, __fadd2_rn(e2, em1));
+    const float2 emK = __ffma2_rn(e3, e3, __fadd2_rn(e3, e3));
+    const float dE = emE.y;
+    const float dE2 = fmaf(dE, dE, dE + dE), dE3 = fmaf(dE2, dE, dE2 + dE);
+    const float dKE = fmaf(dE3, dE3, dE3 + dE3);
+    // phases b = df (2 pi 1e-3 t) as hi + lo
+    const float2 df = make_float2(th[6], th[7]);
+    auto phase = [&df](float2 c, float2 &lo) {
+        const float2 bh = __fmul2_rn(df, f2(c.x));
+        lo = __ffma2_rn(df, f2(c.y), __ffma2_rn(df, f2(c.x), neg2(bh)));
+        return bh;
+    };
+    // e^{-i(bh + bl)} - 1 as (cos - 1, sin); SMALL: |bh| <= pi/4
+    auto phasor = [](float2 bh, float2 bl, bool small, float2 &cm1, float2 &sn1) {
+        float2 sn, cs, cm;
+        if (small) {
+            sincos_small2(neg2(bh), sn, cm);
+            cs = __fadd2_rn(cm, f2(1.0f));
+        } else {
+            sincos_cm2(neg2(bh), sn, cs, cm);
+        }
+        sn1 = __ffma2_rn(cs, neg2(bl), sn);
+        cm1 = __ffma2_rn(sn, bl, cm);
+    };
+    const bool small = (mc.mwi3_flags & kMwi3SmallB) != 0;  // the same for every thread
+    float2 b0l, b1l;
+    const float2 b0h = phase(mc.dd_w0, b0l), b1h = phase(mc.dd_w1, b1l);
+    float2 DR, DI, KR, KI, cmb, snb;
+    phasor(b1h, b1l, small, cmb, snb);
+    DR = __ffma2_rn(em1, cmb, __fadd2_rn(em1, cmb));
+    DI = __ffma2_rn(em1, snb, snb);
+    if (mc.mwi3_flags & kMwi3SmallBK) {
+        // e^{-i bK} - 1 = u (2 + u) from u = e^{-i bK/2} - 1
+        float2 bkl;
+        const float2 bkh = phase(mc.dd_wkh, bkl);
+        float2 ur, ui;
+        phasor(bkh, bkl, true, ur, ui);
+        const float2 ur2 = __fadd2_rn(ur, ur);
+        cmb = __ffma2_rn(ur, ur, __ffma2_rn(neg2(ui), ui, ur2));
+        snb = __ffma2_rn(ur2, ui, __fadd2_rn(ui, ui));
+    } else {
+        float2 bkl;
+        const float2 bkh = phase(mc.dd_wk, bkl);
+        phasor(bkh, bkl, false, cmb, snb);
+    }
+    KR = __ffma2_rn(emK, cmb, __fadd2_rn(emK, cmb));
+    KI = __ffma2_rn(emK, snb, snb);
+    // E_0: e^{i phi0} (1 + cm + i sn) = e^{i phi0} + (ce cm - se sn, se cm + ce sn)
+    float se, ce;
+    sincos_cw(phi0, se, ce);
+    phasor(b0h, b0l, small, cmb, snb);
+    const float2 c0 = __fadd2_rn(f2(ce), __ffma2_rn(f2(ce), cmb, __fmul2_rn(f2(-se), snb)));
+    const float2 s0 = __fadd2_rn(f2(se), __ffma2_rn(f2(se), cmb, __fmul2_rn(f2(ce), snb)));
+    auto amp = [](float2 a, float2 aem, float2 c) {
+        const float2 p = __fmul2_rn(a, c);
+        return __fadd2_rn(p, __ffma2_rn(aem, c, __ffma2_rn(a, c, neg2(p))));
+    };
+    const float2 A = make_float2(th[0], th[1]);
+    const float2 Aem = __fmul2_rn(A, em0);
+    float2 X = amp(A, Aem, c0), Y = amp(A, Aem, s0);
+    float2 Z = amp(f2(th[2]), f2(th[2] * emE.x), make_float2(ce, se));
+    return {X, Y, Z, DR, DI, neg2(DI), KR, KI, neg2(KI), dE, dKE};
+}
+
+__device__ __forceinline__ void mwi3_next_anchor(const Mwi3Rec &r, float2 &X, float2 &Y, float2 &Z) {
+    const float2 xn = __ffma2_rn(X, r.KR, __ffma2_rn(Y, r.NKI, X));
+    Y = __ffma2_rn(Y, r.KR, __ffma2_rn(X, r.KI, Y));
+    X = xn;
+    Z = __ffma2_rn(Z, f2(r.dKE), Z);
+}
+
+// Echoes a .. a+cnt-1 (FULL: cnt = kAnchor) from the block's anchors.
+template <bool FULL, class V>
+__device__ __forceinline__ void mwi3_block_f(const Mwi3Rec &r, float2 x, float2 y, float2 z, int a, int cnt,
+                                             V &visit) {
+#pragma unroll
+    for (int i = 0; i < kAnchor; ++i) {
+        if (FULL || i < cnt) visit(a + i, x.x + x.y + z.x, y.x + y.y + z.y);
+        const float2 xn = __ffma2_rn(x, r.DR, __ffma2_rn(y, r.NDI, x));
+        y = __ffma2_rn(y, r.DR, __ffma2_rn(x, r.DI, y));
+        x = xn;
+        z = __ffma2_rn(z, f2(r.dE), z);
+    }
+}
+
 template <class V>
 __device__ __forceinline__ void eval_mwi3_f(const float *th, const ModelConst &mc, V &&visit) {
     const float phi0 = th[8];
     const int n = mc.n_acq;
     if (mc.even) {
-        // Per pool j: E_0 = A_j e^{-t0/T2*_j} e^{i(phi0 - w_j t0)} and the ratios
-        // R = e^{-dt (1/T2*_j + i w_j)} and R^K, the ratios in delta form
-        // d = R - 1.  The slow pools have |d| << 1, so rounding d costs far
-        // less than an ulp of R, and E <- E + E d advances a term without
-        // compounding R's own rounding over the block.  The set-up, in FP32:
-        //  - a = t / T2* for t = t0, dt as a double-float (t and 1/T2* as
-        //    hi + lo pairs), e^{-a} - 1 = expm1_f2(-a_hi) - a_lo e^{-a};
-        //  - (1 + em_dt)^K - 1 by squaring in delta form;
-        //  - the phases b = w t = df (2 pi 1e-3 t) as double-floats, the
-        //    phasor e^{-ib} - 1 = (cos b - 1, -sin b) of the high part,
-        //    corrected to first order by the low part;
-        //  - d = (1 + em)(1 + cm + i sn) - 1 = em + cm + em cm + i (sn + em sn);
-        //  - E_0 = A (1 + em_0) e^{i phi0} e^{-i b0}, the last factor applied
-        //    in delta form to e^{i phi0} (which the extra-cellular pool uses
-        //    as it is), and A (1 + em_0) c = A c + (A em_0 c + err(A c)).
-        // The myelin- and intra-axonal pools (frequency offsets) are carried as
-        // lane pairs: X = (Re E_MW, Re E_IW), Y = (Im E_MW, Im E_IW); the
-        // extra-cellular pool, whose ratio is real, as Z = (Re E_EW, Im E_EW).
-        static_assert(kAnchor == 6, "R^K is formed as ((1 + d)^2 (1 + d))^2");
-        const float2 T2 = make_float2(th[3], th[4]);
-        const float2 rh = make_float2(rcp_approx(th[3]), rcp_approx(th[4]));
-        const float2 rl = __fmul2_rn(rh, __ffma2_rn(neg2(rh), T2, f2(1.0f)));
-        const float rh2 = rcp_approx(th[5]);
-        const float rl2 = rh2 * fmaf(-rh2, th[5], 1.0f);
-        // e^{-t r} - 1 per lane, t = th + tl, r = rh + rl
-        auto em_of = [](float2 rh_, float2 rl_, float2 th_, float2 tl_, auto small) {
-            const float2 ah = __fmul2_rn(rh_, th_);
-            float2 al = __ffma2_rn(rh_, th_, neg2(ah));
-            al = __ffma2_rn(rl_, th_, al);
-            al = __ffma2_rn(rh_, tl_, al);
-            const float2 em = expm1_f2<decltype(small)::value>(neg2(ah));
-            return __ffma2_rn(neg2(al), em, __fadd2_rn(em, neg2(al)));
-        };
-        using Full = std::false_type;
-        const float2 em0 = em_of(rh, rl, f2(mc.dd_t0.x), f2(mc.dd_t0.y), Full{});  // MW, IW over t0
-        const float2 em1 = em_of(rh, rl, f2(mc.dd_dt.x), f2(mc.dd_dt.y), Full{});  // MW, IW over dt
-        const float2 tE = make_float2(mc.dd_t0.x, mc.dd_dt.x), tlE = make_float2(mc.dd_t0.y, mc.dd_dt.y);
-        const float2 emE = (mc.mwi3_flags & kMwi3SmallEW) ? em_of(f2(rh2), f2(rl2), tE, tlE, std::true_type{})
-                                                          : em_of(f2(rh2), f2(rl2), tE, tlE, Full{});  // EW over t0, dt
-        // (1 + e)^6 - 1: e2 = e (2 + e), e3 = e2 + e + e2 e, e6 = e3 (2 + e3)
-        const float2 e2 = __ffma2_rn(em1, em1, __fadd2_rn(em1, em1));
-        const float2 e3 = __ffma2_rn(e2, em1, __fadd2_rn(e2, em1));
-        const float2 emK = __ffma2_rn(e3, e3, __fadd2_rn(e3, e3));
-        const float dE = emE.y;
-        const float dE2 = fmaf(dE, dE, dE + dE), dE3 = fmaf(dE2, dE, dE2 + dE);
-        const float dKE = fmaf(dE3, dE3, dE3 + dE3);
-        // phases b = df (2 pi 1e-3 t) as hi + lo
-        const float2 df = make_float2(th[6], th[7]);
-        auto phase = [&df](float2 c, float2 &lo) {
-            const float2 bh = __fmul2_rn(df, f2(c.x));
-            lo = __ffma2_rn(df, f2(c.y), __ffma2_rn(df, f2(c.x), neg2(bh)));
-            return bh;
-        };
-        // e^{-i(bh + bl)} - 1 as (cos - 1, sin); SMALL: |bh| <= pi/4
-        auto phasor = [](float2 bh, float2 bl, bool small, float2 &cm1, float2 &sn1) {
-            float2 sn, cs, cm;
-            if (small) {
-                sincos_small2(neg2(bh), sn, cm);
-                cs = __fadd2_rn(cm, f2(1.0f));
-            } else {
-                sincos_cm2(neg2(bh), sn, cs, cm);
-            }
-            sn1 = __ffma2_rn(cs, neg2(bl), sn);
-            cm1 = __ffma2_rn(sn, bl, cm);
-        };
-        const bool small = (mc.mwi3_flags & kMwi3SmallB) != 0;  // the same for every thread
-        float2 b0l, b1l;
-        const float2 b0h = phase(mc.dd_w0, b0l), b1h = phase(mc.dd_w1, b1l);
-        float2 DR, DI, KR, KI, cmb, snb;
-        phasor(b1h, b1l, small, cmb, snb);
-        DR = __ffma2_rn(em1, cmb, __fadd2_rn(em1, cmb));
-        DI = __ffma2_rn(em1, snb, snb);
-        if (mc.mwi3_flags & kMwi3SmallBK) {
-            // e^{-i bK} - 1 = u (2 + u) from u = e^{-i bK/2} - 1
-            float2 bkl;
-            const float2 bkh = phase(mc.dd_wkh, bkl);
-            float2 ur, ui;
-            phasor(bkh, bkl, true, ur, ui);
-            const float2 ur2 = __fadd2_rn(ur, ur);
-            cmb = __ffma2_rn(ur, ur, __ffma2_rn(neg2(ui), ui, ur2));
-            snb = __ffma2_rn(ur2, ui, __fadd2_rn(ui, ui));
-        } else {
-            float2 bkl;
-            const float2 bkh = phase(mc.dd_wk, bkl);
-            phasor(bkh, bkl, false, cmb, snb);
-        }
-        KR = __ffma2_rn(emK, cmb, __fadd2_rn(emK, cmb));
-        KI = __ffma2_rn(emK, snb, snb);
-        // E_0: e^{i phi0} (1 + cm + i sn) = e^{i phi0} + (ce cm - se sn, se cm + ce sn)
-        float se, ce;
-        sincos_cw(phi0, se, ce);
-        phasor(b0h, b0l, small, cmb, snb);
-        const float2 c0 = __fadd2_rn(f2(ce), __ffma2_rn(f2(ce), cmb, __fmul2_rn(f2(-se), snb)));
-        const float2 s0 = __fadd2_rn(f2(se), __ffma2_rn(f2(se), cmb, __fmul2_rn(f2(ce), snb)));
-        auto amp = [](float2 a, float2 aem, float2 c) {
-            const float2 p = __fmul2_rn(a, c);
-            return __fadd2_rn(p, __ffma2_rn(aem, c, __ffma2_rn(a, c, neg2(p))));
-        };
-        const float2 A = make_float2(th[0], th[1]);
-        const float2 Aem = __fmul2_rn(A, em0);
-        float2 X = amp(A, Aem, c0), Y = amp(A, Aem, s0);
-        float2 Z = amp(f2(th[2]), f2(th[2] * emE.x), make_float2(ce, se));
-        const float2 NDI = neg2(DI), NKI = neg2(KI);
-        // one block of echoes a .. a+cnt-1 from the current anchors
-        auto block = [&](int a, int cnt, bool full) {
-            float2 x = X, y = Y, z = Z;
-#pragma unroll
-            for (int i = 0; i < kAnchor; ++i) {
-                if (full || i < cnt) visit(a + i, x.x + x.y + z.x, y.x + y.y + z.y);
-                const float2 xn = __ffma2_rn(x, DR, __ffma2_rn(y, NDI, x));
-                y = __ffma2_rn(y, DR, __ffma2_rn(x, DI, y));
-                x = xn;
-                z = __ffma2_rn(z, f2(dE), z);
-            }
-        };
+        const Mwi3Rec r = mwi3_setup_f(th, mc);
+        float2 X = r.X, Y = r.Y, Z = r.Z;
         int a = 0;
         for (; a + kAnchor <= n; a += kAnchor) {
-            block(a, kAnchor, true);
+            mwi3_block_f<true>(r, X, Y, Z, a, kAnchor, visit);
             end_block(visit, 0);
-            const float2 xn = __ffma2_rn(X, KR, __ffma2_rn(Y, NKI, X));
-            Y = __ffma2_rn(Y, KR, __ffma2_rn(X, KI, Y));
-            X = xn;
-            Z = __ffma2_rn(Z, f2(dKE), Z);
+            mwi3_next_anchor(r, X, Y, Z);
         }
-        if (a < n) block(a, n - a, false);
+        if (a < n) mwi3_block_f<false>(r, X, Y, Z, a, n - a, visit);
     } else {
         float rate[3], w[3];
 #pragma unroll
@@ -882,7 +922,7 @@ struct ResidualVisitor {
         const float2 yk = reinterpret_cast<const float2 *>(y)[k];
         acc.add2(__ffma2_rn(make_float2(sr, si), f2(-1.0f), yk));  // y - s, both parts
     }
-    __device__ __forceinline__ void operator()(int k, float s) const { acc.add(y[k] - s); }
+    __device__ __forceinline__ void operator()(int k, float s) const { acc.add(__fsub_rn(y[k], s)); }
     __device__ __forceinline__ void block_end() const { acc.block_end(); }
 };
 

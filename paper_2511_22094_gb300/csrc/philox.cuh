@@ -85,17 +85,27 @@ __device__ __forceinline__ double u01_d(uint32_t w) {
 // The radius is taken as sqrt(k log2 u1) with k = -2 ln 2 s^2, which scales
 // both normals by s > 0 (the MH step multiplier) at no extra cost; the
 // default k gives the standard pair (s = 1).
+// The pair is built in two parts: bm_prefix (log2 u1 and the angle's sine and
+// cosine: what depends only on the words) and bm_finish (the radius, which
+// takes the step multiplier); the lane-split sampler draws the prefixes ahead.
 constexpr float kNeg2Ln2 = -1.38629436111989061883f;  // -2 ln 2
-__device__ __forceinline__ void box_muller_f(uint32_t w1, uint32_t w2, float &z0, float &z1,
-                                             float k = kNeg2Ln2) {
-    const float x = fmaxf(k * __log2f(u01_f(w1)), 1e-30f);
-    const float r = x * rsqrtf(x);
+__device__ __forceinline__ void bm_prefix(uint32_t w1, uint32_t w2, float &lg, float &s, float &c) {
+    lg = __log2f(u01_f(w1));
     const float ang = fmaf(static_cast<float>(static_cast<int32_t>(w2)), 1.46291807926715968e-9f,
                            7.31459039633579840e-10f);  // 2 pi 2^-32, pi 2^-32
-    float s, c;
     __sincosf(ang, &s, &c);
+}
+__device__ __forceinline__ void bm_finish(float lg, float s, float c, float k, float &z0, float &z1) {
+    const float x = fmaxf(k * lg, 1e-30f);
+    const float r = x * rsqrtf(x);
     z0 = r * c;
     z1 = r * s;
+}
+__device__ __forceinline__ void box_muller_f(uint32_t w1, uint32_t w2, float &z0, float &z1,
+                                             float k = kNeg2Ln2) {
+    float lg, s, c;
+    bm_prefix(w1, w2, lg, s, c);
+    bm_finish(lg, s, c, k, z0, z1);
 }
 
 // k = -2 s^2 scales both normals by s > 0; -2 gives the standard pair.

@@ -41,7 +41,7 @@ class McmcOpts(ct.Structure):
     _fields_ = [("iterations", ct.c_int), ("burnin", ct.c_int), ("thin", ct.c_int),
                 ("n_chains", ct.c_int), ("seed", ct.c_uint64), ("voxel_base", ct.c_uint64),
                 ("precision", ct.c_int), ("moments_mode", ct.c_int), ("trace_n_vox", ct.c_int),
-                ("adapt_window", ct.c_int), ("adapt_target", ct.c_double)]
+                ("adapt_window", ct.c_int), ("adapt_target", ct.c_double), ("lanes_per_chain", ct.c_int)]
 
 
 class TraceRec(ct.Structure):
@@ -195,9 +195,9 @@ def gac_model_info(model_id: int):
 
 def make_opts(iterations, burnin, thin, n_chains, seed, voxel_base=0, precision=PREC_MIXED,
               moments_mode=MOMENTS_THINNED, trace_n_vox=0, adapt_window=0,
-              adapt_target=0.0) -> McmcOpts:
+              adapt_target=0.0, lanes_per_chain=0) -> McmcOpts:
     return McmcOpts(iterations, burnin, thin, n_chains, seed, voxel_base, precision, moments_mode,
-                    trace_n_vox, adapt_window, adapt_target)
+                    trace_n_vox, adapt_window, adapt_target, lanes_per_chain)
 
 
 def gac_result_sizes(model_id: int, n_vox: int, opts: McmcOpts):
@@ -363,7 +363,7 @@ def n_samples(iterations: int, burnin: int, thin: int) -> int:
 def run_host(model_id: int, data: np.ndarray, sigma, *, iterations, burnin, thin, n_chains, seed,
              x0=None, sigma_scalar=0.0, voxel_base=0, precision=PREC_MIXED,
              moments_mode=MOMENTS_THINNED, trace_n_vox=0, want_samples=True, adapt_window=0,
-             adapt_target=0.0):
+             adapt_target=0.0, lanes_per_chain=0):
     """Runs the sampler on host numpy inputs (the library stages them through
     device memory) and returns host numpy outputs."""
     P, M = gac_model_info(model_id)
@@ -379,7 +379,7 @@ def run_host(model_id: int, data: np.ndarray, sigma, *, iterations, burnin, thin
     sig = None if sigma is None else np.ascontiguousarray(sigma, np.float32)
     x0a = None if x0 is None else np.ascontiguousarray(x0, np.float32)
     opts = make_opts(iterations, burnin, thin, n_chains, seed, voxel_base, precision, moments_mode,
-                     trace_n_vox, adapt_window, adapt_target)
+                     trace_n_vox, adapt_window, adapt_target, lanes_per_chain)
     gac_mcmc_run(model_id, data, N, sig, sigma_scalar, x0a, opts, out)
     return out
 

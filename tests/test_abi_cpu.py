@@ -96,6 +96,9 @@ def test_run_argument_validation(gac):
         dict(precision=3), dict(moments_mode=2), dict(trace_n_vox=5),
         dict(adapt_window=-1), dict(adapt_window=10, adapt_target=0.0),
         dict(adapt_window=10, adapt_target=1.0), dict(adapt_window=10, adapt_target=float("nan")),
+        dict(lanes_per_chain=-1), dict(lanes_per_chain=3), dict(lanes_per_chain=8),
+        # lanes need MIXED precision, no trace, and no more blocks of six echoes than lanes
+        dict(lanes_per_chain=2, precision=1), dict(lanes_per_chain=2, precision=2),
     ]
     for c in cases:
         kw = dict(iterations=10, burnin=0, thin=1, n_chains=1, seed=1)
@@ -114,8 +117,17 @@ def test_run_argument_validation(gac):
     assert e.value.status == 2
     with pytest.raises(gac.GacError):  # trace requested without a buffer
         gac.gac_mcmc_run(mid, y, 4, None, 0.01, None, gac.make_opts(10, 0, 1, 1, 1, trace_n_vox=1), out)
+    uneven = gac.gac_model_register(**dict(MONO, acq=[1.0, 2.0, 4.0, 8.0] * 3))
+    one_block = gac.gac_model_register(**dict(MONO, acq=[2.0, 5.0, 8.0, 11.0]))
+    for m in (uneven, one_block):  # lanes split blocks of evenly spaced echoes: 2..4 of them
+        with pytest.raises(gac.GacError) as e:
+            gac.gac_mcmc_run(m, np.zeros((4, 4), np.float32) if m == one_block else y, 4, None, 0.01, None,
+                             gac.make_opts(10, 0, 1, 1, 1, lanes_per_chain=2), out)
+        assert e.value.status == 1
     # zero voxels: nothing to do, no GPU needed
     gac.gac_mcmc_run(mid, np.zeros((0, 12), np.float32), 0, None, 0.01, None, opts, out)
+    gac.gac_mcmc_run(mid, np.zeros((0, 12), np.float32), 0, None, 0.01, None,
+                     gac.make_opts(10, 0, 1, 1, 1, lanes_per_chain=2), out)
 
 
 def test_result_sizes(gac):

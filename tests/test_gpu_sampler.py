@@ -293,3 +293,41 @@ def test_mixed_all_postburnin_moments_blocked(gac, orc):
     print(f"blocked vs per-state moments: |dmean|/SD max {dm.max():.2e}, |dSD|/SD max {ds.max():.2e}")
     assert dm.max() <= 1e-5 and ds.max() <= 1e-4
     assert np.all(blocked["std"][~ok] <= 1e-6)
+
+
+LANE_CASES = [
+    # (workload, echoes kept, voxels, chains, lane counts compared with one lane)
+    ("monoexp", 12, 1000, 1, (2, 4)),
+    ("monoexp", 12, 333, 3, (2, 4)),
+    ("mwi3", 24, 301, 4, (4,)),
+    ("mwi3", 12, 257, 2, (2, 4)),
+    ("mwi3", 22, 150, 4, (4,)),  # a partial last block
+]
+
+
+@pytest.mark.parametrize("case", LANE_CASES, ids=[f"{c[0]}_{c[1]}echo_{c[2]}x{c[3]}" for c in LANE_CASES])
+def test_lane_split_gives_the_same_bits(gac, orc, case):
+    """Lanes per chain (each lane one block of six echoes, the block sums
+    combined by warp shuffles in the one-thread kernel's Kahan order, random
+    numbers drawn a round ahead by rotating lanes) give the one-thread
+    kernel's results bit for bit: samples, moments, R-hat, acceptance rates
+    and step multipliers, with thinned moments and with moments over every
+    post-burn-in state, burn-in adaptation, a start x0, ragged tiles and
+    several chains per voxel."""
+    name, n_echo, n, C, lanes = case
+    base = W.MONOEXP_4K if name == "monoexp" else W.MWI3_1M
+    w = base.with_(acq=base.acq[:n_echo])
+    mid = _register(gac, w)
+    th, sig, y = make_voxels(orc, w, 0, n)
+    x0 = np.repeat(th[:, None, :], C, axis=1).astype(np.float32)
+    keys = ("samples", "mean", "std", "rhat", "accept_rate", "nonfinite", "step_scale")
+    runs = [dict(iterations=600, burnin=200, thin=5, n_chains=C, seed=21),
+            dict(iterations=700, burnin=300, thin=7, n_chains=C, seed=22, adapt_window=50, adapt_target=0.3,
+                 moments_mode=gac.MOMENTS_ALL_POSTBURNIN, x0=x0)]
+    for kw in runs:
+        one = gac.run_host(mid, y, sig, lanes_per_chain=1, **kw)
+        for g in lanes:
+            split = gac.run_host(mid, y, sig, lanes_per_chain=g, **kw)
+            for k in keys:
+                np.testing.assert_array_equal(split[k], one[k], err_msg=f"{k} with {g} lanes")
+        assert np.isfinite(one["mean"]).all()
