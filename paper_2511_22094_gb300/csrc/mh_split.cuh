@@ -59,6 +59,57 @@ __device__ __forceinline__ SplitDraw<P> split_draw(uint32_t t, uint32_t vg, uint
     return d;
 }
 
+// A draw's Philox calls in flight, so that their ten rounds can be spread
+// over the iterations of a round (the same rounds, keys and words as
+// draw_words).
+template <int P>
+struct PhiloxRun {
+    uint32_t c[n_calls(P)][4];
+};
+
+template <int P>
+__device__ __forceinline__ PhiloxRun<P> philox_start(uint32_t t, uint32_t vg, uint32_t c) {
+    PhiloxRun<P> s;
+#pragma unroll
+    for (int k = 0; k < n_calls(P); ++k) {
+        s.c[k][0] = t;
+        s.c[k][1] = vg;
+        s.c[k][2] = (c << 8) | static_cast<uint32_t>(k);
+        s.c[k][3] = 0u;
+    }
+    return s;
+}
+
+// Rounds r0 .. r1-1 of every call.
+template <int P>
+__device__ __forceinline__ void philox_part(PhiloxRun<P> &s, int r0, int r1, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r < r0 || r >= r1) continue;  // constant after unrolling
+#pragma unroll
+        for (int k = 0; k < n_calls(P); ++k)
+            philox_round(s.c[k][0], s.c[k][1], s.c[k][2], s.c[k][3], k0 + static_cast<uint32_t>(r) * kPhiloxW0,
+                         k1 + static_cast<uint32_t>(r) * kPhiloxW1);
+    }
+}
+
+// The draw from a finished run (as split_draw).
+template <int P>
+__device__ __forceinline__ SplitDraw<P> split_prefix(const PhiloxRun<P> &s) {
+    constexpr int NW = n_words(P);
+    uint32_t w[4 * n_calls(P)];
+#pragma unroll
+    for (int k = 0; k < n_calls(P); ++k)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) w[4 * k + j] = s.c[k][j];
+    SplitDraw<P> d;
+#pragma unroll
+    for (int j = 0; j < SplitDraw<P>::kPairs; ++j) bm_prefix(w[2 * j], w[2 * j + 1], d.lg[j], d.sn[j], d.cs[j]);
+    d.w_acc = w[NW - 1];
+    d.lu = __logf(u01_f(d.w_acc));
+    return d;
+}
+
 // The draw of lane `src` of the warp.
 template <int P>
 __device__ __forceinline__ SplitDraw<P> split_take(const SplitDraw<P> &d, int src) {
@@ -295,8 +346,15 @@ __device__ __forceinline__ void run_tile_split(const ModelConst &mc, const RunAr
 
         // draws of this round and the next (lane g: iteration t0 + g), and
         // the first iteration's normals
+        // cur, nxt: the draws of this round and the next (the next one's
+        // Box-Muller prefixes are taken in this round's first iteration, from
+        // the finished Philox run `wnx`); `pr`: the Philox calls of the round
+        // after next, advanced a part in every iteration of this round
         SplitDraw<P> cur = split_draw<P>(static_cast<uint32_t>(1 + g), vg, cu, ra.k0, ra.k1);
-        SplitDraw<P> nxt = split_draw<P>(static_cast<uint32_t>(1 + G + g), vg, cu, ra.k0, ra.k1);
+        SplitDraw<P> nxt;
+        PhiloxRun<P> wnx = philox_start<P>(static_cast<uint32_t>(1 + G + g), vg, cu);
+        philox_part<P>(wnx, 0, 10, ra.k0, ra.k1);
+        PhiloxRun<P> pr = philox_start<P>(static_cast<uint32_t>(1 + 2 * G + g), vg, cu);
         float z[P];
         float lu;
         uint32_t w_acc;
@@ -311,6 +369,8 @@ __device__ __forceinline__ void run_tile_split(const ModelConst &mc, const RunAr
             for (int i = 0; i < G; ++i) {
                 const int t = t0 + i;
                 if (t > ra.I) break;  // the same t for every lane
+                if (i == 0) nxt = split_prefix<P>(wnx);
+                philox_part<P>(pr, (10 * i) / G, (10 * (i + 1)) / G, ra.k0, ra.k1);
                 // a4: proposal
                 float prop[P];
 #pragma unroll
@@ -330,54 +390,32 @@ __device__ __forceinline__ void run_tile_split(const ModelConst &mc, const RunAr
                 bool acc = gap > 0.0f;
                 const bool near = !(fabsf(gap) > margin);
                 n_bad += !isfinite(Lp);
-                if constexpr (ALL) {
-                    if (t > ra.B) {
-                        if (near) acc = log(u01_d(w_acc)) < static_cast<double>(Lp) - static_cast<double>(L);
-                        float *s1 = bs + slot, *s2 = bs + P * CB + slot, *ref = bs + 2 * P * CB + slot;
-                        if (blk_n == 0) {
+                // the FP32 decision takes effect at once; the rare branch below
+                // corrects it where the FP64 re-decision differs
+                float th_old[P];
+                const float L_old = L;
 #pragma unroll
-                            for (int p = 0; p < P; ++p)
-                                if (p % G == g) {
-                                    ref[p * CB] = acc ? prop[p] : th[p];
-                                    s1[p * CB] = 0.0f;
-                                    s2[p * CB] = 0.0f;
-                                }
-                        } else {
+                for (int p = 0; p < P; ++p) {
+                    th_old[p] = th[p];
+                    th[p] = acc ? prop[p] : th[p];
+                }
+                L = acc ? Lp : L;
+                n_acc += acc ? 1 : 0;
+                if (__builtin_expect(__any_sync(kFullMask, near) || t == t_event, 0)) {
+                    if (near) {
+                        const bool acc64 = log(u01_d(w_acc)) < static_cast<double>(Lp) - static_cast<double>(L_old);
+                        if (acc64 != acc) {
 #pragma unroll
-                            for (int p = 0; p < P; ++p)
-                                if (p % G == g) {
-                                    const float dd = (acc ? prop[p] : th[p]) - ref[p * CB];
-                                    s1[p * CB] += dd;
-                                    s2[p * CB] = fmaf(dd, dd, s2[p * CB]);
-                                }
-                        }
-                        if (++blk_n == kMomBlock || t == ra.I) {
-                            const double nb = blk_n, nn = static_cast<double>(n_mom) + nb;
-                            const double inv_nb = 1.0 / nb, w_b = nb / nn, cross = static_cast<double>(n_mom) * w_b;
-#pragma unroll
-                            for (int p = 0; p < P; ++p)
-                                if (p % G == g && active) {
-                                    const double a = s1[p * CB];
-                                    const double mb = static_cast<double>(ref[p * CB]) + a * inv_nb;
-                                    const double m2b = fma(-a, a * inv_nb, static_cast<double>(s2[p * CB]));
-                                    const double m = wf_mean[p * CB + slot];
-                                    const double delta = mb - m;
-                                    wf_mean[p * CB + slot] = fma(delta, w_b, m);
-                                    wf_m2[p * CB + slot] += fma(delta * delta, cross, m2b);
-                                }
-                            n_mom += blk_n;
-                            blk_n = 0;
+                            for (int p = 0; p < P; ++p) th[p] = acc64 ? prop[p] : th_old[p];
+                            L = acc64 ? Lp : L_old;
+                            n_acc += acc64 ? 1 : -1;
+                            acc = acc64;
                         }
                     }
-                }
-                if (__any_sync(kFullMask, near) || t == t_event) {
-                    if (near) acc = log(u01_d(w_acc)) < static_cast<double>(Lp) - static_cast<double>(L);
                     if (t == t_event) {
                         if (t == to_thin) {
                             to_thin += ra.T;
-                            float x[P];
-#pragma unroll
-                            for (int p = 0; p < P; ++p) x[p] = acc ? prop[p] : th[p];
+                            const float *x = th;
                             if (ra.samples && active) {
                                 const int sidx = (t - ra.B) / ra.T - 1;
                                 float *dst = ra.samples + ((static_cast<int64_t>(sidx) * C + c) * P) * ra.n_vox + v;
@@ -401,10 +439,9 @@ __device__ __forceinline__ void run_tile_split(const ModelConst &mc, const RunAr
                             }
                         }
                         if (t == to_adapt) {  // a window of the burn-in adaptation ends
-                            const int na = n_acc + (acc ? 1 : 0);
-                            const int a = na - ad_acc0;
+                            const int a = n_acc - ad_acc0;
                             ad_e += (a > ra.adapt_hi && ad_e < GAC_ADAPT_EMAX) - (a < ra.adapt_lo && ad_e > GAC_ADAPT_EMIN);
-                            ad_acc0 = na;
+                            ad_acc0 = n_acc;
                             bm_k = adapt_bm_scale<float>(ad_e);
                             to_adapt = (W_ad <= ra.B - t) ? t + W_ad : INT_MAX;
                             split_normals<P>(dn, bm_k, zn);  // the next iteration takes the new steps
@@ -412,11 +449,44 @@ __device__ __forceinline__ void run_tile_split(const ModelConst &mc, const RunAr
                         t_event = min(to_thin, to_adapt);
                     }
                 }
-                if (acc) {
+                if constexpr (ALL) {
+                    if (t > ra.B) {
+                        float *s1 = bs + slot, *s2 = bs + P * CB + slot, *ref = bs + 2 * P * CB + slot;
+                        if (blk_n == 0) {
 #pragma unroll
-                    for (int p = 0; p < P; ++p) th[p] = prop[p];
-                    L = Lp;
-                    ++n_acc;
+                            for (int p = 0; p < P; ++p)
+                                if (p % G == g) {
+                                    ref[p * CB] = th[p];
+                                    s1[p * CB] = 0.0f;
+                                    s2[p * CB] = 0.0f;
+                                }
+                        } else {
+#pragma unroll
+                            for (int p = 0; p < P; ++p)
+                                if (p % G == g) {
+                                    const float dd = th[p] - ref[p * CB];
+                                    s1[p * CB] += dd;
+                                    s2[p * CB] = fmaf(dd, dd, s2[p * CB]);
+                                }
+                        }
+                        if (++blk_n == kMomBlock || t == ra.I) {
+                            const double nb = blk_n, nn = static_cast<double>(n_mom) + nb;
+                            const double inv_nb = 1.0 / nb, w_b = nb / nn, cross = static_cast<double>(n_mom) * w_b;
+#pragma unroll
+                            for (int p = 0; p < P; ++p)
+                                if (p % G == g && active) {
+                                    const double a = s1[p * CB];
+                                    const double mb = static_cast<double>(ref[p * CB]) + a * inv_nb;
+                                    const double m2b = fma(-a, a * inv_nb, static_cast<double>(s2[p * CB]));
+                                    const double m = wf_mean[p * CB + slot];
+                                    const double delta = mb - m;
+                                    wf_mean[p * CB + slot] = fma(delta, w_b, m);
+                                    wf_m2[p * CB + slot] += fma(delta * delta, cross, m2b);
+                                }
+                            n_mom += blk_n;
+                            blk_n = 0;
+                        }
+                    }
                 }
 #pragma unroll
                 for (int p = 0; p < P; ++p) z[p] = zn[p];
@@ -424,7 +494,8 @@ __device__ __forceinline__ void run_tile_split(const ModelConst &mc, const RunAr
                 w_acc = dn.w_acc;
             }
             cur = nxt;
-            nxt = split_draw<P>(static_cast<uint32_t>(t0 + 2 * G + g), vg, cu, ra.k0, ra.k1);
+            wnx = pr;
+            pr = philox_start<P>(static_cast<uint32_t>(t0 + 3 * G + g), vg, cu);
         }
         if constexpr (!ALL) {
             if (wpend) {

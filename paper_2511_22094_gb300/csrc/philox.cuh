@@ -21,21 +21,28 @@ struct Words4 {
     uint32_t w[4];
 };
 
-// Ten rounds; each round is two 32x32->64 multiplies (one IMAD.WIDE each)
-// and two three-input XORs.  The key schedule depends only on the seed, so it
-// stays in uniform registers when the seed is a kernel argument.
+// One round with round key (k0, k1): two 32x32->64 multiplies (one IMAD.WIDE
+// each) and two three-input XORs.
+__device__ __forceinline__ void philox_round(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t &c3,
+                                             uint32_t k0, uint32_t k1) {
+    const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * c0;
+    const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c2;
+    const uint32_t n0 = static_cast<uint32_t>(p1 >> 32) ^ c1 ^ k0;
+    const uint32_t n2 = static_cast<uint32_t>(p0 >> 32) ^ c3 ^ k1;
+    c1 = static_cast<uint32_t>(p1);
+    c3 = static_cast<uint32_t>(p0);
+    c0 = n0;
+    c2 = n2;
+}
+
+// Ten rounds, round r keyed (k0 + r W0, k1 + r W1).  The key schedule depends
+// only on the seed, so it stays in uniform registers when the seed is a
+// kernel argument.
 __device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
                                                 uint32_t c3, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * c0;
-        const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c2;
-        const uint32_t n0 = static_cast<uint32_t>(p1 >> 32) ^ c1 ^ k0;
-        const uint32_t n2 = static_cast<uint32_t>(p0 >> 32) ^ c3 ^ k1;
-        c1 = static_cast<uint32_t>(p1);
-        c3 = static_cast<uint32_t>(p0);
-        c0 = n0;
-        c2 = n2;
+        philox_round(c0, c1, c2, c3, k0, k1);
         k0 += kPhiloxW0;
         k1 += kPhiloxW1;
     }
