@@ -202,6 +202,48 @@ def _dist():
     return world, rank, local
 
 
+class RankGroup:
+    """The benchmark's ranks: one process per GPU under torchrun (RANK,
+    LOCAL_RANK, WORLD_SIZE and MASTER_* from the environment).  The process
+    group carries only the barrier around the timed region and the
+    max-over-ranks time; no collective touches the sampler's data."""
+
+    def __init__(self, backend: str = "nccl"):
+        self.world, self.rank, self.local = _dist()
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self, cuda: bool = True):
+        if self.pg is not None:
+            self.pg.barrier()
+        if cuda:
+            import torch
+            torch.cuda.synchronize()
+
+    def max_time(self, t: float, device) -> float:
+        """The largest of the ranks' times (every rank gets it)."""
+        if self.pg is None:
+            return t
+        import torch
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        self.pg.all_reduce(tt, op=self.pg.ReduceOp.MAX)
+        return float(tt.item())
+
+    def close(self):
+        if self.pg is not None:
+            self.pg.destroy_process_group()
+            self.pg = None
+
+
+def weak_value(world: int, units_per_rank_step: int, steps: int, t_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time."""
+    return world * units_per_rank_step * steps / t_max
+
+
 def _host_inputs_for_oracle(w, n):
     import oracle
     th = W.truths(w, 0, n)
@@ -547,12 +589,8 @@ def run_ours(args, w):
     build.build()
     from paper_2511_22094_gb300 import gac
 
-    world, rank, local = _dist()
-    pg = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-        pg = dist
+    group = RankGroup("nccl")
+    world, rank, local = group.world, group.rank, group.local
     torch.cuda.set_device(local)
     dev = torch.device(f"cuda:{local}")
     stream = torch.cuda.current_stream()
@@ -586,10 +624,7 @@ def run_ours(args, w):
         else:
             gac.gac_mcmc_run(mid, y, N, sig, 0.0, None, opts, out, stream)
 
-    def barrier():
-        if pg is not None:
-            pg.barrier()
-        torch.cuda.synchronize()
+    barrier = group.barrier
 
     rates = _pipe_rates(gac, stream)  # the roofline's denominators, before any timing
     for _ in range(args.warmup):
@@ -607,13 +642,9 @@ def run_ours(args, w):
         barrier()
         t_wall = time.perf_counter() - t_wall
     per_step = [e0.elapsed_time(e1) / 1e3 for e0, e1 in ev]
-    t_total = sum(per_step)
-    if pg is not None:
-        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t_total = tt.item()
+    t_total = group.max_time(sum(per_step), dev)
     ci_per_step = N * C * w.iterations
-    value = world * ci_per_step * args.steps / t_total
+    value = weak_value(world, ci_per_step, args.steps, t_total)
     kernel_s = t_total / args.steps
 
     # end to end through the same public call with pinned host buffers
@@ -639,8 +670,7 @@ def run_ours(args, w):
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}
 
     if rank != 0:
-        if pg is not None:
-            pg.destroy_process_group()
+        group.close()
         return
     clocks = clk.summary()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -681,8 +711,7 @@ def run_ours(args, w):
                              for name in ("monoexp_4k", "smt_1p5m")}
         line["serving"] = serving_study(gac, dev, 200, saturated=True)
     print(json.dumps(line), flush=True)
-    if pg is not None:
-        pg.destroy_process_group()
+    group.close()
 
 
 def run_serving(args):

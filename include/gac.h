@@ -335,14 +335,17 @@ gac_status gac_fit_run(int model_id, const void *data, const uint8_t *mask, cons
  *   - precision must be GAC_PREC_MIXED and trace_n_vox 0; results equal
  *     gac_mcmc_run's for the same inputs.
  *   - The first call on a device looks up the array's device address (a
- *     one-time set-up per device); make that first call before any stream
- *     capture.
+ *     one-time set-up per device, kept for the life of the process); make
+ *     that first call before any stream capture.  A process that resets the
+ *     device (cudaDeviceReset) must not call this entry point on that device
+ *     again: the kept address belongs to the destroyed context.
  *   - All calls share the one array, and it keeps the last call's contents
  *     (each call initialises the state it uses, so nothing needs clearing).
  *     Calls whose kernels overlap on the GPU -- on different streams or from
  *     different threads -- race on it and must not be issued.
- *   - Synchronous like gac_mcmc_run.  Errors: INVALID_ARG, UNKNOWN_MODEL,
- *     CUDA. */
+ *   - Synchronous like gac_mcmc_run: it returns after synchronising
+ *     `stream`, once the last slice has finished.  lanes_per_chain is
+ *     ignored.  Errors: INVALID_ARG, UNKNOWN_MODEL, CUDA. */
 #define GAC_NOALLOC_STATE_BYTES (64u << 20)
 gac_status gac_mcmc_run_noalloc(int model_id, const void *data, int64_t n_vox, const float *sigma,
                                 float sigma_scalar, const float *x0, const gac_mcmc_opts *opts,

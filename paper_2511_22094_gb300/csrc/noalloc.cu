@@ -6,6 +6,8 @@
 // allocating routine.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -91,7 +93,8 @@ extern "C" gac_status gac_mcmc_run_noalloc(int model_id, const void *data, int64
     if (o->trace_n_vox != 0) return fail(GAC_ERR_INVALID_ARG, "no step tracing here");
     if (slice_iterations < 1) return fail(GAC_ERR_INVALID_ARG, "slice_iterations must be >= 1");
     if (!out) return fail(GAC_ERR_INVALID_ARG, "out must not be NULL");
-    if (!sigma && !(sigma_scalar > 0.0f)) return fail(GAC_ERR_INVALID_ARG, "sigma is NULL and sigma_scalar <= 0");
+    if (!sigma && !(sigma_scalar > 0.0f && std::isfinite(sigma_scalar)))
+        return fail(GAC_ERR_INVALID_ARG, "sigma is NULL and sigma_scalar is not a positive number");
     if (n_vox == 0) return GAC_OK;
     if (!data) return fail(GAC_ERR_INVALID_ARG, "data must not be NULL");
 
@@ -167,8 +170,9 @@ extern "C" gac_status gac_mcmc_run_noalloc(int model_id, const void *data, int64
     int per_sm = 0, sms = 0, dev = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, smem)) != cudaSuccess)
         return cuda_fail(e, "occupancy");
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return cuda_fail(e, "cudaDeviceGetAttribute");
     const int64_t grid = std::min<int64_t>(ra.n_tiles, static_cast<int64_t>(std::max(per_sm, 1)) * std::max(sms, 1));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // one launch per slice; the first slice initialises every chain (state

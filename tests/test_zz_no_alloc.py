@@ -90,3 +90,9 @@ def test_noalloc_rejects_what_it_cannot_do_without_allocating(gac, orc):
     with pytest.raises(gac.GacError) as e:
         gac.gac_mcmc_run_noalloc(mid, yd, n_big, None, 0.01, None, opts, 50, {})
     assert e.value.status == 1 and "at most" in gac.last_error()
+    # no per-voxel sigma and an infinite scalar: rejected, as by gac_mcmc_run
+    yd_small = torch.from_numpy(y).to(dev)
+    for bad in (float("inf"), float("nan"), 0.0, -1.0):
+        with pytest.raises(gac.GacError) as e:
+            gac.gac_mcmc_run_noalloc(mid, yd_small, 64, None, bad, None, opts, 50, {})
+        assert e.value.status == 1
