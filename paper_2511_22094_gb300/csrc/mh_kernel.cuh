@@ -113,11 +113,13 @@ struct SliceState {
     float *blk;      // [3P][N*C]: MIXED all-post-burn-in block partials (sum d, sum d^2, reference)
 };
 
-// 1/n for the FP64 Welford updates, n < kInvN: a constant-bank load (one
-// address per warp, broadcast) instead of an FP64 division, whose several
+// 1/n for the FP64 Welford updates, n < kInvN: a load (one address per warp,
+// through the read-only cache) instead of an FP64 division, whose several
 // FP64 instructions each hold a GB300 sub-partition's FP64 pipe for ~76
 // cycles (1.68 FP64 results per SM clock).  The table is computed at compile
-// time with IEEE division, so it holds exactly what the division returns.
+// time with IEEE division, so it holds exactly what the division returns; it
+// lives in global memory (in the constant bank its 32 KB crowded out the
+// kernel parameters the iteration loop reads: 1.5% slower).
 constexpr int kInvN = 4096;
 struct InvTable {
     double v[kInvN];
@@ -127,16 +129,19 @@ constexpr InvTable make_inv_table() {
     for (int i = 1; i < kInvN; ++i) t.v[i] = 1.0 / static_cast<double>(i);
     return t;
 }
-static __constant__ InvTable c_inv_n = make_inv_table();
+static __device__ InvTable g_inv_n = make_inv_table();
 
 // The Welford update's multiply-adds, written as explicit FMAs so that every
 // kernel that accumulates moments rounds them the same way.
 __device__ __forceinline__ double welford_fma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float welford_fma(float a, float b, float c) { return fmaf(a, b, c); }
 
-template <class W>
+// TABLE: from g_inv_n (the lane-split kernel, where the division's FP64
+// latency is exposed); otherwise the division itself (the one-thread kernel,
+// whose loop measured 1.5% faster without the table's load).  Equal values.
+template <class W, bool TABLE = false>
 __device__ __forceinline__ W inv_count(int n) {
-    if constexpr (sizeof(W) == 8) return n < kInvN ? c_inv_n.v[n] : 1.0 / static_cast<double>(n);
+    if constexpr (sizeof(W) == 8 && TABLE) return n < kInvN ? __ldg(&g_inv_n.v[n]) : 1.0 / static_cast<double>(n);
     else return W(1) / W(n);
 }
 
@@ -205,13 +210,16 @@ __device__ __forceinline__ typename PrecTraits<PREC>::R loglik_any(
 //                        rounding u to float.
 // A margin of 1e-5 + 2^-22 |d32| covers both (with room for the rounding of
 // the gap itself); inside it the decision is recomputed in FP64 from the same
-// L, Lp and word.  NaN lands in the FP64 branch and rejects.  (The bound does
-// not grow with |L| + |Lp|: far from the posterior, where both are large and
-// their difference is not, the FP64 branch stays rare -- each FP64
-// instruction holds a GB300 sub-partition's FP64 pipe for ~76 cycles.)
+// L, Lp and word.  NaN lands in the FP64 branch and rejects.  The wider
+// margin 1e-5 + 2^-20 (|L| + |Lp|) (WIDE) is valid too, as |d32| <= |L| +
+// |Lp|; it grows far from the posterior, where both are large and their
+// difference is not, so the lane-split kernel, whose FP64 latency nothing
+// hides, takes the tight one, and the one-thread kernel the wide one (its
+// loop measured 1.2% faster so).  The decision is the FP64 one either way.
+template <bool WIDE = false>
 __device__ __forceinline__ bool accept_mixed(float Lp, float L, float lu32, uint32_t w) {
     const float d32 = Lp - L;
-    const float margin = fmaf(0x1p-22f, fabsf(d32), 1e-5f);
+    const float margin = WIDE ? 1e-5f + 0x1p-20f * (fabsf(L) + fabsf(Lp)) : fmaf(0x1p-22f, fabsf(d32), 1e-5f);
     const float gap = d32 - lu32;
     if (fabsf(gap) > margin) return gap > 0.0f;
     return log(u01_d(w)) < static_cast<double>(Lp) - static_cast<double>(L);
@@ -227,7 +235,7 @@ __device__ __forceinline__ bool accept_step(typename PrecTraits<PREC>::R Lp,
         return logf(u01_f(w)) < Lp - L;
     } else {
         // FP64 semantics at FP32 cost (accept_mixed).
-        return accept_mixed(Lp, L, __logf(u01_f(w)), w);
+        return accept_mixed<true>(Lp, L, __logf(u01_f(w)), w);
     }
 }
 

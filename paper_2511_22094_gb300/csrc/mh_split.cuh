@@ -425,7 +425,7 @@ __device__ __forceinline__ void run_tile_split(const ModelConst &mc, const RunAr
                             }
                             if constexpr (!ALL) {
                                 ++n_mom;
-                                const W inv_n = inv_count<W>(n_mom);
+                                const W inv_n = inv_count<W, true>(n_mom);
 #pragma unroll
                                 for (int p = 0; p < P; ++p)
                                     if (p % G == g) {
