@@ -169,8 +169,10 @@ __device__ __forceinline__ float smt_g_f(float x, const ModelConst &mc) {
     constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
     const float t = fmaf(x, 2.0f, kRound);
     const float d = fmaf(t - kRound, -0.5f, x);
-    int i = __float_as_int(t) - __float_as_int(kRound) - mc.gtab_lo;
-    i = min(max(i, 0), mc.gtab_n - 1);
+    // one unsigned min keeps the index in the table (a negative index wraps
+    // to a large unsigned value)
+    const int i = static_cast<int>(min(static_cast<unsigned>(__float_as_int(t) - __float_as_int(kRound) - mc.gtab_lo),
+                                       static_cast<unsigned>(mc.gtab_n - 1)));
     const float4 lo = smt_gtab_s[i];
     const float4 hi = smt_gtab_s[kGTabMax + i];
     float p = fmaf(hi.y, d, hi.x);
@@ -641,18 +643,26 @@ __device__ __forceinline__ void eval_smt_f(const float *th, const ModelConst &mc
     const float f = th[0], da = th[1], dpar = th[2], dperp = th[3];
     const float ddiff = dpar - dperp;
     const int n = mc.n_acq;
+    // S(b = 0) = S0 = 1 exactly, by a select (no branch); blocks of kAnchor
+    // b-values unrolled, and a protocol of at most kAnchor b-values (one
+    // block, the same for every thread) reads them at fixed offsets
+    auto one = [&](int k) {
+        const float b = mc.acq_f[k];
+        const float intra = smt_g_f<TAIL>(b * da, mc);
+        const float extra = ex2_approx(-mc.acq_l2e_f[k] * dperp) * smt_g_f<TAIL>(b * ddiff, mc);
+        visit(k, b == 0.0f ? 1.0f : fmaf(f, intra, (1.0f - f) * extra));
+    };
+    if (n <= kAnchor) {
+#pragma unroll
+        for (int k = 0; k < kAnchor; ++k)
+            if (k < n) one(k);
+        end_block(visit, 0);
+        return;
+    }
     for (int k0 = 0; k0 < n; k0 += kAnchor) {
-        const int k1 = min(k0 + kAnchor, n);
-        for (int k = k0; k < k1; ++k) {
-            const float b = mc.acq_f[k];
-            if (b == 0.0f) {  // S(b = 0) = S0 = 1 (same b for every thread: no divergence)
-                visit(k, 1.0f);
-                continue;
-            }
-            const float intra = smt_g_f<TAIL>(b * da, mc);
-            const float extra = ex2_approx(-mc.acq_l2e_f[k] * dperp) * smt_g_f<TAIL>(b * ddiff, mc);
-            visit(k, fmaf(f, intra, (1.0f - f) * extra));
-        }
+#pragma unroll
+        for (int i = 0; i < kAnchor; ++i)
+            if (k0 + i < n) one(k0 + i);
         end_block(visit, 0);
     }
 }
