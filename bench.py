@@ -572,14 +572,13 @@ def time_workload(gac, name, dev, stream, rates, steps=5, warmup=3):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     clocks = clk.summary()
     roof = _roofline(name, "mh", ci / kernel_s, rates, sms, clocks, _measured(name, "mh"))
+    l2 = ("flushed before every step (256 MB write outside the timed events)" if flush is not None else
+          f"inputs + outputs {touched / 1e9:.1f} GB per step > 129 MB L2")
     del out, y, sig, flush
     torch.cuda.empty_cache()
     return {"value": ci / kernel_s, "unit": UNIT, "ms_per_step": kernel_s * 1e3, "steps": steps,
             "warmup": warmup, "config": {"n_vox": N, "n_chains": C, "iterations": w.iterations,
-                                         "burnin": w.burnin, "thin": w.thin, "samples_stored": True,
-                                         "l2": ("flushed before every step (256 MB write outside the timed events)"
-                                                if flush is not None else
-                                                f"inputs + outputs {touched / 1e9:.1f} GB per step > 129 MB L2")},
+                                         "burnin": w.burnin, "thin": w.thin, "samples_stored": True, "l2": l2},
             "roofline": roof, "clocks": clocks, "gpu_launches": steps}
 
 

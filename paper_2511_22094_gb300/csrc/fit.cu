@@ -42,8 +42,10 @@ struct FitArgs {
     R scale;               // 1 / (n_mask M)
     R lambda_n;            // lambda / n_mask
     R lr, beta1, beta2, eps;
-    int row_stride;        // shared-memory floats per staged measurement row (odd)
+    int row_stride;        // shared-memory floats per staged measurement row (odd; vec4: 4 x odd)
     int double_buffer;     // two staged tiles (the next one copied during the current one) or one
+    int vec4;              // rows staged and read as float4 (M % 4 == 0, 16-byte aligned data)
+    float inv_m4;          // 1 / (M / 4): row of a tile's float4 number e, exact for e < 2^13
     const int *stop;       // set by fit_check_kernel
     double *block_loss;    // [gridDim.x]
 };
@@ -130,7 +132,7 @@ __device__ __forceinline__ void jacobian(const R *th, const ModelConst &mc, V &&
 // the visitor of fit_voxel: r = w (y - s), L1 |r| with d = -w sign(r), L2
 // r^2 with d = -2 w r.  Adds the gradient to g[9]; returns the data loss.
 __device__ __forceinline__ float mwi3_rec_loss_grad_f(const float *th, const ModelConst &mc, const float *yrow,
-                                                      float wgt, bool l1, float *g) {
+                                                      float wgt, bool l1, bool vec4, float *g) {
     const float phi0 = th[8];
     const int n = mc.n_acq;
     const float r0 = 1.0f / th[3], r1 = 1.0f / th[4], r2 = 1.0f / th[5];
@@ -154,11 +156,11 @@ __device__ __forceinline__ float mwi3_rec_loss_grad_f(const float *th, const Mod
     // sums over echoes: amplitude terms, t x amplitude terms, t x frequency terms
     float2 G01 = f2(0.0f), T01 = f2(0.0f), C01 = f2(0.0f);
     float G2 = 0.0f, T2 = 0.0f, G8 = 0.0f, loss = 0.0f;
-    auto echo = [&](int k, float2 x, float2 y, float2 z) {
+    auto echo = [&](int k, float yr, float yi, float2 x, float2 y, float2 z) {
         const float t = fmaf(static_cast<float>(k), mc.dt_f, mc.t0_f);
         const float re = fmaf(a0, x.x, fmaf(a1, x.y, a2 * z.x));
         const float im = fmaf(a0, y.x, fmaf(a1, y.y, a2 * z.y));
-        const float rr = wgt * (yrow[2 * k] - re), ri = wgt * (yrow[2 * k + 1] - im);
+        const float rr = wgt * (yr - re), ri = wgt * (yi - im);
         const float dr = l1 ? -wgt * sgn(rr) : -2.0f * wgt * rr;
         const float di = l1 ? -wgt * sgn(ri) : -2.0f * wgt * ri;
         loss += l1 ? fabsf(rr) + fabsf(ri) : fmaf(rr, rr, ri * ri);
@@ -177,12 +179,27 @@ __device__ __forceinline__ float mwi3_rec_loss_grad_f(const float *th, const Mod
     for (int a = 0; a < n; a += kAnchor) {
         float2 x = X, y = Y, z = Z;
         const int cnt = min(kAnchor, n - a);
-        for (int i = 0; i < cnt; ++i) {
-            echo(a + i, x, y, z);
+        auto next = [&]() {
             const float2 xn = __ffma2_rn(x, RR, __fmul2_rn(y, NRI));
             y = __ffma2_rn(x, RI, __fmul2_rn(y, RR));
             x = xn;
             z = __fmul2_rn(z, R2);
+        };
+        if (vec4) {  // echoes a + i, a + i + 1 from one 16-byte load (a is even)
+            for (int i = 0; i < cnt; i += 2) {
+                const float4 q = reinterpret_cast<const float4 *>(yrow)[(a + i) >> 1];
+                echo(a + i, q.x, q.y, x, y, z);
+                next();
+                if (i + 1 < cnt) {
+                    echo(a + i + 1, q.z, q.w, x, y, z);
+                    next();
+                }
+            }
+        } else {
+            for (int i = 0; i < cnt; ++i) {
+                echo(a + i, yrow[2 * (a + i)], yrow[2 * (a + i) + 1], x, y, z);
+                next();
+            }
         }
         const float2 xn = __ffma2_rn(X, KR, __fmul2_rn(Y, NKI));
         Y = __ffma2_rn(X, KI, __fmul2_rn(Y, KR));
@@ -205,7 +222,7 @@ __device__ __forceinline__ float mwi3_rec_loss_grad_f(const float *th, const Mod
 // y, the loss gradient, the total-variation subgradient, Adam and the box.
 // Returns the voxel's share of the loss (0 outside the mask).
 template <int KIND, int PREC>
-__device__ __forceinline__ double fit_voxel(const ModelConst &mc, const FitArgs<typename PrecTraits<PREC>::R> &fa,
+__device__ __forceinline__ typename PrecTraits<PREC>::R fit_voxel(const ModelConst &mc, const FitArgs<typename PrecTraits<PREC>::R> &fa,
                                             int64_t v, const float *y, const typename PrecTraits<PREC>::R *u_in,
                                             typename PrecTraits<PREC>::R *u_out, typename PrecTraits<PREC>::R *m1,
                                             typename PrecTraits<PREC>::R *m2, typename PrecTraits<PREC>::R c1,
@@ -214,7 +231,7 @@ __device__ __forceinline__ double fit_voxel(const ModelConst &mc, const FitArgs<
     constexpr int P = model_n_par(KIND);
     const int64_t n = fa.n;
     const int64_t sx = 1, sy = fa.nx, sz = static_cast<int64_t>(fa.nx) * fa.ny;
-    double vl = 0.0;
+    R vl = R(0);  // the voxel's loss share (FP32 kernels: FP32; the block sums it in FP64)
     // Every load the update needs is issued here, before the model's long
     // arithmetic hides its latency: own parameters, mask and weight, the
     // usable neighbours (bit 2d: v + e_d, bit 2d + 1: v - e_d; inside the grid
@@ -230,8 +247,11 @@ __device__ __forceinline__ double fit_voxel(const ModelConst &mc, const FitArgs<
     int p0 = P;                       // first penalised map (P: none)
     R nb0[6];
     if (tv_on) {
-        const int coord[3] = {static_cast<int>(v % fa.nx), static_cast<int>((v / fa.nx) % fa.ny),
-                              static_cast<int>(v / sz)};
+        // 32-bit coordinate arithmetic (the grid has < 2^31 voxels)
+        const unsigned vu = static_cast<unsigned>(v), nxu = static_cast<unsigned>(fa.nx);
+        const unsigned q = vu / nxu, nxy = nxu * static_cast<unsigned>(fa.ny);
+        const int coord[3] = {static_cast<int>(vu - q * nxu), static_cast<int>(q % static_cast<unsigned>(fa.ny)),
+                              static_cast<int>(vu / nxy)};
         const int ext[3] = {fa.nx, fa.ny, fa.nz};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -260,13 +280,7 @@ __device__ __forceinline__ double fit_voxel(const ModelConst &mc, const FitArgs<
     if (!inside) {
 #pragma unroll
         for (int p = 0; p < P; ++p) u_out[p * n + v] = u[p];
-        return 0.0;
-    }
-    // Adam's moments are read at the end: start bringing them into L2 now
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(m1 + p * n + v));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(m2 + p * n + v));
+        return R(0);
     }
 #pragma unroll
     for (int p = 0; p < P; ++p) {
@@ -285,12 +299,12 @@ __device__ __forceinline__ double fit_voxel(const ModelConst &mc, const FitArgs<
         for (int p = 0; p < P; ++p) g[p] = fma(d, J[p], g[p]);
     };
     if constexpr (KIND == GAC_MODEL_MWI3 && PREC == GAC_PREC_FP32) {
-        if (mc.even) loss = mwi3_rec_loss_grad_f(th, mc, y, w, fa.loss == GAC_FIT_L1, g);  // same branch for every thread
+        if (mc.even) loss = mwi3_rec_loss_grad_f(th, mc, y, w, fa.loss == GAC_FIT_L1, fa.vec4, g);  // same branch for every thread
         else jacobian<KIND, R>(th, mc, visit);
     } else {
         jacobian<KIND, R>(th, mc, visit);
     }
-    vl += static_cast<double>(loss) * static_cast<double>(fa.scale);
+    vl += loss * fa.scale;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const R range = sizeof(R) == 8 ? R(mc.ub_d[p] - mc.lb_d[p]) : R(mc.ub_f[p] - mc.lb_f[p]);
@@ -318,17 +332,21 @@ __device__ __forceinline__ double fit_voxel(const ModelConst &mc, const FitArgs<
                 if ((nbit >> (2 * d + 1)) & 1u) tv += sgn(u[p] - nb[2 * d + 1]);
             }
             g[p] = fma(fa.lambda_n, tv, g[p]);
-            vl += static_cast<double>(fa.lambda_n) * static_cast<double>(tv_loss);
+            vl += fa.lambda_n * tv_loss;
         }
     }
-    // Adam (bias-corrected moments), then the box
+    // Adam (bias-corrected moments), then the box.  FP32: the corrections as
+    // the reciprocals c1, c2 carry (1 / (1 - beta^t)); FP64: divided, as the
+    // oracle does
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const R a = fa.beta1 * m1[p * n + v] + (R(1) - fa.beta1) * g[p];
         const R b = fa.beta2 * m2[p * n + v] + (R(1) - fa.beta2) * g[p] * g[p];
         m1[p * n + v] = a;
         m2[p * n + v] = b;
-        const R stepu = fa.lr * (a / c1) / (sqrt(b / c2) + fa.eps);
+        R stepu;
+        if constexpr (sizeof(R) == 8) stepu = fa.lr * (a / c1) / (sqrt(b / c2) + fa.eps);
+        else stepu = fa.lr * (a * c1) / (sqrtf(b * c2) + fa.eps);
         u_out[p * n + v] = fmin(fmax(u[p] - stepu, R(0)), R(1));
     }
     return vl;
@@ -339,6 +357,10 @@ __device__ __forceinline__ double fit_voxel(const ModelConst &mc, const FitArgs<
 __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
     const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -370,14 +392,25 @@ __global__ void __launch_bounds__(kFitBlock, fit_min_blocks(PREC)) fit_step_kern
     const int tile_floats = kFitBlock * fa.row_stride;
     auto stage = [&](int64_t tile, float *dst) {
         const int64_t base = tile * kFitBlock;
-        const int total = static_cast<int>(min(static_cast<int64_t>(kFitBlock), n - base)) * M;
+        const int rows = static_cast<int>(min(static_cast<int64_t>(kFitBlock), n - base));
         const float *src = fa.data + base * M;
-        for (int e = threadIdx.x; e < total; e += kFitBlock) {
-            const int row = e / M;
-            cp_async4(dst + row * fa.row_stride + (e - row * M), src + e);
+        if (fa.vec4) {  // 16-byte copies; row = floor((e + 1/2) / (M/4)) by one float multiply
+            const int M4 = M >> 2, S4 = fa.row_stride >> 2, total4 = rows * M4;
+            for (int e = threadIdx.x; e < total4; e += kFitBlock) {
+                const int row = static_cast<int>((static_cast<float>(e) + 0.5f) * fa.inv_m4);
+                cp_async16(dst + 4 * (row * S4 + (e - row * M4)), src + 4 * e);
+            }
+        } else {
+            const int total = rows * M;
+            for (int e = threadIdx.x; e < total; e += kFitBlock) {
+                const int row = e / M;
+                cp_async4(dst + row * fa.row_stride + (e - row * M), src + e);
+            }
         }
     };
-    double my_loss = 0.0;
+    using R = typename PrecTraits<PREC>::R;
+    R my_loss = R(0);
+    constexpr int P = model_n_par(KIND);
     int64_t tile = blockIdx.x;
     if (fa.double_buffer && tile < n_tiles) stage(tile, ytile);
     cp_async_commit();
@@ -396,13 +429,23 @@ __global__ void __launch_bounds__(kFitBlock, fit_min_blocks(PREC)) fit_step_kern
         }
         __syncthreads();
         const int64_t v = tile * kFitBlock + threadIdx.x;
+        // the next tile's parameters and Adam moments start on their way to L2
+        const int64_t vn = v + static_cast<int64_t>(gridDim.x) * kFitBlock;
+        if (vn < n) {
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(u_in + p * n + vn));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(m1 + p * n + vn));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(m2 + p * n + vn));
+            }
+        }
         if (v < n)
             my_loss += fit_voxel<KIND, PREC>(mc, fa, v, cur + threadIdx.x * fa.row_stride, u_in, u_out, m1, m2, c1, c2);
         __syncthreads();
     }
     cp_async_wait<0>();
     // the block's share of the loss, summed in a fixed order
-    red[threadIdx.x] = my_loss;
+    red[threadIdx.x] = static_cast<double>(my_loss);
     __syncthreads();
     for (int s = kFitBlock / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
@@ -519,7 +562,11 @@ static gac_status fit_run_prec(const ModelConst &mc, const gac_fit_opts *o, cons
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const int row_stride = mc.n_meas | 1;  // odd: the rows of a warp's voxels fall into distinct banks
+    // rows at an odd stride, so that a warp's voxels fall into distinct banks:
+    // odd in floats (4-byte staging and reads), or in float4s (16-byte
+    // staging and reads) when rows are whole float4s and the data is aligned
+    const bool vec4 = mc.n_meas % 4 == 0 && (reinterpret_cast<uintptr_t>(d_data) & 15) == 0;
+    const int row_stride = vec4 ? 4 * ((mc.n_meas / 4) | 1) : (mc.n_meas | 1);
     const size_t tile_bytes = static_cast<size_t>(kFitBlock) * row_stride * sizeof(float);
     const bool dbl = 4 * tile_bytes + 8 * 1024 <= static_cast<size_t>(smem_max);
     const size_t smem = (dbl ? 2 : 1) * tile_bytes;
@@ -578,13 +625,19 @@ static gac_status fit_run_prec(const ModelConst &mc, const gac_fit_opts *o, cons
     fa.block_loss = block_loss;
     fa.row_stride = row_stride;
     fa.double_buffer = dbl;
+    fa.vec4 = vec4;
+    fa.inv_m4 = vec4 ? 1.0f / static_cast<float>(mc.n_meas / 4) : 0.0f;
     // iterations in chunks; the stop flag is read between chunks
     constexpr int kChunk = 64;
     int t = 1;
     while (t <= I) {
         const int t_end = std::min(I, t + kChunk - 1);
         for (; t <= t_end; ++t) {
-            const double c1 = 1.0 - std::pow(o->beta1, t), c2 = 1.0 - std::pow(o->beta2, t);
+            double c1 = 1.0 - std::pow(o->beta1, t), c2 = 1.0 - std::pow(o->beta2, t);
+            if (PREC == GAC_PREC_FP32) {  // the FP32 kernel multiplies by the reciprocals
+                c1 = 1.0 / c1;
+                c2 = 1.0 / c2;
+            }
             const void *ui = (t & 1) ? u0 : u1;
             void *uo = (t & 1) ? u1 : u0;
             if ((e = launch_step_kind<PREC>(mc.kind, grid, smem, s, mc, fa, ui, uo, m1, m2, c1, c2)) != cudaSuccess)

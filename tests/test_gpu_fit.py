@@ -4,12 +4,12 @@ device against the FP64 oracle.
 FP64 kernel: the oracle's trajectory, parameters and loss history to
 rounding, for every model with L1 and L2 losses, a mask with holes, per-
 voxel weights and 3D total variation; both stopping rules stop at the
-oracle's iteration.  FP32 kernel: the first update equals the oracle's to the
-FP32 error of the gradient (Adam's first step is lr against the gradient's
-sign, so only near-zero gradient components may differ), and after 200
-updates the loss (to 1%) and the parameter maps (95% within 2% of the prior
-range) agree: the L1 subgradient and the TV signs flip where FP32 and FP64
-residuals straddle zero, after which the trajectories part by Adam steps.
+oracle's iteration.  FP32 kernel: every parameter of every voxel within
+2e-6 + 5e-7 t of the prior range at each of the first 20 updates; the first
+update to the FP32 error of the gradient; and over 200 updates, where the
+L1 subgradient and the TV signs flip where FP32 and FP64 residuals straddle
+zero and the trajectories part by Adam steps, the loss (to 1%) and the
+parameter maps (95% within 2% of the prior range).
 Volumes of 40k-120k voxels give every persistent block two or more tiles of
 256 voxels and end in a ragged tile; 64 echoes of the 3-pool model (128
 values a voxel) take the one-buffer staging path.
@@ -84,6 +84,33 @@ def test_stopping_rules_match_the_oracle(gac, orc):
                                          precision=gac.PREC_FP64, **kw_g)
         assert g_done == r_done < 300
         np.testing.assert_allclose(g_hist, r_hist, rtol=1e-9)
+
+
+FP32_CASES = [(k, loss) for k in (MONOEXP, MWI3, SMT) for loss in (1, 2)]
+
+
+@pytest.mark.parametrize("kind,loss", FP32_CASES, ids=[f"{k}-L{l}" for k, l in FP32_CASES])
+def test_fp32_follows_the_oracle_for_20_iterations(gac, orc, kind, loss):
+    """The FP32 kernel's state after each of the first 20 updates, every
+    parameter of every voxel, against the FP64 oracle's: |d theta| / range
+    <= 2e-6 + 5e-7 t at iteration t (the float parameters and moments drift
+    apart by a few 1e-8 of the range per update; measured on GB300 at most
+    6.4e-6 at t = 20, 3-pool L1), and the loss history to 1e-5 (measured
+    <= 2.5e-6).  Weighted data, a mask with holes and 3D total variation."""
+    acq, lb, ub, y, theta0, mask, weight = _problem(orc, kind)
+    mid = gac.gac_model_register(kind, acq, lb, ub, np.zeros(len(lb)))
+    worst = 0.0
+    for t in range(1, 21):
+        kw = dict(loss=loss, iterations=t, lr=0.01, lam=0.01, tv_params=0b1, tv_dims=3)
+        r, r_hist, _ = orc.fit_run(kind, acq, lb, ub, y, theta0, shape=SHAPE, mask=mask, weight=weight, **kw)
+        g, g_hist, g_done = gac.fit_host(mid, y, theta0, shape=SHAPE, mask=mask, weight=weight, iterations=t,
+                                         learning_rate=0.01, loss=loss, tv_lambda=0.01, tv_params=0b1, tv_dims=3)
+        assert g_done == t
+        d = np.abs(g - r) / (ub - lb)
+        assert d.max() <= 2e-6 + 5e-7 * t, (t, d.max())
+        np.testing.assert_allclose(g_hist, r_hist, rtol=1e-5)
+        worst = max(worst, d.max() / (2e-6 + 5e-7 * t))
+    print(f"FP32 kind {kind} L{loss}: worst |dtheta|/range over the first 20 updates {worst:.2f} of the bound")
 
 
 @pytest.mark.parametrize("kind", [MONOEXP, MWI3, SMT])
