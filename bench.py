@@ -95,13 +95,21 @@ def _alu_peaks(mix: dict, rates):
 # code: comments and layout aside) hash to the value they were measured with
 # (otherwise null).
 KERNEL_SOURCES = ("include/gac.h", "paper_2511_22094_gb300/csrc/mh_kernel.cuh",
-                  "paper_2511_22094_gb300/csrc/models.cuh", "paper_2511_22094_gb300/csrc/philox.cuh")
+                  "paper_2511_22094_gb300/csrc/mh_split.cuh", "paper_2511_22094_gb300/csrc/models.cuh",
+                  "paper_2511_22094_gb300/csrc/philox.cuh")
 KIND_SOURCE = {"mwi3_1m": "mh_mwi3.cu", "smt_1p5m": "mh_smt.cu", "monoexp_4k": "mh_monoexp.cu",
                "axcal_250k": "mh_axcal.cu"}
 MEASURED = {
-    "mwi3_1m": dict(sources="989bafbcb8bbf4ac", traffic_bytes=282.5e6 + 6620.6e6, warp_instr=966.2),
-    "smt_1p5m": dict(sources="2022dc6fdbec6948", traffic_bytes=111.9e6 + 4425.4e6, warp_instr=511.0),
-    "axcal_250k": dict(sources="89b09c945f92ef7f", traffic_bytes=106.3e6 + 3599.1e6, warp_instr=1244.8),
+    # traffic: DRAM bytes of a quarter-size launch (262,144 / 393,216 / 65,536
+    # voxels, all iterations, so every term scales with the voxels) x 3.81;
+    # the lines still in L2 when the small launch ends are not counted
+    # (~1-3% of its writes).  warp_instr: from the small-case --set full captures.
+    "mwi3_1m": dict(sources="8b352975cdad8812", traffic_bytes=(78.07e6 + 1696.83e6) * 1e6 / 262144, warp_instr=918.8),
+    "smt_1p5m": dict(sources="6aa13ef41a5a4ef2", traffic_bytes=(32.19e6 + 1120.72e6) * 1.5e6 / 393216, warp_instr=495.2),
+    "axcal_250k": dict(sources="b905d93628b32296", traffic_bytes=(37.59e6 + 910.33e6) * 250000 / 65536, warp_instr=1215.1),
+    # the lane-split kernel (2 lanes a chain): the 4,096-voxel workload's data
+    # and samples stay in L2, so no DRAM figure
+    "monoexp_4k": dict(sources="4ad3763a92ec82bb", traffic_bytes=None, warp_instr=377.2),
 }
 
 
@@ -484,11 +492,19 @@ def run_reference(args, w):
 
 
 def _roofline(base_name, sampler, ci_s, rates, sms, clocks, meas):
-    """The direct-form ALU roofline of a sampler workload at ci_s
-    chain-iterations (or walker moves) per second: the model's algorithmic
-    MUFU and FP32+INT counts against the measured pipe rates at the maximum
-    SM clock, whichever bounds; with the executed-instruction (issue) fraction
-    when an ncu count for the current sources exists."""
+    """The ALU roofline of a sampler workload at ci_s chain-iterations (or
+    walker moves) per second.
+
+    Headline (when an ncu count exists for the current kernel sources): the
+    executed-instruction issue roofline, the warp instructions the kernel
+    executes per chain-iteration (all pipes) against 4 warp-instructions per
+    SM clock at the maximum SM clock -- the limit these issue- and
+    FMA-pipe-bound kernels meet.  `direct_form_equivalent`: the model's
+    direct-form MUFU and FP32+INT counts (every echo with its own exp, sin,
+    cos) against the measured pipe rates; the kernels evaluate evenly spaced
+    echoes by a recurrence and execute fewer special-function operations, so
+    this ratio can exceed 1 and is not a fraction of a peak.  Without a count
+    the headline falls back to it."""
     f_max = (_peaks().get("sm_max_mhz") or 2070.0) * 1e6
     ops = (OPS_ENSEMBLE if sampler == "ensemble" else OPS)[base_name]
     n_mufu = sum(ops["mufu"].values())
@@ -503,16 +519,22 @@ def _roofline(base_name, sampler, ci_s, rates, sms, clocks, meas):
         peak = sms * fp32_clk * f_max / 1e9
         per_clk = fp32_clk
     f_med = (clocks.get("sm_mhz") or 0) * 1e6
-    roof = {"bound": "alu", "pipe": pipe, "count": "direct-form", "achieved": achieved,
-            "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
-            "peak_basis": f"{sms} SMs x {per_clk:.2f}/clk ({rate_basis}) x {f_max / 1e6:.0f} MHz (max SM clock)",
-            "frac_at_sampled_clock": (achieved / peak * f_max / f_med) if f_med else None}
+    direct = {"pipe": pipe, "count": "direct-form", "achieved": achieved, "peak": peak, "unit": "Gop/s",
+              "ratio": achieved / peak,
+              "peak_basis": f"{sms} SMs x {per_clk:.2f}/clk ({rate_basis}) x {f_max / 1e6:.0f} MHz (max SM clock)"}
     if meas.get("warp_instr"):
-        issue_peak = sms * ISSUE_PER_CLK_SM * f_max
-        roof["executed"] = {"warp_instr_per_32_units": meas["warp_instr"],
-                            "issue_frac": meas["warp_instr"] * ci_s / 32 / issue_peak,
-                            "basis": f"{sms} SMs x {ISSUE_PER_CLK_SM} warp-instr/clk x {f_max / 1e6:.0f} MHz"}
-    return roof
+        issue_peak = sms * ISSUE_PER_CLK_SM * f_max * 32 / 1e9  # thread-instructions / s, in G
+        ach = meas["warp_instr"] * ci_s / 1e9  # thread-instructions / s (warp_instr per 32 units x 32 / 32)
+        return {"bound": "alu", "pipe": "issue", "count": "executed (ncu: warp instructions per 32 chain-"
+                "iterations, all pipes)", "achieved": ach, "peak": issue_peak, "unit": "Ginstr/s",
+                "frac": ach / issue_peak, "frac_at_sampled_clock": (ach / issue_peak * f_max / f_med) if f_med else None,
+                "peak_basis": f"{sms} SMs x {ISSUE_PER_CLK_SM} warp-instructions/clk x 32 lanes x "
+                              f"{f_max / 1e6:.0f} MHz (max SM clock)",
+                "warp_instr_per_32_units": meas["warp_instr"], "direct_form_equivalent": direct}
+    return {"bound": "alu", "pipe": pipe, "count": "direct-form (no executed count for these sources)",
+            "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
+            "frac_at_sampled_clock": (achieved / peak * f_max / f_med) if f_med else None,
+            "peak_basis": direct["peak_basis"], "direct_form_equivalent": direct}
 
 
 def _device_inputs(gac, w, mid, dev, stream, base=0):
