@@ -335,8 +335,8 @@ gac_status gac_fit_run(int model_id, const void *data, const uint8_t *mask, cons
  *   - precision must be GAC_PREC_MIXED and trace_n_vox 0; results equal
  *     gac_mcmc_run's for the same inputs.
  *   - The first call on a device looks up the array's device address (a
- *     one-time set-up per device, kept for the life of the process); make
- *     that first call before any stream capture.  A process that resets the
+ *     one-time set-up per device, kept for the life of the process).  A
+ *     process that resets the
  *     device (cudaDeviceReset) must not call this entry point on that device
  *     again: the kept address belongs to the destroyed context.
  *   - All calls share the one array, and it keeps the last call's contents
