@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "gac.h"
@@ -46,13 +47,33 @@ struct FitArgs {
     int double_buffer;     // two staged tiles (the next one copied during the current one) or one
     int vec4;              // rows staged and read as float4 (M % 4 == 0, 16-byte aligned data)
     float inv_m4;          // 1 / (M / 4): row of a tile's float4 number e, exact for e < 2^13
+    int fdiv;              // n < 2^24: grid coordinates by float reciprocals (udiv_f)
+    float inv_nx, inv_ny;  // 1 / nx, 1 / ny rounded to float
     const int *stop;       // set by fit_check_kernel
     double *block_loss;    // [gridDim.x]
 };
 
 template <class R>
 __device__ __forceinline__ R sgn(R x) {
-    return static_cast<R>((x > R(0)) - (x < R(0)));
+    return x > R(0) ? R(1) : (x < R(0) ? R(-1) : R(0));
+}
+
+// a / b and a % b for a < 2^24 from the float reciprocal inv_b = fl(1 / b):
+// the float quotient is within 1 of a / b for b >= 2 (two roundings of
+// relative size 2^-24 on a value below 2^23) and exact for b = 1, so one
+// correction step gives the integer quotient.
+__device__ __forceinline__ unsigned udiv_f(unsigned a, unsigned b, float inv_b, unsigned &rem) {
+    unsigned q = __float2uint_rz(__uint2float_rn(a) * inv_b);
+    int r = static_cast<int>(a - q * b);
+    if (r < 0) {
+        --q;
+        r += static_cast<int>(b);
+    } else if (r >= static_cast<int>(b)) {
+        ++q;
+        r -= static_cast<int>(b);
+    }
+    rem = static_cast<unsigned>(r);
+    return q;
 }
 
 // ------------------------------------------------ models and Jacobians ----
@@ -131,11 +152,17 @@ __device__ __forceinline__ void jacobian(const R *th, const ModelConst &mc, V &&
 // two offset pools are carried as lane pairs.  rho and its derivative as in
 // the visitor of fit_voxel: r = w (y - s), L1 |r| with d = -w sign(r), L2
 // r^2 with d = -2 w r.  Adds the gradient to g[9]; returns the data loss.
+template <bool L1>
 __device__ __forceinline__ float mwi3_rec_loss_grad_f(const float *th, const ModelConst &mc, const float *yrow,
-                                                      float wgt, bool l1, bool vec4, float *g) {
+                                                      float wgt, bool vec4, float *g) {
     const float phi0 = th[8];
     const int n = mc.n_acq;
-    const float r0 = 1.0f / th[3], r1 = 1.0f / th[4], r2 = 1.0f / th[5];
+    // 1 / T2* from the special-function reciprocal and one Newton step (within an ulp)
+    auto rcp = [](float x) {
+        const float r = rcp_approx(x);
+        return fmaf(fmaf(-x, r, 1.0f), r, r);
+    };
+    const float r0 = rcp(th[3]), r1 = rcp(th[4]), r2 = rcp(th[5]);
     const float2 w = make_float2(kTwoPiMilli * th[6], kTwoPiMilli * th[7]);
     const float2 m0 = make_float2(expf(-mc.t0_f * r0), expf(-mc.t0_f * r1));
     const float2 m1 = make_float2(expf(-mc.dt_f * r0), expf(-mc.dt_f * r1));
@@ -156,14 +183,18 @@ __device__ __forceinline__ float mwi3_rec_loss_grad_f(const float *th, const Mod
     // sums over echoes: amplitude terms, t x amplitude terms, t x frequency terms
     float2 G01 = f2(0.0f), T01 = f2(0.0f), C01 = f2(0.0f);
     float G2 = 0.0f, T2 = 0.0f, G8 = 0.0f, loss = 0.0f;
-    auto echo = [&](int k, float yr, float yi, float2 x, float2 y, float2 z) {
-        const float t = fmaf(static_cast<float>(k), mc.dt_f, mc.t0_f);
+    // rho'(r) w.r.t. s for r = w (y - s): -w sign(r) (sign(0) = 0) or -2 w r
+    auto deriv = [&](float r) {
+        if constexpr (L1) return r > 0.0f ? -wgt : (r < 0.0f ? wgt : 0.0f);
+        else return -2.0f * wgt * r;
+    };
+    auto echo = [&](float t, float yr, float yi, float2 x, float2 y, float2 z) {
         const float re = fmaf(a0, x.x, fmaf(a1, x.y, a2 * z.x));
         const float im = fmaf(a0, y.x, fmaf(a1, y.y, a2 * z.y));
         const float rr = wgt * (yr - re), ri = wgt * (yi - im);
-        const float dr = l1 ? -wgt * sgn(rr) : -2.0f * wgt * rr;
-        const float di = l1 ? -wgt * sgn(ri) : -2.0f * wgt * ri;
-        loss += l1 ? fabsf(rr) + fabsf(ri) : fmaf(rr, rr, ri * ri);
+        const float dr = deriv(rr), di = deriv(ri);
+        if constexpr (L1) loss += fabsf(rr) + fabsf(ri);
+        else loss += fmaf(rr, rr, ri * ri);
         const float2 D = f2(dr), E = f2(di);
         const float2 inc = __ffma2_rn(E, y, __fmul2_rn(D, x));                       // Re(conj(d) u), pools 0, 1
         const float2 crs = __ffma2_rn(make_float2(-di, -di), x, __fmul2_rn(D, y));  // Im(conj(d) u)
@@ -176,36 +207,41 @@ __device__ __forceinline__ float mwi3_rec_loss_grad_f(const float *th, const Mod
         T2 = fmaf(t, inc2, T2);
         G8 = fmaf(di, re, fmaf(-dr, im, G8));
     };
-    for (int a = 0; a < n; a += kAnchor) {
+    // one block of echoes a .. a + cnt - 1 from the block's anchors (FULL:
+    // cnt = kAnchor, offsets and times fixed); echo times t0 + k dt
+    auto block = [&](int a, int cnt, auto full) {
+        constexpr bool FULL = decltype(full)::value;
         float2 x = X, y = Y, z = Z;
-        const int cnt = min(kAnchor, n - a);
-        auto next = [&]() {
+        const float ta = fmaf(static_cast<float>(a), mc.dt_f, mc.t0_f);
+        const float4 *q4 = reinterpret_cast<const float4 *>(yrow) + (a >> 1);
+#pragma unroll
+        for (int i = 0; i < kAnchor; ++i) {
+            if (!FULL && i >= cnt) break;
+            float yr, yi;
+            if (vec4) {  // echoes a + i, a + i + 1 from one 16-byte load (a is even)
+                const float4 q = q4[i >> 1];
+                yr = (i & 1) ? q.z : q.x;
+                yi = (i & 1) ? q.w : q.y;
+            } else {
+                yr = yrow[2 * (a + i)];
+                yi = yrow[2 * (a + i) + 1];
+            }
+            echo(fmaf(static_cast<float>(i), mc.dt_f, ta), yr, yi, x, y, z);
             const float2 xn = __ffma2_rn(x, RR, __fmul2_rn(y, NRI));
             y = __ffma2_rn(x, RI, __fmul2_rn(y, RR));
             x = xn;
             z = __fmul2_rn(z, R2);
-        };
-        if (vec4) {  // echoes a + i, a + i + 1 from one 16-byte load (a is even)
-            for (int i = 0; i < cnt; i += 2) {
-                const float4 q = reinterpret_cast<const float4 *>(yrow)[(a + i) >> 1];
-                echo(a + i, q.x, q.y, x, y, z);
-                next();
-                if (i + 1 < cnt) {
-                    echo(a + i + 1, q.z, q.w, x, y, z);
-                    next();
-                }
-            }
-        } else {
-            for (int i = 0; i < cnt; ++i) {
-                echo(a + i, yrow[2 * (a + i)], yrow[2 * (a + i) + 1], x, y, z);
-                next();
-            }
         }
+    };
+    int a = 0;
+    for (; a + kAnchor <= n; a += kAnchor) {
+        block(a, kAnchor, std::true_type{});
         const float2 xn = __ffma2_rn(X, KR, __fmul2_rn(Y, NKI));
         Y = __ffma2_rn(X, KI, __fmul2_rn(Y, KR));
         X = xn;
         Z = __fmul2_rn(Z, K2);
     }
+    if (a < n) block(a, n - a, std::false_type{});
     g[0] += G01.x;
     g[1] += G01.y;
     g[2] += G2;
@@ -221,37 +257,52 @@ __device__ __forceinline__ float mwi3_rec_loss_grad_f(const float *th, const Mod
 // One voxel's update: forward model and Jacobian against its staged data row
 // y, the loss gradient, the total-variation subgradient, Adam and the box.
 // Returns the voxel's share of the loss (0 outside the mask).
-template <int KIND, int PREC>
+template <int KIND, int PREC, bool L1>
 __device__ __forceinline__ typename PrecTraits<PREC>::R fit_voxel(const ModelConst &mc, const FitArgs<typename PrecTraits<PREC>::R> &fa,
-                                            int64_t v, const float *y, const typename PrecTraits<PREC>::R *u_in,
+                                            int v, const float *y, const typename PrecTraits<PREC>::R *u_in,
                                             typename PrecTraits<PREC>::R *u_out, typename PrecTraits<PREC>::R *m1,
                                             typename PrecTraits<PREC>::R *m2, typename PrecTraits<PREC>::R c1,
                                             typename PrecTraits<PREC>::R c2) {
     using R = typename PrecTraits<PREC>::R;
     constexpr int P = model_n_par(KIND);
-    const int64_t n = fa.n;
-    const int64_t sx = 1, sy = fa.nx, sz = static_cast<int64_t>(fa.nx) * fa.ny;
+    const int n = static_cast<int>(fa.n);
     R vl = R(0);  // the voxel's loss share (FP32 kernels: FP32; the block sums it in FP64)
     // Every load the update needs is issued here, before the model's long
-    // arithmetic hides its latency: own parameters, mask and weight, the
-    // usable neighbours (bit 2d: v + e_d, bit 2d + 1: v - e_d; inside the grid
-    // and the mask) and the neighbours' values of the first penalised map.
-    R u[P], th[P], g[P];
+    // arithmetic hides its latency: own parameters and Adam moments, mask and
+    // weight, the usable neighbours (bit 2d: v + e_d, bit 2d + 1: v - e_d;
+    // inside the grid and the mask) and the neighbours' values of the first
+    // penalised map.
+    R u[P], th[P], g[P], mo1[P], mo2[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) u[p] = u_in[p * n + v];
     const bool inside = !fa.mask || fa.mask[v];
+    if (inside) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            mo1[p] = m1[p * n + v];
+            mo2[p] = m2[p * n + v];
+        }
+    }
     const R w = fa.weight ? R(fa.weight[v]) : R(1);
     const bool tv_on = fa.tv_params && fa.lambda_n != R(0);
-    const int64_t step[3] = {sx, sy, sz};
+    const int step[3] = {1, fa.nx, fa.nx * fa.ny};
     unsigned grid_bit = 0, nbit = 0;  // neighbours inside the grid; inside the grid and the mask
     int p0 = P;                       // first penalised map (P: none)
     R nb0[6];
+    auto offset = [&](int j) { return ((grid_bit >> j) & 1u) ? ((j & 1) ? -step[j >> 1] : step[j >> 1]) : 0; };
     if (tv_on) {
-        // 32-bit coordinate arithmetic (the grid has < 2^31 voxels)
-        const unsigned vu = static_cast<unsigned>(v), nxu = static_cast<unsigned>(fa.nx);
-        const unsigned q = vu / nxu, nxy = nxu * static_cast<unsigned>(fa.ny);
-        const int coord[3] = {static_cast<int>(vu - q * nxu), static_cast<int>(q % static_cast<unsigned>(fa.ny)),
-                              static_cast<int>(vu / nxy)};
+        const unsigned vu = static_cast<unsigned>(v), nxu = static_cast<unsigned>(fa.nx), nyu = static_cast<unsigned>(fa.ny);
+        unsigned cx, cy, q, cz;
+        if (fa.fdiv) {  // the same for every thread
+            q = udiv_f(vu, nxu, fa.inv_nx, cx);
+            cz = udiv_f(q, nyu, fa.inv_ny, cy);
+        } else {
+            q = vu / nxu;
+            cx = vu - q * nxu;
+            cz = q / nyu;
+            cy = q - cz * nyu;
+        }
+        const int coord[3] = {static_cast<int>(cx), static_cast<int>(cy), static_cast<int>(cz)};
         const int ext[3] = {fa.nx, fa.ny, fa.nz};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -263,18 +314,12 @@ __device__ __forceinline__ typename PrecTraits<PREC>::R fit_voxel(const ModelCon
         nbit = grid_bit;
         if (fa.mask) {
 #pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                const int64_t o = ((grid_bit >> j) & 1u) ? ((j & 1) ? -step[j >> 1] : step[j >> 1]) : 0;
-                nbit &= ~(static_cast<unsigned>(fa.mask[v + o] == 0) << j);
-            }
+            for (int j = 0; j < 6; ++j) nbit &= ~(static_cast<unsigned>(fa.mask[v + offset(j)] == 0) << j);
         }
         p0 = __ffs(fa.tv_params) - 1;
         if (p0 < P) {
 #pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                const int64_t o = ((grid_bit >> j) & 1u) ? ((j & 1) ? -step[j >> 1] : step[j >> 1]) : 0;
-                nb0[j] = u_in[p0 * n + v + o];
-            }
+            for (int j = 0; j < 6; ++j) nb0[j] = u_in[p0 * n + v + offset(j)];
         }
     }
     if (!inside) {
@@ -293,13 +338,19 @@ __device__ __forceinline__ typename PrecTraits<PREC>::R fit_voxel(const ModelCon
     R loss = R(0);
     auto visit = [&](int k, R s, const R *J) {
         const R r = w * (R(y[k]) - s);
-        const R d = fa.loss == GAC_FIT_L1 ? -w * sgn(r) : R(-2) * w * r;
-        loss += fa.loss == GAC_FIT_L1 ? fabs(r) : r * r;
+        R d;
+        if constexpr (L1) {
+            d = -w * sgn(r);
+            loss += fabs(r);
+        } else {
+            d = R(-2) * w * r;
+            loss += r * r;
+        }
 #pragma unroll
         for (int p = 0; p < P; ++p) g[p] = fma(d, J[p], g[p]);
     };
     if constexpr (KIND == GAC_MODEL_MWI3 && PREC == GAC_PREC_FP32) {
-        if (mc.even) loss = mwi3_rec_loss_grad_f(th, mc, y, w, fa.loss == GAC_FIT_L1, fa.vec4, g);  // same branch for every thread
+        if (mc.even) loss = mwi3_rec_loss_grad_f<L1>(th, mc, y, w, fa.vec4, g);  // same branch for every thread
         else jacobian<KIND, R>(th, mc, visit);
     } else {
         jacobian<KIND, R>(th, mc, visit);
@@ -317,10 +368,7 @@ __device__ __forceinline__ typename PrecTraits<PREC>::R fit_voxel(const ModelCon
             if (!((fa.tv_params >> p) & 1u)) continue;
             R nb[6];
 #pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                const int64_t o = ((grid_bit >> j) & 1u) ? ((j & 1) ? -step[j >> 1] : step[j >> 1]) : 0;
-                nb[j] = p == p0 ? nb0[j] : u_in[p * n + v + o];
-            }
+            for (int j = 0; j < 6; ++j) nb[j] = p == p0 ? nb0[j] : u_in[p * n + v + offset(j)];
             R tv = R(0), tv_loss = R(0);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
@@ -336,17 +384,23 @@ __device__ __forceinline__ typename PrecTraits<PREC>::R fit_voxel(const ModelCon
         }
     }
     // Adam (bias-corrected moments), then the box.  FP32: the corrections as
-    // the reciprocals c1, c2 carry (1 / (1 - beta^t)); FP64: divided, as the
-    // oracle does
+    // the reciprocals c1, c2 carry (1 / (1 - beta^t)), the step's square root
+    // and quotient on the special-function unit (a few ulp); FP64: divided,
+    // as the oracle does
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const R a = fa.beta1 * m1[p * n + v] + (R(1) - fa.beta1) * g[p];
-        const R b = fa.beta2 * m2[p * n + v] + (R(1) - fa.beta2) * g[p] * g[p];
+        const R a = fa.beta1 * mo1[p] + (R(1) - fa.beta1) * g[p];
+        const R b = fa.beta2 * mo2[p] + (R(1) - fa.beta2) * g[p] * g[p];
         m1[p * n + v] = a;
         m2[p * n + v] = b;
         R stepu;
-        if constexpr (sizeof(R) == 8) stepu = fa.lr * (a / c1) / (sqrt(b / c2) + fa.eps);
-        else stepu = fa.lr * (a * c1) / (sqrtf(b * c2) + fa.eps);
+        if constexpr (sizeof(R) == 8) {
+            stepu = fa.lr * (a / c1) / (sqrt(b / c2) + fa.eps);
+        } else {
+            float sq;
+            asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sq) : "f"(b * c2));
+            stepu = __fdividef(fa.lr * (a * c1), sq + fa.eps);
+        }
         u_out[p * n + v] = fmin(fmax(u[p] - stepu, R(0)), R(1));
     }
     return vl;
@@ -366,14 +420,18 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Persistent blocks over tiles of kFitBlock voxels (tile b, b + grid, ...).
-// The measurement rows of the next tile are copied into the second of two
-// shared-memory buffers while the current tile computes; rows sit at an odd
-// float stride so that a warp's reads of one column hit distinct banks.
-// FP32 kernels keep two blocks (16 warps) on an SM.
+// Persistent warps over tiles of 32 voxels (warp tile w, w + all warps, ...).
+// Each warp stages its own tiles' measurement rows in its own part of shared
+// memory: the next tile's rows are copied into the second of two buffers
+// while the current tile computes, and only the warp waits for them, so warps
+// drift apart and hide each other's memory latency instead of meeting at a
+// block barrier every tile.  Rows sit at an odd stride (in floats, or in
+// float4s for 16-byte copies) so that a warp's reads of one column hit
+// distinct banks.  FP32 kernels keep two blocks (16 warps) on an SM.
+constexpr int kFitWarps = kFitBlock / 32;
 constexpr int fit_min_blocks(int prec) { return prec == GAC_PREC_FP32 ? 2 : 1; }
 
-template <int KIND, int PREC>
+template <int KIND, int PREC, bool L1>
 __global__ void __launch_bounds__(kFitBlock, fit_min_blocks(PREC)) fit_step_kernel(const ModelConst mc, const FitArgs<typename PrecTraits<PREC>::R> fa,
                                                              const typename PrecTraits<PREC>::R *u_in,
                                                              typename PrecTraits<PREC>::R *u_out,
@@ -381,28 +439,30 @@ __global__ void __launch_bounds__(kFitBlock, fit_min_blocks(PREC)) fit_step_kern
                                                              typename PrecTraits<PREC>::R *m2,
                                                              typename PrecTraits<PREC>::R c1,
                                                              typename PrecTraits<PREC>::R c2) {
-    __shared__ double red[kFitBlock];
+    __shared__ double red[kFitWarps];
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *ytile = reinterpret_cast<float *>(smem_raw);  // [1 or 2][kFitBlock][row_stride]
     if (*fa.stop) return;  // the same for every thread
     model_smem_load<KIND>(mc);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int M = mc.n_meas;
-    const int64_t n = fa.n;
-    const int64_t n_tiles = (n + kFitBlock - 1) / kFitBlock;
-    const int tile_floats = kFitBlock * fa.row_stride;
-    auto stage = [&](int64_t tile, float *dst) {
-        const int64_t base = tile * kFitBlock;
-        const int rows = static_cast<int>(min(static_cast<int64_t>(kFitBlock), n - base));
-        const float *src = fa.data + base * M;
+    const int n = static_cast<int>(fa.n);
+    const int n_tiles = (n + 31) / 32;
+    const int tile_floats = 32 * fa.row_stride;
+    float *wbuf = reinterpret_cast<float *>(smem_raw) + warp * (fa.double_buffer ? 2 : 1) * tile_floats;
+    auto stage = [&](int tile, float *dst) {
+        const int base = tile * 32;
+        const int rows = min(32, n - base);
+        const float *src = fa.data + static_cast<int64_t>(base) * M;
         if (fa.vec4) {  // 16-byte copies; row = floor((e + 1/2) / (M/4)) by one float multiply
             const int M4 = M >> 2, S4 = fa.row_stride >> 2, total4 = rows * M4;
-            for (int e = threadIdx.x; e < total4; e += kFitBlock) {
+            for (int e = lane; e < total4; e += 32) {
                 const int row = static_cast<int>((static_cast<float>(e) + 0.5f) * fa.inv_m4);
                 cp_async16(dst + 4 * (row * S4 + (e - row * M4)), src + 4 * e);
             }
         } else {
             const int total = rows * M;
-            for (int e = threadIdx.x; e < total; e += kFitBlock) {
+            for (int e = lane; e < total; e += 32) {
                 const int row = e / M;
                 cp_async4(dst + row * fa.row_stride + (e - row * M), src + e);
             }
@@ -411,26 +471,27 @@ __global__ void __launch_bounds__(kFitBlock, fit_min_blocks(PREC)) fit_step_kern
     using R = typename PrecTraits<PREC>::R;
     R my_loss = R(0);
     constexpr int P = model_n_par(KIND);
-    int64_t tile = blockIdx.x;
-    if (fa.double_buffer && tile < n_tiles) stage(tile, ytile);
+    const int stride = gridDim.x * kFitWarps;
+    int tile = blockIdx.x * kFitWarps + warp;
+    if (fa.double_buffer && tile < n_tiles) stage(tile, wbuf);
     cp_async_commit();
-    for (int buf = 0; tile < n_tiles; tile += gridDim.x, buf ^= 1) {
-        const float *cur = ytile;
+    for (int buf = 0; tile < n_tiles; tile += stride, buf ^= 1) {
+        const float *cur = wbuf;
         if (fa.double_buffer) {
-            // the other buffer was last read before the barrier that ended the previous tile
-            if (tile + gridDim.x < n_tiles) stage(tile + gridDim.x, ytile + (buf ^ 1) * tile_floats);
+            // the other buffer was last read before the __syncwarp that ended the previous tile
+            if (tile + stride < n_tiles) stage(tile + stride, wbuf + (buf ^ 1) * tile_floats);
             cp_async_commit();
             cp_async_wait<1>();
             cur += buf * tile_floats;
         } else {
-            stage(tile, ytile);
+            stage(tile, wbuf);
             cp_async_commit();
             cp_async_wait<0>();
         }
-        __syncthreads();
-        const int64_t v = tile * kFitBlock + threadIdx.x;
+        __syncwarp();
+        const int v = tile * 32 + lane;
         // the next tile's parameters and Adam moments start on their way to L2
-        const int64_t vn = v + static_cast<int64_t>(gridDim.x) * kFitBlock;
+        const int vn = v + stride * 32;
         if (vn < n) {
 #pragma unroll
             for (int p = 0; p < P; ++p) {
@@ -439,19 +500,23 @@ __global__ void __launch_bounds__(kFitBlock, fit_min_blocks(PREC)) fit_step_kern
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(m2 + p * n + vn));
             }
         }
-        if (v < n)
-            my_loss += fit_voxel<KIND, PREC>(mc, fa, v, cur + threadIdx.x * fa.row_stride, u_in, u_out, m1, m2, c1, c2);
-        __syncthreads();
+        if (v < n) my_loss += fit_voxel<KIND, PREC, L1>(mc, fa, v, cur + lane * fa.row_stride, u_in, u_out, m1, m2, c1, c2);
+        __syncwarp();
     }
     cp_async_wait<0>();
-    // the block's share of the loss, summed in a fixed order
-    red[threadIdx.x] = static_cast<double>(my_loss);
+    // the block's share of the loss, summed in a fixed order: lanes by
+    // shuffles within each warp, then the warps
+    double sum = static_cast<double>(my_loss);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+    if (lane == 0) red[warp] = sum;
     __syncthreads();
-    for (int s = kFitBlock / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int i = 0; i < kFitWarps; ++i) t += red[i];
+        fa.block_loss[blockIdx.x] = t;
     }
-    if (threadIdx.x == 0) fa.block_loss[blockIdx.x] = red[0];
 }
 
 // Sums the block shares (fixed order), records loss t, applies the stopping
@@ -514,35 +579,41 @@ __global__ void u_to_theta_kernel(const ModelConst mc, const R *u, const uint8_t
     }
 }
 
-template <int PREC>
+template <int PREC, bool L1>
 static const void *step_ptr(int kind) {
     switch (kind) {
-    case GAC_MODEL_MONOEXP: return reinterpret_cast<const void *>(&fit_step_kernel<GAC_MODEL_MONOEXP, PREC>);
-    case GAC_MODEL_MWI3: return reinterpret_cast<const void *>(&fit_step_kernel<GAC_MODEL_MWI3, PREC>);
-    case GAC_MODEL_SMT: return reinterpret_cast<const void *>(&fit_step_kernel<GAC_MODEL_SMT, PREC>);
-    default: return reinterpret_cast<const void *>(&fit_step_kernel<GAC_MODEL_LINEAR_TEST, PREC>);
+    case GAC_MODEL_MONOEXP: return reinterpret_cast<const void *>(&fit_step_kernel<GAC_MODEL_MONOEXP, PREC, L1>);
+    case GAC_MODEL_MWI3: return reinterpret_cast<const void *>(&fit_step_kernel<GAC_MODEL_MWI3, PREC, L1>);
+    case GAC_MODEL_SMT: return reinterpret_cast<const void *>(&fit_step_kernel<GAC_MODEL_SMT, PREC, L1>);
+    default: return reinterpret_cast<const void *>(&fit_step_kernel<GAC_MODEL_LINEAR_TEST, PREC, L1>);
     }
 }
 
 template <int KIND, int PREC>
-static cudaError_t launch_step(int grid, size_t smem, cudaStream_t s, const ModelConst &mc,
+static cudaError_t launch_step(bool l1, int grid, size_t smem, cudaStream_t s, const ModelConst &mc,
                                const FitArgs<typename PrecTraits<PREC>::R> &fa, const void *u_in, void *u_out,
                                void *m1, void *m2, double c1, double c2) {
     using R = typename PrecTraits<PREC>::R;
-    fit_step_kernel<KIND, PREC><<<grid, kFitBlock, smem, s>>>(mc, fa, static_cast<const R *>(u_in), static_cast<R *>(u_out),
-                                                           static_cast<R *>(m1), static_cast<R *>(m2), R(c1), R(c2));
+    auto *ui = static_cast<const R *>(u_in);
+    auto *uo = static_cast<R *>(u_out);
+    if (l1)
+        fit_step_kernel<KIND, PREC, true><<<grid, kFitBlock, smem, s>>>(mc, fa, ui, uo, static_cast<R *>(m1),
+                                                                       static_cast<R *>(m2), R(c1), R(c2));
+    else
+        fit_step_kernel<KIND, PREC, false><<<grid, kFitBlock, smem, s>>>(mc, fa, ui, uo, static_cast<R *>(m1),
+                                                                        static_cast<R *>(m2), R(c1), R(c2));
     return cudaGetLastError();
 }
 
 template <int PREC>
-static cudaError_t launch_step_kind(int kind, int grid, size_t smem, cudaStream_t s, const ModelConst &mc,
+static cudaError_t launch_step_kind(int kind, bool l1, int grid, size_t smem, cudaStream_t s, const ModelConst &mc,
                                     const FitArgs<typename PrecTraits<PREC>::R> &fa, const void *u_in, void *u_out,
                                     void *m1, void *m2, double c1, double c2) {
     switch (kind) {
-    case GAC_MODEL_MONOEXP: return launch_step<GAC_MODEL_MONOEXP, PREC>(grid, smem, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
-    case GAC_MODEL_MWI3: return launch_step<GAC_MODEL_MWI3, PREC>(grid, smem, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
-    case GAC_MODEL_SMT: return launch_step<GAC_MODEL_SMT, PREC>(grid, smem, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
-    default: return launch_step<GAC_MODEL_LINEAR_TEST, PREC>(grid, smem, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
+    case GAC_MODEL_MONOEXP: return launch_step<GAC_MODEL_MONOEXP, PREC>(l1, grid, smem, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
+    case GAC_MODEL_MWI3: return launch_step<GAC_MODEL_MWI3, PREC>(l1, grid, smem, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
+    case GAC_MODEL_SMT: return launch_step<GAC_MODEL_SMT, PREC>(l1, grid, smem, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
+    default: return launch_step<GAC_MODEL_LINEAR_TEST, PREC>(l1, grid, smem, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
     }
 }
 
@@ -570,17 +641,18 @@ static gac_status fit_run_prec(const ModelConst &mc, const gac_fit_opts *o, cons
     const size_t tile_bytes = static_cast<size_t>(kFitBlock) * row_stride * sizeof(float);
     const bool dbl = 4 * tile_bytes + 8 * 1024 <= static_cast<size_t>(smem_max);
     const size_t smem = (dbl ? 2 : 1) * tile_bytes;
-    const void *fn = step_ptr<PREC>(mc.kind);
+    const bool l1 = o->loss == GAC_FIT_L1;
+    const void *fn = l1 ? step_ptr<PREC, true>(mc.kind) : step_ptr<PREC, false>(mc.kind);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int per_sm = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFitBlock, smem);
     if (e != cudaSuccess) return cuda_fail(e, "fit kernel attributes");
-    // persistent blocks, each given the same number of tiles (+-1)
-    const int64_t tiles = (N + kFitBlock - 1) / kFitBlock;
-    const int64_t slots = static_cast<int64_t>(sms) * std::max(per_sm, 1);
-    const int64_t per_block = (tiles + slots - 1) / slots;
-    const int grid = static_cast<int>((tiles + per_block - 1) / per_block);
+    // persistent warps, each given the same number of 32-voxel tiles (+-1)
+    const int64_t tiles = (N + 31) / 32;
+    const int64_t slots = static_cast<int64_t>(sms) * std::max(per_sm, 1) * kFitWarps;
+    const int64_t per_warp = (tiles + slots - 1) / slots;
+    const int grid = static_cast<int>((tiles + per_warp * kFitWarps - 1) / (per_warp * kFitWarps));
     // work arrays: u (two buffers), Adam moments, block losses, history, flags
     const int I = o->iterations;
     const size_t bytes_u = static_cast<size_t>(N) * P * RB;
@@ -627,6 +699,9 @@ static gac_status fit_run_prec(const ModelConst &mc, const gac_fit_opts *o, cons
     fa.double_buffer = dbl;
     fa.vec4 = vec4;
     fa.inv_m4 = vec4 ? 1.0f / static_cast<float>(mc.n_meas / 4) : 0.0f;
+    fa.fdiv = N < (int64_t(1) << 24);
+    fa.inv_nx = 1.0f / static_cast<float>(o->nx);
+    fa.inv_ny = 1.0f / static_cast<float>(o->ny);
     // iterations in chunks; the stop flag is read between chunks
     constexpr int kChunk = 64;
     int t = 1;
@@ -640,7 +715,7 @@ static gac_status fit_run_prec(const ModelConst &mc, const gac_fit_opts *o, cons
             }
             const void *ui = (t & 1) ? u0 : u1;
             void *uo = (t & 1) ? u1 : u0;
-            if ((e = launch_step_kind<PREC>(mc.kind, grid, smem, s, mc, fa, ui, uo, m1, m2, c1, c2)) != cudaSuccess)
+            if ((e = launch_step_kind<PREC>(mc.kind, l1, grid, smem, s, mc, fa, ui, uo, m1, m2, c1, c2)) != cudaSuccess)
                 return cuda_fail(e, "fit step");
             fit_check_kernel<<<1, kFitBlock, 0, s>>>(block_loss, grid, t, o->tol, o->convergence_value,
                                                     o->convergence_window, hist, flags, flags + 1);
@@ -698,6 +773,8 @@ extern "C" gac_status gac_fit_run(int model_id, const void *data, const uint8_t 
         return fail(GAC_ERR_INVALID_ARG, "precision must be FP32 or FP64");
     const int64_t N = static_cast<int64_t>(o->nx) * o->ny * o->nz;
     const int M = mc.n_meas;
+    if (N * mc.n_par >= (int64_t(1) << 31))
+        return fail(GAC_ERR_INVALID_ARG, "the fit takes fewer than 2^31 / %d voxels (32-bit indexing)", mc.n_par);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     keep_staging_pool();
     if (o->iterations == 0) {
