@@ -308,7 +308,8 @@ typedef struct {
  *            (voxels outside the mask keep theirs)
  *   loss_history [iterations] double or NULL: the loss of each iteration
  *   *iterations_done: the number of updates taken
- * Synchronous.  Errors: INVALID_ARG, UNKNOWN_MODEL, OOM, CUDA. */
+ * Synchronous.  Errors: INVALID_ARG (also for grids of 2^31 / P voxels or more:
+ * the kernels index [P][N] arrays with 32 bits), UNKNOWN_MODEL, OOM, CUDA. */
 gac_status gac_fit_run(int model_id, const void *data, const uint8_t *mask, const float *weight,
                        const gac_fit_opts *opts, double *theta, double *loss_history, int *iterations_done,
                        void *stream);

@@ -210,6 +210,10 @@ def test_fit_argument_validation(gac):
     with pytest.raises(gac.GacError):  # no analytic gradient for AxCaliberSMT
         ax = gac.gac_model_register(4, [1.0, 13.0, 6.0], [0.2, 0, 0, 0.05], [16, 1, 1, 1.7], [0.1] * 4)
         gac.fit_host(ax, np.zeros((8, 1), np.float32), np.ones((8, 4)), shape=(2, 2, 2))
+    # a grid of 2^31 / P voxels or more is rejected before any buffer is read
+    with pytest.raises(gac.GacError) as e:
+        gac.gac_fit_run(mid, y, None, None, gac.make_fit_opts((1 << 10, 1 << 10, 1 << 10), iterations=1), th)
+    assert e.value.status == 1
     # zero iterations, or an empty mask: nothing to do, no GPU needed
     th2, hist, done = gac.fit_host(mid, y, th, shape=(2, 2, 2), iterations=0)
     assert done == 0 and (th2 == th).all()
