@@ -43,7 +43,7 @@ struct FitArgs {
     R scale;               // 1 / (n_mask M)
     R lambda_n;            // lambda / n_mask
     R lr, beta1, beta2, eps;
-    int row_stride;        // shared-memory floats per staged measurement row (odd; vec4: 4 x odd)
+    int row_stride;        // shared-memory floats per staged measurement row (4 x odd, >= M)
     int double_buffer;     // two staged tiles (the next one copied during the current one) or one
     int vec4;              // rows staged and read as float4 (M % 4 == 0, 16-byte aligned data)
     float inv_m4;          // 1 / (M / 4): row of a tile's float4 number e, exact for e < 2^13
@@ -151,10 +151,11 @@ __device__ __forceinline__ void jacobian(const R *th, const ModelConst &mc, V &&
 // and of t Im(conj(d) u_j) (the frequencies, scaled by A_j 2 pi 1e-3); the
 // two offset pools are carried as lane pairs.  rho and its derivative as in
 // the visitor of fit_voxel: r = w (y - s), L1 |r| with d = -w sign(r), L2
-// r^2 with d = -2 w r.  Adds the gradient to g[9]; returns the data loss.
+// r^2 with d = -2 w r (the weight factored out of the sums).  Adds the
+// gradient to g[9]; returns the data loss.
 template <bool L1>
 __device__ __forceinline__ float mwi3_rec_loss_grad_f(const float *th, const ModelConst &mc, const float *yrow,
-                                                      float wgt, bool vec4, float *g) {
+                                                      float wgt, float *g) {
     const float phi0 = th[8];
     const int n = mc.n_acq;
     // 1 / T2* from the special-function reciprocal and one Newton step (within an ulp)
@@ -183,18 +184,21 @@ __device__ __forceinline__ float mwi3_rec_loss_grad_f(const float *th, const Mod
     // sums over echoes: amplitude terms, t x amplitude terms, t x frequency terms
     float2 G01 = f2(0.0f), T01 = f2(0.0f), C01 = f2(0.0f);
     float G2 = 0.0f, T2 = 0.0f, G8 = 0.0f, loss = 0.0f;
-    // rho'(r) w.r.t. s for r = w (y - s): -w sign(r) (sign(0) = 0) or -2 w r
-    auto deriv = [&](float r) {
-        if constexpr (L1) return r > 0.0f ? -wgt : (r < 0.0f ? wgt : 0.0f);
-        else return -2.0f * wgt * r;
+    // rho'(r) w.r.t. s for r = w e, e = y - s: L1 -w sign(w e) = -|w| sign(e)
+    // (sign(0) = 0), L2 -2 w r = -2 w^2 e; the loss sums |e| or e^2 and takes
+    // the weight's |w| or w^2 once at the end
+    const float aw = fabsf(wgt), k2 = -2.0f * wgt * wgt;
+    auto deriv = [&](float e) {
+        if constexpr (L1) return e > 0.0f ? -aw : (e < 0.0f ? aw : 0.0f);
+        else return k2 * e;
     };
     auto echo = [&](float t, float yr, float yi, float2 x, float2 y, float2 z) {
         const float re = fmaf(a0, x.x, fmaf(a1, x.y, a2 * z.x));
         const float im = fmaf(a0, y.x, fmaf(a1, y.y, a2 * z.y));
-        const float rr = wgt * (yr - re), ri = wgt * (yi - im);
-        const float dr = deriv(rr), di = deriv(ri);
-        if constexpr (L1) loss += fabsf(rr) + fabsf(ri);
-        else loss += fmaf(rr, rr, ri * ri);
+        const float er = yr - re, ei = yi - im;
+        const float dr = deriv(er), di = deriv(ei);
+        if constexpr (L1) loss += fabsf(er) + fabsf(ei);
+        else loss = fmaf(er, er, fmaf(ei, ei, loss));
         const float2 D = f2(dr), E = f2(di);
         const float2 inc = __ffma2_rn(E, y, __fmul2_rn(D, x));                       // Re(conj(d) u), pools 0, 1
         const float2 crs = __ffma2_rn(make_float2(-di, -di), x, __fmul2_rn(D, y));  // Im(conj(d) u)
@@ -207,41 +211,40 @@ __device__ __forceinline__ float mwi3_rec_loss_grad_f(const float *th, const Mod
         T2 = fmaf(t, inc2, T2);
         G8 = fmaf(di, re, fmaf(-dr, im, G8));
     };
-    // one block of echoes a .. a + cnt - 1 from the block's anchors (FULL:
-    // cnt = kAnchor, offsets and times fixed); echo times t0 + k dt
-    auto block = [&](int a, int cnt, auto full) {
-        constexpr bool FULL = decltype(full)::value;
-        float2 x = X, y = Y, z = Z;
-        const float ta = fmaf(static_cast<float>(a), mc.dt_f, mc.t0_f);
-        const float4 *q4 = reinterpret_cast<const float4 *>(yrow) + (a >> 1);
-#pragma unroll
-        for (int i = 0; i < kAnchor; ++i) {
-            if (!FULL && i >= cnt) break;
-            float yr, yi;
-            if (vec4) {  // echoes a + i, a + i + 1 from one 16-byte load (a is even)
-                const float4 q = q4[i >> 1];
-                yr = (i & 1) ? q.z : q.x;
-                yi = (i & 1) ? q.w : q.y;
-            } else {
-                yr = yrow[2 * (a + i)];
-                yi = yrow[2 * (a + i) + 1];
-            }
-            echo(fmaf(static_cast<float>(i), mc.dt_f, ta), yr, yi, x, y, z);
-            const float2 xn = __ffma2_rn(x, RR, __fmul2_rn(y, NRI));
-            y = __ffma2_rn(x, RI, __fmul2_rn(y, RR));
-            x = xn;
-            z = __fmul2_rn(z, R2);
-        }
+    // echoes a + i, a + i + 1 (a even) come in one 16-byte load: rows are
+    // staged at a multiple of four floats, padded past an odd echo count
+    const float4 *q4 = reinterpret_cast<const float4 *>(yrow);
+    auto step = [&](float2 &x, float2 &y, float2 &z) {
+        const float2 xn = __ffma2_rn(x, RR, __fmul2_rn(y, NRI));
+        y = __ffma2_rn(x, RI, __fmul2_rn(y, RR));
+        x = xn;
+        z = __fmul2_rn(z, R2);
     };
     int a = 0;
-    for (; a + kAnchor <= n; a += kAnchor) {
-        block(a, kAnchor, std::true_type{});
+    for (; a + kAnchor <= n; a += kAnchor) {  // full blocks: offsets and times fixed
+        float2 x = X, y = Y, z = Z;
+        const float ta = fmaf(static_cast<float>(a), mc.dt_f, mc.t0_f);
+#pragma unroll
+        for (int i = 0; i < kAnchor; i += 2) {
+            const float4 q = q4[(a + i) >> 1];
+            echo(fmaf(static_cast<float>(i), mc.dt_f, ta), q.x, q.y, x, y, z);
+            step(x, y, z);
+            echo(fmaf(static_cast<float>(i + 1), mc.dt_f, ta), q.z, q.w, x, y, z);
+            step(x, y, z);
+        }
         const float2 xn = __ffma2_rn(X, KR, __fmul2_rn(Y, NKI));
         Y = __ffma2_rn(X, KI, __fmul2_rn(Y, KR));
         X = xn;
         Z = __fmul2_rn(Z, K2);
     }
-    if (a < n) block(a, n - a, std::false_type{});
+    // the last, partial block (not unrolled: it runs once)
+    float2 x = X, y = Y, z = Z;
+#pragma unroll 1
+    for (int k = a; k < n; ++k) {
+        const float4 q = q4[k >> 1];
+        echo(fmaf(static_cast<float>(k), mc.dt_f, mc.t0_f), (k & 1) ? q.z : q.x, (k & 1) ? q.w : q.y, x, y, z);
+        step(x, y, z);
+    }
     g[0] += G01.x;
     g[1] += G01.y;
     g[2] += G2;
@@ -251,15 +254,20 @@ __device__ __forceinline__ float mwi3_rec_loss_grad_f(const float *th, const Mod
     g[6] += a0 * kTwoPiMilli * C01.x;
     g[7] += a1 * kTwoPiMilli * C01.y;
     g[8] += G8;
-    return loss;
+    return L1 ? aw * loss : wgt * wgt * loss;
 }
 
 // One voxel's update: forward model and Jacobian against its staged data row
 // y, the loss gradient, the total-variation subgradient, Adam and the box.
 // Returns the voxel's share of the loss (0 outside the mask).
-template <int KIND, int PREC, bool L1>
+// The voxel's own parameters u, mask flag and weight w arrive from the
+// caller, which loaded them while the previous voxel computed; `next` issues
+// the loads of the lane's next voxel once the model is done.
+template <int KIND, int PREC, bool L1, class N>
 __device__ __forceinline__ typename PrecTraits<PREC>::R fit_voxel(const ModelConst &mc, const FitArgs<typename PrecTraits<PREC>::R> &fa,
-                                            int v, const float *y, const typename PrecTraits<PREC>::R *u_in,
+                                            int v, const float *y, const typename PrecTraits<PREC>::R (&u)[model_n_par(KIND)],
+                                            bool inside, typename PrecTraits<PREC>::R w, N &&next,
+                                            const typename PrecTraits<PREC>::R *u_in,
                                             typename PrecTraits<PREC>::R *u_out, typename PrecTraits<PREC>::R *m1,
                                             typename PrecTraits<PREC>::R *m2, typename PrecTraits<PREC>::R c1,
                                             typename PrecTraits<PREC>::R c2) {
@@ -267,23 +275,16 @@ __device__ __forceinline__ typename PrecTraits<PREC>::R fit_voxel(const ModelCon
     constexpr int P = model_n_par(KIND);
     const int n = static_cast<int>(fa.n);
     R vl = R(0);  // the voxel's loss share (FP32 kernels: FP32; the block sums it in FP64)
-    // Every load the update needs is issued here, before the model's long
-    // arithmetic hides its latency: own parameters and Adam moments, mask and
-    // weight, the usable neighbours (bit 2d: v + e_d, bit 2d + 1: v - e_d;
-    // inside the grid and the mask) and the neighbours' values of the first
-    // penalised map.
-    R u[P], th[P], g[P], mo1[P], mo2[P];
+    // Every other load the update needs is issued here, before the model's
+    // long arithmetic hides its latency: the Adam moments, the usable
+    // neighbours (bit 2d: v + e_d, bit 2d + 1: v - e_d; inside the grid and
+    // the mask) and the neighbours' values of the first penalised map.
+    R th[P], g[P], mo1[P], mo2[P];
 #pragma unroll
-    for (int p = 0; p < P; ++p) u[p] = u_in[p * n + v];
-    const bool inside = !fa.mask || fa.mask[v];
-    if (inside) {
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            mo1[p] = m1[p * n + v];
-            mo2[p] = m2[p * n + v];
-        }
+    for (int p = 0; p < P; ++p) {
+        mo1[p] = m1[p * n + v];
+        mo2[p] = m2[p * n + v];
     }
-    const R w = fa.weight ? R(fa.weight[v]) : R(1);
     const bool tv_on = fa.tv_params && fa.lambda_n != R(0);
     const int step[3] = {1, fa.nx, fa.nx * fa.ny};
     unsigned grid_bit = 0, nbit = 0;  // neighbours inside the grid; inside the grid and the mask
@@ -323,6 +324,7 @@ __device__ __forceinline__ typename PrecTraits<PREC>::R fit_voxel(const ModelCon
         }
     }
     if (!inside) {
+        next();
 #pragma unroll
         for (int p = 0; p < P; ++p) u_out[p * n + v] = u[p];
         return R(0);
@@ -350,11 +352,12 @@ __device__ __forceinline__ typename PrecTraits<PREC>::R fit_voxel(const ModelCon
         for (int p = 0; p < P; ++p) g[p] = fma(d, J[p], g[p]);
     };
     if constexpr (KIND == GAC_MODEL_MWI3 && PREC == GAC_PREC_FP32) {
-        if (mc.even) loss = mwi3_rec_loss_grad_f<L1>(th, mc, y, w, fa.vec4, g);  // same branch for every thread
+        if (mc.even) loss = mwi3_rec_loss_grad_f<L1>(th, mc, y, w, g);  // same branch for every thread
         else jacobian<KIND, R>(th, mc, visit);
     } else {
         jacobian<KIND, R>(th, mc, visit);
     }
+    next();
     vl += loss * fa.scale;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
@@ -473,6 +476,20 @@ __global__ void __launch_bounds__(kFitBlock, fit_min_blocks(PREC)) fit_step_kern
     constexpr int P = model_n_par(KIND);
     const int stride = gridDim.x * kFitWarps;
     int tile = blockIdx.x * kFitWarps + warp;
+    // the lane's next voxel: parameters, mask flag and weight, loaded one
+    // voxel ahead
+    R un[P];
+    bool in_n = true;
+    R w_n = R(1);
+    auto load_next = [&](int vv) {
+        if (vv < n) {
+#pragma unroll
+            for (int p = 0; p < P; ++p) un[p] = u_in[p * n + vv];
+            in_n = !fa.mask || fa.mask[vv];
+            w_n = fa.weight ? R(fa.weight[vv]) : R(1);
+        }
+    };
+    load_next(tile * 32 + lane);
     if (fa.double_buffer && tile < n_tiles) stage(tile, wbuf);
     cp_async_commit();
     for (int buf = 0; tile < n_tiles; tile += stride, buf ^= 1) {
@@ -490,17 +507,14 @@ __global__ void __launch_bounds__(kFitBlock, fit_min_blocks(PREC)) fit_step_kern
         }
         __syncwarp();
         const int v = tile * 32 + lane;
-        // the next tile's parameters and Adam moments start on their way to L2
-        const int vn = v + stride * 32;
-        if (vn < n) {
+        R u[P];
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(u_in + p * n + vn));
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(m1 + p * n + vn));
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(m2 + p * n + vn));
-            }
-        }
-        if (v < n) my_loss += fit_voxel<KIND, PREC, L1>(mc, fa, v, cur + lane * fa.row_stride, u_in, u_out, m1, m2, c1, c2);
+        for (int p = 0; p < P; ++p) u[p] = un[p];
+        const bool inside = in_n;
+        const R w = w_n;
+        auto next = [&]() { load_next(v + stride * 32); };
+        if (v < n) my_loss += fit_voxel<KIND, PREC, L1>(mc, fa, v, cur + lane * fa.row_stride, u, inside, w, next, u_in,
+                                                        u_out, m1, m2, c1, c2);
         __syncwarp();
     }
     cp_async_wait<0>();
@@ -633,11 +647,11 @@ static gac_status fit_run_prec(const ModelConst &mc, const gac_fit_opts *o, cons
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    // rows at an odd stride, so that a warp's voxels fall into distinct banks:
-    // odd in floats (4-byte staging and reads), or in float4s (16-byte
-    // staging and reads) when rows are whole float4s and the data is aligned
+    // rows at an odd number of float4s (padded up), so that a warp's 16-byte
+    // reads of one column fall into distinct banks; staged by 16-byte copies
+    // when rows are whole float4s and the data is aligned, else by 4-byte ones
     const bool vec4 = mc.n_meas % 4 == 0 && (reinterpret_cast<uintptr_t>(d_data) & 15) == 0;
-    const int row_stride = vec4 ? 4 * ((mc.n_meas / 4) | 1) : (mc.n_meas | 1);
+    const int row_stride = 4 * (((mc.n_meas + 3) / 4) | 1);
     const size_t tile_bytes = static_cast<size_t>(kFitBlock) * row_stride * sizeof(float);
     const bool dbl = 4 * tile_bytes + 8 * 1024 <= static_cast<size_t>(smem_max);
     const size_t smem = (dbl ? 2 : 1) * tile_bytes;
