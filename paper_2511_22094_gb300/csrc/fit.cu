@@ -290,6 +290,7 @@ __device__ __forceinline__ typename PrecTraits<PREC>::R fit_voxel(const ModelCon
     unsigned grid_bit = 0, nbit = 0;  // neighbours inside the grid; inside the grid and the mask
     int p0 = P;                       // first penalised map (P: none)
     R nb0[6];
+    uint8_t nmask[6];
     auto offset = [&](int j) { return ((grid_bit >> j) & 1u) ? ((j & 1) ? -step[j >> 1] : step[j >> 1]) : 0; };
     if (tv_on) {
         const unsigned vu = static_cast<unsigned>(v), nxu = static_cast<unsigned>(fa.nx), nyu = static_cast<unsigned>(fa.ny);
@@ -311,11 +312,12 @@ __device__ __forceinline__ typename PrecTraits<PREC>::R fit_voxel(const ModelCon
             grid_bit |= static_cast<unsigned>(use && coord[d] + 1 < ext[d]) << (2 * d) |
                         static_cast<unsigned>(use && coord[d] > 0) << (2 * d + 1);
         }
-        // the mask loads and the neighbour values do not wait on each other
+        // the neighbours' mask bytes and values load here and are used after
+        // the model (nothing waits on them before it)
         nbit = grid_bit;
         if (fa.mask) {
 #pragma unroll
-            for (int j = 0; j < 6; ++j) nbit &= ~(static_cast<unsigned>(fa.mask[v + offset(j)] == 0) << j);
+            for (int j = 0; j < 6; ++j) nmask[j] = fa.mask[v + offset(j)];
         }
         p0 = __ffs(fa.tv_params) - 1;
         if (p0 < P) {
@@ -366,6 +368,10 @@ __device__ __forceinline__ typename PrecTraits<PREC>::R fit_voxel(const ModelCon
     }
     // total variation: pairs (v - e_d, v) and (v, v + e_d) of masked neighbours
     if (tv_on) {
+        if (fa.mask) {
+#pragma unroll
+            for (int j = 0; j < 6; ++j) nbit &= ~(static_cast<unsigned>(nmask[j] == 0) << j);
+        }
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             if (!((fa.tv_params >> p) & 1u)) continue;
