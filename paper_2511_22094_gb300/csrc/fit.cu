@@ -1,16 +1,15 @@
 // Whole-volume gradient fit (askadam.m, Sec. 2.2.1; Eq. 2, 4, 5): Adam on
 // the L1 or L2 data loss over a masked voxel grid, with an optional total-
 // variation penalty on chosen parameter maps.  One launch per iteration:
-//   fit_step_kernel   every voxel (one thread each, grid-stride): forward
-//                     model and its analytic Jacobian, the data loss and its
-//                     gradient, the total-variation subgradient from the six
-//                     (or four) neighbours' current parameters, and the Adam
-//                     update into the other parameter buffer; each block
-//                     writes its share of the loss;
-//   fit_check_kernel  one block sums the block shares in a fixed order,
-//                     records the iteration's loss and applies the stopping
-//                     rules; once it sets the stop flag, later launches return
-//                     at once.
+//   fit_step_kernel   every voxel (one thread each): forward model and its
+//                     analytic Jacobian, the data loss and its gradient, the
+//                     total-variation subgradient from the six (or four)
+//                     neighbours' current parameters, and the Adam update
+//                     into the other parameter buffer; each block writes its
+//                     share of the loss, and the last block to finish sums
+//                     the shares in a fixed order, records the iteration's
+//                     loss and applies the stopping rules; once it sets the
+//                     stop flag, later launches return at once.
 // Parameters are optimised in normalised form u = (theta - lb) / (ub - lb),
 // clamped to [0, 1] after each update, stored [P][N] (structure of arrays).
 #include <cuda_runtime.h>
@@ -49,7 +48,12 @@ struct FitArgs {
     float inv_m4;          // 1 / (M / 4): row of a tile's float4 number e, exact for e < 2^13
     int fdiv;              // n < 2^24: grid coordinates by float reciprocals (udiv_f)
     float inv_nx, inv_ny;  // 1 / nx, 1 / ny rounded to float
-    const int *stop;       // set by fit_check_kernel
+    int *stop;             // set by the last block of the iteration that stops
+    int *done;             // updates taken
+    unsigned *arrive;      // blocks of the current launch that have finished (reset by the last)
+    double *hist;          // [iterations] loss history
+    double tol, conv_value;
+    int window;
     double *block_loss;    // [gridDim.x]
 };
 
@@ -447,8 +451,9 @@ __global__ void __launch_bounds__(kFitBlock, fit_min_blocks(PREC)) fit_step_kern
                                                              typename PrecTraits<PREC>::R *m1,
                                                              typename PrecTraits<PREC>::R *m2,
                                                              typename PrecTraits<PREC>::R c1,
-                                                             typename PrecTraits<PREC>::R c2) {
-    __shared__ double red[kFitWarps];
+                                                             typename PrecTraits<PREC>::R c2, int t_iter) {
+    __shared__ double red[kFitBlock];
+    __shared__ bool last;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (*fa.stop) return;  // the same for every thread
     model_smem_load<KIND>(mc);
@@ -536,18 +541,25 @@ __global__ void __launch_bounds__(kFitBlock, fit_min_blocks(PREC)) fit_step_kern
 #pragma unroll
         for (int i = 0; i < kFitWarps; ++i) t += red[i];
         fa.block_loss[blockIdx.x] = t;
+        __threadfence();  // the share is visible before the count says so
+        last = atomicAdd(fa.arrive, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {  // every other block's share has landed
+        __threadfence();
+        fit_check(fa, gridDim.x, t_iter, red);
+        if (threadIdx.x == 0) *fa.arrive = 0u;  // for the next launch, which starts after this one ends
     }
 }
 
-// Sums the block shares (fixed order), records loss t, applies the stopping
-// rules: loss < tol, or |least-squares slope of the last `window` losses| <
-// conv_value.
-__global__ void fit_check_kernel(const double *block_loss, int n_blocks, int t, double tol, double conv_value,
-                                 int window, double *hist, int *stop, int *done) {
-    __shared__ double red[kFitBlock];
-    if (*stop) return;
+// Run by the last block of iteration t: sums the block shares (fixed order:
+// thread i the shares i, i + 256, ..., then a tree), records loss t and
+// applies the stopping rules: loss < tol, or |least-squares slope of the
+// last `window` losses| < conv_value.
+template <class FA>
+__device__ void fit_check(const FA &fa, int n_blocks, int t, double *red) {
     double s = 0.0;
-    for (int i = threadIdx.x; i < n_blocks; i += blockDim.x) s += block_loss[i];
+    for (int i = threadIdx.x; i < n_blocks; i += blockDim.x) s += __ldcg(fa.block_loss + i);
     red[threadIdx.x] = s;
     __syncthreads();
     for (int k = kFitBlock / 2; k > 0; k >>= 1) {
@@ -556,11 +568,12 @@ __global__ void fit_check_kernel(const double *block_loss, int n_blocks, int t, 
     }
     if (threadIdx.x != 0) return;
     const double loss = red[0];
-    hist[t - 1] = loss;
-    *done = t;
-    bool halt = tol > 0.0 && loss < tol;
-    if (!halt && conv_value > 0.0 && window > 1 && t >= window) {
-        const double *yv = hist + t - window;
+    fa.hist[t - 1] = loss;
+    *fa.done = t;
+    bool halt = fa.tol > 0.0 && loss < fa.tol;
+    const int window = fa.window;
+    if (!halt && fa.conv_value > 0.0 && window > 1 && t >= window) {
+        const double *yv = fa.hist + t - window;
         const double xm = 0.5 * (window - 1);
         double ym = 0.0, sxy = 0.0, sxx = 0.0;
         for (int i = 0; i < window; ++i) ym += yv[i];
@@ -569,9 +582,27 @@ __global__ void fit_check_kernel(const double *block_loss, int n_blocks, int t, 
             sxy += (i - xm) * (yv[i] - ym);
             sxx += (i - xm) * (i - xm);
         }
-        halt = fabs(sxy / sxx) < conv_value;
+        halt = fabs(sxy / sxx) < fa.conv_value;
     }
-    if (halt) *stop = 1;
+    if (halt) *fa.stop = 1;
+}
+
+// The number of non-zero mask bytes (one atomic add per block).
+__global__ void count_mask_kernel(const uint8_t *mask, int64_t n, unsigned long long *count) {
+    __shared__ unsigned part[8];
+    unsigned c = 0;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        c += mask[i] != 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += part[w];
+        atomicAdd(count, t);
+    }
 }
 
 // theta [N][P] (double) <-> u [P][N]; outside the mask theta is left alone.
@@ -612,28 +643,28 @@ static const void *step_ptr(int kind) {
 template <int KIND, int PREC>
 static cudaError_t launch_step(bool l1, int grid, size_t smem, cudaStream_t s, const ModelConst &mc,
                                const FitArgs<typename PrecTraits<PREC>::R> &fa, const void *u_in, void *u_out,
-                               void *m1, void *m2, double c1, double c2) {
+                               void *m1, void *m2, double c1, double c2, int t) {
     using R = typename PrecTraits<PREC>::R;
     auto *ui = static_cast<const R *>(u_in);
     auto *uo = static_cast<R *>(u_out);
     if (l1)
         fit_step_kernel<KIND, PREC, true><<<grid, kFitBlock, smem, s>>>(mc, fa, ui, uo, static_cast<R *>(m1),
-                                                                       static_cast<R *>(m2), R(c1), R(c2));
+                                                                       static_cast<R *>(m2), R(c1), R(c2), t);
     else
         fit_step_kernel<KIND, PREC, false><<<grid, kFitBlock, smem, s>>>(mc, fa, ui, uo, static_cast<R *>(m1),
-                                                                        static_cast<R *>(m2), R(c1), R(c2));
+                                                                        static_cast<R *>(m2), R(c1), R(c2), t);
     return cudaGetLastError();
 }
 
 template <int PREC>
 static cudaError_t launch_step_kind(int kind, bool l1, int grid, size_t smem, cudaStream_t s, const ModelConst &mc,
                                     const FitArgs<typename PrecTraits<PREC>::R> &fa, const void *u_in, void *u_out,
-                                    void *m1, void *m2, double c1, double c2) {
+                                    void *m1, void *m2, double c1, double c2, int t) {
     switch (kind) {
-    case GAC_MODEL_MONOEXP: return launch_step<GAC_MODEL_MONOEXP, PREC>(l1, grid, smem, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
-    case GAC_MODEL_MWI3: return launch_step<GAC_MODEL_MWI3, PREC>(l1, grid, smem, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
-    case GAC_MODEL_SMT: return launch_step<GAC_MODEL_SMT, PREC>(l1, grid, smem, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
-    default: return launch_step<GAC_MODEL_LINEAR_TEST, PREC>(l1, grid, smem, s, mc, fa, u_in, u_out, m1, m2, c1, c2);
+    case GAC_MODEL_MONOEXP: return launch_step<GAC_MODEL_MONOEXP, PREC>(l1, grid, smem, s, mc, fa, u_in, u_out, m1, m2, c1, c2, t);
+    case GAC_MODEL_MWI3: return launch_step<GAC_MODEL_MWI3, PREC>(l1, grid, smem, s, mc, fa, u_in, u_out, m1, m2, c1, c2, t);
+    case GAC_MODEL_SMT: return launch_step<GAC_MODEL_SMT, PREC>(l1, grid, smem, s, mc, fa, u_in, u_out, m1, m2, c1, c2, t);
+    default: return launch_step<GAC_MODEL_LINEAR_TEST, PREC>(l1, grid, smem, s, mc, fa, u_in, u_out, m1, m2, c1, c2, t);
     }
 }
 
@@ -676,7 +707,7 @@ static gac_status fit_run_prec(const ModelConst &mc, const gac_fit_opts *o, cons
     // work arrays: u (two buffers), Adam moments, block losses, history, flags
     const int I = o->iterations;
     const size_t bytes_u = static_cast<size_t>(N) * P * RB;
-    const size_t total = 4 * bytes_u + grid * sizeof(double) + static_cast<size_t>(std::max(I, 1)) * sizeof(double) + 2 * sizeof(int);
+    const size_t total = 4 * bytes_u + grid * sizeof(double) + static_cast<size_t>(std::max(I, 1)) * sizeof(double) + 3 * sizeof(int);
     void *base = nullptr;
     e = cudaMallocAsync(&base, total, s);
     if (e != cudaSuccess) return cuda_fail(e, "fit work arrays");
@@ -689,9 +720,9 @@ static gac_status fit_run_prec(const ModelConst &mc, const gac_fit_opts *o, cons
     void *u0 = b, *u1 = b + bytes_u, *m1 = b + 2 * bytes_u, *m2 = b + 3 * bytes_u;
     double *block_loss = reinterpret_cast<double *>(b + 4 * bytes_u);
     double *hist = block_loss + grid;
-    int *flags = reinterpret_cast<int *>(hist + std::max(I, 1));  // stop, done
+    int *flags = reinterpret_cast<int *>(hist + std::max(I, 1));  // stop, done, arrival count
     if ((e = cudaMemsetAsync(m1, 0, 2 * bytes_u, s)) != cudaSuccess) return cuda_fail(e, "fit memset");
-    if ((e = cudaMemsetAsync(flags, 0, 2 * sizeof(int), s)) != cudaSuccess) return cuda_fail(e, "fit memset");
+    if ((e = cudaMemsetAsync(flags, 0, 3 * sizeof(int), s)) != cudaSuccess) return cuda_fail(e, "fit memset");
     const int conv_grid = static_cast<int>(std::min<int64_t>((N * P + 255) / 256, static_cast<int64_t>(sms) * 8));
     theta_to_u_kernel<R><<<conv_grid, 256, 0, s>>>(mc, static_cast<const double *>(d_theta.ptr), N, static_cast<R *>(u0));
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "theta to u");
@@ -714,6 +745,12 @@ static gac_status fit_run_prec(const ModelConst &mc, const gac_fit_opts *o, cons
     fa.beta2 = static_cast<R>(o->beta2);
     fa.eps = static_cast<R>(o->epsilon);
     fa.stop = flags;
+    fa.done = flags + 1;
+    fa.arrive = reinterpret_cast<unsigned *>(flags + 2);
+    fa.hist = hist;
+    fa.tol = o->tol;
+    fa.conv_value = o->convergence_value;
+    fa.window = o->convergence_window;
     fa.block_loss = block_loss;
     fa.row_stride = row_stride;
     fa.double_buffer = dbl;
@@ -735,11 +772,8 @@ static gac_status fit_run_prec(const ModelConst &mc, const gac_fit_opts *o, cons
             }
             const void *ui = (t & 1) ? u0 : u1;
             void *uo = (t & 1) ? u1 : u0;
-            if ((e = launch_step_kind<PREC>(mc.kind, l1, grid, smem, s, mc, fa, ui, uo, m1, m2, c1, c2)) != cudaSuccess)
+            if ((e = launch_step_kind<PREC>(mc.kind, l1, grid, smem, s, mc, fa, ui, uo, m1, m2, c1, c2, t)) != cudaSuccess)
                 return cuda_fail(e, "fit step");
-            fit_check_kernel<<<1, kFitBlock, 0, s>>>(block_loss, grid, t, o->tol, o->convergence_value,
-                                                    o->convergence_window, hist, flags, flags + 1);
-            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "fit check");
         }
         int stop = 0;
         if ((e = cudaMemcpyAsync(&stop, flags, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
@@ -801,19 +835,33 @@ extern "C" gac_status gac_fit_run(int model_id, const void *data, const uint8_t 
         if (iterations_done) *iterations_done = 0;
         return GAC_OK;
     }
-    // the mask count, from the caller's buffer (host or device)
-    std::vector<uint8_t> mk;
+    // the mask count, from the caller's buffer: counted in place (host), or
+    // on the device with only the count read back
     int64_t n_mask = N;
     if (mask) {
-        mk.resize(N);
         if (is_device_ptr(mask)) {
-            cudaError_t e = cudaMemcpy(mk.data(), mask, N, cudaMemcpyDeviceToHost);
-            if (e != cudaSuccess) return cuda_fail(e, "mask");
+            unsigned long long *d_count = nullptr, h_count = 0;
+            cudaError_t e = cudaMallocAsync(&d_count, sizeof *d_count, s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(d_count, 0, sizeof *d_count, s);
+            if (e == cudaSuccess) {
+                int dev = 0, sms = 0;
+                e = cudaGetDevice(&dev);
+                if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+                if (e == cudaSuccess) {
+                    const int g = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, int64_t(sms) * 4)));
+                    count_mask_kernel<<<g, 256, 0, s>>>(mask, N, d_count);
+                    e = cudaGetLastError();
+                }
+            }
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&h_count, d_count, sizeof h_count, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (d_count) cudaFreeAsync(d_count, s);
+            if (e != cudaSuccess) return cuda_fail(e, "mask count");
+            n_mask = static_cast<int64_t>(h_count);
         } else {
-            std::memcpy(mk.data(), mask, N);
+            n_mask = 0;
+            for (int64_t i = 0; i < N; ++i) n_mask += mask[i] != 0;
         }
-        n_mask = 0;
-        for (uint8_t x : mk) n_mask += x != 0;
     }
     if (n_mask == 0) {
         if (iterations_done) *iterations_done = 0;
