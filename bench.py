@@ -341,6 +341,10 @@ def run_oracle_study(args):
 
 FIT_METRIC = "whole-volume fit voxel-iterations/s"
 FIT_UNIT = "voxel-iter/s"
+# Algorithmic bytes of one voxel-update of the 3-pool fit: data row 48 x 4,
+# parameters in and out 2 x 9 x 4, Adam moments in and out 4 x 9 x 4, mask 1,
+# weight 4
+FIT_BYTES = 48 * 4 + 2 * 9 * 4 + 4 * 9 * 4 + 1 + 4
 # Direct-form counts per voxel-iteration of the 3-pool fit (24 echoes x 3
 # pools: exp, sin, cos and 18 Jacobian entries per echo; Adam on 9 parameters)
 FIT_OPS = dict(mufu=24 * 3 * 3, fp32=24 * (3 * 14 + 2 * 9 * 2) + 9 * 12)
@@ -435,17 +439,24 @@ def run_fit(args):
     fp32_clk = rates["ffma"] if rates else FP32_PER_CLK_SM
     peak = sms * fp32_clk * f_max / 1e9
     achieved = FIT_OPS["fp32"] * vi_s / 1e9
+    hbm = _peaks().get("hbm_gbs")
+    hbm_peak, hbm_basis = (hbm, "measured copy bandwidth") if hbm else (6800.0, "fallback")
+    ach_gbs = FIT_BYTES * vi_s / 1e9
     line = {"metric": FIT_METRIC, "value": value, "unit": FIT_UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "mwi3_1m as a 100^3 grid", "loss": "L1", "optimiser": "Adam lr 0.01",
                        "tv": "3D, A_MW, lambda 1e-3", "mask": "inner 98^3", "iterations_per_step": it,
                        "updates_done": done},
-            "roofline": {"bound": "alu", "pipe": "fp32", "count": "direct-form", "achieved": achieved,
-                         "peak": peak, "unit": "Gop/s", "frac": achieved / peak, "traffic": None,
-                         "peak_basis": f"{sms} SMs x {fp32_clk:.2f}/clk ("
-                                       f"{'measured by the pipe-rate probe' if rates else 'data sheet'}) x "
-                                       f"{f_max / 1e6:.0f} MHz (max SM clock)"},
+            "roofline": {"bound": "hbm", "achieved": ach_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": ach_gbs / hbm_peak, "traffic": None, "peak_basis": hbm_basis,
+                         "bytes_per_unit": FIT_BYTES,
+                         "direct_form_equivalent": {
+                             "pipe": "fp32", "count": "direct-form", "achieved": achieved, "peak": peak,
+                             "unit": "Gop/s", "ratio": achieved / peak,
+                             "peak_basis": f"{sms} SMs x {fp32_clk:.2f}/clk ("
+                                           f"{'measured by the pipe-rate probe' if rates else 'data sheet'}) x "
+                                           f"{f_max / 1e6:.0f} MHz (max SM clock)"}},
             "pipe_rates_per_sm_clk": rates,
             "e2e": {"value": vi / e2e_s, "unit": FIT_UNIT, "h2d_bytes_per_step": y.numel() * 4 + N * (1 + 4 + 8 * P),
                     "d2h_bytes_per_step": N * 8 * P + it * 8},
