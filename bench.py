@@ -95,21 +95,22 @@ def _alu_peaks(mix: dict, rates):
 # code: comments and layout aside) hash to the value they were measured with
 # (otherwise null).
 KERNEL_SOURCES = ("include/gac.h", "paper_2511_22094_gb300/csrc/mh_kernel.cuh",
-                  "paper_2511_22094_gb300/csrc/mh_split.cuh", "paper_2511_22094_gb300/csrc/models.cuh",
-                  "paper_2511_22094_gb300/csrc/philox.cuh")
-KIND_SOURCE = {"mwi3_1m": "mh_mwi3.cu", "smt_1p5m": "mh_smt.cu", "monoexp_4k": "mh_monoexp.cu",
-               "axcal_250k": "mh_axcal.cu"}
+                  "paper_2511_22094_gb300/csrc/models.cuh", "paper_2511_22094_gb300/csrc/philox.cuh")
+# the measured kernel's own file; the lane-split kernel (the 4,096-voxel
+# workload's) also depends on mh_split.cuh, the one-thread kernel does not
+KIND_SOURCE = {"mwi3_1m": ("mh_mwi3.cu",), "smt_1p5m": ("mh_smt.cu",),
+               "monoexp_4k": ("mh_monoexp.cu", "mh_split.cuh"), "axcal_250k": ("mh_axcal.cu",)}
 MEASURED = {
     # traffic: DRAM bytes of a quarter-size launch (262,144 / 393,216 / 65,536
     # voxels, all iterations, so every term scales with the voxels) x 3.81;
     # the lines still in L2 when the small launch ends are not counted
     # (~1-3% of its writes).  warp_instr: from the small-case --set full captures.
-    "mwi3_1m": dict(sources="8b352975cdad8812", traffic_bytes=(78.07e6 + 1696.83e6) * 1e6 / 262144, warp_instr=918.8),
-    "smt_1p5m": dict(sources="6aa13ef41a5a4ef2", traffic_bytes=(32.19e6 + 1120.72e6) * 1.5e6 / 393216, warp_instr=495.2),
-    "axcal_250k": dict(sources="b905d93628b32296", traffic_bytes=(37.59e6 + 910.33e6) * 250000 / 65536, warp_instr=1215.1),
+    "mwi3_1m": dict(sources="a8792946f2bdfa8f", traffic_bytes=(78.07e6 + 1696.83e6) * 1e6 / 262144, warp_instr=918.8),
+    "smt_1p5m": dict(sources="559b4e0b19e2b689", traffic_bytes=(32.19e6 + 1120.72e6) * 1.5e6 / 393216, warp_instr=495.2),
+    "axcal_250k": dict(sources="493f595b548eebc5", traffic_bytes=(37.59e6 + 910.33e6) * 250000 / 65536, warp_instr=1215.1),
     # the lane-split kernel (2 lanes a chain): the 4,096-voxel workload's data
     # and samples stay in L2, so no DRAM figure
-    "monoexp_4k": dict(sources="4ad3763a92ec82bb", traffic_bytes=None, warp_instr=377.2),
+    "monoexp_4k": dict(sources="4a349ced4e667773", traffic_bytes=None, warp_instr=377.2),
 }
 
 
@@ -125,7 +126,7 @@ def _code_only(text: str) -> str:
 
 def _sources_hash(workload: str) -> str:
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES + ("paper_2511_22094_gb300/csrc/" + KIND_SOURCE[workload],):
+    for rel in KERNEL_SOURCES + tuple("paper_2511_22094_gb300/csrc/" + f for f in KIND_SOURCE[workload]):
         with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
             h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]

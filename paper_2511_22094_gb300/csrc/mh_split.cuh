@@ -391,7 +391,10 @@ __device__ __forceinline__ void run_tile_split(const ModelConst &mc, const RunAr
                 const bool near = !(fabsf(gap) > margin);
                 n_bad += !isfinite(Lp);
                 // the FP32 decision takes effect at once; the rare branch below
-                // corrects it where the FP64 re-decision differs
+                // corrects it where the FP64 re-decision differs.  Only the
+                // lanes with a near decision enter it between events (it holds
+                // no warp-wide operation); at a thinning or adaptation event
+                // every lane does
                 float th_old[P];
                 const float L_old = L;
 #pragma unroll
@@ -401,7 +404,7 @@ __device__ __forceinline__ void run_tile_split(const ModelConst &mc, const RunAr
                 }
                 L = acc ? Lp : L;
                 n_acc += acc ? 1 : 0;
-                if (__builtin_expect(__any_sync(kFullMask, near) || t == t_event, 0)) {
+                if (__builtin_expect(near || t == t_event, 0)) {
                     if (near) {
                         const bool acc64 = log(u01_d(w_acc)) < static_cast<double>(Lp) - static_cast<double>(L_old);
                         if (acc64 != acc) {
