@@ -193,7 +193,7 @@ __device__ __forceinline__ float mwi3_rec_loss_grad_f(const float *th, const Mod
     // the weight's |w| or w^2 once at the end
     const float aw = fabsf(wgt), k2 = -2.0f * wgt * wgt;
     auto deriv = [&](float e) {
-        if constexpr (L1) return e > 0.0f ? -aw : (e < 0.0f ? aw : 0.0f);
+        if constexpr (L1) return e != 0.0f ? copysignf(aw, -e) : 0.0f;
         else return k2 * e;
     };
     auto echo = [&](float t, float yr, float yi, float2 x, float2 y, float2 z) {
@@ -470,6 +470,7 @@ __global__ void __launch_bounds__(kFitBlock, fit_min_blocks(PREC)) fit_step_kern
         const float *src = fa.data + static_cast<int64_t>(base) * M;
         if (fa.vec4) {  // 16-byte copies; row = floor((e + 1/2) / (M/4)) by one float multiply
             const int M4 = M >> 2, S4 = fa.row_stride >> 2, total4 = rows * M4;
+#pragma unroll 4
             for (int e = lane; e < total4; e += 32) {
                 const int row = static_cast<int>((static_cast<float>(e) + 0.5f) * fa.inv_m4);
                 cp_async16(dst + 4 * (row * S4 + (e - row * M4)), src + 4 * e);
