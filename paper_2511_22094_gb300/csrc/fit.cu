@@ -57,9 +57,10 @@ struct FitArgs {
     double *block_loss;    // [gridDim.x]
 };
 
+// sign(x) with sign(0) = 0, branch-free (a select and a sign-bit copy)
 template <class R>
 __device__ __forceinline__ R sgn(R x) {
-    return x > R(0) ? R(1) : (x < R(0) ? R(-1) : R(0));
+    return x != R(0) ? copysign(R(1), x) : R(0);
 }
 
 // a / b and a % b for a < 2^24 from the float reciprocal inv_b = fl(1 / b):
@@ -438,9 +439,9 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // memory: the next tile's rows are copied into the second of two buffers
 // while the current tile computes, and only the warp waits for them, so warps
 // drift apart and hide each other's memory latency instead of meeting at a
-// block barrier every tile.  Rows sit at an odd stride (in floats, or in
-// float4s for 16-byte copies) so that a warp's reads of one column hit
-// distinct banks.  FP32 kernels keep two blocks (16 warps) on an SM.
+// block barrier every tile.  Rows sit at an odd number of float4s, so that
+// a warp's 16-byte reads of one echo pair hit distinct banks.  FP32 kernels
+// keep two blocks (16 warps) on an SM.
 constexpr int kFitWarps = kFitBlock / 32;
 constexpr int fit_min_blocks(int prec) { return prec == GAC_PREC_FP32 ? 2 : 1; }
 
