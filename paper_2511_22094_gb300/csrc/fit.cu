@@ -26,7 +26,8 @@
 
 namespace gac {
 
-constexpr int kFitBlock = 256;
+constexpr int kFitBlock = 128;
+constexpr int kFitMinBlocks32 = 5;  // FP32: 20 warps an SM (registers <= 102)
 constexpr int kFitMaxWindow = 4096;
 
 template <class R>
@@ -43,7 +44,6 @@ struct FitArgs {
     R lambda_n;            // lambda / n_mask
     R lr, beta1, beta2, eps;
     int row_stride;        // shared-memory floats per staged measurement row (4 x odd, >= M)
-    int double_buffer;     // two staged tiles (the next one copied during the current one) or one
     int vec4;              // rows staged and read as float4 (M % 4 == 0, 16-byte aligned data)
     float inv_m4;          // 1 / (M / 4): row of a tile's float4 number e, exact for e < 2^13
     int fdiv;              // n < 2^24: grid coordinates by float reciprocals (udiv_f)
@@ -265,39 +265,38 @@ __device__ __forceinline__ float mwi3_rec_loss_grad_f(const float *th, const Mod
 // One voxel's update: forward model and Jacobian against its staged data row
 // y, the loss gradient, the total-variation subgradient, Adam and the box.
 // Returns the voxel's share of the loss (0 outside the mask).
-// The voxel's own parameters u, mask flag and weight w arrive from the
-// caller, which loaded them while the previous voxel computed; `next` issues
-// the loads of the lane's next voxel once the model is done.
-template <int KIND, int PREC, bool L1, class N>
-__device__ __forceinline__ typename PrecTraits<PREC>::R fit_voxel(const ModelConst &mc, const FitArgs<typename PrecTraits<PREC>::R> &fa,
-                                            int v, const float *y, const typename PrecTraits<PREC>::R (&u)[model_n_par(KIND)],
-                                            bool inside, typename PrecTraits<PREC>::R w, N &&next,
-                                            const typename PrecTraits<PREC>::R *u_in,
-                                            typename PrecTraits<PREC>::R *u_out, typename PrecTraits<PREC>::R *m1,
-                                            typename PrecTraits<PREC>::R *m2, typename PrecTraits<PREC>::R c1,
-                                            typename PrecTraits<PREC>::R c2) {
+// One voxel's update in two phases around the warp's staging points (the
+// kernel below): phase A issues the loads of the total-variation neighbours
+// and evaluates the model and its Jacobian against the staged data row y
+// (loss and gradient into loss, g); phase B adds the total-variation
+// subgradient and takes the Adam step and the box, with the voxel's Adam
+// moments from shared memory (mo: m1 at [p * 32], m2 at [(P + p) * 32]).
+template <int KIND, class R>
+struct FitTv {
+    unsigned grid_bit = 0, nbit = 0;  // neighbours inside the grid; inside the grid and the mask
+    int p0 = model_n_par(KIND);       // first penalised map (P: none)
+    R nb0[6];                         // its neighbours' values
+    uint8_t nmask[6];                 // the neighbours' mask bytes
+};
+
+template <int KIND, class R>
+__device__ __forceinline__ int fit_offset(const FitTv<KIND, R> &tv, int j, const int (&step)[3]) {
+    return ((tv.grid_bit >> j) & 1u) ? ((j & 1) ? -step[j >> 1] : step[j >> 1]) : 0;
+}
+
+// Phase A.  The neighbours' mask bytes and values load first and are used in
+// phase B, so nothing waits on them before the model.
+template <int KIND, int PREC, bool L1>
+__device__ __forceinline__ void fit_phase_a(const ModelConst &mc, const FitArgs<typename PrecTraits<PREC>::R> &fa, int v,
+                                            const float *y, const typename PrecTraits<PREC>::R (&u)[model_n_par(KIND)],
+                                            bool inside, typename PrecTraits<PREC>::R w,
+                                            const typename PrecTraits<PREC>::R *u_in, FitTv<KIND, typename PrecTraits<PREC>::R> &tv,
+                                            typename PrecTraits<PREC>::R &loss, typename PrecTraits<PREC>::R (&g)[model_n_par(KIND)]) {
     using R = typename PrecTraits<PREC>::R;
     constexpr int P = model_n_par(KIND);
     const int n = static_cast<int>(fa.n);
-    R vl = R(0);  // the voxel's loss share (FP32 kernels: FP32; the block sums it in FP64)
-    // Every other load the update needs is issued here, before the model's
-    // long arithmetic hides its latency: the Adam moments, the usable
-    // neighbours (bit 2d: v + e_d, bit 2d + 1: v - e_d; inside the grid and
-    // the mask) and the neighbours' values of the first penalised map.
-    R th[P], g[P], mo1[P], mo2[P];
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-        mo1[p] = m1[p * n + v];
-        mo2[p] = m2[p * n + v];
-    }
-    const bool tv_on = fa.tv_params && fa.lambda_n != R(0);
     const int step[3] = {1, fa.nx, fa.nx * fa.ny};
-    unsigned grid_bit = 0, nbit = 0;  // neighbours inside the grid; inside the grid and the mask
-    int p0 = P;                       // first penalised map (P: none)
-    R nb0[6];
-    uint8_t nmask[6];
-    auto offset = [&](int j) { return ((grid_bit >> j) & 1u) ? ((j & 1) ? -step[j >> 1] : step[j >> 1]) : 0; };
-    if (tv_on) {
+    if (fa.tv_params && fa.lambda_n != R(0)) {
         const unsigned vu = static_cast<unsigned>(v), nxu = static_cast<unsigned>(fa.nx), nyu = static_cast<unsigned>(fa.ny);
         unsigned cx, cy, q, cz;
         if (fa.fdiv) {  // the same for every thread
@@ -314,37 +313,32 @@ __device__ __forceinline__ typename PrecTraits<PREC>::R fit_voxel(const ModelCon
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const bool use = d < fa.tv_dims;
-            grid_bit |= static_cast<unsigned>(use && coord[d] + 1 < ext[d]) << (2 * d) |
-                        static_cast<unsigned>(use && coord[d] > 0) << (2 * d + 1);
+            tv.grid_bit |= static_cast<unsigned>(use && coord[d] + 1 < ext[d]) << (2 * d) |
+                           static_cast<unsigned>(use && coord[d] > 0) << (2 * d + 1);
         }
-        // the neighbours' mask bytes and values load here and are used after
-        // the model (nothing waits on them before it)
-        nbit = grid_bit;
+        tv.nbit = tv.grid_bit;
         if (fa.mask) {
 #pragma unroll
-            for (int j = 0; j < 6; ++j) nmask[j] = fa.mask[v + offset(j)];
+            for (int j = 0; j < 6; ++j) tv.nmask[j] = fa.mask[v + fit_offset(tv, j, step)];
         }
-        p0 = __ffs(fa.tv_params) - 1;
-        if (p0 < P) {
+        tv.p0 = __ffs(fa.tv_params) - 1;
+        if (tv.p0 < P) {
 #pragma unroll
-            for (int j = 0; j < 6; ++j) nb0[j] = u_in[p0 * n + v + offset(j)];
+            for (int j = 0; j < 6; ++j) tv.nb0[j] = u_in[tv.p0 * n + v + fit_offset(tv, j, step)];
         }
     }
-    if (!inside) {
-        next();
+    loss = R(0);
 #pragma unroll
-        for (int p = 0; p < P; ++p) u_out[p * n + v] = u[p];
-        return R(0);
-    }
+    for (int p = 0; p < P; ++p) g[p] = R(0);
+    if (!inside) return;
+    R th[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const R lo = sizeof(R) == 8 ? R(mc.lb_d[p]) : R(mc.lb_f[p]);
         const R hi = sizeof(R) == 8 ? R(mc.ub_d[p]) : R(mc.ub_f[p]);
         th[p] = lo + u[p] * (hi - lo);
-        g[p] = R(0);
     }
     // data term: rho(w (y - s)), drho/ds = -w sign(r) (L1) or -2 w r (L2)
-    R loss = R(0);
     auto visit = [&](int k, R s, const R *J) {
         const R r = w * (R(y[k]) - s);
         R d;
@@ -364,25 +358,45 @@ __device__ __forceinline__ typename PrecTraits<PREC>::R fit_voxel(const ModelCon
     } else {
         jacobian<KIND, R>(th, mc, visit);
     }
-    next();
-    vl += loss * fa.scale;
+}
+
+// Phase B; returns the voxel's share of the loss (0 outside the mask).
+template <int KIND, int PREC>
+__device__ __forceinline__ typename PrecTraits<PREC>::R fit_phase_b(
+    const ModelConst &mc, const FitArgs<typename PrecTraits<PREC>::R> &fa, int v,
+    const typename PrecTraits<PREC>::R (&u)[model_n_par(KIND)], bool inside, const FitTv<KIND, typename PrecTraits<PREC>::R> &tv_in,
+    typename PrecTraits<PREC>::R loss, typename PrecTraits<PREC>::R (&g)[model_n_par(KIND)],
+    const typename PrecTraits<PREC>::R *mo, const typename PrecTraits<PREC>::R *u_in, typename PrecTraits<PREC>::R *u_out,
+    typename PrecTraits<PREC>::R *m1, typename PrecTraits<PREC>::R *m2, typename PrecTraits<PREC>::R c1,
+    typename PrecTraits<PREC>::R c2) {
+    using R = typename PrecTraits<PREC>::R;
+    constexpr int P = model_n_par(KIND);
+    const int n = static_cast<int>(fa.n);
+    if (!inside) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) u_out[p * n + v] = u[p];
+        return R(0);
+    }
+    R vl = loss * fa.scale;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const R range = sizeof(R) == 8 ? R(mc.ub_d[p] - mc.lb_d[p]) : R(mc.ub_f[p] - mc.lb_f[p]);
         g[p] *= fa.scale * range;
     }
     // total variation: pairs (v - e_d, v) and (v, v + e_d) of masked neighbours
-    if (tv_on) {
+    if (fa.tv_params && fa.lambda_n != R(0)) {
+        const int step[3] = {1, fa.nx, fa.nx * fa.ny};
+        unsigned nbit = tv_in.nbit;
         if (fa.mask) {
 #pragma unroll
-            for (int j = 0; j < 6; ++j) nbit &= ~(static_cast<unsigned>(nmask[j] == 0) << j);
+            for (int j = 0; j < 6; ++j) nbit &= ~(static_cast<unsigned>(tv_in.nmask[j] == 0) << j);
         }
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             if (!((fa.tv_params >> p) & 1u)) continue;
             R nb[6];
 #pragma unroll
-            for (int j = 0; j < 6; ++j) nb[j] = p == p0 ? nb0[j] : u_in[p * n + v + offset(j)];
+            for (int j = 0; j < 6; ++j) nb[j] = p == tv_in.p0 ? tv_in.nb0[j] : u_in[p * n + v + fit_offset(tv_in, j, step)];
             R tv = R(0), tv_loss = R(0);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
@@ -403,8 +417,8 @@ __device__ __forceinline__ typename PrecTraits<PREC>::R fit_voxel(const ModelCon
     // as the oracle does
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const R a = fa.beta1 * mo1[p] + (R(1) - fa.beta1) * g[p];
-        const R b = fa.beta2 * mo2[p] + (R(1) - fa.beta2) * g[p] * g[p];
+        const R a = fa.beta1 * mo[p * 32] + (R(1) - fa.beta1) * g[p];
+        const R b = fa.beta2 * mo[(P + p) * 32] + (R(1) - fa.beta2) * g[p] * g[p];
         m1[p * n + v] = a;
         m2[p * n + v] = b;
         R stepu;
@@ -426,6 +440,12 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
     const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(sizeof(T)) : "memory");
+}
 __device__ __forceinline__ void cp_async16(float *dst, const float *src) {
     const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
@@ -435,15 +455,25 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // Persistent warps over tiles of 32 voxels (warp tile w, w + all warps, ...).
-// Each warp stages its own tiles' measurement rows in its own part of shared
-// memory: the next tile's rows are copied into the second of two buffers
-// while the current tile computes, and only the warp waits for them, so warps
-// drift apart and hide each other's memory latency instead of meeting at a
-// block barrier every tile.  Rows sit at an odd number of float4s, so that
-// a warp's 16-byte reads of one echo pair hit distinct banks.  FP32 kernels
-// keep two blocks (16 warps) on an SM.
+// Each warp stages its own tile's measurement rows and Adam moments in its
+// own part of shared memory (fit_warp_smem) with cp.async copies, and only
+// the warp waits for them, so warps drift apart and hide each other's memory
+// latency instead of meeting at a block barrier.  The copies are placed where
+// their buffers fall free: the next tile's rows as soon as the model has read
+// the current ones (before phase B), the next tile's moments after phase B;
+// each lane's next parameters, mask flag and weight load into registers
+// during phase B.  So neither the moments nor the next parameters occupy
+// registers during the model, and more warps fit on an SM.  Rows sit at an
+// odd number of float4s, so that a warp's 16-byte reads of one echo pair hit
+// distinct banks.
 constexpr int kFitWarps = kFitBlock / 32;
-constexpr int fit_min_blocks(int prec) { return prec == GAC_PREC_FP32 ? 2 : 1; }
+constexpr int fit_min_blocks(int prec) { return prec == GAC_PREC_FP32 ? kFitMinBlocks32 : 1; }
+
+// Shared memory of one warp: 32 staged rows, then the tile's moments
+// [2][P][32] (m1, m2).
+__host__ __device__ constexpr size_t fit_warp_smem(int row_stride, int P, size_t rbytes) {
+    return 32 * static_cast<size_t>(row_stride) * sizeof(float) + 2 * static_cast<size_t>(P) * 32 * rbytes;
+}
 
 template <int KIND, int PREC, bool L1>
 __global__ void __launch_bounds__(kFitBlock, fit_min_blocks(PREC)) fit_step_kernel(const ModelConst mc, const FitArgs<typename PrecTraits<PREC>::R> fa,
@@ -453,6 +483,8 @@ __global__ void __launch_bounds__(kFitBlock, fit_min_blocks(PREC)) fit_step_kern
                                                              typename PrecTraits<PREC>::R *m2,
                                                              typename PrecTraits<PREC>::R c1,
                                                              typename PrecTraits<PREC>::R c2, int t_iter) {
+    using R = typename PrecTraits<PREC>::R;
+    constexpr int P = model_n_par(KIND);
     __shared__ double red[kFitBlock];
     __shared__ bool last;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -463,9 +495,10 @@ __global__ void __launch_bounds__(kFitBlock, fit_min_blocks(PREC)) fit_step_kern
     const int M = mc.n_meas;
     const int n = static_cast<int>(fa.n);
     const int n_tiles = (n + 31) / 32;
-    const int tile_floats = 32 * fa.row_stride;
-    float *wbuf = reinterpret_cast<float *>(smem_raw) + warp * (fa.double_buffer ? 2 : 1) * tile_floats;
-    auto stage = [&](int tile, float *dst) {
+    unsigned char *wmem = smem_raw + warp * fit_warp_smem(fa.row_stride, P, sizeof(R));
+    float *rows_s = reinterpret_cast<float *>(wmem);
+    R *mo_s = reinterpret_cast<R *>(wmem + 32 * static_cast<size_t>(fa.row_stride) * sizeof(float));
+    auto stage_rows = [&](int tile) {
         const int base = tile * 32;
         const int rows = min(32, n - base);
         const float *src = fa.data + static_cast<int64_t>(base) * M;
@@ -474,23 +507,27 @@ __global__ void __launch_bounds__(kFitBlock, fit_min_blocks(PREC)) fit_step_kern
 #pragma unroll 4
             for (int e = lane; e < total4; e += 32) {
                 const int row = static_cast<int>((static_cast<float>(e) + 0.5f) * fa.inv_m4);
-                cp_async16(dst + 4 * (row * S4 + (e - row * M4)), src + 4 * e);
+                cp_async16(rows_s + 4 * (row * S4 + (e - row * M4)), src + 4 * e);
             }
         } else {
             const int total = rows * M;
             for (int e = lane; e < total; e += 32) {
                 const int row = e / M;
-                cp_async4(dst + row * fa.row_stride + (e - row * M), src + e);
+                cp_async4(rows_s + row * fa.row_stride + (e - row * M), src + e);
             }
         }
     };
-    using R = typename PrecTraits<PREC>::R;
-    R my_loss = R(0);
-    constexpr int P = model_n_par(KIND);
-    const int stride = gridDim.x * kFitWarps;
-    int tile = blockIdx.x * kFitWarps + warp;
-    // the lane's next voxel: parameters, mask flag and weight, loaded one
-    // voxel ahead
+    auto stage_moments = [&](int tile) {
+        const int e = tile * 32 + lane;
+        if (e < n) {
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                cp_async_elem(mo_s + p * 32 + lane, m1 + p * n + e);
+                cp_async_elem(mo_s + (P + p) * 32 + lane, m2 + p * n + e);
+            }
+        }
+    };
+    // the lane's next voxel: parameters, mask flag and weight
     R un[P];
     bool in_n = true;
     R w_n = R(1);
@@ -502,33 +539,37 @@ __global__ void __launch_bounds__(kFitBlock, fit_min_blocks(PREC)) fit_step_kern
             w_n = fa.weight ? R(fa.weight[vv]) : R(1);
         }
     };
-    load_next(tile * 32 + lane);
-    if (fa.double_buffer && tile < n_tiles) stage(tile, wbuf);
+    R my_loss = R(0);
+    const int stride = gridDim.x * kFitWarps;
+    int tile = blockIdx.x * kFitWarps + warp;
+    if (tile < n_tiles) {
+        stage_rows(tile);
+        stage_moments(tile);
+    }
     cp_async_commit();
-    for (int buf = 0; tile < n_tiles; tile += stride, buf ^= 1) {
-        const float *cur = wbuf;
-        if (fa.double_buffer) {
-            // the other buffer was last read before the __syncwarp that ended the previous tile
-            if (tile + stride < n_tiles) stage(tile + stride, wbuf + (buf ^ 1) * tile_floats);
-            cp_async_commit();
-            cp_async_wait<1>();
-            cur += buf * tile_floats;
-        } else {
-            stage(tile, wbuf);
-            cp_async_commit();
-            cp_async_wait<0>();
-        }
+    load_next(tile * 32 + lane);
+    for (; tile < n_tiles; tile += stride) {
+        cp_async_wait<0>();
         __syncwarp();
         const int v = tile * 32 + lane;
+        const bool active = v < n;
         R u[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) u[p] = un[p];
-        const bool inside = in_n;
+        const bool inside = active && in_n;
         const R w = w_n;
-        auto next = [&]() { load_next(v + stride * 32); };
-        if (v < n) my_loss += fit_voxel<KIND, PREC, L1>(mc, fa, v, cur + lane * fa.row_stride, u, inside, w, next, u_in,
-                                                        u_out, m1, m2, c1, c2);
-        __syncwarp();
+        FitTv<KIND, R> tv;
+        R loss, g[P];
+        if (active) fit_phase_a<KIND, PREC, L1>(mc, fa, v, rows_s + lane * fa.row_stride, u, inside, w, u_in, tv, loss, g);
+        __syncwarp();  // the model has read every row: the buffer takes the next tile's
+        const int next = tile + stride;
+        if (next < n_tiles) stage_rows(next);
+        cp_async_commit();
+        load_next(next * 32 + lane);
+        if (active) my_loss += fit_phase_b<KIND, PREC>(mc, fa, v, u, inside, tv, loss, g, mo_s + lane, u_in, u_out, m1, m2, c1, c2);
+        __syncwarp();  // phase B has read every moment
+        if (next < n_tiles) stage_moments(next);
+        cp_async_commit();
     }
     cp_async_wait<0>();
     // the block's share of the loss, summed in a fixed order: lanes by
@@ -681,7 +722,6 @@ static gac_status fit_run_prec(const ModelConst &mc, const gac_fit_opts *o, cons
     DevBuf d_theta;
     gac_status st = d_theta.make(theta, static_cast<size_t>(N) * P * sizeof(double), true, s, "theta");
     if (st != GAC_OK) return st;
-    // staged data tiles: two when they fit beside a second block on the SM
     int sms = 0, dev = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -691,9 +731,10 @@ static gac_status fit_run_prec(const ModelConst &mc, const gac_fit_opts *o, cons
     // when rows are whole float4s and the data is aligned, else by 4-byte ones
     const bool vec4 = mc.n_meas % 4 == 0 && (reinterpret_cast<uintptr_t>(d_data) & 15) == 0;
     const int row_stride = 4 * (((mc.n_meas + 3) / 4) | 1);
-    const size_t tile_bytes = static_cast<size_t>(kFitBlock) * row_stride * sizeof(float);
-    const bool dbl = 4 * tile_bytes + 8 * 1024 <= static_cast<size_t>(smem_max);
-    const size_t smem = (dbl ? 2 : 1) * tile_bytes;
+    const size_t smem = kFitWarps * fit_warp_smem(row_stride, P, sizeof(R));
+    if (smem > static_cast<size_t>(smem_max))
+        return fail(GAC_ERR_INVALID_ARG, "fit: %d measurements per voxel need %zu bytes of staging, more than the %d a block has",
+                    mc.n_meas, smem, smem_max);
     const bool l1 = o->loss == GAC_FIT_L1;
     const void *fn = l1 ? step_ptr<PREC, true>(mc.kind) : step_ptr<PREC, false>(mc.kind);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -755,7 +796,6 @@ static gac_status fit_run_prec(const ModelConst &mc, const gac_fit_opts *o, cons
     fa.window = o->convergence_window;
     fa.block_loss = block_loss;
     fa.row_stride = row_stride;
-    fa.double_buffer = dbl;
     fa.vec4 = vec4;
     fa.inv_m4 = vec4 ? 1.0f / static_cast<float>(mc.n_meas / 4) : 0.0f;
     fa.fdiv = N < (int64_t(1) << 24);
