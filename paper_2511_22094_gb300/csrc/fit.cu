@@ -488,6 +488,10 @@ __global__ void __launch_bounds__(kFitBlock, fit_min_blocks(PREC)) fit_step_kern
     __shared__ double red[kFitBlock];
     __shared__ bool last;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // launched as a programmatic dependent of the previous update: its blocks
+    // become resident while that launch drains, and wait here until it has
+    // completed and its writes are visible
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (*fa.stop) return;  // the same for every thread
     model_smem_load<KIND>(mc);
     __syncthreads();
@@ -690,13 +694,22 @@ static cudaError_t launch_step(bool l1, int grid, size_t smem, cudaStream_t s, c
     using R = typename PrecTraits<PREC>::R;
     auto *ui = static_cast<const R *>(u_in);
     auto *uo = static_cast<R *>(u_out);
-    if (l1)
-        fit_step_kernel<KIND, PREC, true><<<grid, kFitBlock, smem, s>>>(mc, fa, ui, uo, static_cast<R *>(m1),
-                                                                       static_cast<R *>(m2), R(c1), R(c2), t);
-    else
-        fit_step_kernel<KIND, PREC, false><<<grid, kFitBlock, smem, s>>>(mc, fa, ui, uo, static_cast<R *>(m1),
-                                                                        static_cast<R *>(m2), R(c1), R(c2), t);
-    return cudaGetLastError();
+    // programmatic stream serialization: the launch may begin while the
+    // previous kernel in the stream drains (the kernel waits for it first)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kFitBlock);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    auto *m1r = static_cast<R *>(m1);
+    auto *m2r = static_cast<R *>(m2);
+    if (l1) return cudaLaunchKernelEx(&cfg, fit_step_kernel<KIND, PREC, true>, mc, fa, ui, uo, m1r, m2r, R(c1), R(c2), t);
+    return cudaLaunchKernelEx(&cfg, fit_step_kernel<KIND, PREC, false>, mc, fa, ui, uo, m1r, m2r, R(c1), R(c2), t);
 }
 
 template <int PREC>
@@ -802,7 +815,7 @@ static gac_status fit_run_prec(const ModelConst &mc, const gac_fit_opts *o, cons
     fa.inv_nx = 1.0f / static_cast<float>(o->nx);
     fa.inv_ny = 1.0f / static_cast<float>(o->ny);
     // iterations in chunks; the stop flag is read between chunks
-    constexpr int kChunk = 64;
+    constexpr int kChunk = 128;
     int t = 1;
     while (t <= I) {
         const int t_end = std::min(I, t + kChunk - 1);
