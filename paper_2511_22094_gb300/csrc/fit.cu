@@ -37,7 +37,6 @@ struct FitArgs {
     const float *weight;   // [N] or nullptr
     int nx, ny, nz;
     int64_t n;
-    int loss;              // GAC_FIT_L1 / GAC_FIT_L2
     uint32_t tv_params;
     int tv_dims;
     R scale;               // 1 / (n_mask M)
@@ -791,7 +790,6 @@ static gac_status fit_run_prec(const ModelConst &mc, const gac_fit_opts *o, cons
     fa.ny = o->ny;
     fa.nz = o->nz;
     fa.n = N;
-    fa.loss = o->loss;
     fa.tv_params = o->tv_params;
     fa.tv_dims = o->tv_dims;
     fa.scale = static_cast<R>(1.0 / (static_cast<double>(n_mask) * mc.n_meas));
