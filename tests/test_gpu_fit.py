@@ -157,3 +157,26 @@ def test_large_volume_many_tiles_per_block(gac, orc, kind, acq, shape, prec):
     else:
         np.testing.assert_allclose(g_hist, r_hist, rtol=1e-5)
         assert (d <= 1e-5).mean() >= 0.995, np.quantile(d, 0.99)
+
+
+@pytest.mark.parametrize("kind", [MWI3, SMT])
+def test_device_buffers_give_the_host_buffers_result(gac, orc, kind):
+    """The same fit from device tensors (the mask counted on the device, the
+    data read in place) and from host arrays (the mask counted on the host,
+    the data staged): the same updates bit for bit, including a voxel count
+    that is not a multiple of 32 (a partial last tile) and masked-out voxels."""
+    torch = pytest.importorskip("torch")
+    shape = (7, 5, 3)
+    acq, lb, ub, y, theta0, mask, weight = _problem(orc, kind, shape=shape)
+    mid = gac.gac_model_register(kind, acq, lb, ub, np.zeros(len(lb)))
+    kw = dict(iterations=6, learning_rate=0.01, loss=1, tv_lambda=0.01, tv_params=0b1, tv_dims=3)
+    g_host, h_host, d_host = gac.fit_host(mid, y, theta0, shape=shape, mask=mask, weight=weight, **kw)
+    dev = torch.device("cuda")
+    yd, md, wd = (torch.from_numpy(a).to(dev) for a in (y, mask, weight))
+    th = torch.from_numpy(theta0.copy()).to(dev)
+    hist = torch.full((kw["iterations"],), float("nan"), dtype=torch.float64, device=dev)
+    done = gac.gac_fit_run(mid, yd, md, wd, gac.make_fit_opts(shape, **kw), th, hist)
+    torch.cuda.synchronize()
+    assert done == d_host == kw["iterations"]
+    np.testing.assert_array_equal(th.cpu().numpy(), g_host)
+    np.testing.assert_array_equal(hist.cpu().numpy()[:done], h_host)
