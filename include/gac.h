@@ -335,11 +335,9 @@ gac_status gac_fit_run(int model_id, const void *data, const uint8_t *mask, cons
  *     GAC_ERR_INVALID_ARG and a message giving the limit.
  *   - precision must be GAC_PREC_MIXED and trace_n_vox 0; results equal
  *     gac_mcmc_run's for the same inputs.
- *   - The first call on a device looks up the array's device address (a
- *     one-time set-up per device, kept for the life of the process).  A
- *     process that resets the
- *     device (cudaDeviceReset) must not call this entry point on that device
- *     again: the kept address belongs to the destroyed context.
+ *   - Each call looks up the array's device address in the current context
+ *     (a host-side query), so calls after a device reset use the new
+ *     context's array.
  *   - All calls share the one array, and it keeps the last call's contents
  *     (each call initialises the state it uses, so nothing needs clearing).
  *     Calls whose kernels overlap on the GPU -- on different streams or from

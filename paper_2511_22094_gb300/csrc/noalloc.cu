@@ -10,7 +10,6 @@
 
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 
 #include "gac.h"
 #include "gac_internal.h"
@@ -53,24 +52,15 @@ static void noalloc_launch(int kind, int grid, size_t smem, cudaStream_t s, cons
     }
 }
 
-// Device address of g_noalloc_state, looked up once per device (host code
-// only sees a host-side stand-in under that name).
-static std::mutex g_state_mu;
-static void *g_state_ptr[64] = {};
-
+// Device address of g_noalloc_state in the current context, looked up on
+// every call (a host-side query once the module is loaded), so that a new
+// context after a device reset gets its own address (host code only sees a
+// host-side stand-in under that name).
 static gac_status state_address(void **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= 64) return fail(GAC_ERR_CUDA, "device index %d out of range", dev);
-    std::lock_guard<std::mutex> lk(g_state_mu);
-    if (!g_state_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_state);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(chain-state array)");
-        g_state_ptr[dev] = p;
-    }
-    *out = g_state_ptr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_state);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(chain-state array)");
+    *out = p;
     return GAC_OK;
 }
 
